@@ -1,0 +1,295 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError on a
+mismatch.  They are run against the real oracle (test_oracle_pins.py) and
+against deliberately broken copies of it (test_oracle_mutants.py), which shows
+that a plausible mistake anywhere in the oracle fails at least one of them.
+
+None of the expected values below comes from the oracle's own recurrences:
+they come from closed forms, exhaustive enumeration of warping paths,
+explicit band sets, scipy's sliding-window filters, or inequalities that the
+paper proves (Theorems 1 and 2).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.ndimage import maximum_filter1d, minimum_filter1d
+
+from oracle import paths
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _rel_close(x, y, rtol):
+    return abs(x - y) <= rtol * max(abs(x), abs(y), 1e-300)
+
+
+def _series(rng, L):
+    return rng.standard_normal(L)
+
+
+# --------------------------------------------------------------------- DTW ---
+
+def pin_dtw_w0_is_squared_euclidean(orc, trials=40):
+    """DTW_0 is the (squared) Euclidean distance (Sec. 2.1)."""
+    rng = _rng(1)
+    for _ in range(trials):
+        L = int(rng.integers(1, 80))
+        a, b = _series(rng, L), _series(rng, L)
+        exact = math.fsum((a - b) ** 2)
+        got = orc.dtw(a, b, 0)
+        assert _rel_close(got, exact, 1e-13), (L, got, exact)
+
+
+def pin_dtw_equals_min_over_all_paths(orc, max_L=6):
+    """DTW_W is the minimum cost over all warping paths inside the window
+    (boundary, continuity and monotonicity constraints of Sec. 2.1)."""
+    rng = _rng(2)
+    for L in range(1, max_L + 1):
+        for W in range(0, L + 1):
+            for _ in range(3):
+                a, b = _series(rng, L), _series(rng, L)
+                exact = paths.dtw_by_paths(a, b, W)
+                got = orc.dtw(a, b, W)
+                assert _rel_close(got, exact, 1e-12), (L, W, got, exact)
+
+
+def pin_dtw_symmetric_and_monotone(orc, trials=20):
+    """DTW_W(A,B) = DTW_W(B,A); DTW_W is non-increasing in W; every W >= L-1
+    gives the unconstrained DTW (Sec. 2.1)."""
+    rng = _rng(3)
+    for _ in range(trials):
+        L = int(rng.integers(2, 40))
+        a, b = _series(rng, L), _series(rng, L)
+        vals = [orc.dtw(a, b, W) for W in range(0, L + 2)]
+        for W in range(0, L + 2):
+            assert orc.dtw(b, a, W) == vals[W]
+        for W in range(1, L + 2):
+            assert vals[W] <= vals[W - 1], (W, vals[W], vals[W - 1])
+        assert vals[L - 1] == vals[L] == vals[L + 1] == orc.dtw(a, b, 10 * L)
+
+
+def pin_dtw_early_abandon(orc, trials=30):
+    """Early abandoning never changes a distance that is within the cutoff,
+    and only ever answers +inf for distances above it."""
+    rng = _rng(4)
+    for _ in range(trials):
+        L = int(rng.integers(2, 50))
+        W = int(rng.integers(0, L))
+        a, b = _series(rng, L), _series(rng, L)
+        d = orc.dtw(a, b, W)
+        assert orc.dtw(a, b, W, cutoff=d) == d
+        assert orc.dtw(a, b, W, cutoff=d * 1.5) == d
+        r = orc.dtw(a, b, W, cutoff=d * 0.5)
+        assert r == d or math.isinf(r)
+
+
+# -------------------------------------------------------------- envelopes ---
+
+def pin_envelope_is_sliding_max_min(orc, trials=30):
+    """U and Lo (Eq. 3-4) are the sliding max / min over the clipped window;
+    scipy's filters with edge replication compute the same thing."""
+    rng = _rng(5)
+    for _ in range(trials):
+        L = int(rng.integers(1, 120))
+        W = int(rng.integers(0, L + 3))
+        b = _series(rng, L)
+        U, Lo = orc.envelope(b, W)
+        size = 2 * W + 1
+        np.testing.assert_array_equal(U, maximum_filter1d(b, size=size, mode="nearest"))
+        np.testing.assert_array_equal(Lo, minimum_filter1d(b, size=size, mode="nearest"))
+    b = _series(rng, 33)
+    U, Lo = orc.envelope(b, 0)
+    np.testing.assert_array_equal(U, b)
+    np.testing.assert_array_equal(Lo, b)
+    U, Lo = orc.envelope(b, 32)
+    assert np.all(U == b.max()) and np.all(Lo == b.min())
+
+
+# ---------------------------------------------------------------- LB_Keogh ---
+
+def pin_lb_keogh(orc, trials=40):
+    """LB_Keogh at W=0 is the Euclidean distance; LB_Keogh <= DTW_W."""
+    rng = _rng(6)
+    for _ in range(trials):
+        L = int(rng.integers(2, 60))
+        a, b = _series(rng, L), _series(rng, L)
+        U, Lo = orc.envelope(b, 0)
+        assert _rel_close(orc.lb_keogh(a, U, Lo), math.fsum((a - b) ** 2), 1e-13)
+        W = int(rng.integers(0, L + 1))
+        U, Lo = orc.envelope(b, W)
+        assert orc.lb_keogh(a, U, Lo) <= orc.dtw(a, b, W) * (1 + 1e-12)
+
+
+# ------------------------------------------------------------- LB_Enhanced ---
+
+def pin_lb_enhanced_matches_band_sets(orc, max_L=12):
+    """Algorithm 1 (with D = +inf) equals Eq. 7 summed from explicit band sets."""
+    rng = _rng(7)
+    for L in range(2, max_L + 1):
+        for W in range(0, L + 1):
+            for V in range(1, L // 2 + 1):
+                a, b = _series(rng, L), _series(rng, L)
+                U, Lo = orc.envelope(b, W)
+                got = orc.lb_enhanced(a, b, U, Lo, W, V)
+                exact = paths.lb_enhanced_by_sets(a, b, W, V)
+                assert _rel_close(got, exact, 1e-12), (L, W, V, got, exact)
+
+
+def pin_theorems_1_and_2(orc, trials=60):
+    """Theorem 1 (left bands), its right-band analogue and Theorem 2
+    (LB_Enhanced^V <= the proof's intermediate sum <= DTW_W)."""
+    rng = _rng(8)
+    for _ in range(trials):
+        L = int(rng.integers(2, 14))
+        W = int(rng.integers(0, L + 1))
+        V = int(rng.integers(1, L // 2 + 1))
+        a, b = _series(rng, L), _series(rng, L)
+        d = orc.dtw(a, b, W)
+        tol = 1 + 1e-12
+        assert paths.full_left_band_bound(a, b, W) <= d * tol
+        assert paths.full_right_band_bound(a, b, W) <= d * tol
+        U, Lo = orc.envelope(b, W)
+        lb = orc.lb_enhanced(a, b, U, Lo, W, V)
+        mid = paths.theorem2_intermediate(a, b, W, V)
+        assert lb <= mid * tol and mid <= d * tol, (L, W, V, lb, mid, d)
+
+
+def pin_lb_enhanced_bounds_dtw_larger(orc, trials=40):
+    """Theorem 2 on longer series, with LB_Keogh alongside; LB_Enhanced^1 is
+    at least LB_Keogh (its first and last terms replace envelope distances
+    by point distances of cells inside the envelope's window)."""
+    rng = _rng(9)
+    for _ in range(trials):
+        L = int(rng.integers(16, 200))
+        W = int(rng.integers(0, L))
+        V = int(rng.integers(1, min(20, L // 2) + 1))
+        a, b = _series(rng, L), _series(rng, L)
+        U, Lo = orc.envelope(b, W)
+        d = orc.dtw(a, b, W)
+        lbe = orc.lb_enhanced(a, b, U, Lo, W, V)
+        lbk = orc.lb_keogh(a, U, Lo)
+        assert lbe <= d * (1 + 1e-12)
+        assert orc.lb_enhanced(a, b, U, Lo, W, 1) >= lbk * (1 - 1e-12)
+
+
+def pin_lb_enhanced_w0_is_euclidean(orc, trials=30):
+    """At W=0 every band is the single diagonal cell and U = Lo = B, so
+    LB_Enhanced^V = DTW_0 = the Euclidean distance for every V."""
+    rng = _rng(10)
+    for _ in range(trials):
+        L = int(rng.integers(2, 64))
+        a, b = _series(rng, L), _series(rng, L)
+        U, Lo = orc.envelope(b, 0)
+        exact = math.fsum((a - b) ** 2)
+        for V in (1, 2, max(1, L // 2)):
+            assert _rel_close(orc.lb_enhanced(a, b, U, Lo, 0, V), exact, 1e-13)
+
+
+def pin_algorithm1_abandon(orc, trials=30):
+    """Algorithm 1 returns +inf exactly when the band sum reaches D."""
+    rng = _rng(11)
+    for _ in range(trials):
+        L = int(rng.integers(4, 20))
+        W = int(rng.integers(1, L))
+        V = int(rng.integers(1, L // 2 + 1))
+        a, b = _series(rng, L), _series(rng, L)
+        U, Lo = orc.envelope(b, W)
+        nb = min(L // 2, V)
+        band = math.fsum([paths.band_min(a, b, paths.left_band(i, L, W)) for i in range(1, nb + 1)]
+                         + [paths.band_min(a, b, paths.right_band(i, L, W))
+                            for i in range(L - nb + 1, L + 1)])
+        full = orc.lb_enhanced(a, b, U, Lo, W, V)
+        assert math.isinf(orc.lb_enhanced(a, b, U, Lo, W, V, D=band * (1 - 1e-9)))
+        assert orc.lb_enhanced(a, b, U, Lo, W, V, D=band * (1 + 1e-9)) == full
+        assert math.isinf(orc.lb_enhanced(a, b, U, Lo, W, V, D=0.0))
+
+
+# ------------------------------------------------------------------ 1-NN ---
+
+def _small_set(seed, N, Q, L, classes=3):
+    rng = _rng(seed)
+    train = rng.standard_normal((N, L)).cumsum(axis=1)
+    test = rng.standard_normal((Q, L)).cumsum(axis=1)
+    labels = rng.integers(0, classes, N).astype(np.int32)
+    return train, labels, test
+
+
+def pin_nn_brute_by_paths(orc):
+    """1-NN by the oracle equals the argmin (lowest index on ties) of the
+    path-enumeration DTW on tiny series."""
+    train, labels, test = _small_set(12, 7, 4, 5)
+    for W in (0, 1, 2, 4):
+        idx, lab, dist = orc.nn_brute(train, labels, test, W)
+        for q in range(test.shape[0]):
+            ds = [paths.dtw_by_paths(test[q], train[t], W) for t in range(train.shape[0])]
+            best = int(np.argmin(ds))
+            assert idx[q] == best and lab[q] == labels[best]
+            assert _rel_close(dist[q], ds[best], 1e-12)
+
+
+def pin_nn_w0_is_euclidean_nn(orc):
+    """At W=0 the 1-NN is the Euclidean nearest neighbour."""
+    train, labels, test = _small_set(13, 40, 10, 30)
+    idx, _, _ = orc.nn_brute(train, labels, test, 0)
+    for q in range(test.shape[0]):
+        ed = [math.fsum((test[q] - t) ** 2) for t in train]
+        assert idx[q] == int(np.argmin(ed))
+
+
+def pin_nn_pruned_equals_brute(orc):
+    """The paper's lower-bound search (Sec. 4) gives exactly the brute-force
+    result, ties included: duplicated training series resolve to the lowest
+    index in both."""
+    train, labels, test = _small_set(14, 60, 12, 40)
+    dup = np.concatenate([train, train[:20]], axis=0)   # exact duplicates at higher indices
+    dlab = np.concatenate([labels, labels[:20]])
+    front = np.concatenate([train[20:40], train], axis=0)  # duplicates at lower indices
+    flab = np.concatenate([labels[20:40], labels])
+    for tr, lb in ((train, labels), (dup, dlab), (front, flab)):
+        for W in (0, 3, 8, 39):
+            for V in (1, 2, 5):
+                bi, bl, bd = orc.nn_brute(tr, lb, test, W)
+                pi, pl, pd, _ = orc.nn_pruned(tr, lb, test, W, V)
+                np.testing.assert_array_equal(bi, pi)
+                np.testing.assert_array_equal(bl, pl)
+                np.testing.assert_array_equal(bd, pd)
+    # exact duplicate at a higher index never wins; at a lower index it always does
+    bi, _, _ = orc.nn_brute(dup, dlab, test, 5)
+    assert np.all(bi < 60)
+    fi, _, _ = orc.nn_brute(front, flab, test, 5)
+    assert not np.any((fi >= 40) & (fi < 60))
+    # A tie that the Euclidean ordering visits in the "wrong" order: train 0 is
+    # the query shifted by one step (DTW_1 = 0, ED = 2), train 1 is the query
+    # itself (DTW = ED = 0).  Both are at distance 0, so index 0 must win,
+    # although the search meets index 1 first.
+    q = np.array([[0.0, 1.0, 0.0, 0.0]])
+    tr = np.array([[0.0, 0.0, 1.0, 0.0], [0.0, 1.0, 0.0, 0.0], [3.0, 3.0, 3.0, 3.0]])
+    lb = np.array([7, 8, 9], np.int32)
+    for V in (1, 2):
+        bi, bl, bd = orc.nn_brute(tr, lb, q, 1)
+        pi, pl, pd, _ = orc.nn_pruned(tr, lb, q, 1, V)
+        assert bi[0] == 0 and bl[0] == 7 and bd[0] == 0.0
+        assert pi[0] == 0 and pl[0] == 7 and pd[0] == 0.0
+
+
+ALL_PINS = [
+    pin_dtw_w0_is_squared_euclidean,
+    pin_dtw_equals_min_over_all_paths,
+    pin_dtw_symmetric_and_monotone,
+    pin_dtw_early_abandon,
+    pin_envelope_is_sliding_max_min,
+    pin_lb_keogh,
+    pin_lb_enhanced_matches_band_sets,
+    pin_theorems_1_and_2,
+    pin_lb_enhanced_bounds_dtw_larger,
+    pin_lb_enhanced_w0_is_euclidean,
+    pin_algorithm1_abandon,
+    pin_nn_brute_by_paths,
+    pin_nn_w0_is_euclidean_nn,
+    pin_nn_pruned_equals_brute,
+]

@@ -1,0 +1,63 @@
+"""Plant plausible mistakes in copies of the oracle and check that the pins
+catch each one (CPU only; the real oracle source is never modified)."""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "nndtw_oracle.c")
+
+MUTANTS = {
+    "dtw_drops_diagonal_predecessor": (
+        "double m = dmin(dmin(prev[j - 1], cur[j - 1]), prev[j]);",
+        "double m = dmin(cur[j - 1], prev[j]);"),
+    "dtw_window_one_short": (
+        "int jlo = imax(1, i - W), jhi = imin(L, i + W);\n        cur[jlo - 1] = INF;",
+        "int jlo = imax(1, i - W), jhi = imin(L, i + W - 1 < i ? i : i + W - 1);\n        cur[jlo - 1] = INF;"),
+    "delta_not_squared": ("double t = d * d;", "double t = d < 0 ? -d : d;"),
+    "envelope_window_one_short": (
+        "int jlo = imax(1, i - W), jhi = imin(L, i + W);\n        double u",
+        "int jlo = imax(1, i - W + (W > 0)), jhi = imin(L, i + W);\n        double u"),
+    "envelope_max_min_swapped": ("if (B[j - 1] > u) u = B[j - 1];", "if (B[j - 1] < u) u = B[j - 1];"),
+    "keogh_lower_uses_upper": (
+        "else if (A[i] < Lo[i]) res = res + delta(A[i], Lo[i]);",
+        "else if (A[i] < Lo[i]) res = res + delta(A[i], U[i]);"),
+    "lbenh_drops_last_end": (
+        "double res = delta(a(1), b(1)) + delta(a(L), b(L));",
+        "double res = delta(a(1), b(1));"),
+    "lbenh_right_band_index_off": (
+        "minR = dmin(minR, delta(a(L - i + 1), b(L - j + 1)));",
+        "minR = dmin(minR, delta(a(L - i + 1), b(L - j)));"),
+    "lbenh_left_band_transposed": (
+        "minL = dmin(minL, delta(a(j), b(i)));",
+        "minL = dmin(minL, delta(a(j), b(j)));"),
+    "lbenh_n_bands_plus_one": ("int n_bands = imin(L / 2, V);", "int n_bands = imin(L / 2, V + 1);"),
+    "lbenh_keogh_bridge_overlaps_bands": (
+        "for (int i = n_bands + 1; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])",
+        "for (int i = n_bands; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])"),
+    "lbenh_abandon_wrong_way": ("if (res >= D) return INFINITY;", "if (res < D) return INFINITY;"),
+    "nn_ties_to_highest_index": ("if (d < best) { best = d; bi = t; }", "if (d <= best) { best = d; bi = t; }"),
+    "pruned_search_drops_tie_update": (
+        "if (d < D || (d == D && t < bi)) { D = d; bi = t; }",
+        "if (d < D) { D = d; bi = t; }"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = oracle.compile_oracle(str(path), str(tmp_path / "libmut.so"))
+    orc = oracle.Oracle(oracle.load(so))
+    failures = []
+    for pin in oracle_pins.ALL_PINS:
+        try:
+            pin(orc)
+        except AssertionError:
+            failures.append(pin.__name__)
+    assert failures, f"mutant {name} passed every pin"
