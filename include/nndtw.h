@@ -1,0 +1,192 @@
+/*
+ * nndtw.h -- C ABI of libnndtw.so: exact 1-nearest-neighbour classification
+ * under Sakoe-Chiba windowed DTW, pruned by the LB_Enhanced^V lower bound of
+ * Tan, Petitjean and Webb, "Elastic bands across the path: a new framework
+ * and method to lower bound DTW" (arXiv 1808.09617).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Series are row-major, contiguous: a set of N series of length L is N*L
+ *    elements, series t starting at element t*L.  All series of one call have
+ *    the same length L (Sec. 2 assumes equal lengths).
+ *  - delta(a, b) = (a - b)^2 and every distance and bound is in squared units:
+ *    the square root of Eq. 2 is never taken (it does not change the nearest
+ *    neighbour).
+ *  - W is the integer warping window, |i - j| <= W (Sec. 2.1).  W >= L-1 is
+ *    the unconstrained DTW; larger values are treated as L-1.
+ *  - V is LB_Enhanced's band count (Sec. 3.1); the number of bands used is
+ *    min(floor(L/2), V), as in Algorithm 1.
+ *  - Envelopes are interleaved: env[2*(t*L + i)] = U_i, env[2*(t*L + i) + 1]
+ *    = Lo_i of series t (Eq. 3-4).
+ *  - Pointers named d_* are DEVICE memory owned by the caller; h_* are HOST
+ *    memory owned by the caller.  The library never frees or retains them.
+ *  - Unless stated, calls are asynchronous on `stream` (a cudaStream_t passed
+ *    as void*; NULL is the legacy default stream) and allocate nothing: any
+ *    scratch memory is the caller's `d_workspace`.
+ *  - Return value: NNDTW_OK (0) or a positive NNDTW_E* code; no exception or
+ *    longjmp ever crosses the ABI.  Argument errors are reported before any
+ *    work is enqueued.  NNDTW_ECUDA means a CUDA call failed; the CUDA error
+ *    string is available from nn_dtw_last_cuda_error().
+ *  - Inputs must be finite with magnitude below 1e15 (FP32 entry points) or
+ *    1e150 (FP64 entry points); the kernels use +-1e30 / +-1e200 sentinels
+ *    outside the series.  NNDTW_CHECK_FINITE makes the search verify this.
+ *  - Limits: 2 <= L <= NNDTW_MAX_L, 1 <= N and N*Q below 2^31 for the search.
+ */
+#ifndef NNDTW_H
+#define NNDTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NNDTW_API __attribute__((visibility("default")))
+#else
+#define NNDTW_API
+#endif
+
+#define NNDTW_MAX_L 4096
+
+/* status codes */
+#define NNDTW_OK 0
+#define NNDTW_EINVAL 1      /* null pointer, size or parameter out of range   */
+#define NNDTW_ECUDA 2       /* a CUDA runtime call or kernel launch failed    */
+#define NNDTW_ENOSPACE 3    /* workspace smaller than the size function says  */
+#define NNDTW_EUNSUPPORTED 4/* valid request this build cannot serve          */
+#define NNDTW_ENONFINITE 5  /* NNDTW_CHECK_FINITE found a non-finite input    */
+
+/* flags */
+#define NNDTW_LB_KEOGH (1u << 0)     /* lb_enhanced*: compute LB_Keogh instead       */
+#define NNDTW_LB_SAFE (1u << 1)      /* lb_enhanced*: write rounding-safe bounds     */
+#define NNDTW_EXACT_DIST (1u << 2)   /* search: FP64 distance for every query's NN   */
+#define NNDTW_NO_PRUNE (1u << 3)     /* search: run DTW on every pair (no LB prune)  */
+#define NNDTW_NO_ABANDON (1u << 4)   /* search: no early abandoning inside DTW      */
+#define NNDTW_CHECK_FINITE (1u << 5) /* search: reject non-finite or huge inputs     */
+
+/* Work counters of one search (filled only when a non-NULL pointer is given;
+ * doing so makes the call wait for the stream). */
+typedef struct nndtw_stats {
+    int64_t pairs;          /* Q * N query x train pairs                        */
+    int64_t lb_pruned;      /* pairs whose bound exceeded the query's bound     */
+    int64_t dtw_started;    /* DTW computations started (seeds included)        */
+    int64_t dtw_abandoned;  /* of those, abandoned early                        */
+    int64_t dtw_cells;      /* band cells swept by the FP32/FP64 DTW kernels    */
+    int64_t rechecked;      /* FP64 re-evaluations of near-tie candidates       */
+    int64_t recheck_queries;/* queries that needed at least one                 */
+    int64_t reserved;
+} nndtw_stats;
+
+/*
+ * Upper and lower envelopes of every training series (Sec. 2.2.3, Eq. 3-4):
+ *   U_i = max B_j, Lo_i = min B_j over max(1, i-W) <= j <= min(L, i+W).
+ * d_train: [N][L]; d_env: [N][L][2] written (U, Lo).  Exact (min/max only).
+ * Errors: NNDTW_EINVAL for null pointers, N < 0, L < 1 or L > NNDTW_MAX_L,
+ * W < 0.  N == 0 is a no-op.
+ */
+NNDTW_API int nn_dtw_build_envelopes(const float *d_train, int64_t N, int L, int W, float *d_env,
+                           void *stream);
+NNDTW_API int nn_dtw_build_envelopes_f64(const double *d_train, int64_t N, int L, int W,
+                               double *d_env, void *stream);
+
+/*
+ * LB_Enhanced^V_W(A, B) (Sec. 3.1, Eq. 7; Algorithm 1 with D = +inf) for every
+ * query A = test_q and training series B = train_t:
+ *   delta(A_1,B_1) + delta(A_L,B_L)
+ *   + sum_{i=2..n} [min over the left band L^W_i + min over the right band]
+ *   + sum_{i=n+1..L-n} LB_Keogh term of A_i against (U_i, Lo_i),
+ * with n = min(floor(L/2), V).  flags & NNDTW_LB_KEOGH computes LB_Keogh
+ * (Sec. 2.2.3) instead.  flags & NNDTW_LB_SAFE scales each value down by the
+ * FP32 (or FP64) rounding margin so that it never exceeds the exact bound.
+ * d_test: [Q][L]; d_train: [N][L]; d_env: [N][L][2] from
+ * nn_dtw_build_envelopes with the same W; d_lb_out: [Q][N], row-major.
+ * Errors: NNDTW_EINVAL for null pointers, Q < 0, N < 0, L < 2 or > NNDTW_MAX_L,
+ * W < 0, V < 1.
+ */
+NNDTW_API int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const float *d_env,
+                int64_t N, int L, int W, int V, unsigned flags, float *d_lb_out,
+                void *stream);
+NNDTW_API int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train,
+                    const double *d_env, int64_t N, int L, int W, int V, unsigned flags,
+                    double *d_lb_out, void *stream);
+
+/*
+ * DTW_W(test_q, train_t) (Sec. 2.1, Eq. 1; D(L,L) in squared units) for P
+ * explicit pairs, no pruning or abandoning.  d_pairs: [P][2] int32 (q, t);
+ * d_out: [P].  The FP32 entry point computes in FP32; the FP64 one evaluates
+ * every cell as (a-b)*(a-b) + min(...) with two roundings, in the same order
+ * as the plain definition.
+ * Errors: NNDTW_EINVAL for null pointers, P < 0, L < 1 or > NNDTW_MAX_L, W < 0.
+ * Pair indices are not range-checked: they must address the given arrays.
+ */
+NNDTW_API int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pairs,
+                 int64_t P, int L, int W, float *d_out, void *stream);
+NNDTW_API int dtw_windowed_f64(const double *d_test, const double *d_train, const int32_t *d_pairs,
+                     int64_t P, int L, int W, double *d_out, void *stream);
+
+/* Bytes of device workspace that nn_dtw_search (fp64 = 0) or
+ * nn_dtw_search_f64 (fp64 = 1) needs for these sizes.  0 on invalid sizes. */
+NNDTW_API size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V, int fp64);
+
+/*
+ * Exact 1-NN classification of Q test series against N labelled training
+ * series under DTW_W: the lower-bound search of Sec. 4 with LB_Enhanced^V
+ * (Algorithm 1) as the bound.  For every query q:
+ *   d_nn_idx[q]   = argmin_t DTW_W(test_q, train_t), ties to the lowest t;
+ *   d_nn_label[q] = d_train_labels[d_nn_idx[q]];
+ *   d_nn_dist[q]  = that distance (squared units).
+ * The index and label equal those of an exhaustive FP64 evaluation.  The FP32
+ * entry point computes bounds and DTW in FP32 with rounding margins and
+ * re-evaluates in FP64 the candidates whose FP32 distance is within the
+ * margin of the best; d_nn_dist is FP64-exact for those queries (and for all
+ * with NNDTW_EXACT_DIST), otherwise the FP32 value.  The FP64 entry point
+ * computes everything in FP64 and its distances are exact.
+ * d_env may be NULL (envelopes are then built into the workspace).
+ * Q == 0 is a no-op.  d_workspace must hold nn_dtw_workspace_size() bytes
+ * (NNDTW_ENOSPACE otherwise), 256-byte aligned.  stats may be NULL.
+ * Errors: NNDTW_EINVAL for null pointers, N < 1, Q < 0, L < 2 or
+ * > NNDTW_MAX_L, W < 0, V < 1, N*Q >= 2^31; NNDTW_ENONFINITE (with
+ * NNDTW_CHECK_FINITE; the call then waits for the stream).
+ */
+NNDTW_API int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N,
+                  const float *d_test, int64_t Q, int L, int W, int V,
+                  const float *d_env, unsigned flags, int32_t *d_nn_idx,
+                  int32_t *d_nn_label, double *d_nn_dist, void *d_workspace,
+                  size_t workspace_bytes, nndtw_stats *stats, void *stream);
+NNDTW_API int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int64_t N,
+                      const double *d_test, int64_t Q, int L, int W, int V,
+                      const double *d_env, unsigned flags, int32_t *d_nn_idx,
+                      int32_t *d_nn_label, double *d_nn_dist, void *d_workspace,
+                      size_t workspace_bytes, nndtw_stats *stats, void *stream);
+
+/* Bytes of device memory nn_dtw_search_host needs (inputs, outputs and the
+ * search workspace). 0 on invalid sizes. */
+NNDTW_API size_t nn_dtw_host_buffer_size(int64_t N, int64_t Q, int L, int W, int V);
+
+/*
+ * nn_dtw_search on HOST buffers: copies h_train, h_train_labels and h_test to
+ * the caller's device buffer, runs the FP32 search, copies the results back to
+ * h_nn_idx, h_nn_label, h_nn_dist and waits for the stream before returning.
+ * Pinned host memory makes the copies faster; pageable memory also works.
+ * d_buffer: nn_dtw_host_buffer_size() bytes of device memory, 256-byte
+ * aligned.  Same results and errors as nn_dtw_search.
+ */
+NNDTW_API int nn_dtw_search_host(const float *h_train, const int32_t *h_train_labels, int64_t N,
+                       const float *h_test, int64_t Q, int L, int W, int V, unsigned flags,
+                       int32_t *h_nn_idx, int32_t *h_nn_label, double *h_nn_dist,
+                       void *d_buffer, size_t buffer_bytes, nndtw_stats *stats,
+                       void *stream);
+
+/* Static description of a status code.  Never NULL. */
+NNDTW_API const char *nn_dtw_strerror(int code);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+NNDTW_API const char *nn_dtw_last_cuda_error(void);
+/* ABI version (major * 100 + minor). */
+NNDTW_API int nn_dtw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNDTW_H */

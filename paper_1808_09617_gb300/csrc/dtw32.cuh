@@ -1,0 +1,300 @@
+// S4: windowed DTW (Sec. 2.1, Eq. 1) in FP32 with early abandoning, one
+// pair per group of G lanes (G = 1, 2, ..., 32), persistent over a work list.
+//
+// Layout.  The band |i - j| <= W is stored by diagonals: diagonal
+// k = j - i + W (0 <= k <= 2W) holds the cells (i, i + k - W).  The cells with
+// the same anti-diagonal t = i + j are mutually independent, and the cell of
+// diagonal k at anti-diagonal t depends only on diagonal k at t-2 and on
+// diagonals k-1, k+1 at t-1.  So each diagonal keeps ONE register (its latest
+// value) and the sweep alternates between even and odd diagonals: a
+// "super-step" advances every diagonal by one cell.  Lane g of a group owns
+// C_g consecutive diagonals (C_g = 2H, or 2H-2 for the first s lanes, with
+// sum C_g = 2W + 2): one slot beyond the band (diagonal 2W+1, kept at +inf)
+// and no per-cell masking.  A lane exchanges one boundary value with each
+// neighbour per super-step (warp shuffles), and the series values flow
+// through the group: query values A_i enter at lane 0 and move right, training
+// values B_j enter at the last lane and move left, one per super-step, each
+// lane keeping a window of H of each in registers.  Per cell the work is
+// d = A_i - B_j; D = fma(d, d, min3(D_diag, D_left, D_up)).
+//
+// Cells outside the L x L matrix read sentinels (query +1e30, training -1e30)
+// whose squared difference overflows to +inf.  D(-1,-1) = 0 is seeded in the
+// register of diagonal W.
+//
+// Early abandoning: every path from (1,1) to (L,L) visits one of any two
+// consecutive anti-diagonals, and D never decreases along a path, so the
+// minimum of all current diagonal registers (which hold anti-diagonals t and
+// t-1) is a lower bound on D(L,L).  Scaled down by the FP32 rounding margin,
+// a value above the query's current upper bound abandons the pair (strict
+// test, so ties are never abandoned).
+#pragma once
+
+#include "internal.cuh"
+
+namespace nndtw {
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// number of band cells (i, j) in [0,L)^2, |i-j| <= W, with i + j <= smax
+__device__ inline long long band_cells_upto(int L, int W, int smax) {
+    long long n = 0;
+    const int dmax = smax < 2 * L - 2 ? smax : 2 * L - 2;
+    for (int d = 0; d <= dmax; d++) {
+        int lo = d - L + 1 > 0 ? d - L + 1 : 0;
+        int hi = d < L - 1 ? d : L - 1;
+        int blo = (d - W + 1) >> 1;       // ceil((d - W) / 2)
+        if (d - W < 0) blo = -(((W - d)) >> 1);
+        int bhi = (d + W) >> 1;
+        if (blo > lo) lo = blo;
+        if (bhi < hi) hi = bhi;
+        if (hi >= lo) n += hi - lo + 1;
+    }
+    return n;
+}
+
+template <int H, int U>
+__global__ void __launch_bounds__(128)
+dtw32_kernel(DtwJob32 job, int G) {
+    constexpr int C = 2 * H;
+    const float INF = __int_as_float(0x7f800000);
+    const float APAD = Pad<float>::v, BPAD = -Pad<float>::v;
+    const int L = job.L, W = job.W;
+
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int s = G * H - (W + 1);               // short lanes: 0 <= s <= G-1
+    const bool shortl = gl < s;
+    const int k0 = gl * C - 2 * (gl < s ? gl : s);
+    const int Cg = shortl ? C - 2 : C;
+    const bool lastl = gl == G - 1;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const bool hasW = W >= k0 && W < k0 + Cg;
+    const int cW = W - k0;
+    const int t_first = -(W & 1);
+    const int I0 = (W >> 1) - (k0 >> 1);        // I at the first super-step's A step
+    const int J0 = t_first - I0;
+
+    const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
+                                       : job.n_seed;
+
+    const long long n_groups = (long long)gridDim.x * (blockDim.x / G);
+    long long next_static = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+
+    float R[C], Aw[H + U], Bw[H + U];
+    // per-pair state
+    long long pid = -1;
+    int q = 0, tt = 0, u = 0;
+    bool done = true, finished = false;
+    float ub = INF, res = INF;
+    const float *ap = job.test, *bp = job.train;
+    float acur = 0.f, bcur = 0.f;   // stream values for the current super-step
+    int since_check = 0;
+
+    while (true) {
+        // ---- claim new pairs at a block boundary ---------------------------
+        const bool need = done && !finished;
+        const unsigned needmask = __ballot_sync(0xffffffffu, need && gl == 0);
+        if (needmask) {
+            long long mine = -1;
+            if (job.head) {
+                // dynamic: one atomic per warp for all groups that need work
+                unsigned long long base = 0;
+                const int leader = __ffs(needmask) - 1;
+                if (lane == leader) base = atomicAdd(job.head, (unsigned long long)__popc(needmask));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (need && gl == 0) mine = (long long)base + __popc(needmask & ((1u << lane) - 1));
+                mine = __shfl_sync(0xffffffffu, mine, lane & ~(G - 1));
+            } else if (need) {
+                // static: group k takes pairs k, k + n_groups, ...
+                mine = next_static;
+                next_static += n_groups;
+            }
+            if (need) {
+                if (mine >= n_work) {
+                    finished = true;
+                    pid = -1;
+                } else {
+                    pid = mine;
+                    if (job.pairs) {
+                        const uint2 pr = job.pairs[pid];
+                        q = (int)pr.x; tt = (int)pr.y;
+                    } else {
+                        q = (int)pid; tt = (int)key_idx(job.seed_keys[pid]);
+                    }
+                    ap = job.test + (long long)q * L;
+                    bp = job.train + (long long)tt * L;
+                    done = false;
+                    u = 0;
+                    res = INF;
+                    since_check = 0;
+                    ub = INF;
+                    if (job.abandon && job.bsf) {
+                        const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
+                        if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
+                    }
+                    // windows for the first super-step (v = 0 mappings)
+#pragma unroll
+                    for (int m = 0; m < H; m++) {
+                        const int ia = I0 - m;
+                        Aw[m + U - 1] = (ia >= 0 && ia < L) ? ap[ia] : APAD;
+                        const int jb = J0 + m;
+                        Bw[m] = (jb >= 0 && jb < L) ? bp[jb] : BPAD;
+                    }
+#pragma unroll
+                    for (int c = 0; c < C; c++) R[c] = (hasW && c == cW) ? 0.f : INF;
+                    {   // stream values for super-step 0
+                        const int ia = I0 + 1, jb = J0 + H;
+                        acur = (gl == 0) ? ((ia >= 0 && ia < L) ? ap[ia] : APAD) : 0.f;
+                        bcur = lastl ? ((jb >= 0 && jb < L) ? bp[jb] : BPAD) : 0.f;
+                    }
+                    if (job.counters && gl == 0) atomicAdd(job.counters + C_STARTED, 1ull);
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, finished)) break;
+
+        // ---- one block of U super-steps ------------------------------------
+#pragma unroll
+        for (int v = 0; v < U; v++) {
+            // prefetch next super-step's stream values
+            float anx = 0.f, bnx = 0.f;
+            {
+                const int ia = I0 + u + 2, jb = J0 + u + 1 + H;
+                if (gl == 0) anx = (ia >= 0 && ia < L) ? ap[ia] : APAD;
+                if (lastl) bnx = (jb >= 0 && jb < L) ? bp[jb] : BPAD;
+            }
+            // step A: even slots
+            {
+                float send;
+                if constexpr (H >= 2) send = shortl ? R[C - 3] : R[C - 1];
+                else send = R[C - 1];
+                float left = __shfl_up_sync(0xffffffffu, send, 1, G);
+                if (gl == 0) left = INF;
+#pragma unroll
+                for (int m = 0; m < H; m++) {
+                    const int c = 2 * m;
+                    const float a = Aw[m + U - 1 - v];
+                    const float b = Bw[m + v];
+                    const float lft = (m == 0) ? left : R[c - 1];
+                    const float d = a - b;
+                    R[c] = fmaf(d, d, min3f(R[c], lft, R[c + 1]));
+                }
+            }
+            // b-shift
+            {
+                const float sendb = Bw[v];
+                float nb = __shfl_down_sync(0xffffffffu, sendb, 1, G);
+                if (lastl) nb = bcur;
+                Bw[H + v] = nb;
+                if constexpr (H >= 2) {
+                    if (shortl) Bw[H - 1 + v] = nb;
+                }
+            }
+            // step B: odd slots
+            {
+                float right = __shfl_down_sync(0xffffffffu, R[0], 1, G);
+                if (lastl) right = INF;
+#pragma unroll
+                for (int m = 0; m < H; m++) {
+                    const int c = 2 * m + 1;
+                    const float a = Aw[m + U - 1 - v];
+                    const float b = Bw[m + v + 1];
+                    float rgt;
+                    if (c == C - 1) rgt = right;
+                    else if (c == C - 3) rgt = shortl ? right : R[c + 1];
+                    else rgt = R[c + 1];
+                    const float d = a - b;
+                    R[c] = fmaf(d, d, min3f(R[c], R[c - 1], rgt));
+                }
+                if (lastl) R[C - 1] = INF;
+            }
+            // result of the pair: anti-diagonal 2L-2 was just computed
+            if (u == L - 1 && !done) {
+                float r = INF;
+#pragma unroll
+                for (int c = 0; c < C; c++) r = (hasW && c == cW) ? R[c] : r;
+                res = r;
+            }
+            // a-shift
+            {
+                float senda;
+                if constexpr (H >= 2) senda = shortl ? Aw[H - 2 + U - 1 - v] : Aw[H - 1 + U - 1 - v];
+                else senda = Aw[H - 1 + U - 1 - v];
+                float na = __shfl_up_sync(0xffffffffu, senda, 1, G);
+                if (gl == 0) na = acur;
+                if (v + 1 < U) {
+                    Aw[U - 2 - v] = na;
+                } else {
+#pragma unroll
+                    for (int m = H - 1; m >= 1; m--) Aw[m + U - 1] = Aw[m - 1];
+                    Aw[U - 1] = na;
+                }
+            }
+            acur = anx;
+            bcur = bnx;
+            u++;
+        }
+        // realign the b window
+#pragma unroll
+        for (int m = 0; m < H; m++) Bw[m] = Bw[m + U];
+
+        // ---- completion / abandon ------------------------------------------
+        // Everything below branches on group-uniform state only (all lanes of
+        // a group share pid, u and done), so group reductions use the group's
+        // lane mask.
+        const bool completed = !done && u >= L;
+        if (completed) {
+            // broadcast the result from the lane holding diagonal W
+            float r = hasW ? res : INF;
+            for (int off = 1; off < G; off <<= 1) r = fminf(r, __shfl_xor_sync(gmask, r, off, G));
+            res = r;
+            if (gl == 0) {
+                if (job.out) job.out[pid] = res;
+                if (job.bsf) {
+                    const unsigned long long key = pack_key(res, (uint32_t)tt);
+                    const unsigned long long old = atomicMin(job.bsf + q, key);
+                    const unsigned long long cur = old < key ? old : key;
+                    const float ubn = upper32(key_dist(cur), job.dtw_hi, job.abs32);
+                    if (job.cand && lower32(res, job.dtw_lo, job.abs32) <= ubn) {
+                        const unsigned long long slot = atomicAdd(job.cand_count, 1ull);
+                        Cand cd;
+                        cd.q = q; cd.t = tt; cd.d = res; cd.pad = 0;
+                        job.cand[slot] = cd;
+                    }
+                }
+                if (job.counters)
+                    atomicAdd(job.counters + C_CELLS,
+                              (unsigned long long)band_cells_upto(L, W, 2 * L));
+            }
+            done = true;
+        } else if (!done && job.abandon) {
+            since_check += U;
+            if (since_check >= 16) {
+                since_check = 0;
+                float mn = R[0];
+#pragma unroll
+                for (int c = 1; c < C; c++) mn = fminf(mn, R[c]);
+                for (int off = 1; off < G; off <<= 1)
+                    mn = fminf(mn, __shfl_xor_sync(gmask, mn, off, G));
+                if (job.bsf) {
+                    const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
+                    if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
+                }
+                if (lower32(mn, job.dtw_lo, job.abs32) > ub) {
+                    if (gl == 0 && job.counters) {
+                        atomicAdd(job.counters + C_ABANDONED, 1ull);
+                        atomicAdd(job.counters + C_CELLS,
+                                  (unsigned long long)band_cells_upto(L, W, 2 * u + t_first - 1));
+                    }
+                    done = true;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace nndtw

@@ -1,0 +1,18 @@
+// Explicit instantiation helpers for the FP32 DTW kernel (one per H).
+#pragma once
+#include "dtw32.cuh"
+
+namespace nndtw {
+
+using Dtw32Fn = void (*)(DtwJob32, int);
+
+// Super-steps per register-window block: the windows are realigned with
+// 2H-1 moves once per block, so larger U costs fewer moves and more code.
+template <int H> struct Dtw32U { static constexpr int value = H > 24 ? 4 : 8; };
+
+template <int H> Dtw32Fn dtw32_fn();
+
+#define NNDTW_INST_DTW32(H) \
+    template <> Dtw32Fn dtw32_fn<H>() { return &dtw32_kernel<H, Dtw32U<H>::value>; }
+
+}  // namespace nndtw

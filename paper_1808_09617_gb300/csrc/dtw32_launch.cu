@@ -1,0 +1,71 @@
+// Launcher of the FP32 DTW kernel: picks the group width G and per-lane
+// diagonal-pair count H for a window W and sizes the persistent grid.
+#include <mutex>
+
+#include "dtw32_inst.cuh"
+
+namespace nndtw {
+
+namespace {
+
+Dtw32Fn pick_fn(int H) {
+    switch (H) {
+#define C_(h) case h: return dtw32_fn<h>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13)
+        C_(14) C_(15) C_(16) C_(17) C_(18) C_(19) C_(20) C_(21) C_(22) C_(23) C_(24) C_(25)
+        C_(26) C_(27) C_(28) C_(29) C_(30) C_(31) C_(32)
+#undef C_
+        default: return nullptr;
+    }
+}
+
+struct OccCache {
+    std::mutex mu;
+    int blocks[33][64] = {};  // [H][device]
+};
+OccCache g_occ;
+
+}  // namespace
+
+// G lanes per pair and H diagonal pairs per lane with G*H >= W+1, at most
+// G-1 short lanes.  Smallest G first: fewer shuffles per cell.
+bool dtw32_shape(int W, int *G, int *H) {
+    for (int g = 1; g <= 32; g <<= 1) {
+        const int h = (W + 1 + g - 1) / g;
+        if (h <= 32) { *G = g; *H = h; return true; }
+    }
+    return false;
+}
+
+cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
+    int G = 0, H = 0;
+    if (!dtw32_shape(job.W, &G, &H)) return cudaErrorNotSupported;
+    Dtw32Fn fn = pick_fn(H);
+    if (!fn) return cudaErrorNotSupported;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_occ.mu);
+        if (dev < 64) bps = g_occ.blocks[H][dev];
+        if (bps == 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0);
+            if (e != cudaSuccess) return e;
+            if (bps < 1) bps = 1;
+            if (dev < 64) g_occ.blocks[H][dev] = bps;
+        }
+    }
+    long long grid = (long long)sm_count * bps;
+    if (!job.pairs || !job.count) {
+        const long long n = job.pairs ? job.n_pairs : job.n_seed;
+        if (n <= 0) return cudaSuccess;
+        const long long groups_per_block = 128 / G;
+        const long long need = (n + groups_per_block - 1) / groups_per_block;
+        if (need < grid) grid = need;
+    }
+    fn<<<(unsigned)grid, 128, 0, s>>>(job, G);
+    return cudaGetLastError();
+}
+
+}  // namespace nndtw

@@ -1,0 +1,143 @@
+// S1: upper/lower envelopes U, Lo of every training series (Sec. 2.2.3,
+// Eq. 3-4): U_i = max B_j and Lo_i = min B_j over the window
+// max(1, i-W) <= j <= min(L, i+W).
+//
+// Method (a block decomposition in the spirit of van Herk / Gil-Werman):
+// split the series into aligned tiles of T = 2^floor(log2 W) elements (capped
+// at 32, one tile never straddles a warp).  Warp shuffles give, per element,
+// the max/min from its tile's start (prefix P) and to its tile's end (suffix
+// S).  Every window is at least W+1 > T long, so it covers the end of one
+// tile and the start of a later one: U_i = max(S[lo], P[hi], tiles between).
+// With T > W/2 at most three tiles lie between; with T = 32 a sparse table
+// over tile maxima answers the middle range with two lookups.  min/max are
+// exact, so the result is bit-identical to a naive scan.
+#include "internal.cuh"
+
+namespace nndtw {
+namespace {
+
+constexpr int kEnvThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+
+template <typename T>
+__global__ void __launch_bounds__(kEnvThreads)
+envelope_kernel(const T *__restrict__ train, int64_t N, int L, int W, T *__restrict__ env,
+                int T_tile, int levels) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Pmax = reinterpret_cast<T *>(smem_raw);
+    T *Pmin = Pmax + L;
+    T *Smax = Pmin + L;
+    T *Smin = Smax + L;
+    T *Mmax = Smin + L;                       // [levels+1][nt]
+    const int nt = (L + T_tile - 1) / T_tile;
+    T *Mmin = Mmax + (size_t)(levels + 1) * nt;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int r = lane & (T_tile - 1);
+    const T NEG = -inf_of<T>(), POS = inf_of<T>();
+
+    for (int64_t s = blockIdx.x; s < N; s += gridDim.x) {
+        const T *x = train + s * (int64_t)L;
+        T *out = env + s * 2 * (int64_t)L;
+        if (W == 0) {
+            for (int i = tid; i < L; i += kEnvThreads) {
+                T v = x[i];
+                out[2 * i] = v;
+                out[2 * i + 1] = v;
+            }
+            continue;
+        }
+        // tile prefix / suffix scans
+        for (int base = 0; base < L; base += kEnvThreads) {
+            const int k = base + tid;
+            const T v = k < L ? x[k] : T(0);
+            T pmx = k < L ? v : NEG, pmn = k < L ? v : POS;
+            T smx = pmx, smn = pmn;
+            for (int d = 1; d < T_tile; d <<= 1) {
+                T a = __shfl_up_sync(0xffffffffu, pmx, d);
+                T b = __shfl_up_sync(0xffffffffu, pmn, d);
+                T c = __shfl_down_sync(0xffffffffu, smx, d);
+                T e = __shfl_down_sync(0xffffffffu, smn, d);
+                if (r >= d) { pmx = tmax(pmx, a); pmn = tmin(pmn, b); }
+                if (r + d < T_tile) { smx = tmax(smx, c); smn = tmin(smn, e); }
+            }
+            if (k < L) {
+                Pmax[k] = pmx; Pmin[k] = pmn; Smax[k] = smx; Smin[k] = smn;
+                if (r == 0) { Mmax[k / T_tile] = smx; Mmin[k / T_tile] = smn; }
+            }
+        }
+        __syncthreads();
+        // sparse table over tile extremes (level j covers 2^j tiles)
+        for (int j = 1; j <= levels; j++) {
+            const int half = 1 << (j - 1);
+            const int cnt = nt - (1 << j) + 1;
+            const T *pmx = Mmax + (size_t)(j - 1) * nt, *pmn = Mmin + (size_t)(j - 1) * nt;
+            T *cmx = Mmax + (size_t)j * nt, *cmn = Mmin + (size_t)j * nt;
+            for (int t = tid; t < cnt; t += kEnvThreads) {
+                cmx[t] = tmax(pmx[t], pmx[t + half]);
+                cmn[t] = tmin(pmn[t], pmn[t + half]);
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < L; i += kEnvThreads) {
+            const int lo = i - W < 0 ? 0 : i - W;
+            const int hi = i + W > L - 1 ? L - 1 : i + W;
+            const int tlo = lo / T_tile, thi = hi / T_tile;
+            T u = tmax(Smax[lo], Pmax[hi]);
+            T l = tmin(Smin[lo], Pmin[hi]);
+            const int a = tlo + 1, b = thi - 1;
+            if (b >= a) {
+                if (levels == 0) {
+                    for (int t = a; t <= b; t++) { u = tmax(u, Mmax[t]); l = tmin(l, Mmin[t]); }
+                } else {
+                    const int len = b - a + 1;
+                    const int j = 31 - __clz(len);
+                    const T *mx = Mmax + (size_t)j * nt, *mn = Mmin + (size_t)j * nt;
+                    const int b2 = b - (1 << j) + 1;
+                    u = tmax(u, tmax(mx[a], mx[b2]));
+                    l = tmin(l, tmin(mn[a], mn[b2]));
+                }
+            }
+            out[2 * i] = u;
+            out[2 * i + 1] = l;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    int Weff = W > L - 1 ? L - 1 : W;
+    int T_tile = 1, levels = 0;
+    if (Weff >= 32) {
+        T_tile = 32;
+        const int nt = (L + 31) / 32;
+        while ((2 << levels) <= nt) levels++;
+    } else if (Weff > 0) {
+        while (T_tile * 2 <= Weff) T_tile *= 2;
+    }
+    const int nt = (L + T_tile - 1) / T_tile;
+    const size_t smem = sizeof(T) * (4 * (size_t)L + 2 * (size_t)(levels + 1) * nt);
+    cudaError_t e = cudaFuncSetAttribute(envelope_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int sms = device_sm_count();
+    int64_t grid = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
+    envelope_kernel<T><<<(unsigned)grid, kEnvThreads, smem, s>>>(train, N, L, Weff, env, T_tile,
+                                                                  levels);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_envelopes<float>(const float *, int64_t, int, int, float *,
+                                             cudaStream_t);
+template cudaError_t launch_envelopes<double>(const double *, int64_t, int, int, double *,
+                                              cudaStream_t);
+
+}  // namespace nndtw

@@ -1,0 +1,142 @@
+// Internal declarations shared by the CUDA translation units of libnndtw.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "../../include/nndtw.h"
+
+namespace nndtw {
+
+// Sentinels placed outside a series: a query is padded with +PAD and a
+// training series with -PAD, so every band cell that falls outside the
+// L x L matrix gets delta = (2 PAD)^2 = +inf and never wins a minimum.
+template <typename T> struct Pad;
+template <> struct Pad<float> { static constexpr float v = 1e30f; };
+template <> struct Pad<double> { static constexpr double v = 1e200; };
+
+template <typename T> __host__ __device__ inline T inf_of();
+template <> __host__ __device__ inline float inf_of<float>() { return __builtin_huge_valf(); }
+template <> __host__ __device__ inline double inf_of<double>() { return __builtin_huge_val(); }
+
+// Ordered key of a (non-negative FP32 distance, index) pair: comparing keys
+// as unsigned 64-bit integers compares distances first, then indices, which
+// gives the lowest-index tie rule under atomicMin.
+__device__ __forceinline__ uint64_t pack_key(float d, uint32_t idx) {
+    return (static_cast<uint64_t>(__float_as_uint(d)) << 32) | idx;
+}
+__device__ __forceinline__ float key_dist(uint64_t k) {
+    return __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+__device__ __forceinline__ uint32_t key_idx(uint64_t k) { return static_cast<uint32_t>(k); }
+
+// Non-negative doubles order like their bit patterns.
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
+// Rounding margins (Higham, Accuracy and Stability of Numerical Algorithms,
+// Lemma 3.1: gamma_n = n u / (1 - n u)).  A floating-point value x_hat of a
+// bound or of DTW evaluated with at most n roundings along any chain
+// satisfies |x_hat - x| <= gamma_n |x| (all terms are non-negative).
+//  lo : multiply a computed value to get a number <= the exact one;
+//  hi : multiply a computed value to get a number >= the exact one;
+//  abs: absolute slack for terms that underflow to subnormals.
+struct Margins {
+    float lb_lo, dtw_lo, dtw_hi, abs32;
+    double lb_lo64, abs64;
+};
+
+Margins make_margins(int L);
+
+// Conservative images of a computed FP32 value x under the margins.
+__device__ __forceinline__ float lower32(float x, float lo, float abs_s) {
+    return __fsub_rd(__fmul_rd(x, lo), abs_s);
+}
+__device__ __forceinline__ float upper32(float x, float hi, float abs_s) {
+    return __fadd_ru(__fmul_ru(x, hi), abs_s);
+}
+
+// Device-side counters (all 64-bit), zeroed at the start of a search.
+enum Counter : int {
+    C_QUEUE = 0,     // survivors appended by compaction
+    C_HEAD,          // next queue entry to claim
+    C_CAND,          // completed candidates appended
+    C_RECHECK,       // FP64 re-evaluations queued
+    C_STARTED,       // DTWs started
+    C_ABANDONED,     // DTWs abandoned
+    C_CELLS,         // band cells swept
+    C_RQUERIES,      // queries with a recheck
+    C_SEEDHEAD,      // next seed pair to claim
+    C_BAD,           // non-finite input elements found
+    C_COUNT
+};
+
+// Candidate (a DTW that ran to completion within the margin of the best).
+struct Cand {
+    int32_t q, t;
+    float d;
+    int32_t pad;
+};
+struct Cand64 {
+    int32_t q, t;
+    double d;
+};
+
+// ---- launchers implemented in the .cu files --------------------------------
+template <typename T>
+cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
+                      int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
+                      T *lb_out, unsigned long long *seed_keys, cudaStream_t s);
+
+// FP32 DTW over a work list.  Pairs come from `pairs` ([count] of (q, t)) or,
+// when pairs == nullptr, from seed keys (pair p = (p, key_idx(seed_keys[p]))).
+struct DtwJob32 {
+    const float *test, *train;
+    int L, W;
+    const uint2 *pairs;                 // or nullptr
+    const unsigned long long *seed_keys;// used when pairs == nullptr
+    const unsigned long long *count;    // device count of pairs (nullptr: n_pairs)
+    long long n_pairs;                  // host count of pairs
+    long long n_seed;                   // number of seed pairs (seed mode)
+    unsigned long long *head;           // claim counter
+    unsigned long long *bsf;            // [Q] packed (dist, idx) keys; nullptr: none
+    Cand *cand;                         // completed-candidate list; nullptr: none
+    unsigned long long *cand_count;
+    float *out;                         // plain mode: out[p] = DTW
+    unsigned long long *counters;       // stats (C_STARTED ...), may be nullptr
+    float dtw_lo, dtw_hi, abs32;        // margins
+    int abandon;                        // 1: abandon against bsf
+};
+cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
+
+// FP64 DTW: same job shape, exact evaluation order.  Inputs are double
+// (test/train) or FP32 promoted in-kernel (test32/train32, for the recheck of
+// the FP32 search).
+struct DtwJob64 {
+    const double *test, *train;
+    const float *test32, *train32;
+    int L, W;
+    const uint2 *pairs;                 // or nullptr (seed mode)
+    const unsigned long long *seed_keys;
+    const unsigned long long *count;    // device count (nullptr: use n_pairs)
+    long long n_pairs;                  // host count (pairs or seeds)
+    unsigned long long *head;
+    unsigned long long *bsf64;          // [Q] double bits; nullptr: none
+    Cand64 *cand;
+    unsigned long long *cand_count;
+    double *out;                        // out[p] = DTW (nullptr: none)
+    unsigned long long *counters;
+    int abandon;
+};
+cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
+
+int device_sm_count();
+void set_last_cuda_error(cudaError_t e);
+
+}  // namespace nndtw

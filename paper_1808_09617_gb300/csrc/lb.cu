@@ -1,0 +1,234 @@
+// S2: LB_Enhanced^V_W (Sec. 3.1, Eq. 7 / Algorithm 1 without the abandon
+// test) or LB_Keogh (Sec. 2.2.3) for every (query, training series) pair.
+//
+// Tiling: a CTA owns 64 queries x 64 training series; each of its 256 threads
+// owns a 4 x 4 register micro-tile of pairs (queries ty + 16 r, series
+// tx + 16 c).  The Keogh bridge streams the series in chunks of 32 elements
+// staged transposed in shared memory (query values and (U, Lo) envelope
+// pairs), so every staged element feeds 4 pairs per thread and 64 per CTA.
+// Elements outside the bridge range [n, L-n) are staged as A = 0 with the
+// envelope (+inf, -inf), which makes their term exactly 0; the inner loop is
+// therefore branch-free: d = A - clamp(A, Lo, U); acc += d * d.
+// The band terms need only the first and last n elements of both series
+// (the left bands use indices <= n, the right bands >= L-n+1); those are
+// staged once per CTA.
+//
+// Outputs: the bound per pair (raw, or scaled down by the rounding margin),
+// and per query the packed key (safe bound, index) of its smallest bound,
+// used to pick the first DTW candidate of the search.
+#include "internal.cuh"
+
+namespace nndtw {
+namespace {
+
+constexpr int kQT = 64, kNT = 64, kLC = 32, kThreads = 256, kNBMax = 32;
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+__device__ __forceinline__ float dsq(float a, float b) { float d = a - b; return d * d; }
+__device__ __forceinline__ double dsq(double a, double b) {
+    double d = __dsub_rn(a, b); return __dmul_rn(d, d);
+}
+__device__ __forceinline__ float tmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double tmin3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
+__device__ __forceinline__ float keogh_term(float a, float u, float l, float acc) {
+    float d = a - fminf(fmaxf(a, l), u);
+    return fmaf(d, d, acc);
+}
+__device__ __forceinline__ double keogh_term(double a, double u, double l, double acc) {
+    double d = a - fmin(fmax(a, l), u);
+    return fma(d, d, acc);
+}
+
+__device__ __forceinline__ float to_key_float(float x) { return x; }
+__device__ __forceinline__ float to_key_float(double x) { return __double2float_rd(x); }
+
+__device__ __forceinline__ float safe_scale(float x, float lo, float abs_s) {
+    float v = __fmul_rd(x, lo) - abs_s;
+    return v > 0.f ? v : 0.f;
+}
+__device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) {
+    double v = __dmul_rd(x, lo) - abs_s;
+    return v > 0.0 ? v : 0.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
+          const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
+          T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys) {
+    using T2 = typename V2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);                      // [kLC][kQT+1]
+    T2 *Es = reinterpret_cast<T2 *>(As + kLC * (kQT + 1) + 1);    // [kLC][kNT+1] (aligned below)
+    Es = reinterpret_cast<T2 *>((reinterpret_cast<uintptr_t>(Es) + 15) & ~uintptr_t(15));
+    T *Ab = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kQT][2nb]
+    T *Bb = Ab + kQT * 2 * (nb <= kNBMax ? nb : 0);                // [kNT][2nb]
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t q0 = (int64_t)blockIdx.y * kQT, t0 = (int64_t)blockIdx.x * kNT;
+
+    T acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = T(0);
+
+    const int mlo = keogh ? 0 : nb, mhi = keogh ? L : L - nb;
+    const T POS = inf_of<T>();
+
+    for (int c0 = (mlo / kLC) * kLC; c0 < mhi; c0 += kLC) {
+        for (int idx = tid; idx < kQT * kLC; idx += kThreads) {
+            const int row = idx / kLC, col = idx % kLC, i = c0 + col;
+            const int64_t q = q0 + row;
+            T v = T(0);
+            if (q < Q && i >= mlo && i < mhi) v = test[q * L + i];
+            As[col * (kQT + 1) + row] = v;
+        }
+        for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
+            const int row = idx / kLC, col = idx % kLC, i = c0 + col;
+            const int64_t t = t0 + row;
+            T2 e;
+            e.x = POS; e.y = -POS;
+            if (t < N && i >= mlo && i < mhi) {
+                const T *p = env + 2 * (t * L + i);
+                e.x = p[0]; e.y = p[1];
+            }
+            Es[col * (kNT + 1) + row] = e;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int col = 0; col < kLC; col++) {
+            T a[4];
+            T2 e[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) a[r] = As[col * (kQT + 1) + ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; c++) e[c] = Es[col * (kNT + 1) + tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = keogh_term(a[r], e[c].x, e[c].y, acc[r][c]);
+        }
+        __syncthreads();
+    }
+
+    if (!keogh) {
+        // stage the first and last nb elements of the tile's series
+        const bool staged = nb <= kNBMax;
+        if (staged) {
+            const int w2 = 2 * nb;
+            for (int idx = tid; idx < kQT * w2; idx += kThreads) {
+                const int row = idx / w2, m = idx % w2;
+                const int i = m < nb ? m : L - w2 + m;
+                const int64_t q = q0 + row;
+                Ab[idx] = q < Q ? test[q * L + i] : T(0);
+            }
+            for (int idx = tid; idx < kNT * w2; idx += kThreads) {
+                const int row = idx / w2, m = idx % w2;
+                const int i = m < nb ? m : L - w2 + m;
+                const int64_t t = t0 + row;
+                Bb[idx] = t < N ? train[t * L + i] : T(0);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t q = q0 + ty + 16 * r;
+            const T *Ag = test + (q < Q ? q : 0) * L;
+            const T *Asg = Ab + (ty + 16 * r) * 2 * nb;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int64_t t = t0 + tx + 16 * c;
+                const T *Bg = train + (t < N ? t : 0) * L;
+                const T *Bsg = Bb + (tx + 16 * c) * 2 * nb;
+                // A(i) / B(i) with 0-based i in the first or last nb elements
+                auto A = [&](int i) -> T {
+                    return staged ? Asg[i < nb ? i : i - L + 2 * nb] : Ag[i];
+                };
+                auto B = [&](int i) -> T {
+                    return staged ? Bsg[i < nb ? i : i - L + 2 * nb] : Bg[i];
+                };
+                T res = dsq(A(0), B(0)) + dsq(A(L - 1), B(L - 1));
+                for (int ii = 1; ii < nb; ii++) {
+                    const int ri = L - 1 - ii;
+                    T mL = dsq(A(ii), B(ii));
+                    T mR = dsq(A(ri), B(ri));
+                    const int jlo = ii - W > 0 ? ii - W : 0;
+                    for (int jj = jlo; jj < ii; jj++) {
+                        const int rj = L - 1 - jj;
+                        mL = tmin3(mL, dsq(A(ii), B(jj)), dsq(A(jj), B(ii)));
+                        mR = tmin3(mR, dsq(A(ri), B(rj)), dsq(A(rj), B(ri)));
+                    }
+                    res = res + mL + mR;
+                }
+                acc[r][c] = res + acc[r][c];
+            }
+        }
+    }
+
+    // outputs
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int64_t q = q0 + ty + 16 * r;
+        unsigned long long best = ~0ull;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int64_t t = t0 + tx + 16 * c;
+            const T raw = acc[r][c];
+            const T sv = safe_scale(raw, lb_lo, abs_slack);
+            if (q < Q && t < N) {
+                if (lb_out) lb_out[q * N + t] = safe ? sv : raw;
+                const unsigned long long k = pack_key(to_key_float(sv), (uint32_t)t);
+                best = k < best ? k : best;
+            }
+        }
+        if (seed_keys) {
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off, 16);
+                best = o < best ? o : best;
+            }
+            if (tx == 0 && q < Q && best != ~0ull) atomicMin(seed_keys + q, best);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
+                      int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
+                      unsigned long long *seed_keys, cudaStream_t s) {
+    if (Q <= 0 || N <= 0) return cudaSuccess;
+    int nb = L / 2 < V ? L / 2 : V;
+    if (nb < 1) nb = 1;
+    const int Weff = W > L - 1 ? L - 1 : W;
+    using T2 = typename V2<T>::type;
+    size_t smem = sizeof(T) * (kLC * (kQT + 1) + 1) + 16 + sizeof(T2) * kLC * (kNT + 1);
+    if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * 2 * nb;
+    cudaError_t e = cudaFuncSetAttribute(lb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    lb_kernel<T><<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0,
+                                              safe ? 1 : 0, lb_lo, abs_slack, lb_out, seed_keys);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
+                                      int, int, int, bool, bool, float, float, float *,
+                                      unsigned long long *, cudaStream_t);
+template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
+                                       int64_t, int, int, int, bool, bool, double, double,
+                                       double *, unsigned long long *, cudaStream_t);
+
+}  // namespace nndtw

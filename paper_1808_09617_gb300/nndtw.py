@@ -1,0 +1,281 @@
+"""Thin Python binding of libnndtw.so (see include/nndtw.h for the contract).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors (device memory and streams come
+from PyTorch); the binding checks dtype, device and contiguity, passes raw
+pointers and sizes, and turns status codes into ``NnDtwError``.  There is no
+CPU fallback: if the library is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libnndtw.so")
+
+NNDTW_MAX_L = 4096
+OK, EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED, ENONFINITE = 0, 1, 2, 3, 4, 5
+LB_KEOGH = 1 << 0
+LB_SAFE = 1 << 1
+EXACT_DIST = 1 << 2
+NO_PRUNE = 1 << 3
+NO_ABANDON = 1 << 4
+CHECK_FINITE = 1 << 5
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_uint = ctypes.c_uint
+_sz = ctypes.c_size_t
+
+
+class NnDtwError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = f"{where}: status {code}"
+        if _lib is not None:
+            msg += f" ({_lib.nn_dtw_strerror(code).decode()})"
+            if code == ECUDA:
+                msg += f": {_lib.nn_dtw_last_cuda_error().decode()}"
+        super().__init__(msg)
+
+
+class NativeLibraryMissing(RuntimeError):
+    pass
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("lb_pruned", ctypes.c_int64),
+                ("dtw_started", ctypes.c_int64), ("dtw_abandoned", ctypes.c_int64),
+                ("dtw_cells", ctypes.c_int64), ("rechecked", ctypes.c_int64),
+                ("recheck_queries", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+def _declare(lib):
+    sig = {
+        "nn_dtw_build_envelopes": [_vp, _i64, _int, _int, _vp, _vp],
+        "nn_dtw_build_envelopes_f64": [_vp, _i64, _int, _int, _vp, _vp],
+        "lb_enhanced": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
+        "lb_enhanced_f64": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
+        "dtw_windowed": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
+        "dtw_windowed_f64": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
+        "nn_dtw_search": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _uint, _vp, _vp, _vp,
+                          _vp, _sz, _vp, _vp],
+        "nn_dtw_search_f64": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _uint, _vp, _vp,
+                              _vp, _vp, _sz, _vp, _vp],
+        "nn_dtw_search_host": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _uint, _vp, _vp, _vp,
+                               _vp, _sz, _vp, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = _int
+    lib.nn_dtw_workspace_size.argtypes = [_i64, _i64, _int, _int, _int, _int]
+    lib.nn_dtw_workspace_size.restype = _sz
+    lib.nn_dtw_host_buffer_size.argtypes = [_i64, _i64, _int, _int, _int]
+    lib.nn_dtw_host_buffer_size.restype = _sz
+    lib.nn_dtw_strerror.argtypes = [_int]
+    lib.nn_dtw_strerror.restype = ctypes.c_char_p
+    lib.nn_dtw_last_cuda_error.argtypes = []
+    lib.nn_dtw_last_cuda_error.restype = ctypes.c_char_p
+    lib.nn_dtw_version.argtypes = []
+    lib.nn_dtw_version.restype = _int
+    return lib
+
+
+def load(path: str | None = None):
+    """Load libnndtw.so (built by ``paper_1808_09617_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise NativeLibraryMissing(
+                    f"{p} not found: build it with `python -m paper_1808_09617_gb300.build` "
+                    "(there is no CPU fallback)")
+            _lib = _declare(ctypes.CDLL(p))
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise NnDtwError(code, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t, dtype, name, ndim=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+    return _vp(t.data_ptr())
+
+
+def _fp(t):
+    import torch
+    return {torch.float32: False, torch.float64: True}[t.dtype]
+
+
+# ------------------------------------------------------------------ entry points
+
+def nn_dtw_build_envelopes(train, W: int, env=None, stream=None):
+    """Envelopes (U, Lo) of every training series, Eq. 3-4: tensor [N, L, 2]."""
+    import torch
+    lib = load()
+    f64 = _fp(train)
+    N, L = train.shape
+    if env is None:
+        env = torch.empty((N, L, 2), dtype=train.dtype, device=train.device)
+    fn = lib.nn_dtw_build_envelopes_f64 if f64 else lib.nn_dtw_build_envelopes
+    _check(fn(_dev(train, train.dtype, "train", 2), N, L, int(W),
+              _dev(env, train.dtype, "env"), _stream(stream)), "nn_dtw_build_envelopes")
+    return env
+
+
+def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: bool = False,
+                out=None, stream=None):
+    """LB_Enhanced^V (or LB_Keogh) for all pairs: tensor [Q, N]."""
+    import torch
+    lib = load()
+    f64 = _fp(test)
+    Q, L = test.shape
+    N = train.shape[0]
+    if out is None:
+        out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
+    flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0)
+    fn = lib.lb_enhanced_f64 if f64 else lib.lb_enhanced
+    _check(fn(_dev(test, test.dtype, "test", 2), Q, _dev(train, test.dtype, "train", 2),
+              _dev(env, test.dtype, "env"), N, L, int(W), int(V), flags,
+              _dev(out, test.dtype, "out"), _stream(stream)), "lb_enhanced")
+    return out
+
+
+def dtw_windowed(test, train, pairs, W: int, out=None, stream=None):
+    """DTW_W for explicit (q, t) pairs (int32 tensor [P, 2]): tensor [P]."""
+    import torch
+    lib = load()
+    f64 = _fp(test)
+    L = test.shape[1]
+    P = pairs.shape[0]
+    if out is None:
+        out = torch.empty((P,), dtype=test.dtype, device=test.device)
+    fn = lib.dtw_windowed_f64 if f64 else lib.dtw_windowed
+    _check(fn(_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", 2),
+              _dev(pairs, torch.int32, "pairs", 2), P, L, int(W),
+              _dev(out, test.dtype, "out"), _stream(stream)), "dtw_windowed")
+    return out
+
+
+def nn_dtw_workspace_size(N: int, Q: int, L: int, W: int, V: int, fp64: bool = False) -> int:
+    return int(load().nn_dtw_workspace_size(N, Q, L, W, V, 1 if fp64 else 0))
+
+
+@dataclass
+class SearchResult:
+    nn_idx: object
+    nn_label: object
+    nn_dist: object
+    stats: dict | None = None
+
+
+def nn_dtw_search(train, labels, test, W: int, V: int, env=None, flags: int = 0,
+                  workspace=None, out=None, stats: bool = False, stream=None) -> SearchResult:
+    """Exact 1-NN under DTW_W with LB_Enhanced^V pruning (FP32 or FP64 by dtype)."""
+    import torch
+    lib = load()
+    f64 = _fp(train)
+    N, L = train.shape
+    Q = test.shape[0]
+    need = lib.nn_dtw_workspace_size(N, Q, L, int(W), int(V), 1 if f64 else 0)
+    if need == 0:
+        raise NnDtwError(EINVAL, "nn_dtw_workspace_size")
+    if workspace is None:
+        workspace = torch.empty((need,), dtype=torch.uint8, device=train.device)
+    if out is None:
+        out = (torch.empty((Q,), dtype=torch.int32, device=train.device),
+               torch.empty((Q,), dtype=torch.int32, device=train.device),
+               torch.empty((Q,), dtype=torch.float64, device=train.device))
+    idx, lab, dist = out
+    st = Stats() if stats else None
+    fn = lib.nn_dtw_search_f64 if f64 else lib.nn_dtw_search
+    envp = _dev(env, train.dtype, "env") if env is not None else None
+    _check(fn(_dev(train, train.dtype, "train", 2), _dev(labels, torch.int32, "labels", 1), N,
+              _dev(test, train.dtype, "test", 2), Q, L, int(W), int(V), envp, int(flags),
+              _dev(idx, torch.int32, "nn_idx"), _dev(lab, torch.int32, "nn_label"),
+              _dev(dist, torch.float64, "nn_dist"), _dev(workspace, torch.uint8, "workspace"),
+              workspace.numel(), ctypes.byref(st) if st is not None else None, _stream(stream)),
+           "nn_dtw_search")
+    return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
+
+
+def nn_dtw_search_f64(train, labels, test, W: int, V: int, **kw) -> SearchResult:
+    import torch
+    if train.dtype != torch.float64:
+        raise TypeError("nn_dtw_search_f64 takes float64 tensors")
+    return nn_dtw_search(train, labels, test, W, V, **kw)
+
+
+def nn_dtw_host_buffer_size(N: int, Q: int, L: int, W: int, V: int) -> int:
+    return int(load().nn_dtw_host_buffer_size(N, Q, L, W, V))
+
+
+def _host(a, dtype, name):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return _vp(a.ctypes.data)
+
+
+def nn_dtw_search_host(train, labels, test, W: int, V: int, flags: int = 0, buffer=None,
+                       out=None, stats: bool = False, stream=None) -> SearchResult:
+    """The FP32 search on host (numpy) buffers; copies in and out inside the call."""
+    import torch
+    lib = load()
+    N, L = train.shape
+    Q = test.shape[0]
+    need = lib.nn_dtw_host_buffer_size(N, Q, L, int(W), int(V))
+    if need == 0:
+        raise NnDtwError(EINVAL, "nn_dtw_host_buffer_size")
+    if buffer is None:
+        buffer = torch.empty((need,), dtype=torch.uint8, device="cuda")
+    if out is None:
+        out = (np.empty(Q, np.int32), np.empty(Q, np.int32), np.empty(Q, np.float64))
+    idx, lab, dist = out
+    st = Stats() if stats else None
+    _check(lib.nn_dtw_search_host(
+        _host(train, np.float32, "train"), _host(labels, np.int32, "labels"), N,
+        _host(test, np.float32, "test"), Q, L, int(W), int(V), int(flags),
+        _host(idx, np.int32, "nn_idx"), _host(lab, np.int32, "nn_label"),
+        _host(dist, np.float64, "nn_dist"), _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
+        ctypes.byref(st) if st is not None else None, _stream(stream)), "nn_dtw_search_host")
+    return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
+
+
+def nn_dtw_strerror(code: int) -> str:
+    return load().nn_dtw_strerror(int(code)).decode()
+
+
+def nn_dtw_version() -> int:
+    return int(load().nn_dtw_version())

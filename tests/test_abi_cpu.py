@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every declared symbol (CPU only: no
+call here touches a GPU; argument validation happens before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nndtw.h")
+
+
+@pytest.fixture(scope="module")
+def clib():
+    from paper_1808_09617_gb300 import build, nndtw
+    if not os.path.exists(nndtw.LIB_PATH):
+        build.build()
+    return nndtw.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"NNDTW_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("nn_dtw_build_envelopes", "lb_enhanced", "nn_dtw_search",
+                 "nn_dtw_workspace_size", "nn_dtw_strerror"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(clib):
+    for name in declared_symbols():
+        assert hasattr(clib, name), name
+        assert ctypes.cast(getattr(clib, name), ctypes.c_void_p).value
+
+
+def test_host_only_calls(clib):
+    from paper_1808_09617_gb300 import nndtw
+    assert clib.nn_dtw_version() >= 100
+    for code in range(0, 7):
+        assert clib.nn_dtw_strerror(code)
+    assert nndtw.nn_dtw_workspace_size(500, 500, 256, 26, 5) > 500 * 500 * 4
+    assert nndtw.nn_dtw_workspace_size(500, 500, 256, 26, 5, fp64=True) > 0
+    # invalid sizes give 0 bytes
+    assert nndtw.nn_dtw_workspace_size(0, 5, 256, 26, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, 1, 0, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, 8192, 0, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, 64, -1, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, 64, 3, 0) == 0
+    assert nndtw.nn_dtw_host_buffer_size(10, 4, 64, 6, 2) > nndtw.nn_dtw_workspace_size(
+        10, 4, 64, 6, 2)
+
+
+def test_invalid_arguments_rejected_before_cuda(clib):
+    from paper_1808_09617_gb300 import nndtw
+    vp = ctypes.c_void_p
+    # N = 0
+    assert clib.nn_dtw_search(vp(8), vp(8), 0, vp(8), 1, 16, 2, 1, None, 0, vp(8), vp(8),
+                              vp(8), vp(256), 1 << 20, None, None) == nndtw.EINVAL
+    # null pointers
+    assert clib.nn_dtw_search(None, vp(8), 4, vp(8), 1, 16, 2, 1, None, 0, vp(8), vp(8),
+                              vp(8), vp(256), 1 << 20, None, None) == nndtw.EINVAL
+    # misaligned workspace
+    assert clib.nn_dtw_search(vp(8), vp(8), 4, vp(8), 1, 16, 2, 1, None, 0, vp(8), vp(8),
+                              vp(8), vp(257), 1 << 20, None, None) == nndtw.EINVAL
+    # workspace too small
+    assert clib.nn_dtw_search(vp(8), vp(8), 4, vp(8), 1, 16, 2, 1, None, 0, vp(8), vp(8),
+                              vp(8), vp(256), 16, None, None) == nndtw.ENOSPACE
+    # Q = 0 is a no-op
+    assert clib.nn_dtw_search(vp(8), vp(8), 4, vp(8), 0, 16, 2, 1, None, 0, vp(8), vp(8),
+                              vp(8), vp(256), 1 << 20, None, None) == nndtw.OK
+    assert clib.lb_enhanced(vp(8), 2, vp(8), vp(8), 2, 1, 0, 1, 0, vp(8), None) == nndtw.EINVAL
+    assert clib.lb_enhanced(vp(8), 2, vp(8), vp(8), 2, 8, 0, 0, 0, vp(8), None) == nndtw.EINVAL
+    assert clib.nn_dtw_build_envelopes(None, 3, 8, 1, vp(8), None) == nndtw.EINVAL
+    assert clib.nn_dtw_build_envelopes(vp(8), 0, 8, 1, vp(8), None) == nndtw.OK
+    assert clib.dtw_windowed(vp(8), vp(8), vp(8), -1, 8, 1, vp(8), None) == nndtw.EINVAL
+    assert clib.nn_dtw_search_host(None, None, 4, None, 0, 16, 2, 1, 0, None, None, None,
+                                   None, 0, None, None) == nndtw.OK
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_1808_09617_gb300 import nndtw
+    with pytest.raises(nndtw.NativeLibraryMissing):
+        saved = nndtw._lib
+        nndtw._lib = None
+        try:
+            nndtw.load(str(tmp_path / "missing.so"))
+        finally:
+            nndtw._lib = saved

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP32 LB and DTW values within 1e-4 relative of the oracle (the
+FP32 error bound of a sum of n non-negative terms is about n * 2^-24 in the
+worst case and ~sqrt(n) * 2^-24 in practice); FP64 DTW and every FP64 search
+result bit-identical; NN indices and labels bit-identical in every mode.
+"""
+import numpy as np
+import pytest
+
+from paper_1808_09617_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL32 = 1e-4
+
+
+def _t(x, dev="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def _series(seed, n, L, dtype=np.float32):
+    return synth.random_series(seed, n, L, dtype)
+
+
+# ---------------------------------------------------------------- envelopes
+
+ENV_CASES = [(2, 0), (2, 1), (3, 1), (5, 2), (17, 3), (100, 13), (256, 26), (300, 31),
+             (300, 32), (300, 33), (129, 1), (24, 24), (1024, 102), (1024, 512), (1024, 1023),
+             (1024, 5000), (4096, 409), (4096, 100), (4096, 4095), (33, 7)]
+
+
+@pytest.mark.parametrize("L,W", ENV_CASES)
+def test_envelopes_bit_exact(lib, orc, L, W):
+    x = _series(L * 7 + W, 37, L)
+    env = lib.nn_dtw_build_envelopes(_t(x), W).cpu().numpy()
+    U, Lo = orc.envelopes(x, W)
+    np.testing.assert_array_equal(env[..., 0], U.astype(np.float32))
+    np.testing.assert_array_equal(env[..., 1], Lo.astype(np.float32))
+
+
+@pytest.mark.parametrize("L,W", [(128, 13), (7, 3), (1000, 999)])
+def test_envelopes_f64_bit_exact(lib, orc, L, W):
+    x = _series(L + W, 11, L, np.float64)
+    env = lib.nn_dtw_build_envelopes(_t(x), W).cpu().numpy()
+    U, Lo = orc.envelopes(x, W)
+    np.testing.assert_array_equal(env[..., 0], U)
+    np.testing.assert_array_equal(env[..., 1], Lo)
+
+
+# ---------------------------------------------------------------- bounds
+
+LB_CASES = [(256, 26, 1), (256, 26, 2), (256, 26, 5), (100, 0, 3), (57, 56, 20), (200, 50, 64),
+            (2, 1, 1), (5, 2, 2), (1024, 102, 5), (130, 3, 7), (31, 30, 15)]
+
+
+@pytest.mark.parametrize("L,W,V", LB_CASES)
+def test_lb_enhanced_parity(lib, orc, L, W, V):
+    test = _series(1000 + L, 37, L)
+    train = _series(2000 + W, 70, L)
+    env = lib.nn_dtw_build_envelopes(_t(train), W)
+    lb = lib.lb_enhanced(_t(test), _t(train), env, W, V).cpu().numpy()
+    safe = lib.lb_enhanced(_t(test), _t(train), env, W, V, safe=True).cpu().numpy()
+    keo = lib.lb_enhanced(_t(test), _t(train), env, W, V, keogh=True).cpu().numpy()
+    ref = orc.lb_matrix(test, train, W, V, "enhanced")
+    refk = orc.lb_matrix(test, train, W, V, "keogh")
+    np.testing.assert_allclose(lb, ref, rtol=RTOL32, atol=1e-6)
+    np.testing.assert_allclose(keo, refk, rtol=RTOL32, atol=1e-6)
+    assert np.all(safe.astype(np.float64) <= ref), "safe bound above the exact bound"
+    assert np.all(safe <= lb)
+
+
+@pytest.mark.parametrize("L,W,V", [(128, 13, 5), (33, 4, 16), (300, 299, 2)])
+def test_lb_enhanced_f64_parity(lib, orc, L, W, V):
+    test = _series(3000 + L, 19, L, np.float64)
+    train = _series(4000 + L, 65, L, np.float64)
+    env = lib.nn_dtw_build_envelopes(_t(train), W)
+    lb = lib.lb_enhanced(_t(test), _t(train), env, W, V).cpu().numpy()
+    ref = orc.lb_matrix(test, train, W, V, "enhanced")
+    np.testing.assert_allclose(lb, ref, rtol=1e-12, atol=1e-15)
+    keo = lib.lb_enhanced(_t(test), _t(train), env, W, V, keogh=True).cpu().numpy()
+    np.testing.assert_allclose(keo, orc.lb_matrix(test, train, W, V, "keogh"), rtol=1e-12,
+                               atol=1e-15)
+
+
+def test_lb_never_exceeds_dtw(lib, orc):
+    L, W, V = 200, 20, 5
+    test = _series(51, 16, L)
+    train = _series(52, 40, L)
+    env = lib.nn_dtw_build_envelopes(_t(train), W)
+    safe = lib.lb_enhanced(_t(test), _t(train), env, W, V, safe=True).cpu().numpy()
+    d = orc.dtw_pairs(test, train, W)
+    assert np.all(safe <= d)
+
+
+# ---------------------------------------------------------------- DTW values
+
+# W spans every group width: G=1 (W<=31), 2 (32..63), 4, 8, 16, 32 (W<=1023)
+DTW_CASES = [(2, 0), (2, 1), (3, 1), (3, 2), (40, 0), (40, 1), (64, 13), (256, 26), (256, 31),
+             (256, 32), (256, 63), (300, 64), (300, 127), (600, 128), (600, 255), (1000, 256),
+             (1024, 511), (1024, 512), (1024, 1023), (2048, 1023), (777, 776), (50, 49),
+             (4096, 409), (129, 64), (128, 127)]
+
+
+@pytest.mark.parametrize("L,W", DTW_CASES)
+def test_dtw_parity(lib, orc, L, W):
+    import torch
+    nq, nt = 5, 9
+    test = _series(5000 + L, nq, L)
+    train = _series(6000 + W, nt, L)
+    rng = np.random.default_rng(L * 31 + W)
+    P = 23
+    pairs = np.stack([rng.integers(0, nq, P), rng.integers(0, nt, P)], 1).astype(np.int32)
+    pairs[0] = (0, 0)
+    got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W).cpu().numpy()
+    ref = orc.dtw_pairs(test, train, W, pairs=pairs)
+    np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0)
+    got64 = lib.dtw_windowed(_t(test.astype(np.float64)), _t(train.astype(np.float64)),
+                             _t(pairs), W).cpu().numpy()
+    np.testing.assert_array_equal(got64, ref)
+    # identical series: distance exactly 0
+    z = lib.dtw_windowed(_t(train), _t(train), _t(np.array([[1, 1]], np.int32)), W)
+    assert float(z.cpu()[0]) == 0.0
+    torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------- search
+
+def _search(lib, train, labels, test, W, V, **kw):
+    r = lib.nn_dtw_search(_t(train), _t(labels), _t(test), W, V, **kw)
+    return r.nn_idx.cpu().numpy(), r.nn_label.cpu().numpy(), r.nn_dist.cpu().numpy(), r.stats
+
+
+def _check_search(lib, orc, train, labels, test, W, V, flags=0, brute=None):
+    idx, lab, dist, st = _search(lib, train, labels, test, W, V, flags=flags, stats=True)
+    bi, bl, bd = brute if brute is not None else orc.nn_brute(train, labels, test, W)
+    np.testing.assert_array_equal(idx, bi)
+    np.testing.assert_array_equal(lab, bl)
+    if train.dtype == np.float64 or (flags & lib.EXACT_DIST):
+        np.testing.assert_array_equal(dist, bd)
+    else:
+        np.testing.assert_allclose(dist, bd, rtol=RTOL32, atol=0)
+    Q, N = test.shape[0], train.shape[0]
+    assert st["pairs"] == Q * N
+    assert 0 <= st["lb_pruned"] <= Q * N - Q
+    assert st["dtw_started"] >= Q
+    return st
+
+
+def test_search_tiny_golden(lib, orc):
+    import os
+    ds = synth.make_tiny()
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                 "tiny_nn.txt")) if not l.startswith("#")]
+    gi = np.array([int(r[1]) for r in rows], np.int32)
+    gl = np.array([int(r[2]) for r in rows], np.int32)
+    gd = np.array([float.fromhex(r[3]) for r in rows])
+    # FP64 form on the FP64 data: everything bit-exact
+    idx, lab, dist, _ = _search(lib, ds.train, ds.train_labels, ds.test, ds.W, ds.V)
+    np.testing.assert_array_equal(idx, gi)
+    np.testing.assert_array_equal(lab, gl)
+    np.testing.assert_array_equal(dist, gd)
+
+
+@pytest.mark.parametrize("V", [1, 2, 5])
+def test_search_pairs_workload(lib, orc, V):
+    ds = synth.make_pairs(V)
+    brute = orc.nn_brute(ds.train, ds.train_labels, ds.test, ds.W)
+    st = _check_search(lib, orc, ds.train, ds.train_labels, ds.test, ds.W, V, brute=brute)
+    assert st["lb_pruned"] > 0
+    _check_search(lib, orc, ds.train, ds.train_labels, ds.test, ds.W, V,
+                  flags=lib.EXACT_DIST, brute=brute)
+
+
+SEARCH_CASES = [
+    # N, Q, L, W, V
+    (1, 1, 16, 3, 2), (3, 100, 40, 5, 3), (70, 65, 2, 1, 1), (70, 65, 3, 0, 1),
+    (130, 33, 64, 0, 5), (130, 33, 64, 63, 5), (130, 33, 64, 100, 5), (129, 67, 77, 7, 40),
+    (200, 50, 150, 40, 5), (100, 20, 300, 130, 8), (64, 10, 1024, 300, 5),
+    (40, 8, 1024, 1023, 5), (257, 31, 101, 10, 4),
+]
+
+
+@pytest.mark.parametrize("N,Q,L,W,V", SEARCH_CASES)
+def test_search_parity(lib, orc, N, Q, L, W, V):
+    rng = np.random.default_rng(N * 1000 + Q * 10 + L)
+    train = _series(7000 + N + L, N, L)
+    test = _series(8000 + Q + W, Q, L)
+    labels = rng.integers(0, 5, N).astype(np.int32)
+    brute = orc.nn_brute(train, labels, test, W)
+    _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+    _check_search(lib, orc, train.astype(np.float64), labels, test.astype(np.float64), W, V)
+
+
+def test_search_ties_lowest_index(lib, orc):
+    L, W, V = 60, 6, 3
+    base = _series(9001, 40, L)
+    train = np.concatenate([base, base[:20], base[5:15]], axis=0)  # exact duplicates later
+    train = np.concatenate([train[30:40], train], axis=0)          # and some earlier
+    labels = np.arange(train.shape[0], dtype=np.int32) % 7
+    test = np.concatenate([_series(9002, 30, L), base[:10]], axis=0)  # some queries equal a series
+    brute = orc.nn_brute(train, labels, test, W)
+    _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+    _check_search(lib, orc, train, labels, test, W, V, flags=lib.EXACT_DIST, brute=brute)
+    # all training series identical: every query's NN is index 0
+    same = np.repeat(base[:1], 50, axis=0)
+    idx, _, _, _ = _search(lib, same, labels[:50], test, W, V)
+    assert np.all(idx == 0)
+
+
+@pytest.mark.parametrize("flag", ["NO_PRUNE", "NO_ABANDON", "EXACT_DIST", "CHECK_FINITE"])
+def test_search_flags(lib, orc, flag):
+    ds = synth.make_pairs(5)
+    train, test = ds.train[:300], ds.test[:120]
+    labels = ds.train_labels[:300]
+    brute = orc.nn_brute(train, labels, test, ds.W)
+    _check_search(lib, orc, train, labels, test, ds.W, 5, flags=getattr(lib, flag), brute=brute)
+
+
+def test_search_rejects_nonfinite(lib):
+    train = _series(11, 20, 32)
+    train[3, 5] = np.inf
+    test = _series(12, 4, 32)
+    with pytest.raises(lib.NnDtwError) as e:
+        _search(lib, train, np.zeros(20, np.int32), test, 3, 2, flags=lib.CHECK_FINITE)
+    assert e.value.code == lib.ENONFINITE
+
+
+def test_search_host_entry_matches(lib, orc):
+    ds = synth.make_pairs(5)
+    r = lib.nn_dtw_search_host(ds.train, ds.train_labels, ds.test, ds.W, 5, stats=True)
+    idx, lab, dist, _ = _search(lib, ds.train, ds.train_labels, ds.test, ds.W, 5)
+    np.testing.assert_array_equal(r.nn_idx, idx)
+    np.testing.assert_array_equal(r.nn_label, lab)
+    np.testing.assert_array_equal(r.nn_dist, dist)
+
+
+def test_search_workspace_too_small(lib):
+    import torch
+    train = _t(_series(13, 10, 32))
+    test = _t(_series(14, 3, 32))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.NnDtwError) as e:
+        lib.nn_dtw_search(train, _t(np.zeros(10, np.int32)), test, 3, 2, workspace=ws)
+    assert e.value.code == lib.ENOSPACE
+
+
+@pytest.mark.parametrize("W_ratio", [0.1, 0.5, 1.0])
+def test_search_precision_workload_sampled(lib, orc, W_ratio):
+    """The full-size precision workload (10,000 x 2,000, L=1024) on the GPU,
+    checked on a sample of queries with the oracle's exact pruned search."""
+    ds = synth.make_precision(W_ratio)
+    idx, lab, dist, st = _search(lib, ds.train, ds.train_labels, ds.test, ds.W, ds.V, stats=True)
+    sample = np.random.default_rng(5).choice(ds.Q, 6, replace=False)
+    ri, rl, rd, _ = orc.nn_pruned(ds.train, ds.train_labels, ds.test[sample], ds.W, ds.V)
+    np.testing.assert_array_equal(idx[sample], ri)
+    np.testing.assert_array_equal(lab[sample], rl)
+    np.testing.assert_allclose(dist[sample], rd, rtol=RTOL32, atol=0)
