@@ -65,18 +65,37 @@ extern "C" {
 #define NNDTW_NO_PRUNE (1u << 3)     /* search: run DTW on every pair (no LB prune)  */
 #define NNDTW_NO_ABANDON (1u << 4)   /* search: no early abandoning inside DTW      */
 #define NNDTW_CHECK_FINITE (1u << 5) /* search: reject non-finite or huge inputs     */
+#define NNDTW_TIME_STAGES (1u << 6)  /* search: record stage events (see below)      */
+/* search / dtw_windowed: lanes per pair of the FP32 DTW kernel, a tuning
+ * choice that never changes results: NNDTW_DTW_GROUP(log2 G) with
+ * G = 1, 2, 4, ..., 32; 0 (the default) lets the library choose.  A G that
+ * cannot hold the window (more than 64 diagonals per lane) is ignored. */
+#define NNDTW_DTW_GROUP(log2g) ((unsigned)((log2g) + 1) << 8)
+#define NNDTW_DTW_GROUP_MASK (7u << 8)
 
-/* Work counters of one search (filled only when a non-NULL pointer is given;
- * doing so makes the call wait for the stream). */
+/* stage indices of nn_dtw_stage_times() */
+#define NNDTW_STAGE_ENVELOPES 0 /* S1 (0 when envelopes are supplied)            */
+#define NNDTW_STAGE_LB 1        /* S2 bounds of all pairs                        */
+#define NNDTW_STAGE_SEED 2      /* S4 DTW of each query's first candidate        */
+#define NNDTW_STAGE_COMPACT 3   /* S3 compaction of the surviving pairs          */
+#define NNDTW_STAGE_DTW 4       /* S4 DTW of the survivors with early abandoning */
+#define NNDTW_STAGE_RECHECK 5   /* S5 FP64 recheck of near ties                  */
+#define NNDTW_STAGE_FINAL 6     /* S5 argmin, labels                             */
+#define NNDTW_STAGE_TOTAL 7     /* whole call, first to last kernel              */
+
+/* Work counters of one search, filled only when a non-NULL pointer is given;
+ * doing so makes the call wait for the stream and makes the DTW kernels count
+ * their work with atomics (unless NNDTW_TIME_STAGES is also set, in which case
+ * dtw_started, dtw_abandoned, dtw_cells and seed_cells stay 0). */
 typedef struct nndtw_stats {
     int64_t pairs;          /* Q * N query x train pairs                        */
     int64_t lb_pruned;      /* pairs whose bound exceeded the query's bound     */
     int64_t dtw_started;    /* DTW computations started (seeds included)        */
     int64_t dtw_abandoned;  /* of those, abandoned early                        */
-    int64_t dtw_cells;      /* band cells swept by the FP32/FP64 DTW kernels    */
+    int64_t dtw_cells;      /* band cells (i,j) evaluated by the DTW kernels    */
     int64_t rechecked;      /* FP64 re-evaluations of near-tie candidates       */
     int64_t recheck_queries;/* queries that needed at least one                 */
-    int64_t reserved;
+    int64_t seed_cells;     /* of dtw_cells, those of the first-candidate pass  */
 } nndtw_stats;
 
 /*
@@ -123,6 +142,9 @@ NNDTW_API int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_t
  */
 NNDTW_API int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pairs,
                  int64_t P, int L, int W, float *d_out, void *stream);
+/* dtw_windowed with flags (NNDTW_DTW_GROUP only). */
+NNDTW_API int dtw_windowed_ex(const float *d_test, const float *d_train, const int32_t *d_pairs,
+                              int64_t P, int L, int W, unsigned flags, float *d_out, void *stream);
 NNDTW_API int dtw_windowed_f64(const double *d_test, const double *d_train, const int32_t *d_pairs,
                      int64_t P, int L, int W, double *d_out, void *stream);
 
@@ -178,6 +200,30 @@ NNDTW_API int nn_dtw_search_host(const float *h_train, const int32_t *h_train_la
                        int32_t *h_nn_idx, int32_t *h_nn_label, double *h_nn_dist,
                        void *d_buffer, size_t buffer_bytes, nndtw_stats *stats,
                        void *stream);
+
+/*
+ * Measurement aid, not part of the method.  A search called with
+ * NNDTW_TIME_STAGES records CUDA events on its stream at every stage boundary
+ * (events created once per thread and device; the call does not wait).  This
+ * function waits for the last such search issued by the calling thread and
+ * writes its stage times in milliseconds to h_ms[0..7] (NNDTW_STAGE_*).
+ * NNDTW_EINVAL if the thread issued no timed search or h_ms is NULL.
+ */
+NNDTW_API int nn_dtw_stage_times(float *h_ms);
+
+/*
+ * Measurement aid, not part of the method: the FP32 CUDA-core rate of the DTW
+ * cell update (one subtraction, one three-input minimum, one fused
+ * multiply-add per cell, the instruction mix of the FP32 DTW kernel) with
+ * independent cells and no memory traffic, over the whole GPU.  Runs `iters`
+ * iterations of 16 cells per thread on every SM, waits for the stream and
+ * writes the measured cells per second to *h_cells_per_s.  d_sink: device
+ * memory of at least nn_dtw_probe_sink_bytes() bytes (receives the results so
+ * the work is not optimised away).
+ */
+NNDTW_API size_t nn_dtw_probe_sink_bytes(void);
+NNDTW_API int nn_dtw_probe_cell_rate(void *d_sink, size_t sink_bytes, int iters,
+                                     double *h_cells_per_s, void *stream);
 
 /* Static description of a status code.  Never NULL. */
 NNDTW_API const char *nn_dtw_strerror(int code);

@@ -1,0 +1,101 @@
+"""Autotuner for the search's launch shapes.
+
+The only shape with a large effect is G, the number of lanes that share one
+(query, train) pair in the FP32 DTW kernel: G = 1 gives every lane its own
+pair (no shuffles, but many concurrent pairs, so uneven early-abandoning
+leaves lanes idle when work is scarce); larger G sweeps each pair faster with
+more exchange per cell.  The tuner times ``nn_dtw_search`` with every
+admissible G on the caller's data (results never depend on G) and keeps the
+fastest, cached in memory and optionally in a JSON file keyed by device, L,
+W, V and power-of-two buckets of N and Q.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import nndtw
+
+_lock = threading.Lock()
+_mem: dict = {}
+
+
+def _bucket(n: int) -> int:
+    b = 1
+    while b < n:
+        b <<= 1
+    return b
+
+
+def key(device_name: str, N: int, Q: int, L: int, W: int, V: int) -> str:
+    return f"{device_name}|L{L}|W{min(W, L - 1)}|V{V}|N{_bucket(N)}|Q{_bucket(Q)}"
+
+
+def admissible_groups(W: int):
+    out = []
+    for g in (1, 2, 4, 8, 16, 32):
+        h = (W + g) // g
+        if h <= 32 and not (h == 1 and g != W + 1):
+            out.append(g)
+    return out
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, reps: int = 3,
+                cache_path: str | None = None) -> int:
+    """Return the fastest lanes-per-pair G for this search (0 if nothing to tune)."""
+    import torch
+    N, L = train.shape
+    Q = test.shape[0]
+    Weff = min(W, L - 1)
+    dev = torch.cuda.get_device_name(train.device)
+    k = key(dev, N, Q, L, Weff, V)
+    with _lock:
+        if k in _mem:
+            return _mem[k]
+        if cache_path and k in _load(cache_path):
+            _mem[k] = int(_load(cache_path)[k])
+            return _mem[k]
+    groups = admissible_groups(Weff)
+    if not groups:
+        return 0
+    if workspace is None:
+        workspace = torch.empty(nndtw.nn_dtw_workspace_size(N, Q, L, W, V), dtype=torch.uint8,
+                                device=train.device)
+    if out is None:
+        out = (torch.empty(Q, dtype=torch.int32, device=train.device),
+               torch.empty(Q, dtype=torch.int32, device=train.device),
+               torch.empty(Q, dtype=torch.float64, device=train.device))
+    best, best_ms = groups[0], float("inf")
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for g in groups:
+        f = nndtw.DTW_GROUP(g)
+        nndtw.nn_dtw_search(train, labels, test, W, V, flags=f, workspace=workspace, out=out)
+        times = []
+        for _ in range(reps):
+            s.record()
+            nndtw.nn_dtw_search(train, labels, test, W, V, flags=f, workspace=workspace, out=out)
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+        ms = sorted(times)[len(times) // 2]
+        if ms < best_ms:
+            best, best_ms = g, ms
+    with _lock:
+        _mem[k] = best
+        if cache_path:
+            d = _load(cache_path)
+            d[k] = best
+            tmp = cache_path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(d, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache_path)
+    return best

@@ -17,9 +17,14 @@
 // lane keeping a window of H of each in registers.  Per cell the work is
 // d = A_i - B_j; D = fma(d, d, min3(D_diag, D_left, D_up)).
 //
-// Cells outside the L x L matrix read sentinels (query +1e30, training -1e30)
-// whose squared difference overflows to +inf.  D(-1,-1) = 0 is seeded in the
-// register of diagonal W.
+// Cells outside the L x L matrix read sentinels: +1e30 for the query outside
+// [0, L), -1e30 for the training series before its start and +1e30 after its
+// end.  A cell with one index inside and one outside, or both before the
+// start, gets delta = +inf and never wins a minimum; cells with both indices
+// past the end get delta = 0, so they inherit exactly D(L,L) (their only
+// finite entry is the diagonal step out of (L,L)) and diagonal W keeps the
+// result after the sweep ends.  D(-1,-1) = 0 is seeded in the register of
+// diagonal W.
 //
 // Early abandoning: every path from (1,1) to (L,L) visits one of any two
 // consecutive anti-diagonals, and D never decreases along a path, so the
@@ -39,29 +44,42 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return r;
 }
 
-// number of band cells (i, j) in [0,L)^2, |i-j| <= W, with i + j <= smax
-__device__ inline long long band_cells_upto(int L, int W, int smax) {
-    long long n = 0;
-    const int dmax = smax < 2 * L - 2 ? smax : 2 * L - 2;
-    for (int d = 0; d <= dmax; d++) {
-        int lo = d - L + 1 > 0 ? d - L + 1 : 0;
-        int hi = d < L - 1 ? d : L - 1;
-        int blo = (d - W + 1) >> 1;       // ceil((d - W) / 2)
-        if (d - W < 0) blo = -(((W - d)) >> 1);
-        int bhi = (d + W) >> 1;
-        if (blo > lo) lo = blo;
-        if (bhi < hi) hi = bhi;
-        if (hi >= lo) n += hi - lo + 1;
+// Number of band cells (i, j) in [0,L)^2 with |i-j| <= W and i + j <= S, in
+// closed form: anti-diagonals d <= W hold d+1 cells, the middle ones W or W+1
+// alternately, the last W ones 2L-1-d.
+__device__ inline long long band_cells_upto(int L, int W, long long S) {
+    if (S < 0) return 0;
+    if (W > L - 1) W = L - 1;
+    if (S > 2ll * L - 2) S = 2ll * L - 2;
+    const long long a = S < W ? S : W;
+    long long tot = (a + 1) * (a + 2) / 2;
+    if (W >= L - 1) {
+        if (S >= L) tot += (3ll * L - 2 - S) * (S - L + 1) / 2;
+        return tot;
     }
-    return n;
+    if (S > W) {
+        const long long m_end = S < 2ll * L - 3 - W ? S : 2ll * L - 3 - W;
+        const long long n = m_end - W;
+        if (n > 0) tot += n * W + n / 2;
+    }
+    if (S >= 2ll * L - 2 - W) tot += (W + 2ll * L - S) * (S - (2ll * L - 2 - W) + 1) / 2;
+    return tot;
+}
+
+// Resident 128-thread blocks per SM requested from the register allocator for
+// each H (the diagonal registers, the two windows and the per-pair state need
+// about 4H + 2U + 40 registers); chosen from a compile sweep as the largest
+// count that causes no more than a few bytes of spills.
+__host__ __device__ constexpr int dtw32_min_blocks(int H) {
+    return H <= 4 ? 8 : H <= 9 ? 6 : H == 12 ? 4 : H <= 13 ? 5 : H <= 20 ? 4 : H <= 28 ? 3 : 2;
 }
 
 template <int H, int U>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, dtw32_min_blocks(H))
 dtw32_kernel(DtwJob32 job, int G) {
     constexpr int C = 2 * H;
     const float INF = __int_as_float(0x7f800000);
-    const float APAD = Pad<float>::v, BPAD = -Pad<float>::v;
+    const float APAD = Pad<float>::v, BPAD = -Pad<float>::v, EPAD = Pad<float>::v;
     const int L = job.L, W = job.W;
 
     const int lane = threadIdx.x & 31;
@@ -142,14 +160,14 @@ dtw32_kernel(DtwJob32 job, int G) {
                         const int ia = I0 - m;
                         Aw[m + U - 1] = (ia >= 0 && ia < L) ? ap[ia] : APAD;
                         const int jb = J0 + m;
-                        Bw[m] = (jb >= 0 && jb < L) ? bp[jb] : BPAD;
+                        Bw[m] = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
                     }
 #pragma unroll
                     for (int c = 0; c < C; c++) R[c] = (hasW && c == cW) ? 0.f : INF;
                     {   // stream values for super-step 0
                         const int ia = I0 + 1, jb = J0 + H;
                         acur = (gl == 0) ? ((ia >= 0 && ia < L) ? ap[ia] : APAD) : 0.f;
-                        bcur = lastl ? ((jb >= 0 && jb < L) ? bp[jb] : BPAD) : 0.f;
+                        bcur = lastl ? (jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD)) : 0.f;
                     }
                     if (job.counters && gl == 0) atomicAdd(job.counters + C_STARTED, 1ull);
                 }
@@ -165,7 +183,7 @@ dtw32_kernel(DtwJob32 job, int G) {
             {
                 const int ia = I0 + u + 2, jb = J0 + u + 1 + H;
                 if (gl == 0) anx = (ia >= 0 && ia < L) ? ap[ia] : APAD;
-                if (lastl) bnx = (jb >= 0 && jb < L) ? bp[jb] : BPAD;
+                if (lastl) bnx = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
             }
             // step A: even slots
             {
@@ -212,13 +230,6 @@ dtw32_kernel(DtwJob32 job, int G) {
                 }
                 if (lastl) R[C - 1] = INF;
             }
-            // result of the pair: anti-diagonal 2L-2 was just computed
-            if (u == L - 1 && !done) {
-                float r = INF;
-#pragma unroll
-                for (int c = 0; c < C; c++) r = (hasW && c == cW) ? R[c] : r;
-                res = r;
-            }
             // a-shift
             {
                 float senda;
@@ -248,8 +259,10 @@ dtw32_kernel(DtwJob32 job, int G) {
         // lane mask.
         const bool completed = !done && u >= L;
         if (completed) {
-            // broadcast the result from the lane holding diagonal W
-            float r = hasW ? res : INF;
+            // the result: diagonal W holds D(L,L) (kept by the past-the-end cells)
+            float r = INF;
+#pragma unroll
+            for (int c = 0; c < C; c++) r = (hasW && c == cW) ? R[c] : r;
             for (int off = 1; off < G; off <<= 1) r = fminf(r, __shfl_xor_sync(gmask, r, off, G));
             res = r;
             if (gl == 0) {
@@ -268,7 +281,7 @@ dtw32_kernel(DtwJob32 job, int G) {
                 }
                 if (job.counters)
                     atomicAdd(job.counters + C_CELLS,
-                              (unsigned long long)band_cells_upto(L, W, 2 * L));
+                              (unsigned long long)band_cells_upto(L, W, 2ll * L));
             }
             done = true;
         } else if (!done && job.abandon) {
@@ -288,7 +301,7 @@ dtw32_kernel(DtwJob32 job, int G) {
                     if (gl == 0 && job.counters) {
                         atomicAdd(job.counters + C_ABANDONED, 1ull);
                         atomicAdd(job.counters + C_CELLS,
-                                  (unsigned long long)band_cells_upto(L, W, 2 * u + t_first - 1));
+                                  (unsigned long long)band_cells_upto(L, W, 2ll * u + t_first - 1));
                     }
                     done = true;
                 }

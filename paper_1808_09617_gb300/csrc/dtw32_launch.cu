@@ -27,19 +27,44 @@ OccCache g_occ;
 
 }  // namespace
 
-// G lanes per pair and H diagonal pairs per lane with G*H >= W+1, at most
-// G-1 short lanes.  Smallest G first: fewer shuffles per cell.
-bool dtw32_shape(int W, int *G, int *H) {
-    for (int g = 1; g <= 32; g <<= 1) {
-        const int h = (W + 1 + g - 1) / g;
-        if (h <= 32) { *G = g; *H = h; return true; }
+// G lanes per pair and H diagonal pairs per lane with G*H >= W+1 and at most
+// G-1 short lanes (H = ceil((W+1)/G)).  A lane needs at least one live pair,
+// so H = 1 is allowed only without short lanes.
+static bool shape_ok(int W, int g, int *H) {
+    const int h = (W + 1 + g - 1) / g;
+    if (h > 32) return false;
+    if (h == 1 && g * h != W + 1) return false;
+    *H = h;
+    return true;
+}
+
+// Default: the smallest G whose lanes hold the window (fewest shuffles per
+// cell); `want` (if valid) overrides it.
+bool dtw32_shape(int W, int want, int *G, int *H) {
+    if (want >= 1 && want <= 32 && (want & (want - 1)) == 0 && shape_ok(W, want, H)) {
+        *G = want;
+        return true;
     }
+    for (int g = 1; g <= 32; g <<= 1)
+        if (shape_ok(W, g, H)) { *G = g; return true; }
     return false;
+}
+
+int dtw32_wide_group(int W) {
+    int H;
+    for (int g = 32; g >= 1; g >>= 1)
+        if (shape_ok(W, g, &H)) return g;
+    return 0;
+}
+
+bool dtw32_supported(int W) {
+    int G, H;
+    return dtw32_shape(W, 0, &G, &H);
 }
 
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
     int G = 0, H = 0;
-    if (!dtw32_shape(job.W, &G, &H)) return cudaErrorNotSupported;
+    if (!dtw32_shape(job.W, job.group, &G, &H)) return cudaErrorNotSupported;
     Dtw32Fn fn = pick_fn(H);
     if (!fn) return cudaErrorNotSupported;
     int dev = 0;

@@ -112,8 +112,11 @@ struct DtwJob32 {
     unsigned long long *counters;       // stats (C_STARTED ...), may be nullptr
     float dtw_lo, dtw_hi, abs32;        // margins
     int abandon;                        // 1: abandon against bsf
+    int group;                          // lanes per pair (0: library's choice)
 };
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
+bool dtw32_supported(int W);   // window W (<= L-1) fits the FP32 DTW kernel
+int dtw32_wide_group(int W);   // widest lanes-per-pair choice for W (latency-bound passes)
 
 // FP64 DTW: same job shape, exact evaluation order.  Inputs are double
 // (test/train) or FP32 promoted in-kernel (test32/train32, for the recheck of

@@ -1,9 +1,10 @@
 // S2: LB_Enhanced^V_W (Sec. 3.1, Eq. 7 / Algorithm 1 without the abandon
 // test) or LB_Keogh (Sec. 2.2.3) for every (query, training series) pair.
 //
-// Tiling: a CTA owns 64 queries x 64 training series; each of its 256 threads
-// owns a 4 x 4 register micro-tile of pairs (queries ty + 16 r, series
-// tx + 16 c).  The Keogh bridge streams the series in chunks of 32 elements
+// Tiling: a CTA of 256 threads owns 16 MR queries x 16 MC training series;
+// each thread owns an MR x MC register micro-tile of pairs (queries ty + 16 r,
+// series tx + 16 c).  MR = MC = 4 (64 x 64 tiles) when the tile grid fills
+// the GPU, 2 x 2 (32 x 32) for small problems.  The Keogh bridge streams the series in chunks of 32 elements
 // staged transposed in shared memory (query values and (U, Lo) envelope
 // pairs), so every staged element feeds 4 pairs per thread and 64 per CTA.
 // Elements outside the bridge range [n, L-n) are staged as A = 0 with the
@@ -13,15 +14,20 @@
 // (the left bands use indices <= n, the right bands >= L-n+1); those are
 // staged once per CTA.
 //
-// Outputs: the bound per pair (raw, or scaled down by the rounding margin),
-// and per query the packed key (safe bound, index) of its smallest bound,
-// used to pick the first DTW candidate of the search.
+// Outputs: the bound per pair (raw, or scaled down by the rounding margin)
+// and, for the search, per query the packed key (distance, index) of its
+// nearest training series in squared Euclidean distance, fused into the same
+// pass (2 more operations per pair-element over the same staged values): the
+// search's first DTW candidate, as in the paper's protocol of starting from
+// the candidate nearest in Euclidean distance (Sec. 4).  ED = DTW_0 is an
+// upper bound of DTW_W, and that candidate is usually far closer to the
+// nearest neighbour than the one with the smallest bound.
 #include "internal.cuh"
 
 namespace nndtw {
 namespace {
 
-constexpr int kQT = 64, kNT = 64, kLC = 32, kThreads = 256, kNBMax = 32;
+constexpr int kLC = 32, kThreads = 256, kNBMax = 32;
 
 template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
@@ -59,38 +65,48 @@ __device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) 
     return v > 0.0 ? v : 0.0;
 }
 
-template <typename T>
+template <typename T, bool ED, int MR, int MC>
 __global__ void __launch_bounds__(kThreads)
 lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
           const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
           T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys) {
     using T2 = typename V2<T>::type;
+    constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);                      // [kLC][kQT+1]
     T2 *Es = reinterpret_cast<T2 *>(As + kLC * (kQT + 1) + 1);    // [kLC][kNT+1] (aligned below)
     Es = reinterpret_cast<T2 *>((reinterpret_cast<uintptr_t>(Es) + 15) & ~uintptr_t(15));
-    T *Ab = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kQT][2nb]
+    T *Bs = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kLC][kNT+1] (ED only)
+    T *Ab = Bs + (ED ? kLC * (kNT + 1) : 0);                       // [kQT][2nb]
     T *Bb = Ab + kQT * 2 * (nb <= kNBMax ? nb : 0);                // [kNT][2nb]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t q0 = (int64_t)blockIdx.y * kQT, t0 = (int64_t)blockIdx.x * kNT;
 
-    T acc[4][4];
+    T acc[MR][MC], ed[MR][MC];
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+    for (int r = 0; r < MR; r++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = T(0);
+        for (int c = 0; c < MC; c++) { acc[r][c] = T(0); ed[r][c] = T(0); }
 
     const int mlo = keogh ? 0 : nb, mhi = keogh ? L : L - nb;
     const T POS = inf_of<T>();
 
-    for (int c0 = (mlo / kLC) * kLC; c0 < mhi; c0 += kLC) {
+    const int cbeg = ED ? 0 : (mlo / kLC) * kLC, cend = ED ? L : mhi;
+    for (int c0 = cbeg; c0 < cend; c0 += kLC) {
         for (int idx = tid; idx < kQT * kLC; idx += kThreads) {
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
             const int64_t q = q0 + row;
             T v = T(0);
-            if (q < Q && i >= mlo && i < mhi) v = test[q * L + i];
+            if (q < Q && i < L) v = test[q * L + i];
             As[col * (kQT + 1) + row] = v;
+        }
+        if (ED) {
+            for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
+                const int row = idx / kLC, col = idx % kLC, i = c0 + col;
+                const int64_t t = t0 + row;
+                Bs[col * (kNT + 1) + row] = (t < N && i < L) ? train[t * L + i] : T(0);
+            }
         }
         for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
@@ -106,16 +122,28 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
         __syncthreads();
 #pragma unroll 4
         for (int col = 0; col < kLC; col++) {
-            T a[4];
-            T2 e[4];
+            T a[MR];
+            T2 e[MC];
 #pragma unroll
-            for (int r = 0; r < 4; r++) a[r] = As[col * (kQT + 1) + ty + 16 * r];
+            for (int r = 0; r < MR; r++) a[r] = As[col * (kQT + 1) + ty + 16 * r];
 #pragma unroll
-            for (int c = 0; c < 4; c++) e[c] = Es[col * (kNT + 1) + tx + 16 * c];
+            for (int c = 0; c < MC; c++) e[c] = Es[col * (kNT + 1) + tx + 16 * c];
 #pragma unroll
-            for (int r = 0; r < 4; r++)
+            for (int r = 0; r < MR; r++)
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[r][c] = keogh_term(a[r], e[c].x, e[c].y, acc[r][c]);
+                for (int c = 0; c < MC; c++) acc[r][c] = keogh_term(a[r], e[c].x, e[c].y, acc[r][c]);
+            if (ED) {
+                T b[MC];
+#pragma unroll
+                for (int c = 0; c < MC; c++) b[c] = Bs[col * (kNT + 1) + tx + 16 * c];
+#pragma unroll
+                for (int r = 0; r < MR; r++)
+#pragma unroll
+                    for (int c = 0; c < MC; c++) {
+                        const T d = a[r] - b[c];
+                        ed[r][c] = fma(d, d, ed[r][c]);
+                    }
+            }
         }
         __syncthreads();
     }
@@ -140,32 +168,32 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             __syncthreads();
         }
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
+        for (int r = 0; r < MR; r++) {
             const int64_t q = q0 + ty + 16 * r;
             const T *Ag = test + (q < Q ? q : 0) * L;
             const T *Asg = Ab + (ty + 16 * r) * 2 * nb;
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < MC; c++) {
                 const int64_t t = t0 + tx + 16 * c;
                 const T *Bg = train + (t < N ? t : 0) * L;
                 const T *Bsg = Bb + (tx + 16 * c) * 2 * nb;
-                // A(i) / B(i) with 0-based i in the first or last nb elements
-                auto A = [&](int i) -> T {
-                    return staged ? Asg[i < nb ? i : i - L + 2 * nb] : Ag[i];
-                };
-                auto B = [&](int i) -> T {
-                    return staged ? Bsg[i < nb ? i : i - L + 2 * nb] : Bg[i];
-                };
-                T res = dsq(A(0), B(0)) + dsq(A(L - 1), B(L - 1));
+                // element i (0-based, in the first or last nb) of A and B:
+                // staged copies hold the first nb then the last nb elements
+                const T *Ap = staged ? Asg : Ag;
+                const T *Bp = staged ? Bsg : Bg;
+                const int sh = staged ? L - 2 * nb : 0;   // offset of the last nb
+                const int last = L - 1 - sh;
+                T res = dsq(Ap[0], Bp[0]) + dsq(Ap[last], Bp[last]);
                 for (int ii = 1; ii < nb; ii++) {
-                    const int ri = L - 1 - ii;
-                    T mL = dsq(A(ii), B(ii));
-                    T mR = dsq(A(ri), B(ri));
+                    const int ri = last - ii;
+                    const T ai = Ap[ii], bi = Bp[ii], ar = Ap[ri], br = Bp[ri];
+                    T mL = dsq(ai, bi);
+                    T mR = dsq(ar, br);
                     const int jlo = ii - W > 0 ? ii - W : 0;
                     for (int jj = jlo; jj < ii; jj++) {
-                        const int rj = L - 1 - jj;
-                        mL = tmin3(mL, dsq(A(ii), B(jj)), dsq(A(jj), B(ii)));
-                        mR = tmin3(mR, dsq(A(ri), B(rj)), dsq(A(rj), B(ri)));
+                        const int rj = last - jj;
+                        mL = tmin3(mL, dsq(ai, Bp[jj]), dsq(Ap[jj], bi));
+                        mR = tmin3(mR, dsq(ar, Bp[rj]), dsq(Ap[rj], br));
                     }
                     res = res + mL + mR;
                 }
@@ -176,21 +204,23 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
 
     // outputs
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
+    for (int r = 0; r < MR; r++) {
         const int64_t q = q0 + ty + 16 * r;
         unsigned long long best = ~0ull;
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
+        for (int c = 0; c < MC; c++) {
             const int64_t t = t0 + tx + 16 * c;
             const T raw = acc[r][c];
             const T sv = safe_scale(raw, lb_lo, abs_slack);
             if (q < Q && t < N) {
                 if (lb_out) lb_out[q * N + t] = safe ? sv : raw;
-                const unsigned long long k = pack_key(to_key_float(sv), (uint32_t)t);
-                best = k < best ? k : best;
+                if (ED) {
+                    const unsigned long long k = pack_key(to_key_float(ed[r][c]), (uint32_t)t);
+                    best = k < best ? k : best;
+                }
             }
         }
-        if (seed_keys) {
+        if (ED) {
 #pragma unroll
             for (int off = 8; off > 0; off >>= 1) {
                 unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off, 16);
@@ -199,6 +229,26 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             if (tx == 0 && q < Q && best != ~0ull) atomicMin(seed_keys + q, best);
         }
     }
+}
+
+template <typename T, int MR, int MC>
+cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
+                           int L, int Weff, int nb, bool keogh, bool safe, T lb_lo, T abs_slack,
+                           T *lb_out, unsigned long long *seed_keys, cudaStream_t s) {
+    using T2 = typename V2<T>::type;
+    constexpr int kQT = 16 * MR, kNT = 16 * MC;
+    const bool ed = seed_keys != nullptr;
+    size_t smem = sizeof(T) * (kLC * (kQT + 1) + 1) + 16 + sizeof(T2) * kLC * (kNT + 1);
+    if (ed) smem += sizeof(T) * kLC * (kNT + 1);
+    if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * 2 * nb;
+    auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
+                                    lb_lo, abs_slack, lb_out, seed_keys);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -211,17 +261,13 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
     int nb = L / 2 < V ? L / 2 : V;
     if (nb < 1) nb = 1;
     const int Weff = W > L - 1 ? L - 1 : W;
-    using T2 = typename V2<T>::type;
-    size_t smem = sizeof(T) * (kLC * (kQT + 1) + 1) + 16 + sizeof(T2) * kLC * (kNT + 1);
-    if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * 2 * nb;
-    cudaError_t e = cudaFuncSetAttribute(lb_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    lb_kernel<T><<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0,
-                                              safe ? 1 : 0, lb_lo, abs_slack, lb_out, seed_keys);
-    return cudaGetLastError();
+    // 64 x 64 tiles when they give at least two CTAs per SM, else 32 x 32
+    const int sms = device_sm_count();
+    const bool small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
+    if (small) return launch_lb_tile<T, 2, 2>(test, Q, train, env, N, L, Weff, nb, keogh, safe,
+                                              lb_lo, abs_slack, lb_out, seed_keys, s);
+    return launch_lb_tile<T, 4, 4>(test, Q, train, env, N, L, Weff, nb, keogh, safe, lb_lo,
+                                   abs_slack, lb_out, seed_keys, s);
 }
 
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,

@@ -197,6 +197,50 @@ __global__ void finalize64_kernel(int64_t Q, const unsigned long long *__restric
 
 // ---------------------------------------------------------------- workspace
 
+long long band_cells(int L, int W) {
+    const long long w = W > L - 1 ? L - 1 : W;
+    return (long long)L * (2 * w + 1) - w * (w + 1);
+}
+
+// CUDA events at the stage boundaries of one search (NNDTW_TIME_STAGES).
+// One set of events per thread and device, created on first use and reused;
+// the set of the thread's last timed search is read by nn_dtw_stage_times().
+struct EventSet {
+    cudaEvent_t ev[8] = {};
+    bool ready = false;
+};
+thread_local EventSet t_events[64];
+thread_local int t_last_dev = -1;
+
+struct StageTimer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    EventSet *set = nullptr;
+    cudaError_t start(bool enabled, cudaStream_t st) {
+        on = enabled;
+        s = st;
+        if (!on) return cudaSuccess;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        set = &t_events[dev];
+        if (!set->ready) {
+            for (int i = 0; i < 8; i++) {
+                e = cudaEventCreate(&set->ev[i]);
+                if (e != cudaSuccess) return e;
+            }
+            set->ready = true;
+        }
+        t_last_dev = dev;
+        return mark(0);
+    }
+    cudaError_t mark(int i) {
+        if (!on) return cudaSuccess;
+        return cudaEventRecord(set->ev[i], s);
+    }
+};
+
 struct Carve {
     char *base;
     size_t off = 0;
@@ -293,15 +337,19 @@ dim3 grid_compact(int64_t Q, int64_t N) {
         if (e_ != cudaSuccess) { set_last_cuda_error(e_); return NNDTW_ECUDA; } \
     } while (0)
 
-void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t Q) {
+void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t Q, int L,
+                int W, bool counted) {
+    std::memset(st, 0, sizeof(*st));
     st->pairs = Q * N;
     st->lb_pruned = Q * N - Q - (int64_t)h[C_QUEUE];
-    st->dtw_started = (int64_t)h[C_STARTED];
-    st->dtw_abandoned = (int64_t)h[C_ABANDONED];
-    st->dtw_cells = (int64_t)h[C_CELLS];
     st->rechecked = (int64_t)h[C_RECHECK];
     st->recheck_queries = (int64_t)h[C_RQUERIES];
-    st->reserved = 0;
+    if (counted) {
+        st->dtw_started = (int64_t)h[C_STARTED];
+        st->dtw_abandoned = (int64_t)h[C_ABANDONED];
+        st->dtw_cells = (int64_t)h[C_CELLS];
+        st->seed_cells = Q * band_cells(L, W);
+    }
 }
 
 template <typename T>
@@ -375,7 +423,16 @@ using namespace nndtw;
 
 extern "C" {
 
-int nn_dtw_version(void) { return 100; }
+int nn_dtw_version(void) { return 101; }
+
+int nn_dtw_stage_times(float *h_ms) {
+    if (!h_ms || t_last_dev < 0) return NNDTW_EINVAL;
+    EventSet &set = t_events[t_last_dev];
+    CK(cudaEventSynchronize(set.ev[7]));
+    for (int k = 0; k < 7; k++) CK(cudaEventElapsedTime(&h_ms[k], set.ev[k], set.ev[k + 1]));
+    CK(cudaEventElapsedTime(&h_ms[7], set.ev[0], set.ev[7]));
+    return NNDTW_OK;
+}
 
 const char *nn_dtw_strerror(int code) {
     switch (code) {
@@ -436,14 +493,26 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
 
 int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pairs, int64_t P,
                  int L, int W, float *d_out, void *stream) {
+    return dtw_windowed_ex(d_test, d_train, d_pairs, P, L, W, 0, d_out, stream);
+}
+
+static int group_from_flags(unsigned flags) {
+    const unsigned v = (flags & NNDTW_DTW_GROUP_MASK) >> 8;
+    return v ? 1 << (v - 1) : 0;
+}
+
+int dtw_windowed_ex(const float *d_test, const float *d_train, const int32_t *d_pairs, int64_t P,
+                    int L, int W, unsigned flags, float *d_out, void *stream) {
     if (P < 0 || L < 1 || L > NNDTW_MAX_L || W < 0) return NNDTW_EINVAL;
     if (P == 0) return NNDTW_OK;
     if (!d_test || !d_train || !d_pairs || !d_out) return NNDTW_EINVAL;
+    if (!dtw32_supported(W > L - 1 ? L - 1 : W)) return NNDTW_EUNSUPPORTED;
     DtwJob32 j{};
     j.test = d_test; j.train = d_train; j.L = L; j.W = W > L - 1 ? L - 1 : W;
     j.pairs = reinterpret_cast<const uint2 *>(d_pairs);
     j.n_pairs = P;
     j.out = d_out;
+    j.group = group_from_flags(flags);
     const Margins m = make_margins(L);
     j.dtw_lo = m.dtw_lo; j.dtw_hi = m.dtw_hi; j.abs32 = m.abs32;
     j.head = nullptr;  // static assignment: pair count known here
@@ -484,6 +553,7 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
         !d_workspace)
         return NNDTW_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return NNDTW_EINVAL;
+    if (!dtw32_supported(W > L - 1 ? L - 1 : W)) return NNDTW_EUNSUPPORTED;
     const Layout32 ws = layout32(d_workspace, N, Q, L);
     if (workspace_bytes < ws.bytes) return NNDTW_ENOSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -492,6 +562,9 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     const int sms = device_sm_count();
     const int exact = (flags & NNDTW_EXACT_DIST) ? 1 : 0;
 
+    const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
+    StageTimer tm;
+    CK(tm.start(timing, s));
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
     CK(cudaMemsetAsync(ws.bsf, 0xff, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
@@ -515,28 +588,38 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
         CK(launch_envelopes<float>(d_train, N, L, Weff, ws.env, s));
         env = ws.env;
     }
-    // S2: safe bounds and the smallest-bound candidate per query
+    CK(tm.mark(1));
+    // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
     CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
                         ws.lb, ws.seed, s));
-    unsigned long long *cnt = stats ? ws.counters : nullptr;
+    CK(tm.mark(2));
+    unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     // S4 on the first candidate of every query: initial upper bounds
     DtwJob32 j{};
     j.test = d_test; j.train = d_train; j.L = L; j.W = Weff;
     j.dtw_lo = m.dtw_lo; j.dtw_hi = m.dtw_hi; j.abs32 = m.abs32;
     j.bsf = ws.bsf; j.cand = ws.cand; j.cand_count = ws.counters + C_CAND;
     j.counters = cnt;
+    j.group = group_from_flags(flags);
     j.pairs = nullptr; j.seed_keys = ws.seed; j.n_seed = Q; j.head = nullptr; j.abandon = 0;
+    // one pair per query: latency-bound, so spread each pair over the widest group
+    const int main_group = j.group;
+    j.group = dtw32_wide_group(Weff);
     CK(launch_dtw32(j, sms, s));
+    j.group = main_group;
+    CK(tm.mark(3));
     // S3: compaction against the upper bounds
     compact32_kernel<<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
         ws.lb, Q, N, ws.bsf, ws.seed, m.dtw_hi, m.abs32, (flags & NNDTW_NO_PRUNE) ? 1 : 0,
         ws.queue, ws.counters + C_QUEUE);
     CK(cudaGetLastError());
+    CK(tm.mark(4));
     // S4 on the survivors, with early abandoning
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
     j.head = ws.counters + C_HEAD;
     j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
     CK(launch_dtw32(j, sms, s));
+    CK(tm.mark(5));
     // S5: near-tie recheck in FP64 and the final argmin
     const long long cap = (long long)Q * N + Q;
     const unsigned gs = grid_small(cap);
@@ -555,15 +638,17 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     ties32_kernel<<<gs, kSmallThreads, 0, s>>>(ws.rlist, ws.counters + C_RECHECK, ws.d64,
                                                ws.best64, ws.bestidx);
     CK(cudaGetLastError());
+    CK(tm.mark(6));
     finalize32_kernel<<<grid_small(Q), kSmallThreads, 0, s>>>(
         Q, ws.bsf, ws.rcount, ws.best64, ws.bestidx, exact, d_train_labels, d_nn_idx, d_nn_label,
         d_nn_dist);
     CK(cudaGetLastError());
+    CK(tm.mark(7));
     if (stats) {
         unsigned long long h[C_COUNT];
         CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        fill_stats(stats, h, N, Q);
+        fill_stats(stats, h, N, Q, L, Weff, cnt != nullptr);
     }
     return NNDTW_OK;
 }
@@ -589,6 +674,9 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     const Margins m = make_margins(L);
     const int sms = device_sm_count();
 
+    const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
+    StageTimer tm;
+    CK(tm.start(timing, s));
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
     CK(cudaMemsetAsync(ws.bsf64, 0x7f, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
@@ -608,34 +696,42 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
         CK(launch_envelopes<double>(d_train, N, L, Weff, ws.env, s));
         env = ws.env;
     }
+    CK(tm.mark(1));
     CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
                          m.abs64, ws.lb, ws.seed, s));
+    CK(tm.mark(2));
+    unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     DtwJob64 j{};
     j.test = d_test; j.train = d_train; j.L = L; j.W = Weff;
     j.bsf64 = ws.bsf64; j.cand = ws.cand; j.cand_count = ws.counters + C_CAND;
-    j.counters = stats ? ws.counters : nullptr;
+    j.counters = cnt;
     j.pairs = nullptr; j.seed_keys = ws.seed; j.n_pairs = Q; j.head = nullptr; j.abandon = 0;
     CK(launch_dtw64(j, sms, s));
+    CK(tm.mark(3));
     compact64_kernel<<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
         ws.lb, Q, N, ws.bsf64, ws.seed, (flags & NNDTW_NO_PRUNE) ? 1 : 0, ws.queue,
         ws.counters + C_QUEUE);
     CK(cudaGetLastError());
+    CK(tm.mark(4));
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
     j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
     CK(launch_dtw64(j, sms, s));
+    CK(tm.mark(5));
     const long long cap = (long long)Q * N + Q;
     ties64_kernel<<<grid_small(cap), kSmallThreads, 0, s>>>(ws.cand, ws.counters + C_CAND,
                                                             ws.bsf64, ws.bestidx);
     CK(cudaGetLastError());
+    CK(tm.mark(6));
     finalize64_kernel<<<grid_small(Q), kSmallThreads, 0, s>>>(Q, ws.bsf64, ws.bestidx,
                                                               d_train_labels, d_nn_idx,
                                                               d_nn_label, d_nn_dist);
     CK(cudaGetLastError());
+    CK(tm.mark(7));
     if (stats) {
         unsigned long long h[C_COUNT];
         CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        fill_stats(stats, h, N, Q);
+        fill_stats(stats, h, N, Q, L, Weff, cnt != nullptr);
     }
     return NNDTW_OK;
 }

@@ -27,6 +27,15 @@ EXACT_DIST = 1 << 2
 NO_PRUNE = 1 << 3
 NO_ABANDON = 1 << 4
 CHECK_FINITE = 1 << 5
+TIME_STAGES = 1 << 6
+
+
+def DTW_GROUP(g: int) -> int:
+    """Flag selecting G lanes per pair in the FP32 DTW kernel (G = 1..32)."""
+    if g < 1 or g > 32 or g & (g - 1):
+        raise ValueError("G must be a power of two in 1..32")
+    return (g.bit_length()) << 8
+STAGES = ("envelopes", "lb", "seed", "compact", "dtw", "recheck", "final", "total")
 
 _lib = None
 _lock = threading.Lock()
@@ -57,10 +66,10 @@ class Stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("lb_pruned", ctypes.c_int64),
                 ("dtw_started", ctypes.c_int64), ("dtw_abandoned", ctypes.c_int64),
                 ("dtw_cells", ctypes.c_int64), ("rechecked", ctypes.c_int64),
-                ("recheck_queries", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+                ("recheck_queries", ctypes.c_int64), ("seed_cells", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 def _declare(lib):
@@ -70,6 +79,7 @@ def _declare(lib):
         "lb_enhanced": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
         "lb_enhanced_f64": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
         "dtw_windowed": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
+        "dtw_windowed_ex": [_vp, _vp, _vp, _i64, _int, _int, _uint, _vp, _vp],
         "dtw_windowed_f64": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
         "nn_dtw_search": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _uint, _vp, _vp, _vp,
                           _vp, _sz, _vp, _vp],
@@ -92,6 +102,12 @@ def _declare(lib):
     lib.nn_dtw_last_cuda_error.restype = ctypes.c_char_p
     lib.nn_dtw_version.argtypes = []
     lib.nn_dtw_version.restype = _int
+    lib.nn_dtw_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    lib.nn_dtw_stage_times.restype = _int
+    lib.nn_dtw_probe_sink_bytes.argtypes = []
+    lib.nn_dtw_probe_sink_bytes.restype = _sz
+    lib.nn_dtw_probe_cell_rate.argtypes = [_vp, _sz, _int, ctypes.POINTER(ctypes.c_double), _vp]
+    lib.nn_dtw_probe_cell_rate.restype = _int
     return lib
 
 
@@ -173,7 +189,7 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
     return out
 
 
-def dtw_windowed(test, train, pairs, W: int, out=None, stream=None):
+def dtw_windowed(test, train, pairs, W: int, out=None, stream=None, flags: int = 0):
     """DTW_W for explicit (q, t) pairs (int32 tensor [P, 2]): tensor [P]."""
     import torch
     lib = load()
@@ -182,10 +198,13 @@ def dtw_windowed(test, train, pairs, W: int, out=None, stream=None):
     P = pairs.shape[0]
     if out is None:
         out = torch.empty((P,), dtype=test.dtype, device=test.device)
-    fn = lib.dtw_windowed_f64 if f64 else lib.dtw_windowed
-    _check(fn(_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", 2),
-              _dev(pairs, torch.int32, "pairs", 2), P, L, int(W),
-              _dev(out, test.dtype, "out"), _stream(stream)), "dtw_windowed")
+    args = (_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", 2),
+            _dev(pairs, torch.int32, "pairs", 2), P, L, int(W))
+    tail = (_dev(out, test.dtype, "out"), _stream(stream))
+    if f64:
+        _check(lib.dtw_windowed_f64(*args, *tail), "dtw_windowed_f64")
+    else:
+        _check(lib.dtw_windowed_ex(*args, int(flags), *tail), "dtw_windowed")
     return out
 
 
@@ -271,6 +290,26 @@ def nn_dtw_search_host(train, labels, test, W: int, V: int, flags: int = 0, buff
         _host(dist, np.float64, "nn_dist"), _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
         ctypes.byref(st) if st is not None else None, _stream(stream)), "nn_dtw_search_host")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
+
+
+def nn_dtw_stage_times() -> dict:
+    """Stage times (ms) of this thread's last search run with TIME_STAGES."""
+    lib = load()
+    buf = (ctypes.c_float * 8)()
+    _check(lib.nn_dtw_stage_times(buf), "nn_dtw_stage_times")
+    return {name: float(buf[i]) for i, name in enumerate(STAGES)}
+
+
+def nn_dtw_probe_cell_rate(iters: int = 20000, stream=None) -> float:
+    """Measured FP32 DTW cell-update rate of the whole GPU (cells/s), no memory."""
+    import torch
+    lib = load()
+    n = int(lib.nn_dtw_probe_sink_bytes())
+    sink = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    _check(lib.nn_dtw_probe_cell_rate(_dev(sink, torch.uint8, "sink"), n, int(iters),
+                                      ctypes.byref(out), _stream(stream)), "nn_dtw_probe_cell_rate")
+    return float(out.value)
 
 
 def nn_dtw_strerror(code: int) -> str:

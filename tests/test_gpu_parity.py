@@ -257,3 +257,34 @@ def test_search_precision_workload_sampled(lib, orc, W_ratio):
     np.testing.assert_array_equal(idx[sample], ri)
     np.testing.assert_array_equal(lab[sample], rl)
     np.testing.assert_allclose(dist[sample], rd, rtol=RTOL32, atol=0)
+
+
+@pytest.mark.parametrize("L,W", [(300, 26), (257, 63), (600, 200), (1024, 511), (64, 3), (90, 89)])
+def test_dtw_every_group_width_same_values(lib, orc, L, W):
+    """Every admissible lanes-per-pair choice computes the same DTW values."""
+    test = _series(777 + L, 6, L)
+    train = _series(778 + W, 11, L)
+    rng = np.random.default_rng(W)
+    pairs = np.stack([rng.integers(0, 6, 40), rng.integers(0, 11, 40)], 1).astype(np.int32)
+    ref = orc.dtw_pairs(test, train, W, pairs=pairs)
+    for g in (1, 2, 4, 8, 16, 32):
+        got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W,
+                               flags=lib.DTW_GROUP(g)).cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0, err_msg=f"G={g}")
+
+
+@pytest.mark.parametrize("g", [1, 2, 4, 8])
+def test_search_group_override(lib, orc, g):
+    ds = synth.make_pairs(5)
+    brute = orc.nn_brute(ds.train[:200], ds.train_labels[:200], ds.test[:100], ds.W)
+    _check_search(lib, orc, ds.train[:200], ds.train_labels[:200], ds.test[:100], ds.W, 5,
+                  flags=lib.DTW_GROUP(g), brute=brute)
+
+
+def test_unsupported_window_reports(lib):
+    """Windows wider than the FP32 kernel's 2048 diagonals are reported, not run."""
+    train = _t(_series(31, 4, 2048))
+    test = _t(_series(32, 2, 2048))
+    with pytest.raises(lib.NnDtwError) as e:
+        lib.nn_dtw_search(train, _t(np.zeros(4, np.int32)), test, 1500, 5)
+    assert e.value.code == lib.EUNSUPPORTED
