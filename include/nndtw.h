@@ -183,6 +183,36 @@ NNDTW_API int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_la
                       int32_t *d_nn_label, double *d_nn_dist, void *d_workspace,
                       size_t workspace_bytes, nndtw_stats *stats, void *stream);
 
+/*
+ * nn_dtw_search without a workspace argument: the search's scratch memory is
+ * a fixed array of NNDTW_NOALLOC_SCRATCH_BYTES inside the library, so the call
+ * allocates nothing.  It is meant for callers that cannot allocate device
+ * memory themselves: for example code running next to another framework
+ * whose caching allocator owns (or has reserved) all device memory, or code
+ * on a latency-critical path that must not call cudaMalloc, which can
+ * synchronize the device.  The paper has no counterpart to this entry point.
+ *  - Limit: sizes for which nn_dtw_workspace_size(N, Q, L, W, V, 0) exceeds
+ *    NNDTW_NOALLOC_SCRATCH_BYTES (16 MiB: e.g. 500 x 500 series of length 256
+ *    fit) are rejected with NNDTW_ENOSPACE before any work is enqueued.
+ *  - The array is part of the library's device image: every GPU that loads
+ *    the library holds those 16 MiB until the process exits.
+ *  - The first call on a device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array.  Each call clears what must start at
+ *    zero, so an earlier call's leftovers do no harm, but calls whose GPU
+ *    work overlaps (on different streams or from different host threads on
+ *    the same device) race on the array and give wrong results: order them.
+ *  - NNDTW_TIME_STAGES is ignored.  Otherwise inputs, outputs, results,
+ *    errors and stats are those of nn_dtw_search.
+ */
+#define NNDTW_NOALLOC_SCRATCH_BYTES (16u << 20)
+NNDTW_API int nn_dtw_search_noalloc(const float *d_train, const int32_t *d_train_labels,
+                                    int64_t N, const float *d_test, int64_t Q, int L, int W,
+                                    int V, const float *d_env, unsigned flags,
+                                    int32_t *d_nn_idx, int32_t *d_nn_label, double *d_nn_dist,
+                                    nndtw_stats *stats, void *stream);
+
 /* Bytes of device memory nn_dtw_search_host needs (inputs, outputs and the
  * search workspace). 0 on invalid sizes. */
 NNDTW_API size_t nn_dtw_host_buffer_size(int64_t N, int64_t Q, int L, int W, int V);

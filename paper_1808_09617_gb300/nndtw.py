@@ -87,6 +87,8 @@ def _declare(lib):
                               _vp, _vp, _sz, _vp, _vp],
         "nn_dtw_search_host": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _uint, _vp, _vp, _vp,
                                _vp, _sz, _vp, _vp],
+        "nn_dtw_search_noalloc": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _uint, _vp,
+                                  _vp, _vp, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -247,6 +249,32 @@ def nn_dtw_search(train, labels, test, W: int, V: int, env=None, flags: int = 0,
               _dev(dist, torch.float64, "nn_dist"), _dev(workspace, torch.uint8, "workspace"),
               workspace.numel(), ctypes.byref(st) if st is not None else None, _stream(stream)),
            "nn_dtw_search")
+    return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
+
+
+def nn_dtw_search_noalloc(train, labels, test, W: int, V: int, env=None, flags: int = 0,
+                          out=None, stats: bool = False, stream=None) -> SearchResult:
+    """The FP32 search with the library's fixed scratch array: no device memory
+    is allocated for scratch (see include/nndtw.h; at most
+    NNDTW_NOALLOC_SCRATCH_BYTES of workspace).  Outputs are the caller's
+    (allocated here only when ``out`` is not given)."""
+    import torch
+    lib = load()
+    N, L = train.shape
+    Q = test.shape[0]
+    if out is None:
+        out = (torch.empty((Q,), dtype=torch.int32, device=train.device),
+               torch.empty((Q,), dtype=torch.int32, device=train.device),
+               torch.empty((Q,), dtype=torch.float64, device=train.device))
+    idx, lab, dist = out
+    st = Stats() if stats else None
+    envp = _dev(env, torch.float32, "env") if env is not None else None
+    _check(lib.nn_dtw_search_noalloc(
+        _dev(train, torch.float32, "train", 2), _dev(labels, torch.int32, "labels", 1), N,
+        _dev(test, torch.float32, "test", 2), Q, L, int(W), int(V), envp, int(flags),
+        _dev(idx, torch.int32, "nn_idx"), _dev(lab, torch.int32, "nn_label"),
+        _dev(dist, torch.float64, "nn_dist"), ctypes.byref(st) if st is not None else None,
+        _stream(stream)), "nn_dtw_search_noalloc")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
 
