@@ -213,6 +213,44 @@ NNDTW_API int nn_dtw_search_noalloc(const float *d_train, const int32_t *d_train
                                     int32_t *d_nn_idx, int32_t *d_nn_label, double *d_nn_dist,
                                     nndtw_stats *stats, void *stream);
 
+/*
+ * One dataset of a batched search: the arguments of nn_dtw_search for one
+ * training set / test set pair.  Device pointers as in nn_dtw_search.
+ */
+typedef struct nndtw_dataset {
+    const float *d_train;          /* [N][L]                                   */
+    const int32_t *d_train_labels; /* [N]                                      */
+    int64_t N;
+    const float *d_test;           /* [Q][L]                                   */
+    int64_t Q;
+    int L, W, V;
+    const float *d_env;            /* [N][L][2] envelopes for W, or NULL      */
+    int32_t *d_nn_idx;             /* [Q] outputs                              */
+    int32_t *d_nn_label;
+    double *d_nn_dist;
+    unsigned flags;                /* per-dataset flags, OR-ed with the call's */
+} nndtw_dataset;
+
+/* Bytes of device workspace nn_dtw_search_batched needs for these datasets
+ * (host array of n descriptors).  0 if any dataset has invalid sizes. */
+NNDTW_API size_t nn_dtw_batch_workspace_size(const nndtw_dataset *h_sets, int n);
+
+/*
+ * Batched search (the paper's NN-DTW search, Sec. 4, over many independent
+ * datasets at once): exactly the results of n separate nn_dtw_search calls.
+ * The call records work on the caller's stream that forks onto the library's
+ * internal streams (created once per device on first use), runs each
+ * dataset's search there, largest first, and joins back into the caller's
+ * stream, so datasets overlap on the GPU and the whole batch can be captured
+ * as one CUDA graph.  h_sets: host array of n descriptors (read during the
+ * call only); d_workspace: nn_dtw_batch_workspace_size() bytes, 256-byte
+ * aligned.  flags apply to every dataset (NNDTW_TIME_STAGES is rejected).
+ * Errors: NNDTW_EINVAL for invalid descriptors or sizes, NNDTW_ENOSPACE,
+ * NNDTW_ECUDA.  On an error every forked stream is still joined.
+ */
+NNDTW_API int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
+                                    size_t workspace_bytes, unsigned flags, void *stream);
+
 /* Bytes of device memory nn_dtw_search_host needs (inputs, outputs and the
  * search workspace). 0 on invalid sizes. */
 NNDTW_API size_t nn_dtw_host_buffer_size(int64_t N, int64_t Q, int L, int W, int V);

@@ -57,14 +57,13 @@ int dtw32_wide_group(int W) {
     return 0;
 }
 
-bool dtw32_supported(int W) {
-    int G, H;
-    return dtw32_shape(W, 0, &G, &H);
-}
+// Windows up to 1023 use the register kernel; wider ones (up to L-1 with
+// L <= NNDTW_MAX_L) the shared-memory band kernel.
+bool dtw32_supported(int W) { return W >= 0 && W < NNDTW_MAX_L; }
 
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
     int G = 0, H = 0;
-    if (!dtw32_shape(job.W, job.group, &G, &H)) return cudaErrorNotSupported;
+    if (!dtw32_shape(job.W, job.group, &G, &H)) return launch_dtw32_wide(job, sm_count, s);
     Dtw32Fn fn = pick_fn(H);
     if (!fn) return cudaErrorNotSupported;
     int dev = 0;

@@ -115,6 +115,7 @@ struct DtwJob32 {
     int group;                          // lanes per pair (0: library's choice)
 };
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
+cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s);
 bool dtw32_supported(int W);   // window W (<= L-1) fits the FP32 DTW kernel
 int dtw32_wide_group(int W);   // widest lanes-per-pair choice for W (latency-bound passes)
 

@@ -72,6 +72,14 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class DatasetDesc(ctypes.Structure):
+    """Mirror of nndtw_dataset."""
+    _fields_ = [("d_train", _vp), ("d_train_labels", _vp), ("N", ctypes.c_int64),
+                ("d_test", _vp), ("Q", ctypes.c_int64), ("L", ctypes.c_int), ("W", ctypes.c_int),
+                ("V", ctypes.c_int), ("d_env", _vp), ("d_nn_idx", _vp), ("d_nn_label", _vp),
+                ("d_nn_dist", _vp), ("flags", ctypes.c_uint)]
+
+
 def _declare(lib):
     sig = {
         "nn_dtw_build_envelopes": [_vp, _i64, _int, _int, _vp, _vp],
@@ -104,6 +112,10 @@ def _declare(lib):
     lib.nn_dtw_last_cuda_error.restype = ctypes.c_char_p
     lib.nn_dtw_version.argtypes = []
     lib.nn_dtw_version.restype = _int
+    lib.nn_dtw_batch_workspace_size.argtypes = [ctypes.POINTER(DatasetDesc), _int]
+    lib.nn_dtw_batch_workspace_size.restype = _sz
+    lib.nn_dtw_search_batched.argtypes = [ctypes.POINTER(DatasetDesc), _int, _vp, _sz, _uint, _vp]
+    lib.nn_dtw_search_batched.restype = _int
     lib.nn_dtw_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float)]
     lib.nn_dtw_stage_times.restype = _int
     lib.nn_dtw_probe_sink_bytes.argtypes = []
@@ -283,6 +295,97 @@ def nn_dtw_search_f64(train, labels, test, W: int, V: int, **kw) -> SearchResult
     if train.dtype != torch.float64:
         raise TypeError("nn_dtw_search_f64 takes float64 tensors")
     return nn_dtw_search(train, labels, test, W, V, **kw)
+
+
+def _descs(sets, outs):
+    import torch
+    arr = (DatasetDesc * len(sets))()
+    for i, (d, o) in enumerate(zip(sets, outs)):
+        train, test = d["train"], d["test"]
+        N, L = train.shape
+        env = d.get("env")
+        arr[i] = DatasetDesc(
+            _dev(train, torch.float32, "train", 2), _dev(d["labels"], torch.int32, "labels", 1), N,
+            _dev(test, torch.float32, "test", 2), test.shape[0], L, int(d["W"]), int(d["V"]),
+            _dev(env, torch.float32, "env") if env is not None else None,
+            _dev(o[0], torch.int32, "nn_idx"), _dev(o[1], torch.int32, "nn_label"),
+            _dev(o[2], torch.float64, "nn_dist"), int(d.get("flags", 0)))
+    return arr
+
+
+def nn_dtw_batch_workspace_size(sets) -> int:
+    import torch
+    dummy = [(torch.empty(0, dtype=torch.int32, device="cuda"),) * 2 +
+             (torch.empty(0, dtype=torch.float64, device="cuda"),) for _ in sets]
+    arr = _descs(sets, dummy)
+    return int(load().nn_dtw_batch_workspace_size(arr, len(sets)))
+
+
+def nn_dtw_search_batched(sets, workspace=None, outs=None, flags: int = 0, stream=None):
+    """Search many datasets in one call.  ``sets``: list of dicts with keys
+    train, labels, test, W, V (and optional env, flags).  Returns one
+    SearchResult per dataset."""
+    import torch
+    lib = load()
+    if outs is None:
+        outs = [(torch.empty(d["test"].shape[0], dtype=torch.int32, device=d["test"].device),
+                 torch.empty(d["test"].shape[0], dtype=torch.int32, device=d["test"].device),
+                 torch.empty(d["test"].shape[0], dtype=torch.float64, device=d["test"].device))
+                for d in sets]
+    arr = _descs(sets, outs)
+    need = lib.nn_dtw_batch_workspace_size(arr, len(sets))
+    if need == 0:
+        raise NnDtwError(EINVAL, "nn_dtw_batch_workspace_size")
+    if workspace is None:
+        workspace = torch.empty((need,), dtype=torch.uint8, device="cuda")
+    _check(lib.nn_dtw_search_batched(arr, len(sets), _dev(workspace, torch.uint8, "workspace"),
+                                     workspace.numel(), int(flags), _stream(stream)),
+           "nn_dtw_search_batched")
+    return [SearchResult(*o) for o in outs]
+
+
+class BatchedSearch:
+    """A batch of datasets searched by one CUDA graph launch.
+
+    Allocates the outputs and the workspace once, runs the batch eagerly once
+    (which also performs the library's one-time set-up outside the capture),
+    captures one nn_dtw_search_batched call into a CUDA graph and replays it on
+    ``run()``.  Inputs are read from the same tensors at every replay.
+    """
+
+    def __init__(self, sets, flags: int = 0, graph: bool = True):
+        import torch
+        self.sets = sets
+        self.flags = flags
+        self.outs = [(torch.empty(d["test"].shape[0], dtype=torch.int32, device="cuda"),
+                      torch.empty(d["test"].shape[0], dtype=torch.int32, device="cuda"),
+                      torch.empty(d["test"].shape[0], dtype=torch.float64, device="cuda"))
+                     for d in sets]
+        self.workspace = torch.empty((nn_dtw_batch_workspace_size(sets),), dtype=torch.uint8,
+                                     device="cuda")
+        self._call()
+        torch.cuda.synchronize()
+        self.graph = None
+        if graph:
+            self.graph = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(self.graph, stream=s):
+                    self._call()
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+
+    def _call(self):
+        return nn_dtw_search_batched(self.sets, workspace=self.workspace, outs=self.outs,
+                                     flags=self.flags)
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._call()
+        return [SearchResult(*o) for o in self.outs]
 
 
 def nn_dtw_host_buffer_size(N: int, Q: int, L: int, W: int, V: int) -> int:

@@ -100,7 +100,8 @@ def test_lb_never_exceeds_dtw(lib, orc):
 DTW_CASES = [(2, 0), (2, 1), (3, 1), (3, 2), (40, 0), (40, 1), (64, 13), (256, 26), (256, 31),
              (256, 32), (256, 63), (300, 64), (300, 127), (600, 128), (600, 255), (1000, 256),
              (1024, 511), (1024, 512), (1024, 1023), (2048, 1023), (777, 776), (50, 49),
-             (4096, 409), (129, 64), (128, 127)]
+             (4096, 409), (129, 64), (128, 127), (2048, 1024), (2048, 2047), (1500, 1200),
+             (4096, 4095)]
 
 
 @pytest.mark.parametrize("L,W", DTW_CASES)
@@ -281,10 +282,12 @@ def test_search_group_override(lib, orc, g):
                   flags=lib.DTW_GROUP(g), brute=brute)
 
 
-def test_unsupported_window_reports(lib):
-    """Windows wider than the FP32 kernel's 2048 diagonals are reported, not run."""
-    train = _t(_series(31, 4, 2048))
-    test = _t(_series(32, 2, 2048))
-    with pytest.raises(lib.NnDtwError) as e:
-        lib.nn_dtw_search(train, _t(np.zeros(4, np.int32)), test, 1500, 5)
-    assert e.value.code == lib.EUNSUPPORTED
+@pytest.mark.parametrize("N,Q,L,W", [(12, 5, 2048, 1500), (9, 4, 1100, 1099), (7, 3, 2048, 1024)])
+def test_search_wide_windows(lib, orc, N, Q, L, W):
+    """Windows beyond the register kernel (W >= 1024) use the shared-memory band kernel."""
+    train = _series(31 + L, N, L)
+    test = _series(32 + W, Q, L)
+    labels = np.arange(N, dtype=np.int32) % 3
+    brute = orc.nn_brute(train, labels, test, W)
+    _check_search(lib, orc, train, labels, test, W, 5, brute=brute)
+    _check_search(lib, orc, train, labels, test, W, 5, flags=lib.EXACT_DIST, brute=brute)
