@@ -219,6 +219,120 @@ def run_reference(args, ds, desc):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+
+def run_serving(args):
+    """Serving form: 16 resident training sets, Poisson query streams at
+    several rates, continuous batching across sets; p50/p99 latency and
+    sustained queries/s per rate.  Queries cycle through a pool of 1,024
+    pre-drawn series per set (drawing them at 50k/s would dominate)."""
+    import threading
+    import torch
+    from paper_1808_09617_gb300 import serving, synth
+    specs = synth.serving_specs(16)
+    sets = {}
+    for d, sp in enumerate(specs):
+        ds = synth.make_serving_set(d, sp)
+        sets[d] = (ds.train, ds.train_labels, sp["W"], sp["V"])
+    pools = {d: synth.serving_queries(d, specs[d], 1024)[0] for d in sets}
+    srv = serving.Server(sets, n_slots=args.serve_slots, max_batch=args.serve_batch)
+    rng = np.random.default_rng(7)
+    results = []
+    try:
+        # warm-up: one batch per set
+        fs = [srv.submit(pools[d][0], d) for d in sets]
+        [f.result() for f in fs]
+        for rate in args.serve_rates:
+            srv.latencies.clear()
+            srv.completed = 0
+            srv.t_first = srv.t_last = None
+            srv.batches = 0
+            times = synth.arrival_times(rate, args.serve_seconds, seed_index=int(rate))
+            which = rng.integers(0, len(sets), size=times.size)
+            t0 = time.perf_counter() + 0.05
+            futs = []
+            for k, (t, d) in enumerate(zip(times, which)):
+                target = t0 + t
+                while True:
+                    now = time.perf_counter()
+                    if now >= target:
+                        break
+                    if target - now > 2e-4:
+                        time.sleep(target - now - 1e-4)
+                futs.append(srv.submit(pools[int(d)][k % 1024], int(d), t_arrival=target))
+            for f in futs:
+                f.result()
+            st = srv.latency_stats()
+            st.update({"offered_qps": rate, "queries": int(times.size)})
+            results.append(st)
+    finally:
+        srv.close()
+    line = {"metric": "serving: p50/p99 latency and sustained queries/s, continuous batching",
+            "unit": "queries/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "impl": "ours",
+            "config": {"workload": "16 resident sets, L in {128, 512, 1500}, N log-uniform "
+                                   "[1000, 20000], W=0.1 L, V=5; Poisson arrivals, set "
+                                   "uniform per query", "slots": args.serve_slots,
+                       "max_batch": args.serve_batch, "seconds_per_rate": args.serve_seconds},
+            "rates": results}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ batched
+
+def run_batched(args):
+    """Batching form: the 64 heterogeneous datasets searched by one CUDA-graph
+    launch (FP32 with FP64 recheck), against the plain FP64 form run one
+    dataset per call."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw, synth
+    nndtw.load()
+    dsets = synth.make_batched(64)
+    dev = torch.device("cuda")
+    sets = [dict(train=torch.from_numpy(d.train).to(dev), labels=torch.from_numpy(d.train_labels).to(dev),
+                 test=torch.from_numpy(d.test).to(dev), W=d.W, V=d.V) for d in dsets]
+    Qtot = sum(d.Q for d in dsets)
+    cells = sum(d.Q * d.N * band_cells(d.L, d.W) for d in dsets)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    bs = nndtw.BatchedSearch(sets, graph=True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        bs.run()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record()
+        bs.run()
+        b.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    # plain FP64 form, one dataset per call, same data promoted
+    t64 = [(s["train"].double(), s["test"].double()) for s in sets]
+    torch.cuda.synchronize()
+    e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e1.record()
+    for (tr, te), s in zip(t64, sets):
+        nndtw.nn_dtw_search(tr, s["labels"], te, s["W"], s["V"])
+    e2.record()
+    torch.cuda.synchronize()
+    ms64 = e1.elapsed_time(e2)
+    line = {"metric": "batched: exact NN-DTW queries/s, 64 heterogeneous datasets, one CUDA-graph "
+                      "launch (FP32 + FP64 recheck) vs plain FP64 form one dataset per call",
+            "value": Qtot / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": "64 datasets: L log-uniform [24, 2048], N log-uniform "
+                                   "[16, 8000], Q = N/2, W in {0,.05,.1,.2,.5,1} L, V in 1..8",
+                       "queries": Qtot, "l2": "flushed before every step"},
+            "gcups_effective": cells / (ms * 1e-3) / 1e9,
+            "fp64_plain": {"ms_per_batch": ms64, "value": Qtot / (ms64 / 1e3),
+                           "fp32_batched_over_fp64_plain": ms64 / ms}}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -230,6 +344,11 @@ def main():
     ap.add_argument("--workload", default="pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--serve-rates", type=float, nargs="*",
+                    default=[1000, 5000, 10000, 20000, 50000])
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=512)
     ap.add_argument("--dtw-group", type=int, default=-1,
                     help="lanes per pair in the FP32 DTW kernel (-1: autotune, 0: library "
                          "default, else G)")
@@ -241,6 +360,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            run_batched(args)
+        return
     ds, desc = workload(args.workload)
     if args.impl == "reference":
         if rank == 0:

@@ -1,0 +1,241 @@
+"""Continuous-batching NN-DTW server over resident training sets.
+
+Training sets (and their envelopes, built once on the device) stay resident.
+Queries arrive one at a time (``submit``) for any of the sets.  A scheduler
+thread keeps up to ``n_slots`` batches in flight, each on its own CUDA stream:
+whenever a slot is free it takes the dataset whose oldest waiting query has
+waited longest, admits as many of that dataset's waiting queries as fit both
+``max_batch`` and the device-memory budget (the batch's search workspace,
+query and result buffers), copies them to the device and launches
+``nn_dtw_search`` on the slot's stream.  Batches on different slots overlap on
+the GPU; queries that arrive while others run are admitted as soon as a slot
+and memory free up.  Completed batches are detected by CUDA events, their
+results copied back and the futures resolved.  A query's result does not
+depend on which batch it joins (the search is exact per query).
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import nndtw
+
+
+@dataclass(eq=False)
+class _Set:
+    train: object
+    labels: object
+    env: object
+    L: int
+    W: int
+    V: int
+    N: int
+    flags: int = 0
+
+
+@dataclass(eq=False)
+class _Req:
+    query: np.ndarray
+    set_id: int
+    future: Future
+    t_arrival: float
+
+
+@dataclass(eq=False)
+class _Batch:
+    set_id: int
+    reqs: list
+    stream: object
+    event: object
+    out: tuple
+    host_out: tuple
+    nbytes: int
+    t_launch: float
+    keep: list = field(default_factory=list)
+
+
+class Server:
+    def __init__(self, sets: dict, n_slots: int = 4, max_batch: int = 512,
+                 memory_budget: int = 8 << 30, device: str = "cuda", tune: bool = True):
+        """``sets``: {set_id: (train float32 [N, L], labels int32 [N], W, V)}."""
+        import torch
+        self.torch = torch
+        dev = torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+        self.sets: dict[int, _Set] = {}
+        for sid, (train, labels, W, V) in sets.items():
+            t = torch.from_numpy(np.ascontiguousarray(train, dtype=np.float32)).to(self.dev)
+            lab = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.int32)).to(self.dev)
+            env = nndtw.nn_dtw_build_envelopes(t, int(W))
+            self.sets[sid] = _Set(t, lab, env, t.shape[1], int(W), int(V), t.shape[0])
+        torch.cuda.synchronize(self.dev)
+        self.n_slots = n_slots
+        self.max_batch = max_batch
+        self.budget = memory_budget
+        self.in_use = 0
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(n_slots)]
+        self.free_slots = list(range(n_slots))
+        self.pending: dict[int, collections.deque] = {sid: collections.deque() for sid in self.sets}
+        self.inflight: list[_Batch] = []
+        self.lock = threading.Lock()
+        self.wake = threading.Event()
+        self.running = True
+        self.latencies: list[float] = []
+        self.completed = 0
+        self.batches = 0
+        self.t_first = None
+        self.t_last = None
+        if tune:
+            self._tune()
+        self.thread = threading.Thread(target=self._loop, name="nndtw-server", daemon=True)
+        self.thread.start()
+
+    # ------------------------------------------------------------- public API
+    def submit(self, query, set_id: int, t_arrival: float | None = None) -> Future:
+        """Queue one query (float32 [L]) for training set ``set_id``; the future
+        resolves to (nn_index, nn_label, nn_dist)."""
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        if set_id not in self.sets or q.shape != (self.sets[set_id].L,):
+            raise ValueError("query shape does not match the training set")
+        f: Future = Future()
+        r = _Req(q, set_id, f, time.perf_counter() if t_arrival is None else t_arrival)
+        with self.lock:
+            if not self.thread.is_alive() and self.running is False:
+                raise RuntimeError("server is closed")
+            self.pending[set_id].append(r)
+            if self.t_first is None:
+                self.t_first = r.t_arrival
+        self.wake.set()
+        return f
+
+    def close(self):
+        self.running = False
+        self.wake.set()
+        self.thread.join()
+
+    def latency_stats(self) -> dict:
+        with self.lock:
+            lat = np.array(self.latencies)
+            n = self.completed
+            span = (self.t_last - self.t_first) if (self.t_first and self.t_last) else 0.0
+        if lat.size == 0:
+            return {"completed": 0}
+        return {"completed": n, "batches": self.batches,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3),
+                "throughput_qps": n / span if span > 0 else None}
+
+    # --------------------------------------------------------------- internals
+    def _tune(self):
+        """Pick the DTW lanes-per-pair per set on a sample batch of its own series."""
+        from . import autotune
+        for s in self.sets.values():
+            q = s.train[: min(64, s.N)]
+            g = autotune.tune_search(s.train, s.labels, q, s.W, s.V, reps=2)
+            s.flags = nndtw.DTW_GROUP(g) if g else 0
+
+    def _batch_bytes(self, s: _Set, Q: int) -> int:
+        return (nndtw.nn_dtw_workspace_size(s.N, Q, s.L, s.W, s.V) + Q * s.L * 4 + Q * 16 + 4096)
+
+    def _pick(self):
+        """Dataset whose oldest waiting query is oldest, and how many fit."""
+        best, t_best = None, None
+        for sid, dq in self.pending.items():
+            if dq and (t_best is None or dq[0].t_arrival < t_best):
+                best, t_best = sid, dq[0].t_arrival
+        if best is None:
+            return None, 0
+        s = self.sets[best]
+        n = min(len(self.pending[best]), self.max_batch)
+        while n > 0 and self.in_use + self._batch_bytes(s, n) > self.budget:
+            n //= 2
+        return best, n
+
+    def _launch(self, slot: int, sid: int, n: int):
+        torch = self.torch
+        s = self.sets[sid]
+        reqs = [self.pending[sid].popleft() for _ in range(n)]
+        nbytes = self._batch_bytes(s, n)
+        self.in_use += nbytes
+        stream = self.streams[slot]
+        host_q = torch.from_numpy(np.stack([r.query for r in reqs])).pin_memory()
+        with torch.cuda.stream(stream):
+            dq = host_q.to(self.dev, non_blocking=True)
+            ws = torch.empty(nndtw.nn_dtw_workspace_size(s.N, n, s.L, s.W, s.V),
+                             dtype=torch.uint8, device=self.dev)
+            out = (torch.empty(n, dtype=torch.int32, device=self.dev),
+                   torch.empty(n, dtype=torch.int32, device=self.dev),
+                   torch.empty(n, dtype=torch.float64, device=self.dev))
+            nndtw.nn_dtw_search(s.train, s.labels, dq, s.W, s.V, env=s.env, flags=s.flags,
+                                workspace=ws, out=out, stream=stream)
+            host_out = tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in out)
+            for h, o in zip(host_out, out):
+                h.copy_(o, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.inflight.append(_Batch(sid, reqs, stream, ev, out, host_out, nbytes,
+                                    time.perf_counter(), keep=[host_q, dq, ws]))
+        self.batches += 1
+
+    def _retire(self, b: _Batch, slot: int):
+        idx, lab, dist = (h.numpy() for h in b.host_out)
+        now = time.perf_counter()
+        for k, r in enumerate(b.reqs):
+            r.future.set_result((int(idx[k]), int(lab[k]), float(dist[k])))
+            self.latencies.append(now - r.t_arrival)
+        self.completed += len(b.reqs)
+        self.t_last = now
+        self.in_use -= b.nbytes
+        self.free_slots.append(slot)
+
+    def _loop(self):
+        try:
+            self._run()
+        except BaseException as e:  # fail every outstanding request rather than hang
+            with self.lock:
+                self.running = False
+                for b in self.inflight:
+                    for r in b.reqs:
+                        if not r.future.done():
+                            r.future.set_exception(e)
+                self.inflight.clear()
+                for dq in self.pending.values():
+                    while dq:
+                        r = dq.popleft()
+                        if not r.future.done():
+                            r.future.set_exception(e)
+            raise
+
+    def _run(self):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        while self.running or self.inflight or any(self.pending.values()):
+            progressed = False
+            with self.lock:
+                # retire finished batches
+                for b in list(self.inflight):
+                    if b.event.query():
+                        self.inflight.remove(b)
+                        self._retire(b, self.streams.index(b.stream))
+                        progressed = True
+                # admit new batches into free slots
+                while self.free_slots:
+                    sid, n = self._pick()
+                    if sid is None or n == 0:
+                        break
+                    self._launch(self.free_slots.pop(), sid, n)
+                    progressed = True
+            if not progressed:
+                if self.inflight:
+                    time.sleep(5e-5)
+                else:
+                    self.wake.wait(0.01)
+                    self.wake.clear()
