@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the exact NN-DTW search with LB_Enhanced^V pruning.
 
-One step = one full pass of the hot path over one batch: envelopes of the
-training set, LB_Enhanced^V of every query x train pair, compaction, DTW with
-early abandoning, FP64 recheck of near ties, argmin and labels (a single
-``nn_dtw_search`` call).  Default workload: train 500 x test 500 series,
-L=256, W=26 (0.1 L), V=5, seeded synthetic random-walk-plus-class-shape data.
-
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|pairs|tiny|precision-R|serving]
+
+Default workload ("batched"): 64 seeded synthetic datasets of uneven shape
+(L log-uniform in [24, 2048], train size log-uniform in [16, 8000], test size
+half of it, W in {0, .05, .1, .2, .5, 1} L, V in 1..8), searched by ONE CUDA
+graph launch of ``nn_dtw_search_batched`` (FP32 bulk with FP64 recheck).  One
+step = one such launch over all 64 datasets (envelopes, bounds, compaction,
+DTW, recheck, argmin for every query).  It is compared with the plain FP64
+form run one dataset per call.  ``--workload pairs`` is the single-dataset
+bound-comparison workload (500 x 500, L=256, W=26, V=5), one
+``nn_dtw_search`` per step.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-(the paper's search protocol: Euclidean ordering, LB_Enhanced^V, early-
-abandoning DTW) on a bounded sample of the same workload on the host cores.
+(the paper's search protocol) on a bounded sample of the same workload on the
+host cores.  ``--workload serving`` prints the serving (continuous batching)
+line instead.
 """
 from __future__ import annotations
 
@@ -32,14 +38,17 @@ sys.path.insert(0, ROOT)
 METRIC = "exact NN-DTW queries/s + DTW GCUPS on 1 GB300: batched FP32 vs plain FP64 form"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_STEP = 10   # envelopes, lb, dtw(seed), compact, dtw, filter, collect, dtw64, ties, final
-INSTR_PER_CELL = 3      # FADD + 3-input FMNMX + FFMA
-INSTR_PER_LB_ELEM = 4   # FMNMX + FMNMX + FADD + FFMA (Keogh bridge term)
+KERNELS_PER_SEARCH = 11  # envelopes, lb, dtw(seed), compact x2, dtw, filter, collect, dtw64, ties, final
+INSTR_PER_CELL = 3       # FADD + 3-input FMNMX + FFMA
+INSTR_PER_LB_ELEM = 6    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FADD + FFMA
 FP32_LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
+STAGES = ("envelopes", "lb", "seed", "compact", "dtw", "recheck", "final", "total")
 
 
-def workload(name: str):
+# ------------------------------------------------------------------ workloads
+
+def single_workload(name: str):
     from paper_1808_09617_gb300 import synth
     if name == "pairs":
         ds = synth.make_pairs(5)
@@ -55,7 +64,16 @@ def workload(name: str):
         desc = f"precision: train 10000 x test 2000, L=1024, W={ds.W}, V=5, float32"
     else:
         raise SystemExit(f"unknown workload {name}")
-    return ds, desc
+    return [ds], desc
+
+
+def batched_workload():
+    from paper_1808_09617_gb300 import synth
+    dsets = synth.make_batched(64)
+    desc = ("batched: 64 datasets in one CUDA-graph launch; L log-uniform [24, 2048], train "
+            "log-uniform [16, 8000], test = train/2, W in {0,.05,.1,.2,.5,1} L, V in 1..8; "
+            f"{sum(d.Q for d in dsets)} queries, float32")
+    return dsets, desc
 
 
 def band_cells(L, W):
@@ -81,6 +99,7 @@ class ClockSampler:
     def __init__(self, device_sel: str):
         self.sel = device_sel
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -94,7 +113,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
@@ -126,7 +144,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ helpers
+def device_selector(torch, dev, local):
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        u = str(props.uuid)
+        return u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        return str(local)
+
+
+# ------------------------------------------------------------------ roofline
 
 def source_sha(paths):
     h = hashlib.sha256()
@@ -153,67 +180,116 @@ def traffic_for(stage, workload_name):
     except Exception:
         return None
     e = t.get(f"{workload_name}:{stage}")
-    if not e or e.get("source_sha") != source_sha(STAGE_SOURCES[stage]):
+    if not e or stage not in STAGE_SOURCES or e.get("source_sha") != source_sha(STAGE_SOURCES[stage]):
         return None
     return e.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(ds, budget_s=10.0):
+def roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, workload_name):
+    """Roofline of the stage with the largest time.  ``work`` maps stage ->
+    algorithmic units per step; ``launches`` maps stage -> launches per step."""
+    names = [s for s in STAGES if s != "total"]
+    dom = max(names, key=lambda s: stage_ms[s])
+    per_launch_ms = stage_ms[dom] / max(1, launches.get(dom, 1))
+    units = work.get(dom, 0) / max(1, launches.get(dom, 1))
+    if dom in ("dtw", "seed"):
+        achieved = units / (per_launch_ms * 1e-3) / 1e9
+        peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / INSTR_PER_CELL / 1e9
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s",
+             "frac": achieved / peak,
+             "peak_basis": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{sm_max:.0f} MHz / {INSTR_PER_CELL} instructions per cell",
+             "probe_measured": probe / 1e9, "frac_of_probe": achieved / (probe / 1e9)}
+    elif dom == "lb":
+        achieved = units / (per_launch_ms * 1e-3) / 1e9
+        peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / INSTR_PER_LB_ELEM / 1e9
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair-element/s",
+             "frac": achieved / peak,
+             "peak_basis": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{sm_max:.0f} MHz / {INSTR_PER_LB_ELEM} instructions per element"}
+    else:
+        achieved = units / (per_launch_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "peak_source": f"{peak_src} copy bandwidth"}
+    r["kernel"] = dom
+    r["launches_per_step"] = launches.get(dom, 1)
+    r["mean_launch_ms"] = per_launch_ms
+    r["share_of_step"] = stage_ms[dom] / stage_ms["total"] if stage_ms["total"] else None
+    r["traffic"] = traffic_for(dom, workload_name)
+    return r
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _sample_plan(dsets, per_ds):
+    return [(d, np.arange(min(per_ds, d.Q))) for d in dsets]
+
+
+def oracle_sample(dsets, budget_s):
+    """Time the oracle's pruned search on a sample sized to about budget_s."""
     import oracle
     orc = oracle.get()
     threads = oracle.default_threads()
-    n = min(ds.Q, max(8, threads))
-    env = orc.envelopes(ds.train, ds.W)
-    t0 = time.perf_counter()
-    orc.nn_pruned(ds.train, ds.train_labels, ds.test[:n], ds.W, ds.V, env=env, threads=threads)
-    dt = time.perf_counter() - t0
-    n2 = min(ds.Q, max(n, int(n * budget_s / max(dt, 1e-3))))
-    if n2 > n:
+    envs = [orc.envelopes(d.train, d.W) for d in dsets]
+
+    def run(per_ds):
+        n = 0
         t0 = time.perf_counter()
-        orc.nn_pruned(ds.train, ds.train_labels, ds.test[:n2], ds.W, ds.V, env=env,
-                      threads=threads)
-        dt = time.perf_counter() - t0
-        n = n2
-    return {"value": n / dt, "unit": UNIT, "cores": min(threads, n), "kind": "oracle",
-            "sample": f"first {n} of {ds.Q} queries against all {ds.N} training series "
-                      f"(paper's search protocol, FP64, envelopes precomputed), {dt:.1f} s"}
+        for (d, idx), env in zip(_sample_plan(dsets, per_ds), envs):
+            if idx.size:
+                orc.nn_pruned(d.train, d.train_labels, d.test[idx], d.W, d.V, env=env,
+                              threads=threads)
+                n += idx.size
+        return n, time.perf_counter() - t0
+
+    per = max(8, threads)   # the oracle threads over the queries of one dataset
+    n, dt = run(per)
+    maxq = max(d.Q for d in dsets)
+    per2 = min(maxq, max(per, int(per * budget_s / max(dt, 1e-3))))
+    if per2 > per:
+        per = per2
+        n, dt = run(per)
+    return n, dt, per, threads
 
 
-# ------------------------------------------------------------------ reference arm
+def cpu_baseline(dsets, budget_s=10.0):
+    n, dt, per, threads = oracle_sample(dsets, budget_s)
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {per} queries of each of {len(dsets)} dataset(s) ({n} queries) "
+                      f"against all training series, paper's search protocol in FP64 "
+                      f"(envelopes precomputed), {dt:.1f} s"}
 
-def run_reference(args, ds, desc):
+
+def run_reference(args, dsets, desc):
+    total_steps = args.steps + args.warmup
+    n, dt, per, threads = oracle_sample(dsets, min(8.0, 150.0 / total_steps))
     import oracle
     orc = oracle.get()
-    threads = oracle.default_threads()
-    env = orc.envelopes(ds.train, ds.W)
-    n = min(ds.Q, max(threads, 16))
-    t0 = time.perf_counter()
-    orc.nn_pruned(ds.train, ds.train_labels, ds.test[:n], ds.W, ds.V, env=env, threads=threads)
-    probe = time.perf_counter() - t0
-    # size each step so the whole run stays within a few minutes
-    per_q = probe / n
-    total_steps = args.steps + args.warmup
-    n = int(min(ds.Q, max(threads, (150.0 / total_steps) / max(per_q, 1e-6))))
+    envs = [orc.envelopes(d.train, d.W) for d in dsets]
     times = []
     for k in range(total_steps):
-        lo = (k * n) % ds.Q
-        idx = np.arange(lo, lo + n) % ds.Q
         t0 = time.perf_counter()
-        orc.nn_pruned(ds.train, ds.train_labels, ds.test[idx], ds.W, ds.V, env=env,
-                      threads=threads)
+        cnt = 0
+        for (d, idx), env in zip(_sample_plan(dsets, per), envs):
+            if idx.size:
+                idx = (idx + k * per) % d.Q
+                orc.nn_pruned(d.train, d.train_labels, d.test[idx], d.W, d.V, env=env,
+                              threads=threads)
+                cnt += idx.size
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1000.0 * sum(times) / len(times)
-    value = n / (ms / 1000.0)
+    value = cnt / (ms / 1000.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": desc, "sample_queries_per_step": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, n),
-                             "kind": "oracle",
-                             "sample": f"{n} queries per step against all {ds.N} training "
-                                       f"series, paper's search protocol in FP64"},
+            "config": {"workload": desc, "sample_queries_per_step": cnt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per} queries per dataset per step ({cnt} queries) "
+                                       "against all training series, paper's search protocol "
+                                       "in FP64"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -226,8 +302,6 @@ def run_serving(args):
     several rates, continuous batching across sets; p50/p99 latency and
     sustained queries/s per rate.  Queries cycle through a pool of 1,024
     pre-drawn series per set (drawing them at 50k/s would dominate)."""
-    import threading
-    import torch
     from paper_1808_09617_gb300 import serving, synth
     specs = synth.serving_specs(16)
     sets = {}
@@ -239,7 +313,6 @@ def run_serving(args):
     rng = np.random.default_rng(7)
     results = []
     try:
-        # warm-up: one batch per set
         fs = [srv.submit(pools[d][0], d) for d in sets]
         [f.result() for f in fs]
         for rate in args.serve_rates:
@@ -278,61 +351,6 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------ batched
-
-def run_batched(args):
-    """Batching form: the 64 heterogeneous datasets searched by one CUDA-graph
-    launch (FP32 with FP64 recheck), against the plain FP64 form run one
-    dataset per call."""
-    import torch
-    from paper_1808_09617_gb300 import nndtw, synth
-    nndtw.load()
-    dsets = synth.make_batched(64)
-    dev = torch.device("cuda")
-    sets = [dict(train=torch.from_numpy(d.train).to(dev), labels=torch.from_numpy(d.train_labels).to(dev),
-                 test=torch.from_numpy(d.test).to(dev), W=d.W, V=d.V) for d in dsets]
-    Qtot = sum(d.Q for d in dsets)
-    cells = sum(d.Q * d.N * band_cells(d.L, d.W) for d in dsets)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    bs = nndtw.BatchedSearch(sets, graph=True)
-    for _ in range(args.warmup):
-        flush.zero_()
-        bs.run()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for a, b in evs:
-        flush.zero_()
-        a.record()
-        bs.run()
-        b.record()
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
-    # plain FP64 form, one dataset per call, same data promoted
-    t64 = [(s["train"].double(), s["test"].double()) for s in sets]
-    torch.cuda.synchronize()
-    e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.zero_()
-    e1.record()
-    for (tr, te), s in zip(t64, sets):
-        nndtw.nn_dtw_search(tr, s["labels"], te, s["W"], s["V"])
-    e2.record()
-    torch.cuda.synchronize()
-    ms64 = e1.elapsed_time(e2)
-    line = {"metric": "batched: exact NN-DTW queries/s, 64 heterogeneous datasets, one CUDA-graph "
-                      "launch (FP32 + FP64 recheck) vs plain FP64 form one dataset per call",
-            "value": Qtot / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "impl": "ours",
-            "config": {"workload": "64 datasets: L log-uniform [24, 2048], N log-uniform "
-                                   "[16, 8000], Q = N/2, W in {0,.05,.1,.2,.5,1} L, V in 1..8",
-                       "queries": Qtot, "l2": "flushed before every step"},
-            "gcups_effective": cells / (ms * 1e-3) / 1e9,
-            "fp64_plain": {"ms_per_batch": ms64, "value": Qtot / (ms64 / 1e3),
-                           "fp32_batched_over_fp64_plain": ms64 / ms}}
-    print(json.dumps(line), flush=True)
-
-
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -341,17 +359,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pairs")
+    ap.add_argument("--workload", default="batched")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch each step's kernels directly instead of replaying a CUDA graph")
+    ap.add_argument("--no-tune", action="store_true", help="skip the lanes-per-pair autotuner")
     ap.add_argument("--serve-rates", type=float, nargs="*",
                     default=[1000, 5000, 10000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=512)
-    ap.add_argument("--dtw-group", type=int, default=-1,
-                    help="lanes per pair in the FP32 DTW kernel (-1: autotune, 0: library "
-                         "default, else G)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -365,17 +383,16 @@ def main():
             run_serving(args)
         return
     if args.workload == "batched":
-        if rank == 0:
-            run_batched(args)
-        return
-    ds, desc = workload(args.workload)
+        dsets, desc = batched_workload()
+    else:
+        dsets, desc = single_workload(args.workload)
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, ds, desc)
+            run_reference(args, dsets, desc)
         return
 
     import torch
-    from paper_1808_09617_gb300 import nndtw
+    from paper_1808_09617_gb300 import autotune, nndtw
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -384,43 +401,70 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     nndtw.load()
-
     stream = torch.cuda.current_stream()
-    train = torch.from_numpy(ds.train).to(dev)
-    test = torch.from_numpy(ds.test).to(dev)
-    labels = torch.from_numpy(ds.train_labels).to(dev)
-    N, L = ds.train.shape
-    Q = ds.Q
-    W, V = ds.W, ds.V
-    ws = torch.empty(nndtw.nn_dtw_workspace_size(N, Q, L, W, V), dtype=torch.uint8, device=dev)
-    out = (torch.empty(Q, dtype=torch.int32, device=dev), torch.empty(Q, dtype=torch.int32, device=dev),
-           torch.empty(Q, dtype=torch.float64, device=dev))
+    batched = args.workload == "batched"
+
+    sets = [dict(train=torch.from_numpy(d.train).to(dev),
+                 labels=torch.from_numpy(d.train_labels).to(dev),
+                 test=torch.from_numpy(d.test).to(dev), W=d.W, V=d.V, flags=0) for d in dsets]
+    Qtot = sum(d.Q for d in dsets)
+    # lanes-per-pair per dataset (datasets with enough pairs to matter)
+    tuned = {}
+    if not args.no_tune:
+        for i, (d, s) in enumerate(zip(dsets, sets)):
+            if d.N * d.Q >= 50_000:
+                g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)
+                if g:
+                    s["flags"] = nndtw.DTW_GROUP(g)
+                    tuned[i] = g
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    group = args.dtw_group
-    if group < 0:
-        from paper_1808_09617_gb300 import autotune
-        group = autotune.tune_search(train, labels, test, W, V, workspace=ws, out=out)
-    gflag = nndtw.DTW_GROUP(group) if group else 0
+    # counting pass (untimed): pruning and cells per dataset
+    counts = []
+    for s in sets:
+        counts.append(nndtw.nn_dtw_search(s["train"], s["labels"], s["test"], s["W"], s["V"],
+                                          flags=s["flags"], stats=True).stats)
 
-    def step(flags=0):
-        return nndtw.nn_dtw_search(train, labels, test, W, V, flags=flags | gflag, workspace=ws,
-                                   out=out)
+    # the timed step
+    if batched:
+        bs = nndtw.BatchedSearch(sets, graph=not args.no_graph)
+        run = bs.run
+        outs = bs.outs
+    else:
+        s = sets[0]
+        d0 = dsets[0]
+        ws = torch.empty(nndtw.nn_dtw_workspace_size(d0.N, d0.Q, d0.L, d0.W, d0.V),
+                         dtype=torch.uint8, device=dev)
+        out = (torch.empty(d0.Q, dtype=torch.int32, device=dev),
+               torch.empty(d0.Q, dtype=torch.int32, device=dev),
+               torch.empty(d0.Q, dtype=torch.float64, device=dev))
+        outs = [out]
 
-    # counting pass (untimed): pruning and cells
-    counts = nndtw.nn_dtw_search(train, labels, test, W, V, flags=gflag, workspace=ws, out=out,
-                                 stats=True).stats
+        def one(flags=0):
+            nndtw.nn_dtw_search(s["train"], s["labels"], s["test"], s["W"], s["V"],
+                                flags=flags | s["flags"], workspace=ws, out=out)
+        run = lambda: one(nndtw.TIME_STAGES)
+        if not args.no_graph:
+            one(nndtw.TIME_STAGES)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream(dev)
+            cs.wait_stream(stream)
+            with torch.cuda.stream(cs):
+                with torch.cuda.graph(graph, stream=cs):
+                    one(nndtw.TIME_STAGES)
+            stream.wait_stream(cs)
+            torch.cuda.synchronize()
+            run = graph.replay
+
     for _ in range(args.warmup):
         flush.zero_()
-        step(nndtw.TIME_STAGES)
-        nndtw.nn_dtw_stage_times()
+        run()
+        if not batched:
+            nndtw.nn_dtw_stage_times()
     torch.cuda.synchronize()
 
-    props = torch.cuda.get_device_properties(dev)
-    try:
-        sel = f"GPU-{props.uuid}" if not str(props.uuid).startswith("GPU-") else str(props.uuid)
-    except Exception:
-        sel = str(local)
+    sel = device_selector(torch, dev, local)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stages = []
@@ -431,9 +475,24 @@ def main():
         for k in range(args.steps):
             flush.zero_()                      # L2 flush, outside the step's events
             ev_s[k].record(stream)
-            step(nndtw.TIME_STAGES)
+            run()
             ev_e[k].record(stream)
-            stages.append(nndtw.nn_dtw_stage_times())
+            if not batched:
+                stages.append(nndtw.nn_dtw_stage_times())
+        torch.cuda.synchronize()
+        if batched:
+            # stage times of the same kernels: every dataset once more, one
+            # after another on this stream, with stage events (same inputs)
+            for _ in range(max(1, args.steps // 5)):
+                agg = dict.fromkeys(STAGES, 0.0)
+                flush.zero_()
+                for s in sets:
+                    nndtw.nn_dtw_search(s["train"], s["labels"], s["test"], s["W"], s["V"],
+                                        flags=s["flags"] | nndtw.TIME_STAGES)
+                    st = nndtw.nn_dtw_stage_times()
+                    for key in STAGES:
+                        agg[key] += st[key]
+                stages.append(agg)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -443,82 +502,68 @@ def main():
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * Q / (ms / 1000.0)
+    value = world * Qtot / (ms / 1000.0)
     clocks = clk.summary()
 
-    # per-stage means and the dominant kernel
-    names = [s for s in nndtw.STAGES if s != "total"]
-    stage_ms = {s: sum(d[s] for d in stages) / len(stages) for s in nndtw.STAGES}
-    dominant = max(names, key=lambda s: stage_ms[s])
+    stage_ms = {k: sum(d[k] for d in stages) / len(stages) for k in STAGES}
     peaks, peak_src = read_peaks()
-    n_sm = props.multi_processor_count
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0))
-    cells_main = counts["dtw_cells"] - counts["seed_cells"]
-    dtw_cells_total = counts["dtw_cells"]
     probe = nndtw.nn_dtw_probe_cell_rate(20000)
-    if dominant in ("dtw", "seed"):
-        units = cells_main if dominant == "dtw" else counts["seed_cells"]
-        achieved = units / (stage_ms[dominant] * 1e-3) / 1e9
-        peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / INSTR_PER_CELL / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s",
-                "frac": achieved / peak,
-                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz / "
-                              f"{INSTR_PER_CELL} instructions per cell (derived)",
-                "probe_measured": probe / 1e9, "frac_of_probe": achieved / (probe / 1e9)}
-    elif dominant == "lb":
-        units = N * Q * L
-        achieved = units / (stage_ms["lb"] * 1e-3) / 1e9
-        peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / INSTR_PER_LB_ELEM / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair-element/s",
-                "frac": achieved / peak,
-                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz / "
-                              f"{INSTR_PER_LB_ELEM} instructions per pair-element (derived)"}
-    else:
-        byts = 12 * N * L if dominant == "envelopes" else 0
-        achieved = byts / (stage_ms[dominant] * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if peak else None}
-    roof["kernel"] = dominant
-    roof["share_of_step"] = stage_ms[dominant] / stage_ms["total"] if stage_ms["total"] else None
-    roof["traffic"] = traffic_for(dominant, args.workload) if dominant in STAGE_SOURCES else None
-    if roof["bound"] == "hbm":
-        roof["peak_source"] = f"{peak_src} copy bandwidth"
+    seed_cells = sum(c["seed_cells"] for c in counts)
+    main_cells = sum(c["dtw_cells"] for c in counts) - seed_cells
+    nds = len(dsets)
+    work = {"dtw": main_cells, "seed": seed_cells,
+            "lb": sum(d.N * d.Q * d.L for d in dsets),
+            "envelopes": sum(12 * d.N * d.L for d in dsets)}
+    launches = {"dtw": nds, "seed": nds, "lb": nds, "envelopes": nds, "compact": 2 * nds,
+                "recheck": 4 * nds, "final": nds}
+    roof = roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, args.workload)
+    if batched:
+        roof["stage_timing"] = ("per-dataset searches run one after another with stage events "
+                                "(the timed step runs them concurrently in one graph)")
 
-    # plain FP64 form on the same data
-    fp64_ms = None
+    # plain FP64 form, one dataset per call, same data promoted
+    fp64 = None
     if args.fp64_steps > 0:
-        train64, test64 = train.double(), test.double()
-        ws64 = torch.empty(nndtw.nn_dtw_workspace_size(N, Q, L, W, V, fp64=True),
-                           dtype=torch.uint8, device=dev)
-        nndtw.nn_dtw_search(train64, labels, test64, W, V, workspace=ws64, out=out)
+        t64 = [(s["train"].double(), s["test"].double()) for s in sets]
         e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tot = 0.0
         for _ in range(args.fp64_steps):
             flush.zero_()
-            e1.record(stream)
-            nndtw.nn_dtw_search(train64, labels, test64, W, V, workspace=ws64, out=out)
-            e2.record(stream)
+            e1.record()
+            for (tr, te), s in zip(t64, sets):
+                nndtw.nn_dtw_search(tr, s["labels"], te, s["W"], s["V"])
+            e2.record()
             torch.cuda.synchronize()
             tot += e1.elapsed_time(e2)
-        fp64_ms = tot / args.fp64_steps
-        del ws64
+        ms64 = tot / args.fp64_steps
+        fp64 = {"ms_per_step": ms64, "value": world * Qtot / (ms64 / 1e3), "unit": UNIT,
+                "fp32_over_fp64": ms64 / ms, "form": "plain FP64, one dataset per call"}
+        del t64
 
-    # end to end through the host-buffer C call, pinned host memory
-    h_train = torch.from_numpy(ds.train).pin_memory().numpy()
-    h_test = torch.from_numpy(ds.test).pin_memory().numpy()
-    h_lab = torch.from_numpy(ds.train_labels).pin_memory().numpy()
-    h_out = (torch.empty(Q, dtype=torch.int32).pin_memory().numpy(),
-             torch.empty(Q, dtype=torch.int32).pin_memory().numpy(),
-             torch.empty(Q, dtype=torch.float64).pin_memory().numpy())
-    hbuf = torch.empty(nndtw.nn_dtw_host_buffer_size(N, Q, L, W, V), dtype=torch.uint8, device=dev)
-    for _ in range(2):
-        nndtw.nn_dtw_search_host(h_train, h_lab, h_test, W, V, buffer=hbuf, out=h_out)
+    # end to end: host buffers in, the step, results out, every step
+    h_in = [(torch.from_numpy(d.train).pin_memory(), torch.from_numpy(d.test).pin_memory(),
+             torch.from_numpy(d.train_labels).pin_memory()) for d in dsets]
+    h_out = [tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in out)
+             for out in outs]
     e2e_t = []
-    for _ in range(args.steps):
+    for k in range(args.steps + 2):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        nndtw.nn_dtw_search_host(h_train, h_lab, h_test, W, V, buffer=hbuf, out=h_out)
-        e2e_t.append(time.perf_counter() - t0)
+        for (tr, te, lab), s in zip(h_in, sets):
+            s["train"].copy_(tr, non_blocking=True)
+            s["test"].copy_(te, non_blocking=True)
+            s["labels"].copy_(lab, non_blocking=True)
+        run()
+        for ho, o in zip(h_out, outs):
+            for h, x in zip(ho, o):
+                h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= 2:
+            e2e_t.append(time.perf_counter() - t0)
+    if not batched:
+        nndtw.nn_dtw_stage_times()
     e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
     if dist:
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
@@ -527,45 +572,42 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ds)
+        cpu = cpu_baseline(dsets)
 
     if rank == 0:
-        eff_cells = Q * N * band_cells(L, W)
+        eff_cells = sum(d.Q * d.N * band_cells(d.L, d.W) for d in dsets)
+        pairs = sum(c["pairs"] for c in counts)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": desc, "l2": "flushed before every step (256 MiB write, "
-                                               "outside the step's events)",
+            "config": {"workload": desc, "queries_per_step": Qtot,
+                       "l2": "flushed before every step (256 MiB write, outside the step's events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "dtw_group": group or "library default",
-                       "dtw_group_source": "autotune" if args.dtw_group < 0 else "fixed",
-                       "step": "one nn_dtw_search call: envelopes, LB, seed DTW, compaction, "
-                               "DTW, FP64 recheck, argmin"},
+                       "launch": "CUDA graph replay" if not args.no_graph else "direct launches",
+                       "dtw_group_autotuned": {str(k): v for k, v in tuned.items()}},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * Q / (e2e_ms / 1000.0), "unit": UNIT,
-                    "h2d_bytes_per_step": int(ds.train.nbytes + ds.test.nbytes +
-                                              ds.train_labels.nbytes),
-                    "d2h_bytes_per_step": int(Q * (4 + 4 + 8)),
-                    "ms_per_step": e2e_ms},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "e2e": {"value": world * Qtot / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(d.train.nbytes + d.test.nbytes +
+                                                  d.train_labels.nbytes for d in dsets)),
+                    "d2h_bytes_per_step": int(Qtot * (4 + 4 + 8)), "ms_per_step": e2e_ms},
+            "gpu_launches": KERNELS_PER_SEARCH * nds * args.steps,
             "clocks": clocks,
             "gcups_effective": eff_cells / (ms * 1e-3) / 1e9,
-            "gcups_dtw_kernel": (cells_main / (stage_ms["dtw"] * 1e-3) / 1e9
+            "gcups_dtw_kernel": (main_cells / (stage_ms["dtw"] * 1e-3) / 1e9
                                  if stage_ms["dtw"] > 0 else None),
             "stage_ms": stage_ms,
-            "pruning": {"pairs": counts["pairs"], "lb_pruned": counts["lb_pruned"],
-                        "lb_pruned_frac": counts["lb_pruned"] / counts["pairs"],
-                        "dtw_started": counts["dtw_started"],
-                        "dtw_abandoned": counts["dtw_abandoned"],
-                        "dtw_cells": dtw_cells_total,
-                        "rechecked": counts["rechecked"],
-                        "recheck_queries": counts["recheck_queries"]},
-            "fp64_plain": ({"ms_per_step": fp64_ms, "value": world * Q / (fp64_ms / 1000.0),
-                            "unit": UNIT, "fp32_over_fp64": fp64_ms / ms}
-                           if fp64_ms else None),
+            "pruning": {"pairs": pairs,
+                        "lb_pruned": sum(c["lb_pruned"] for c in counts),
+                        "lb_pruned_frac": sum(c["lb_pruned"] for c in counts) / pairs,
+                        "dtw_started": sum(c["dtw_started"] for c in counts),
+                        "dtw_abandoned": sum(c["dtw_abandoned"] for c in counts),
+                        "dtw_cells": main_cells + seed_cells,
+                        "rechecked": sum(c["rechecked"] for c in counts),
+                        "recheck_queries": sum(c["recheck_queries"] for c in counts)},
+            "fp64_plain": fp64,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -72,6 +72,10 @@ extern "C" {
  * cannot hold the window (more than 64 diagonals per lane) is ignored. */
 #define NNDTW_DTW_GROUP(log2g) ((unsigned)((log2g) + 1) << 8)
 #define NNDTW_DTW_GROUP_MASK (7u << 8)
+/* search / dtw_windowed: for full windows (W >= L-1, L <= 2048) sweep DTW by
+ * rows, one pair per warp (the default for such windows when no
+ * NNDTW_DTW_GROUP is given); ignored for other windows. */
+#define NNDTW_DTW_ROWS (7u << 8)
 
 /* stage indices of nn_dtw_stage_times() */
 #define NNDTW_STAGE_ENVELOPES 0 /* S1 (0 when envelopes are supplied)            */

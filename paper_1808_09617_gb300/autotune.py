@@ -32,12 +32,16 @@ def key(device_name: str, N: int, Q: int, L: int, W: int, V: int) -> str:
     return f"{device_name}|L{L}|W{min(W, L - 1)}|V{V}|N{_bucket(N)}|Q{_bucket(Q)}"
 
 
-def admissible_groups(W: int):
+def admissible_groups(W: int, L: int | None = None):
+    """Lanes-per-pair choices of the diagonal layout for window W, plus the
+    row layout (nndtw.ROWS_GROUP) when the window is full (W >= L-1, L <= 2048)."""
     out = []
     for g in (1, 2, 4, 8, 16, 32):
         h = (W + g) // g
         if h <= 32 and not (h == 1 and g != W + 1):
             out.append(g)
+    if L is not None and W >= L - 1 and L <= 2048:
+        out.append(nndtw.ROWS_GROUP)
     return out
 
 
@@ -64,7 +68,7 @@ def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, r
         if cache_path and k in _load(cache_path):
             _mem[k] = int(_load(cache_path)[k])
             return _mem[k]
-    groups = admissible_groups(Weff)
+    groups = admissible_groups(Weff, L)
     if not groups:
         return 0
     if workspace is None:

@@ -52,6 +52,7 @@ bool dtw32_shape(int W, int want, int *G, int *H) {
 
 int dtw32_wide_group(int W) {
     int H;
+    // (callers check dtw32_rows_ok first: full windows go to the row kernel)
     for (int g = 32; g >= 1; g >>= 1)
         if (shape_ok(W, g, &H)) return g;
     return 0;
@@ -62,6 +63,9 @@ int dtw32_wide_group(int W) {
 bool dtw32_supported(int W) { return W >= 0 && W < NNDTW_MAX_L; }
 
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
+    // full windows: the row kernel, unless a diagonal group width is asked for
+    if ((job.group == 0 || job.group == kRowsGroup) && dtw32_rows_ok(job.L, job.W))
+        return launch_dtw32_rows(job, sm_count, s);
     int G = 0, H = 0;
     if (!dtw32_shape(job.W, job.group, &G, &H)) return launch_dtw32_wide(job, sm_count, s);
     Dtw32Fn fn = pick_fn(H);

@@ -112,10 +112,13 @@ struct DtwJob32 {
     unsigned long long *counters;       // stats (C_STARTED ...), may be nullptr
     float dtw_lo, dtw_hi, abs32;        // margins
     int abandon;                        // 1: abandon against bsf
-    int group;                          // lanes per pair (0: library's choice)
+    int group;                          // lanes per pair (0: library's choice; kRowsGroup: rows)
 };
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s);
+cudaError_t launch_dtw32_rows(const DtwJob32 &job, int sm_count, cudaStream_t s);
+bool dtw32_rows_ok(int L, int W);   // full window and L small enough for the row kernel
+constexpr int kRowsGroup = 64;      // DtwJob32::group value selecting the row kernel
 bool dtw32_supported(int W);   // window W (<= L-1) fits the FP32 DTW kernel
 int dtw32_wide_group(int W);   // widest lanes-per-pair choice for W (latency-bound passes)
 

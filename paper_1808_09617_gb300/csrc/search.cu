@@ -42,61 +42,95 @@ __global__ void finite_check_kernel(const T *__restrict__ x, int64_t n, T limit,
     if (cnt) atomicAdd(bad, cnt);
 }
 
-// S3: keep (q, t) iff its safe bound does not exceed the query's upper bound.
-__global__ void compact32_kernel(const float *__restrict__ lb, int64_t Q, int64_t N,
-                                 const unsigned long long *__restrict__ bsf,
-                                 const unsigned long long *__restrict__ seed, float dtw_hi,
-                                 float abs32, int no_prune, uint2 *__restrict__ queue,
-                                 unsigned long long *__restrict__ qcount) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t q = blockIdx.y; q < Q; q += gridDim.y) {
-        const unsigned long long kb = bsf[q];
-        const float ub = kb == ~0ull ? inf_of<float>() : upper32(key_dist(kb), dtw_hi, abs32);
-        const uint32_t st = key_idx(seed[q]);
-        const float *row = lb + q * N;
-        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < N;
-             t0 += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t t = t0 + threadIdx.x;
-            bool keep = false;
-            if (t < N) keep = (no_prune || row[t] <= ub) && (uint32_t)t != st;
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (m) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep)
-                    queue[base + __popc(m & ((1u << lane) - 1u))] =
-                        make_uint2((uint32_t)q, (uint32_t)t);
-            }
-        }
+// S3: keep (q, t) iff its safe bound does not exceed the query's upper bound,
+// and order the kept pairs by the ratio bound / upper bound (kBuckets buckets,
+// counting sort in two passes).  Pairs with a small ratio tend to run their
+// DTW to completion, pairs near 1 to be abandoned early, so this order runs
+// the long pairs first and leaves short ones for the end of the persistent
+// DTW kernel (longest-processing-time-first scheduling).  The queue then holds
+// bucket 0, bucket 1, ...; within a bucket the order is arbitrary.
+constexpr int kBuckets = 8;
+
+template <typename T> struct UbOf;
+template <> struct UbOf<float> {
+    float hi, abs_s;
+    __device__ float operator()(unsigned long long kb) const {
+        return kb == ~0ull ? inf_of<float>() : upper32(key_dist(kb), hi, abs_s);
     }
+};
+template <> struct UbOf<double> {
+    __device__ double operator()(unsigned long long kb) const {
+        return __longlong_as_double((long long)kb);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ int bucket_of(T lb, T ub) {
+    if (!(ub > T(0))) return 0;
+    const T r = lb / ub;
+    int b = (int)(r * T(kBuckets));
+    return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
 }
 
-__global__ void compact64_kernel(const double *__restrict__ lb, int64_t Q, int64_t N,
-                                 const unsigned long long *__restrict__ bsf64,
-                                 const unsigned long long *__restrict__ seed, int no_prune,
-                                 uint2 *__restrict__ queue,
-                                 unsigned long long *__restrict__ qcount) {
-    const int lane = threadIdx.x & 31;
+// pass 1 (scatter == 0): count the kept pairs of every bucket;
+// pass 2 (scatter == 1): write them at bucket offset + position.
+// Both passes aggregate per block in shared memory: one global atomic per
+// bucket per block-iteration (pass 2) or per block (pass 1).
+template <typename T>
+__global__ void __launch_bounds__(256)
+compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
+               const unsigned long long *__restrict__ bsf,
+               const unsigned long long *__restrict__ seed, UbOf<T> ubof, int no_prune,
+               int scatter, unsigned long long *__restrict__ bcount,
+               unsigned long long *__restrict__ bcursor, uint2 *__restrict__ queue,
+               unsigned long long *__restrict__ qcount) {
+    __shared__ unsigned long long boff[kBuckets];
+    __shared__ unsigned int scount[kBuckets];
+    __shared__ unsigned long long sbase[kBuckets];
+    const int tid = threadIdx.x;
+    if (tid < kBuckets) {
+        scount[tid] = 0;
+        if (scatter) {
+            unsigned long long o = 0;
+            for (int k = 0; k < tid; k++) o += bcount[k];
+            boff[tid] = o;
+            if (tid == kBuckets - 1 && blockIdx.x == 0 && blockIdx.y == 0)
+                *qcount = o + bcount[kBuckets - 1];
+        }
+    }
+    __syncthreads();
     for (int64_t q = blockIdx.y; q < Q; q += gridDim.y) {
-        const double ub = __longlong_as_double((long long)bsf64[q]);
+        const T ub = ubof(bsf[q]);
         const uint32_t st = key_idx(seed[q]);
-        const double *row = lb + q * N;
+        const T *row = lb + q * N;
         for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < N;
              t0 += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t t = t0 + threadIdx.x;
+            const int64_t t = t0 + tid;
             bool keep = false;
-            if (t < N) keep = (no_prune || row[t] <= ub) && (uint32_t)t != st;
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (m) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep)
-                    queue[base + __popc(m & ((1u << lane) - 1u))] =
-                        make_uint2((uint32_t)q, (uint32_t)t);
+            int b = 0;
+            if (t < N) {
+                const T v = row[t];
+                keep = (no_prune || v <= ub) && (uint32_t)t != st;
+                b = bucket_of(v, ub);
             }
+            unsigned int pos = 0;
+            if (keep) pos = atomicAdd(&scount[b], 1u);
+            if (!scatter) continue;
+            __syncthreads();
+            if (tid < kBuckets) {
+                const unsigned int c = scount[tid];
+                sbase[tid] = c ? atomicAdd(bcursor + tid, (unsigned long long)c) : 0ull;
+            }
+            __syncthreads();
+            if (keep) queue[boff[b] + sbase[b] + pos] = make_uint2((uint32_t)q, (uint32_t)t);
+            __syncthreads();
+            if (tid < kBuckets) scount[tid] = 0;
+            __syncthreads();
         }
+    }
+    if (!scatter) {
+        __syncthreads();
+        if (tid < kBuckets && scount[tid]) atomicAdd(bcount + tid, (unsigned long long)scount[tid]);
     }
 }
 
@@ -237,6 +271,13 @@ struct StageTimer {
     }
     cudaError_t mark(int i) {
         if (!on) return cudaSuccess;
+        // inside a stream capture the record must be an external graph node
+        // so that the event is recorded every time the graph runs
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return e;
+        if (cs == cudaStreamCaptureStatusActive)
+            return cudaEventRecordWithFlags(set->ev[i], s, cudaEventRecordExternal);
         return cudaEventRecord(set->ev[i], s);
     }
 };
@@ -254,7 +295,7 @@ struct Carve {
 };
 
 struct Layout32 {
-    unsigned long long *counters, *bsf, *seed, *best64;
+    unsigned long long *counters, *bsf, *seed, *best64, *buckets;
     int32_t *rcount, *bestidx;
     float *env, *lb;
     uint2 *queue, *rlist;
@@ -268,6 +309,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
     Layout32 l;
     const size_t cap = (size_t)Q * (size_t)N + (size_t)Q;
     l.counters = c.take<unsigned long long>(C_COUNT);
+    l.buckets = c.take<unsigned long long>(2 * kBuckets);
     l.bsf = c.take<unsigned long long>(Q);
     l.seed = c.take<unsigned long long>(Q);
     l.best64 = c.take<unsigned long long>(Q);
@@ -284,7 +326,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
 }
 
 struct Layout64 {
-    unsigned long long *counters, *bsf64, *seed;
+    unsigned long long *counters, *bsf64, *seed, *buckets;
     int32_t *bestidx;
     double *env, *lb;
     uint2 *queue;
@@ -297,6 +339,7 @@ Layout64 layout64(void *base, int64_t N, int64_t Q, int L) {
     Layout64 l;
     const size_t cap = (size_t)Q * (size_t)N + (size_t)Q;
     l.counters = c.take<unsigned long long>(C_COUNT);
+    l.buckets = c.take<unsigned long long>(2 * kBuckets);
     l.bsf64 = c.take<unsigned long long>(Q);
     l.seed = c.take<unsigned long long>(Q);
     l.bestidx = c.take<int32_t>(Q);
@@ -498,6 +541,7 @@ int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pai
 
 static int group_from_flags(unsigned flags) {
     const unsigned v = (flags & NNDTW_DTW_GROUP_MASK) >> 8;
+    if (v == 7) return kRowsGroup;
     return v ? 1 << (v - 1) : 0;
 }
 
@@ -566,6 +610,7 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     StageTimer tm;
     CK(tm.start(timing, s));
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
+    CK(cudaMemsetAsync(ws.buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, s));
     CK(cudaMemsetAsync(ws.bsf, 0xff, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.best64, 0xff, sizeof(unsigned long long) * Q, s));
@@ -604,15 +649,21 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     j.pairs = nullptr; j.seed_keys = ws.seed; j.n_seed = Q; j.head = nullptr; j.abandon = 0;
     // one pair per query: latency-bound, so spread each pair over the widest group
     const int main_group = j.group;
-    j.group = dtw32_wide_group(Weff);
+    j.group = dtw32_rows_ok(L, Weff) ? kRowsGroup : dtw32_wide_group(Weff);
     CK(launch_dtw32(j, sms, s));
     j.group = main_group;
     CK(tm.mark(3));
     // S3: compaction against the upper bounds
-    compact32_kernel<<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
-        ws.lb, Q, N, ws.bsf, ws.seed, m.dtw_hi, m.abs32, (flags & NNDTW_NO_PRUNE) ? 1 : 0,
-        ws.queue, ws.counters + C_QUEUE);
-    CK(cudaGetLastError());
+    {
+        UbOf<float> ubf{m.dtw_hi, m.abs32};
+        const int np = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
+        for (int pass = 0; pass < 2; pass++) {
+            compact_kernel<float><<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
+                ws.lb, Q, N, ws.bsf, ws.seed, ubf, np, pass, ws.buckets, ws.buckets + kBuckets,
+                ws.queue, ws.counters + C_QUEUE);
+            CK(cudaGetLastError());
+        }
+    }
     CK(tm.mark(4));
     // S4 on the survivors, with early abandoning
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
@@ -678,6 +729,7 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     StageTimer tm;
     CK(tm.start(timing, s));
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
+    CK(cudaMemsetAsync(ws.buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, s));
     CK(cudaMemsetAsync(ws.bsf64, 0x7f, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
     CK(cudaMemsetAsync(ws.bestidx, 0x7f, sizeof(int32_t) * Q, s));
@@ -708,10 +760,16 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     j.pairs = nullptr; j.seed_keys = ws.seed; j.n_pairs = Q; j.head = nullptr; j.abandon = 0;
     CK(launch_dtw64(j, sms, s));
     CK(tm.mark(3));
-    compact64_kernel<<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
-        ws.lb, Q, N, ws.bsf64, ws.seed, (flags & NNDTW_NO_PRUNE) ? 1 : 0, ws.queue,
-        ws.counters + C_QUEUE);
-    CK(cudaGetLastError());
+    {
+        UbOf<double> ubd{};
+        const int np = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
+        for (int pass = 0; pass < 2; pass++) {
+            compact_kernel<double><<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
+                ws.lb, Q, N, ws.bsf64, ws.seed, ubd, np, pass, ws.buckets, ws.buckets + kBuckets,
+                ws.queue, ws.counters + C_QUEUE);
+            CK(cudaGetLastError());
+        }
+    }
     CK(tm.mark(4));
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
     j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;

@@ -30,8 +30,15 @@ CHECK_FINITE = 1 << 5
 TIME_STAGES = 1 << 6
 
 
+ROWS_GROUP = 64        # tuning value meaning "row layout, one pair per warp"
+DTW_ROWS = 7 << 8
+
+
 def DTW_GROUP(g: int) -> int:
-    """Flag selecting G lanes per pair in the FP32 DTW kernel (G = 1..32)."""
+    """Flag selecting G lanes per pair in the FP32 DTW kernel's diagonal layout
+    (G = 1..32), or the row layout for full windows (G = ROWS_GROUP)."""
+    if g == ROWS_GROUP:
+        return DTW_ROWS
     if g < 1 or g > 32 or g & (g - 1):
         raise ValueError("G must be a power of two in 1..32")
     return (g.bit_length()) << 8

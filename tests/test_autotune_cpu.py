@@ -10,6 +10,9 @@ def test_admissible_groups():
     assert autotune.admissible_groups(1023) == [32]
     assert autotune.admissible_groups(1024) == []
     assert autotune.admissible_groups(100)[0] == 4
+    assert autotune.admissible_groups(255, 256)[-1] == 64    # full window: row layout too
+    assert 64 not in autotune.admissible_groups(100, 256)
+    assert 64 not in autotune.admissible_groups(3000, 3001)  # beyond the row kernel's 2048
 
 
 def test_key_buckets():

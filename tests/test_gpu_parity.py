@@ -177,7 +177,7 @@ def test_search_pairs_workload(lib, orc, V):
 SEARCH_CASES = [
     # N, Q, L, W, V
     (1, 1, 16, 3, 2), (3, 100, 40, 5, 3), (70, 65, 2, 1, 1), (70, 65, 3, 0, 1),
-    (130, 33, 64, 0, 5), (130, 33, 64, 63, 5), (130, 33, 64, 100, 5), (129, 67, 77, 7, 40),
+    (130, 33, 64, 0, 5), (130, 33, 64, 63, 5), (130, 33, 64, 100, 5), (129, 67, 77, 7, 40), (150, 40, 300, 299, 5), (60, 25, 1500, 1499, 3), (90, 30, 33, 40, 2),
     (200, 50, 150, 40, 5), (100, 20, 300, 130, 8), (64, 10, 1024, 300, 5),
     (40, 8, 1024, 1023, 5), (257, 31, 101, 10, 4),
 ]
@@ -268,10 +268,25 @@ def test_dtw_every_group_width_same_values(lib, orc, L, W):
     rng = np.random.default_rng(W)
     pairs = np.stack([rng.integers(0, 6, 40), rng.integers(0, 11, 40)], 1).astype(np.int32)
     ref = orc.dtw_pairs(test, train, W, pairs=pairs)
-    for g in (1, 2, 4, 8, 16, 32):
+    for g in (1, 2, 4, 8, 16, 32, lib.ROWS_GROUP):
         got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W,
                                flags=lib.DTW_GROUP(g)).cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0, err_msg=f"G={g}")
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 31, 32, 33, 64, 100, 1000, 2047, 2048])
+def test_dtw_full_window_row_layout(lib, orc, L):
+    """Full windows (W >= L-1) use the row layout by default; the diagonal layout
+    (forced by a group width) must agree."""
+    W = L - 1 if L > 1 else 0
+    test = _series(900 + L, 4, L)
+    train = _series(901 + L, 7, L)
+    pairs = np.array([[q, t] for q in range(4) for t in range(7)], np.int32)
+    ref = orc.dtw_pairs(test, train, W, pairs=pairs)
+    got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0)
+    big = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W + 1000).cpu().numpy()
+    np.testing.assert_array_equal(big, got)
 
 
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
