@@ -58,6 +58,12 @@ def single_workload(name: str):
         ds.train = ds.train.astype(np.float32)
         ds.test = ds.test.astype(np.float32)
         desc = "tiny: train 64 x test 32, L=128, W=13, V=5"
+    elif name.startswith("batched-"):
+        i = int(name.split("-")[1])
+        spec = synth.batched_specs(64)[i]
+        ds = synth.make_batched_dataset(i, spec)
+        desc = (f"batched dataset {i} alone: train {ds.N} x test {ds.Q}, L={ds.L}, W={ds.W}, "
+                f"V={ds.V}, float32")
     elif name.startswith("precision-"):
         r = float(name.split("-")[1])
         ds = synth.make_precision(r)
@@ -365,6 +371,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each step's kernels directly instead of replaying a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the lanes-per-pair autotuner")
+    ap.add_argument("--dtw-group", type=int, default=0,
+                    help="lanes per pair for every dataset (1..32, or 64 for the row layout); "
+                         "implies --no-tune")
     ap.add_argument("--serve-rates", type=float, nargs="*",
                     default=[1000, 5000, 10000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -410,7 +419,11 @@ def main():
     Qtot = sum(d.Q for d in dsets)
     # lanes-per-pair per dataset (datasets with enough pairs to matter)
     tuned = {}
-    if not args.no_tune:
+    if args.dtw_group:
+        for i, s in enumerate(sets):
+            s["flags"] = nndtw.DTW_GROUP(args.dtw_group)
+            tuned[i] = args.dtw_group
+    elif not args.no_tune:
         for i, (d, s) in enumerate(zip(dsets, sets)):
             if d.N * d.Q >= 50_000:
                 g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)

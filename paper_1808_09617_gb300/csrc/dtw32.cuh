@@ -44,6 +44,20 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return r;
 }
 
+// The (query, training series) of work item p: an explicit pair list, or
+// query p with its seed candidate.  Items past the end read nothing.
+__device__ __forceinline__ uint2 work_item(const DtwJob32 &job, long long p, long long n_work) {
+    if (p >= n_work) return make_uint2(0u, 0u);
+    if (job.pairs) return job.pairs[p];
+    return make_uint2((unsigned)p, (unsigned)key_idx(job.seed_keys[p]));
+}
+
+// The distance half (float bits) of query q's best key, read past the
+// caches; ~0u while the query has no candidate yet.
+__device__ __forceinline__ unsigned bsf_dist_bits(const unsigned long long *bsf, int q) {
+    return *(reinterpret_cast<const volatile unsigned *>(bsf + q) + 1);
+}
+
 // Number of band cells (i, j) in [0,L)^2 with |i-j| <= W and i + j <= S, in
 // closed form: anti-diagonals d <= W hold d+1 cells, the middle ones W or W+1
 // alternately, the last W ones 2L-1-d.
@@ -68,10 +82,10 @@ __device__ inline long long band_cells_upto(int L, int W, long long S) {
 
 // Resident 128-thread blocks per SM requested from the register allocator for
 // each H (the diagonal registers, the two windows and the per-pair state need
-// about 4H + 2U + 40 registers); chosen from a compile sweep as the largest
+// about 4H + 2U + 50 registers); chosen from a compile sweep as the largest
 // count that causes no more than a few bytes of spills.
 __host__ __device__ constexpr int dtw32_min_blocks(int H) {
-    return H <= 4 ? 8 : H <= 9 ? 6 : H == 12 ? 4 : H <= 13 ? 5 : H <= 20 ? 4 : H <= 28 ? 3 : 2;
+    return H <= 4 ? 8 : H <= 9 ? 6 : H <= 11 ? 5 : H <= 15 ? 4 : H <= 23 ? 3 : 2;
 }
 
 template <int H, int U>
@@ -80,6 +94,7 @@ dtw32_kernel(DtwJob32 job, int G) {
     constexpr int C = 2 * H;
     const float INF = __int_as_float(0x7f800000);
     const float APAD = Pad<float>::v, BPAD = -Pad<float>::v, EPAD = Pad<float>::v;
+    const unsigned FULL = 0xffffffffu;
     const int L = job.L, W = job.W;
 
     const int lane = threadIdx.x & 31;
@@ -89,71 +104,85 @@ dtw32_kernel(DtwJob32 job, int G) {
     const int k0 = gl * C - 2 * (gl < s ? gl : s);
     const int Cg = shortl ? C - 2 : C;
     const bool lastl = gl == G - 1;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const bool hasW = W >= k0 && W < k0 + Cg;
     const int cW = W - k0;
     const int t_first = -(W & 1);
     const int I0 = (W >> 1) - (k0 >> 1);        // I at the first super-step's A step
     const int J0 = t_first - I0;
+    // The group's series streams: at super-step u its lane 0 takes query
+    // value IA0 + u and its last lane training value JB0 + u.
+    const int k0_last = (G - 1) * C - 2 * (G - 1 < s ? G - 1 : s);
+    const int IA0 = (W >> 1) + 1;
+    const int JB0 = t_first - ((W >> 1) - (k0_last >> 1)) + H;
 
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
-
     const long long n_groups = (long long)gridDim.x * (blockDim.x / G);
-    long long next_static = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool check_bsf = job.abandon && job.bsf;
+    // abandon checks every 16 super-steps, at the same block for the whole warp
+    constexpr int kCheckBlocks = 16 / U > 1 ? 16 / U : 1;
+
+    // Claims run two pairs ahead per group so that no memory latency sits
+    // between two sweeps (the whole warp would wait for it): p1 is the
+    // group's next pair with its item w1 already requested.  `nxt` is the
+    // next static index, or (dynamic claims) the claim after p1, still in
+    // flight in the group's lane 0.
+    long long nxt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    long long p1;
+    if (job.head) {
+        unsigned long long v = 0;
+        if (gl == 0) v = atomicAdd(job.head, 1ull);
+        p1 = (long long)__shfl_sync(FULL, v, 0, G);
+        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+    } else {
+        p1 = nxt;
+        nxt += n_groups;
+    }
+    uint2 w1 = work_item(job, p1, n_work);
 
     float R[C], Aw[H + U], Bw[H + U];
     // per-pair state
     long long pid = -1;
-    int q = 0, tt = 0, u = 0;
+    int q = 0, tt = 0;
+    int ws = 0;                     // warp step at which the pair started
     bool done = true, finished = false;
-    float ub = INF, res = INF;
+    float ub = INF;
+    unsigned kb = ~0u;              // query best (float bits) read at one check, used at the next
     const float *ap = job.test, *bp = job.train;
-    float acur = 0.f, bcur = 0.f;   // stream values for the current super-step
-    int since_check = 0;
+    // Stream values come in chunks of G, one per lane of the group: for warp
+    // steps cG .. cG+G-1, lane k of the group holds the values of warp step
+    // cG + k (the current chunk in ca/cb, the next one in na_/nb_).
+    float ca = 0.f, cb = 0.f, na_ = 0.f, nb_ = 0.f;
+    int wblk = 0;                   // warp step at the start of this block
 
     while (true) {
-        // ---- claim new pairs at a block boundary ---------------------------
+        // ---- start new pairs at a block boundary ---------------------------
+        // (branches on group-uniform state; shuffles use the group's mask)
         const bool need = done && !finished;
-        const unsigned needmask = __ballot_sync(0xffffffffu, need && gl == 0);
-        if (needmask) {
-            long long mine = -1;
-            if (job.head) {
-                // dynamic: one atomic per warp for all groups that need work
-                unsigned long long base = 0;
-                const int leader = __ffs(needmask) - 1;
-                if (lane == leader) base = atomicAdd(job.head, (unsigned long long)__popc(needmask));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (need && gl == 0) mine = (long long)base + __popc(needmask & ((1u << lane) - 1));
-                mine = __shfl_sync(0xffffffffu, mine, lane & ~(G - 1));
-            } else if (need) {
-                // static: group k takes pairs k, k + n_groups, ...
-                mine = next_static;
-                next_static += n_groups;
-            }
+        if (__any_sync(FULL, need)) {
             if (need) {
-                if (mine >= n_work) {
+                if (p1 >= n_work) {
                     finished = true;
                     pid = -1;
                 } else {
-                    pid = mine;
-                    if (job.pairs) {
-                        const uint2 pr = job.pairs[pid];
-                        q = (int)pr.x; tt = (int)pr.y;
+                    pid = p1;
+                    q = (int)w1.x; tt = (int)w1.y;
+                    if (job.head) {
+                        p1 = __shfl_sync(gmask, nxt, 0, G);
+                        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
                     } else {
-                        q = (int)pid; tt = (int)key_idx(job.seed_keys[pid]);
+                        p1 = nxt;
+                        nxt += n_groups;
                     }
+                    w1 = work_item(job, p1, n_work);
                     ap = job.test + (long long)q * L;
                     bp = job.train + (long long)tt * L;
                     done = false;
-                    u = 0;
-                    res = INF;
-                    since_check = 0;
+                    ws = wblk;
                     ub = INF;
-                    if (job.abandon && job.bsf) {
-                        const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
-                        if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
-                    }
+                    kb = ~0u;
+                    if (check_bsf) kb = bsf_dist_bits(job.bsf, q);
                     // windows for the first super-step (v = 0 mappings)
 #pragma unroll
                     for (int m = 0; m < H; m++) {
@@ -164,33 +193,43 @@ dtw32_kernel(DtwJob32 job, int G) {
                     }
 #pragma unroll
                     for (int c = 0; c < C; c++) R[c] = (hasW && c == cW) ? 0.f : INF;
-                    {   // stream values for super-step 0
-                        const int ia = I0 + 1, jb = J0 + H;
-                        acur = (gl == 0) ? ((ia >= 0 && ia < L) ? ap[ia] : APAD) : 0.f;
-                        bcur = lastl ? (jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD)) : 0.f;
+                    {   // the stream chunks holding warp steps wblk and on
+                        const int u0 = (wblk & ~(G - 1)) + gl - wblk;
+                        const int ia = IA0 + u0, jb = JB0 + u0;
+                        ca = (ia >= 0 && ia < L) ? ap[ia] : APAD;
+                        cb = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
+                        const int ia2 = ia + G, jb2 = jb + G;
+                        na_ = (ia2 >= 0 && ia2 < L) ? ap[ia2] : APAD;
+                        nb_ = jb2 < 0 ? BPAD : (jb2 < L ? bp[jb2] : EPAD);
                     }
                     if (job.counters && gl == 0) atomicAdd(job.counters + C_STARTED, 1ull);
                 }
             }
         }
-        if (__all_sync(0xffffffffu, finished)) break;
+        if (__all_sync(FULL, finished)) break;
 
         // ---- one block of U super-steps ------------------------------------
 #pragma unroll
         for (int v = 0; v < U; v++) {
-            // prefetch next super-step's stream values
-            float anx = 0.f, bnx = 0.f;
-            {
-                const int ia = I0 + u + 2, jb = J0 + u + 1 + H;
-                if (gl == 0) anx = (ia >= 0 && ia < L) ? ap[ia] : APAD;
-                if (lastl) bnx = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
+            const int w = wblk + v;
+            const int src = w & (G - 1);
+            const float acur = __shfl_sync(FULL, ca, src, G);
+            const float bcur = __shfl_sync(FULL, cb, src, G);
+            if (src == G - 1) {
+                // next chunk in, and the one after it requested
+                ca = na_;
+                cb = nb_;
+                const int u2 = w + 1 + G + gl - ws;
+                const int ia = IA0 + u2, jb = JB0 + u2;
+                na_ = (ia >= 0 && ia < L) ? ap[ia] : APAD;
+                nb_ = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
             }
             // step A: even slots
             {
                 float send;
                 if constexpr (H >= 2) send = shortl ? R[C - 3] : R[C - 1];
                 else send = R[C - 1];
-                float left = __shfl_up_sync(0xffffffffu, send, 1, G);
+                float left = __shfl_up_sync(FULL, send, 1, G);
                 if (gl == 0) left = INF;
 #pragma unroll
                 for (int m = 0; m < H; m++) {
@@ -205,7 +244,7 @@ dtw32_kernel(DtwJob32 job, int G) {
             // b-shift
             {
                 const float sendb = Bw[v];
-                float nb = __shfl_down_sync(0xffffffffu, sendb, 1, G);
+                float nb = __shfl_down_sync(FULL, sendb, 1, G);
                 if (lastl) nb = bcur;
                 Bw[H + v] = nb;
                 if constexpr (H >= 2) {
@@ -214,7 +253,7 @@ dtw32_kernel(DtwJob32 job, int G) {
             }
             // step B: odd slots
             {
-                float right = __shfl_down_sync(0xffffffffu, R[0], 1, G);
+                float right = __shfl_down_sync(FULL, R[0], 1, G);
                 if (lastl) right = INF;
 #pragma unroll
                 for (int m = 0; m < H; m++) {
@@ -235,7 +274,7 @@ dtw32_kernel(DtwJob32 job, int G) {
                 float senda;
                 if constexpr (H >= 2) senda = shortl ? Aw[H - 2 + U - 1 - v] : Aw[H - 1 + U - 1 - v];
                 else senda = Aw[H - 1 + U - 1 - v];
-                float na = __shfl_up_sync(0xffffffffu, senda, 1, G);
+                float na = __shfl_up_sync(FULL, senda, 1, G);
                 if (gl == 0) na = acur;
                 if (v + 1 < U) {
                     Aw[U - 2 - v] = na;
@@ -245,18 +284,14 @@ dtw32_kernel(DtwJob32 job, int G) {
                     Aw[U - 1] = na;
                 }
             }
-            acur = anx;
-            bcur = bnx;
-            u++;
         }
         // realign the b window
 #pragma unroll
         for (int m = 0; m < H; m++) Bw[m] = Bw[m + U];
+        wblk += U;
+        const int u = wblk - ws;     // super-steps of the current pair so far
 
         // ---- completion / abandon ------------------------------------------
-        // Everything below branches on group-uniform state only (all lanes of
-        // a group share pid, u and done), so group reductions use the group's
-        // lane mask.
         const bool completed = !done && u >= L;
         if (completed) {
             // the result: diagonal W holds D(L,L) (kept by the past-the-end cells)
@@ -264,18 +299,17 @@ dtw32_kernel(DtwJob32 job, int G) {
 #pragma unroll
             for (int c = 0; c < C; c++) r = (hasW && c == cW) ? R[c] : r;
             for (int off = 1; off < G; off <<= 1) r = fminf(r, __shfl_xor_sync(gmask, r, off, G));
-            res = r;
             if (gl == 0) {
-                if (job.out) job.out[pid] = res;
+                if (job.out) job.out[pid] = r;
                 if (job.bsf) {
-                    const unsigned long long key = pack_key(res, (uint32_t)tt);
+                    const unsigned long long key = pack_key(r, (uint32_t)tt);
                     const unsigned long long old = atomicMin(job.bsf + q, key);
                     const unsigned long long cur = old < key ? old : key;
                     const float ubn = upper32(key_dist(cur), job.dtw_hi, job.abs32);
-                    if (job.cand && lower32(res, job.dtw_lo, job.abs32) <= ubn) {
+                    if (job.cand && lower32(r, job.dtw_lo, job.abs32) <= ubn) {
                         const unsigned long long slot = atomicAdd(job.cand_count, 1ull);
                         Cand cd;
-                        cd.q = q; cd.t = tt; cd.d = res; cd.pad = 0;
+                        cd.q = q; cd.t = tt; cd.d = r; cd.pad = 0;
                         job.cand[slot] = cd;
                     }
                 }
@@ -284,18 +318,18 @@ dtw32_kernel(DtwJob32 job, int G) {
                               (unsigned long long)band_cells_upto(L, W, 2ll * L));
             }
             done = true;
-        } else if (!done && job.abandon) {
-            since_check += U;
-            if (since_check >= 16) {
-                since_check = 0;
-                float mn = R[0];
+        }
+        if (job.abandon && ((wblk / U) % kCheckBlocks) == 0) {
+            // the whole warp reduces (uniform); each running group decides
+            float mn = R[0];
 #pragma unroll
-                for (int c = 1; c < C; c++) mn = fminf(mn, R[c]);
-                for (int off = 1; off < G; off <<= 1)
-                    mn = fminf(mn, __shfl_xor_sync(gmask, mn, off, G));
-                if (job.bsf) {
-                    const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
-                    if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
+            for (int c = 1; c < C; c++) mn = fminf(mn, R[c]);
+            for (int off = 1; off < G; off <<= 1)
+                mn = fminf(mn, __shfl_xor_sync(FULL, mn, off, G));
+            if (!done) {
+                if (check_bsf) {
+                    if (kb != ~0u) ub = upper32(__uint_as_float(kb), job.dtw_hi, job.abs32);
+                    kb = bsf_dist_bits(job.bsf, q);
                 }
                 if (lower32(mn, job.dtw_lo, job.abs32) > ub) {
                     if (gl == 0 && job.counters) {

@@ -3,29 +3,126 @@
 //
 // Lane g owns C consecutive columns j = gC .. gC+C-1 of the cost matrix and
 // keeps their training values B_j and their latest D values in registers.
-// The query values stream through the warp: row i reaches lane g at step
-// i + g (one shuffle per step), so at every step lane g updates row s - g
-// of its columns, needing from lane g-1 only that row's value in column
-// gC-1 (computed at the previous step, one shuffle) and the row above's
-// (kept from the step before).  Unlike the diagonal layout used for banded
+// The columns of a lane form two halves (K = 2; one when C < 4), each a
+// dependency chain along its row, and the second half runs one row behind
+// the first so that the two chains are independent.  The query values
+// stream through the warp: the first half of lane g works on row s - K g at
+// step s, needing from lane g-1 only that row's value in column gC-1
+// (computed at the previous step, one shuffle) and the row above's (kept
+// from the step before).  Unlike the diagonal layout used for banded
 // windows, no cell outside the L x L matrix is ever swept, so a full window
-// costs L (L + 31) lane-cells per pair instead of about 2 L^2.  Lanes update
-// only rows 0..L-1, so after the sweep the lane owning column L-1 still
-// holds D(L-1, L-1).  Early abandoning takes the minimum over the last
-// computed row of every column block together with, for each block, the
-// cell of the row above it in the previous block's last column: a warping
-// path leaves the computed region either from a block's last computed row
-// or by a diagonal step out of that cell, so one of them lies on every path.
+// costs L (L + 32K - 1) lane-cells per pair instead of about 2 L^2.  Rows
+// past L-1 are never updated, so after the sweep the lane owning column L-1
+// still holds D(L-1, L-1).
 #include <utility>
 
 #include "dtw32.cuh"
 
 namespace nndtw {
 
-template <int C>
-__global__ void __launch_bounds__(128)
-dtw32_rows_kernel(DtwJob32 job) {
+// Resident 128-thread blocks per SM asked of the register allocator for C
+// columns per lane (the kernel needs about 2C + 55 registers); from a compile
+// sweep, the largest count without spills.
+__host__ __device__ constexpr int rows_min_blocks(int C) {
+    return C <= 15 ? 6 : C <= 18 ? 5 : C <= 30 ? 4 : C <= 44 ? 3 : 2;
+}
+
+// One step of one lane.  The first half of its columns (0..C0-1) advances to
+// row i0 = s - K g, the second half (C0..C-1, when K = 2) to row i0 - 1; each
+// half is a chain D[c] = fma(d, d, min3(D_up, D_left, D_diag)) along its
+// columns, and the two chains are independent.  Rows before the start see
+// the query sentinel and stay +inf; in the drain (DRAIN: some rows past
+// L-1) a half whose row is past the end keeps its values.
+template <int C, int K, int C0, bool DRAIN>
+__device__ __forceinline__ void rows_advance(float (&D)[C], const float (&B)[C], float &a0,
+                                             float &a1, float &qa, float &qn, float &diag_in,
+                                             float &h0prev, const float *ap, int s, int lane,
+                                             int L) {
+    const unsigned FULL = 0xffffffffu;
     const float INF = inf_of<float>();
+    // the query: lane g's new first-half value is the one lane g-1's last
+    // half used at the last step; lane 0 takes a[s] from the chunk
+    float a_in = __shfl_up_sync(FULL, K == 2 ? a1 : a0, 1);
+    const float feed = __shfl_sync(FULL, qa, s & 31);
+    if (lane == 0) a_in = feed;
+    if (K == 2) a1 = a0;
+    a0 = a_in;
+    if ((s & 31) == 31) {
+        qa = qn;
+        const int idx = s + 33 + lane;
+        qn = idx < L ? ap[idx] : 0.f;
+    }
+    // first half: D(i0, gC-1) and D(i0-1, gC-1) from lane g-1's last column
+    float left0 = __shfl_up_sync(FULL, D[C - 1], 1);
+    const int i0 = s - K * lane;
+    float diag0 = diag_in;
+    if (lane == 0) {
+        left0 = INF;
+        diag0 = (i0 == 0) ? 0.f : INF;
+    }
+    diag_in = left0;
+    // second half: the first half's last column one and two rows up
+    const float left1 = D[C0 - 1];
+    const float diag1 = h0prev;
+    if (K == 2) h0prev = left1;
+    const bool run0 = !DRAIN || i0 < L;
+    const bool run1 = !DRAIN || i0 - 1 < L;
+    float l0 = left0, dg0 = diag0, l1 = left1, dg1 = diag1;
+#pragma unroll
+    for (int c = 0; c < C0; c++) {
+        if (run0) {
+            const float old = D[c];
+            const float d = a0 - B[c];
+            D[c] = fmaf(d, d, min3f(old, l0, dg0));
+            dg0 = old;
+            l0 = D[c];
+        }
+        if (K == 2 && C0 + c < C && run1) {
+            const float old = D[C0 + c];
+            const float d = a1 - B[C0 + c];
+            D[C0 + c] = fmaf(d, d, min3f(old, l1, dg1));
+            dg1 = old;
+            l1 = D[C0 + c];
+        }
+    }
+}
+
+// Early abandoning.  The computed cells form a staircase whose row extent
+// drops by at most one from each half-block of columns to the next, so every
+// warping path leaves it from a half-block's last computed row, or
+// diagonally out of the cell one row above that in the previous half-block's
+// last column (h0prev inside a lane, diag_in across lanes).  The minimum over
+// those cells is a lower bound of D(L-1, L-1); scaled down by the FP32
+// margin, a value above the query's upper bound abandons the pair.  The
+// bound uses the query best read at the previous check and requests the
+// next one.
+template <int C>
+__device__ __forceinline__ bool rows_cut_exceeds(const float (&D)[C], float diag_in, float h0prev,
+                                                 unsigned &kb, float &ub, const DtwJob32 &job,
+                                                 int q) {
+    float mn = fminf(diag_in, h0prev);
+#pragma unroll
+    for (int c = 0; c < C; c++) mn = fminf(mn, D[c]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    if (job.bsf) {
+        if (kb != ~0u) ub = upper32(__uint_as_float(kb), job.dtw_hi, job.abs32);
+        kb = bsf_dist_bits(job.bsf, q);
+    }
+    return lower32(mn, job.dtw_lo, job.abs32) > ub;
+}
+
+template <int C>
+__global__ void __launch_bounds__(128, rows_min_blocks(C))
+dtw32_rows_kernel(DtwJob32 job) {
+    // K independent dependency chains per lane: with K = 2 the lane's columns
+    // are split into halves, the second half one row behind the first.
+    constexpr int K = C >= 4 ? 2 : 1;
+    constexpr int C0 = K == 2 ? (C + 1) / 2 : C;   // columns of the first half
+    const float INF = inf_of<float>();
+    const float APAD = -Pad<float>::v;   // query before the start: delta = +inf
+    const unsigned FULL = 0xffffffffu;
     const int L = job.L;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -33,33 +130,41 @@ dtw32_rows_kernel(DtwJob32 job) {
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
     const int last_lane = (L - 1) / C, last_c = (L - 1) % C;
-    long long next_static = warp_g;
+    const bool check_bsf = job.abandon && job.bsf;
+
+    // Claims run two pairs ahead so that no memory latency sits between two
+    // sweeps: p1 is the next pair (its item w1 already requested).
+    long long nxt = warp_g;   // next static index, or lane 0's claim in flight
+    long long p1;
+    if (job.head) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(job.head, 1ull);
+        p1 = (long long)__shfl_sync(FULL, v, 0);
+        if (lane == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+    } else {
+        p1 = nxt;
+        nxt += n_warps;
+    }
+    uint2 w1 = work_item(job, p1, n_work);
 
     while (true) {
-        long long p;
-        if (job.head) {
-            unsigned long long v = 0;
-            if (lane == 0) v = atomicAdd(job.head, 1ull);
-            p = (long long)__shfl_sync(0xffffffffu, v, 0);
-        } else {
-            p = next_static;
-            next_static += n_warps;
-        }
+        const long long p = p1;
         if (p >= n_work) break;
-        int q, t;
-        if (job.pairs) {
-            const uint2 pr = job.pairs[p];
-            q = (int)pr.x; t = (int)pr.y;
+        const int q = (int)w1.x, t = (int)w1.y;
+        if (job.head) {
+            p1 = __shfl_sync(FULL, nxt, 0);
+            if (lane == 0) nxt = (long long)atomicAdd(job.head, 1ull);
         } else {
-            q = (int)p; t = (int)key_idx(job.seed_keys[p]);
+            p1 = nxt;
+            nxt += n_warps;
         }
+        w1 = work_item(job, p1, n_work);
+
         const float *ap = job.test + (long long)q * L;
         const float *bp = job.train + (long long)t * L;
+        unsigned kb = ~0u;
+        if (check_bsf) kb = bsf_dist_bits(job.bsf, q);
         float ub = INF;
-        if (job.abandon && job.bsf) {
-            const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
-            if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
-        }
         if (lane == 0 && job.counters) atomicAdd(job.counters + C_STARTED, 1ull);
 
         float B[C], D[C];
@@ -69,70 +174,54 @@ dtw32_rows_kernel(DtwJob32 job) {
             B[c] = j < L ? bp[j] : Pad<float>::v;   // columns past L: delta = +inf
             D[c] = INF;
         }
-        float a_cur = 0.f;                 // query value of this lane's current row
-        float a_next = ap[0];              // lane 0's value for the next step
-        float diag_in = INF;               // D(i-1, gC-1) from lane g-1
+        // The query enters at lane 0, one value per step, from 32-value chunks
+        // held one per lane (qa: the current chunk, qn: the next, requested a
+        // chunk ahead).
+        float qa = lane < L ? ap[lane] : 0.f;
+        float qn = 32 + lane < L ? ap[32 + lane] : 0.f;
+        float a0 = APAD, a1 = APAD;        // query values of the halves' rows
+        float diag_in = INF;               // D(i0-1, gC-1) from lane g-1
+        float h0prev = INF;                // first half's last column, one row up
         bool abandoned = false;
-        const int steps = L + 31;
+        const int steps = L + 32 * K - 1;
         int s = 0;
-        for (; s < steps; s++) {
-            // stream the query: lane g receives lane g-1's value of the last step
-            float a_in = __shfl_up_sync(0xffffffffu, a_cur, 1);
-            if (lane == 0) {
-                a_in = a_next;
-                a_next = (s + 1 < L) ? ap[s + 1] : 0.f;
+        // every row is below L while s < L; the drain runs the remaining steps
+        for (; s < L; s++) {
+            rows_advance<C, K, C0, false>(D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s, lane, L);
+            if (job.abandon && (s & 15) == 15 &&
+                rows_cut_exceeds<C>(D, diag_in, h0prev, kb, ub, job, q)) {
+                abandoned = true;
+                break;
             }
-            a_cur = a_in;
-            // row s - lane of column gC-1 from lane g-1 (computed last step)
-            float left = __shfl_up_sync(0xffffffffu, D[C - 1], 1);
-            const int i = s - lane;
-            float diag = diag_in;
-            if (lane == 0) {
-                left = INF;
-                diag = (i == 0) ? 0.f : INF;
-            }
-            diag_in = left;
-            if (i >= 0 && i < L) {
-                float l = left, dg = diag;
-#pragma unroll
-                for (int c = 0; c < C; c++) {
-                    const float old = D[c];
-                    const float d = a_cur - B[c];
-                    D[c] = fmaf(d, d, min3f(old, l, dg));
-                    dg = old;
-                    l = D[c];
+        }
+        if (!abandoned) {
+            for (; s < steps; s++) {
+                rows_advance<C, K, C0, true>(D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s, lane,
+                                             L);
+                if (job.abandon && (s & 15) == 15 &&
+                    rows_cut_exceeds<C>(D, diag_in, h0prev, kb, ub, job, q)) {
+                    abandoned = true;
+                    break;
                 }
-            }
-            if (job.abandon && (s & 15) == 15) {
-                // the cut: every lane's last computed row, plus the row above
-                // in the last column of the lane to its left (diag_in), through
-                // which a path can leave diagonally
-                float mn = diag_in;
-#pragma unroll
-                for (int c = 0; c < C; c++) mn = fminf(mn, D[c]);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-                    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-                if (job.bsf) {
-                    const unsigned long long kb = *((volatile unsigned long long *)job.bsf + q);
-                    if (kb != ~0ull) ub = upper32(key_dist(kb), job.dtw_hi, job.abs32);
-                }
-                if (lower32(mn, job.dtw_lo, job.abs32) > ub) { abandoned = true; break; }
             }
         }
         float res = INF;
 #pragma unroll
         for (int c = 0; c < C; c++) res = (lane == last_lane && c == last_c) ? D[c] : res;
-        res = __shfl_sync(0xffffffffu, res, last_lane);
+        res = __shfl_sync(FULL, res, last_lane);
         if (lane == 0) {
             if (job.counters) {
                 long long cells = (long long)L * L;
-                if (abandoned) {   // lane g finished rows 0 .. min(s-g, L-1) of its columns
+                if (abandoned) {   // half-block b of lane g finished rows 0 .. s - K g - b
                     cells = 0;
                     for (int g = 0; g < 32; g++) {
-                        const int cols = min(max(L - g * C, 0), C);
-                        const int rows = min(s - g, L - 1) + 1;
-                        if (rows > 0) cells += (long long)cols * rows;
+                        for (int h = 0; h < K; h++) {
+                            const int lo = g * C + (h ? C0 : 0);
+                            const int hi = g * C + (h ? C : C0);
+                            const int cols = min(max(L - lo, 0), hi - lo);
+                            const int rows = min(s - (K * g + h), L - 1) + 1;
+                            if (rows > 0 && cols > 0) cells += (long long)cols * rows;
+                        }
                     }
                 }
                 atomicAdd(job.counters + C_CELLS, (unsigned long long)cells);
