@@ -169,9 +169,11 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
+_DTW_SOURCES = ["paper_1808_09617_gb300/csrc/dtw32.cuh", "paper_1808_09617_gb300/csrc/dtw32_launch.cu",
+                "paper_1808_09617_gb300/csrc/dtw32_rows.cu", "paper_1808_09617_gb300/csrc/dtw32_wide.cu"]
 STAGE_SOURCES = {
-    "dtw": ["paper_1808_09617_gb300/csrc/dtw32.cuh", "paper_1808_09617_gb300/csrc/dtw32_launch.cu"],
-    "seed": ["paper_1808_09617_gb300/csrc/dtw32.cuh", "paper_1808_09617_gb300/csrc/dtw32_launch.cu"],
+    "dtw": _DTW_SOURCES,
+    "seed": _DTW_SOURCES,
     "lb": ["paper_1808_09617_gb300/csrc/lb.cu"],
     "envelopes": ["paper_1808_09617_gb300/csrc/envelope.cu"],
 }

@@ -9,7 +9,8 @@
 // stream through the warp: the first half of lane g works on row s - K g at
 // step s, needing from lane g-1 only that row's value in column gC-1
 // (computed at the previous step, one shuffle) and the row above's (kept
-// from the step before).  Unlike the diagonal layout used for banded
+// from the step before).  The row values alternate between two register
+// arrays, two steps per loop iteration, so that no value is ever copied.  Unlike the diagonal layout used for banded
 // windows, no cell outside the L x L matrix is ever swept, so a full window
 // costs L (L + 32K - 1) lane-cells per pair instead of about 2 L^2.  Rows
 // past L-1 are never updated, so after the sweep the lane owning column L-1
@@ -21,23 +22,25 @@
 namespace nndtw {
 
 // Resident 128-thread blocks per SM asked of the register allocator for C
-// columns per lane (the kernel needs about 2C + 55 registers); from a compile
+// columns per lane (the kernel needs about 2C + 80 registers); from a compile
 // sweep, the largest count without spills.
 __host__ __device__ constexpr int rows_min_blocks(int C) {
-    return C <= 15 ? 6 : C <= 18 ? 5 : C <= 30 ? 4 : C <= 44 ? 3 : 2;
+    return C <= 12 ? 6 : C <= 15 ? 5 : C <= 25 ? 4 : C <= 38 ? 3 : 2;
 }
 
-// One step of one lane.  The first half of its columns (0..C0-1) advances to
-// row i0 = s - K g, the second half (C0..C-1, when K = 2) to row i0 - 1; each
-// half is a chain D[c] = fma(d, d, min3(D_up, D_left, D_diag)) along its
-// columns, and the two chains are independent.  Rows before the start see
-// the query sentinel and stay +inf; in the drain (DRAIN: some rows past
-// L-1) a half whose row is past the end keeps its values.
+// One step of one lane, from the row values in Din to those in Dout (two
+// register arrays used in turn, so that no value is copied between steps).
+// The first half of the lane's columns (0..C0-1) advances to row
+// i0 = s - K g, the second half (C0..C-1, when K = 2) to row i0 - 1; each
+// half is a chain Dout[c] = fma(d, d, min3(Din[c], Dout[c-1], Din[c-1]))
+// along its columns, and the two chains are independent.  Rows before the
+// start see the query sentinel and come out +inf; in the drain (DRAIN: some
+// rows past L-1) a half whose row is past the end passes its values on.
 template <int C, int K, int C0, bool DRAIN>
-__device__ __forceinline__ void rows_advance(float (&D)[C], const float (&B)[C], float &a0,
-                                             float &a1, float &qa, float &qn, float &diag_in,
-                                             float &h0prev, const float *ap, int s, int lane,
-                                             int L) {
+__device__ __forceinline__ void rows_advance(const float (&Din)[C], float (&Dout)[C],
+                                             const float (&B)[C], float &a0, float &a1,
+                                             float &qa, float &qn, float &diag_in, float &h0prev,
+                                             const float *ap, int s, int lane, int L) {
     const unsigned FULL = 0xffffffffu;
     const float INF = inf_of<float>();
     // the query: lane g's new first-half value is the one lane g-1's last
@@ -53,7 +56,7 @@ __device__ __forceinline__ void rows_advance(float (&D)[C], const float (&B)[C],
         qn = idx < L ? ap[idx] : 0.f;
     }
     // first half: D(i0, gC-1) and D(i0-1, gC-1) from lane g-1's last column
-    float left0 = __shfl_up_sync(FULL, D[C - 1], 1);
+    float left0 = __shfl_up_sync(FULL, Din[C - 1], 1);
     const int i0 = s - K * lane;
     float diag0 = diag_in;
     if (lane == 0) {
@@ -62,27 +65,25 @@ __device__ __forceinline__ void rows_advance(float (&D)[C], const float (&B)[C],
     }
     diag_in = left0;
     // second half: the first half's last column one and two rows up
-    const float left1 = D[C0 - 1];
+    const float left1 = Din[C0 - 1];
     const float diag1 = h0prev;
     if (K == 2) h0prev = left1;
     const bool run0 = !DRAIN || i0 < L;
     const bool run1 = !DRAIN || i0 - 1 < L;
-    float l0 = left0, dg0 = diag0, l1 = left1, dg1 = diag1;
 #pragma unroll
     for (int c = 0; c < C0; c++) {
-        if (run0) {
-            const float old = D[c];
+        {
             const float d = a0 - B[c];
-            D[c] = fmaf(d, d, min3f(old, l0, dg0));
-            dg0 = old;
-            l0 = D[c];
+            const float v = fmaf(d, d, min3f(Din[c], c == 0 ? left0 : Dout[c - 1],
+                                             c == 0 ? diag0 : Din[c - 1]));
+            Dout[c] = run0 ? v : Din[c];
         }
-        if (K == 2 && C0 + c < C && run1) {
-            const float old = D[C0 + c];
-            const float d = a1 - B[C0 + c];
-            D[C0 + c] = fmaf(d, d, min3f(old, l1, dg1));
-            dg1 = old;
-            l1 = D[C0 + c];
+        if (K == 2 && C0 + c < C) {
+            const int e = C0 + c;
+            const float d = a1 - B[e];
+            const float v = fmaf(d, d, min3f(Din[e], c == 0 ? left1 : Dout[e - 1],
+                                             c == 0 ? diag1 : Din[e - 1]));
+            Dout[e] = run1 ? v : Din[e];
         }
     }
 }
@@ -167,7 +168,7 @@ dtw32_rows_kernel(DtwJob32 job) {
         float ub = INF;
         if (lane == 0 && job.counters) atomicAdd(job.counters + C_STARTED, 1ull);
 
-        float B[C], D[C];
+        float B[C], D[C], E[C];
 #pragma unroll
         for (int c = 0; c < C; c++) {
             const int j = lane * C + c;
@@ -184,21 +185,27 @@ dtw32_rows_kernel(DtwJob32 job) {
         float h0prev = INF;                // first half's last column, one row up
         bool abandoned = false;
         const int steps = L + 32 * K - 1;
-        int s = 0;
-        // every row is below L while s < L; the drain runs the remaining steps
-        for (; s < L; s++) {
-            rows_advance<C, K, C0, false>(D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s, lane, L);
-            if (job.abandon && (s & 15) == 15 &&
+        // Two steps per iteration (D -> E -> D); every row is below L while
+        // s + 1 < L, and the drain runs the remaining steps (a step past the
+        // last one changes nothing).  Checks every 8 iterations.
+        int s = 0, it = 0;
+        for (; s + 1 < L; s += 2) {
+            rows_advance<C, K, C0, false>(D, E, B, a0, a1, qa, qn, diag_in, h0prev, ap, s, lane, L);
+            rows_advance<C, K, C0, false>(E, D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s + 1,
+                                          lane, L);
+            if (job.abandon && (++it & 7) == 0 &&
                 rows_cut_exceeds<C>(D, diag_in, h0prev, kb, ub, job, q)) {
                 abandoned = true;
                 break;
             }
         }
         if (!abandoned) {
-            for (; s < steps; s++) {
-                rows_advance<C, K, C0, true>(D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s, lane,
-                                             L);
-                if (job.abandon && (s & 15) == 15 &&
+            for (; s < steps; s += 2) {
+                rows_advance<C, K, C0, true>(D, E, B, a0, a1, qa, qn, diag_in, h0prev, ap, s,
+                                             lane, L);
+                rows_advance<C, K, C0, true>(E, D, B, a0, a1, qa, qn, diag_in, h0prev, ap, s + 1,
+                                             lane, L);
+                if (job.abandon && (++it & 7) == 0 &&
                     rows_cut_exceeds<C>(D, diag_in, h0prev, kb, ub, job, q)) {
                     abandoned = true;
                     break;
@@ -212,14 +219,14 @@ dtw32_rows_kernel(DtwJob32 job) {
         if (lane == 0) {
             if (job.counters) {
                 long long cells = (long long)L * L;
-                if (abandoned) {   // half-block b of lane g finished rows 0 .. s - K g - b
+                if (abandoned) {   // half-block b of lane g finished rows 0 .. s+1 - K g - b
                     cells = 0;
                     for (int g = 0; g < 32; g++) {
                         for (int h = 0; h < K; h++) {
                             const int lo = g * C + (h ? C0 : 0);
                             const int hi = g * C + (h ? C : C0);
                             const int cols = min(max(L - lo, 0), hi - lo);
-                            const int rows = min(s - (K * g + h), L - 1) + 1;
+                            const int rows = min(s + 1 - (K * g + h), L - 1) + 1;
                             if (rows > 0 && cols > 0) cells += (long long)cols * rows;
                         }
                     }

@@ -77,8 +77,11 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     T2 *Es = reinterpret_cast<T2 *>(As + kLC * (kQT + 1) + 1);    // [kLC][kNT+1] (aligned below)
     Es = reinterpret_cast<T2 *>((reinterpret_cast<uintptr_t>(Es) + 15) & ~uintptr_t(15));
     T *Bs = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kLC][kNT+1] (ED only)
-    T *Ab = Bs + (ED ? kLC * (kNT + 1) : 0);                       // [kQT][2nb]
-    T *Bb = Ab + kQT * 2 * (nb <= kNBMax ? nb : 0);                // [kNT][2nb]
+    // band staging, rows padded to an odd stride so that the 16 series a
+    // warp reads at once fall in distinct banks
+    const int bstride = 2 * nb + 1;
+    T *Ab = Bs + (ED ? kLC * (kNT + 1) : 0);                       // [kQT][2nb+1]
+    T *Bb = Ab + kQT * (nb <= kNBMax ? bstride : 0);               // [kNT][2nb+1]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t q0 = (int64_t)blockIdx.y * kQT, t0 = (int64_t)blockIdx.x * kNT;
@@ -157,13 +160,13 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
                 const int row = idx / w2, m = idx % w2;
                 const int i = m < nb ? m : L - w2 + m;
                 const int64_t q = q0 + row;
-                Ab[idx] = q < Q ? test[q * L + i] : T(0);
+                Ab[row * bstride + m] = q < Q ? test[q * L + i] : T(0);
             }
             for (int idx = tid; idx < kNT * w2; idx += kThreads) {
                 const int row = idx / w2, m = idx % w2;
                 const int i = m < nb ? m : L - w2 + m;
                 const int64_t t = t0 + row;
-                Bb[idx] = t < N ? train[t * L + i] : T(0);
+                Bb[row * bstride + m] = t < N ? train[t * L + i] : T(0);
             }
             __syncthreads();
         }
@@ -171,12 +174,12 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
         for (int r = 0; r < MR; r++) {
             const int64_t q = q0 + ty + 16 * r;
             const T *Ag = test + (q < Q ? q : 0) * L;
-            const T *Asg = Ab + (ty + 16 * r) * 2 * nb;
+            const T *Asg = Ab + (ty + 16 * r) * bstride;
 #pragma unroll
             for (int c = 0; c < MC; c++) {
                 const int64_t t = t0 + tx + 16 * c;
                 const T *Bg = train + (t < N ? t : 0) * L;
-                const T *Bsg = Bb + (tx + 16 * c) * 2 * nb;
+                const T *Bsg = Bb + (tx + 16 * c) * bstride;
                 // element i (0-based, in the first or last nb) of A and B:
                 // staged copies hold the first nb then the last nb elements
                 const T *Ap = staged ? Asg : Ag;
@@ -240,7 +243,7 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     const bool ed = seed_keys != nullptr;
     size_t smem = sizeof(T) * (kLC * (kQT + 1) + 1) + 16 + sizeof(T2) * kLC * (kNT + 1);
     if (ed) smem += sizeof(T) * kLC * (kNT + 1);
-    if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * 2 * nb;
+    if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * (2 * nb + 1);
     auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
