@@ -74,8 +74,14 @@ extern "C" {
 #define NNDTW_DTW_GROUP_MASK (7u << 8)
 /* search / dtw_windowed: for full windows (W >= L-1, L <= 2048) sweep DTW by
  * rows, one pair per warp (the default for such windows when no
- * NNDTW_DTW_GROUP is given); ignored for other windows. */
+ * NNDTW_DTW_GROUP is given); ignored for other windows.  Combined with
+ * NNDTW_DTW_ROWS_LANES16 (L <= 1024) or NNDTW_DTW_ROWS_LANES8 (L <= 512) a
+ * pair takes 16 or 8 lanes instead (a tuning choice; results never change;
+ * ignored where L is too long). */
 #define NNDTW_DTW_ROWS (7u << 8)
+#define NNDTW_DTW_ROWS_LANES16 (1u << 12)
+#define NNDTW_DTW_ROWS_LANES8 (2u << 12)
+#define NNDTW_DTW_ROWS_LANES_MASK (3u << 12)
 
 /* stage indices of nn_dtw_stage_times() */
 #define NNDTW_STAGE_ENVELOPES 0 /* S1 (0 when envelopes are supplied)            */

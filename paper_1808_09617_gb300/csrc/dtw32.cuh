@@ -320,26 +320,26 @@ dtw32_kernel(DtwJob32 job, int G) {
             done = true;
         }
         if (job.abandon && ((wblk / U) % kCheckBlocks) == 0) {
-            // the whole warp reduces (uniform); each running group decides
+            // The whole warp reduces; each running group decides with selects
+            // rather than branches (branches here cost register copies in
+            // the sweep).  The bound uses the query best read at the last
+            // check and requests the next one.
             float mn = R[0];
 #pragma unroll
             for (int c = 1; c < C; c++) mn = fminf(mn, R[c]);
             for (int off = 1; off < G; off <<= 1)
                 mn = fminf(mn, __shfl_xor_sync(FULL, mn, off, G));
-            if (!done) {
-                if (check_bsf) {
-                    if (kb != ~0u) ub = upper32(__uint_as_float(kb), job.dtw_hi, job.abs32);
-                    kb = bsf_dist_bits(job.bsf, q);
-                }
-                if (lower32(mn, job.dtw_lo, job.abs32) > ub) {
-                    if (gl == 0 && job.counters) {
-                        atomicAdd(job.counters + C_ABANDONED, 1ull);
-                        atomicAdd(job.counters + C_CELLS,
-                                  (unsigned long long)band_cells_upto(L, W, 2ll * u + t_first - 1));
-                    }
-                    done = true;
-                }
+            const unsigned kbn = check_bsf ? bsf_dist_bits(job.bsf, q) : ~0u;
+            const float ubn = kb != ~0u ? upper32(__uint_as_float(kb), job.dtw_hi, job.abs32) : ub;
+            ub = done ? ub : ubn;
+            kb = done ? kb : kbn;
+            const bool drop = !done && lower32(mn, job.dtw_lo, job.abs32) > ub;
+            if (drop && gl == 0 && job.counters) {
+                atomicAdd(job.counters + C_ABANDONED, 1ull);
+                atomicAdd(job.counters + C_CELLS,
+                          (unsigned long long)band_cells_upto(L, W, 2ll * u + t_first - 1));
             }
+            done = done || drop;
         }
     }
 }

@@ -64,7 +64,11 @@ bool dtw32_supported(int W) { return W >= 0 && W < NNDTW_MAX_L; }
 
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
     // full windows: the row kernel, unless a diagonal group width is asked for
-    if ((job.group == 0 || job.group == kRowsGroup) && dtw32_rows_ok(job.L, job.W))
+    if (job.group == kRowsGroup + 1 && dtw32_rowsg_ok(job.L, job.W, 16))
+        return launch_dtw32_rowsg(job, 16, sm_count, s);
+    if (job.group == kRowsGroup + 2 && dtw32_rowsg_ok(job.L, job.W, 8))
+        return launch_dtw32_rowsg(job, 8, sm_count, s);
+    if ((job.group == 0 || job.group >= kRowsGroup) && dtw32_rows_ok(job.L, job.W))
         return launch_dtw32_rows(job, sm_count, s);
     int G = 0, H = 0;
     if (!dtw32_shape(job.W, job.group, &G, &H)) return launch_dtw32_wide(job, sm_count, s);

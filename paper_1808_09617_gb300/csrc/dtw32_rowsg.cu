@@ -1,0 +1,264 @@
+// FP32 DTW (Sec. 2.1, Eq. 1) for full windows (W >= L-1), laid out by rows
+// with a group of G = 8 or 16 lanes per pair (32 / G pairs per warp),
+// L <= 64 G.
+//
+// The same row layout as the one-pair-per-warp kernel: lane g of a group
+// owns C consecutive columns, split into two independent halves one row
+// apart, and the rows stream through the group.  With fewer lanes per pair
+// the wavefront fills in 2G steps instead of 64, which is what matters when
+// most pairs are abandoned after a few dozen rows.  The pairs of a warp
+// advance independently, so everything that differs between them is kept
+// out of the step loop:
+//  - the G C columns are placed so that column L-1 is the last column of
+//    the last lane; the G C - L columns in front of column 0 hold a
+//    training sentinel (their cells are +inf).  The one just before column
+//    0 starts at 0, which is D(-1,-1) for cell (0,0), and holds the query's
+//    own sentinel, so that the rows before the start (which see that
+//    sentinel) give it delta = 0 and keep the 0 until row 0 reads it;
+//  - the query enters at the group's lane 0 from a load one step ahead,
+//    clamped to the series (rows past L-1 are never used);
+//  - the result is picked from the last lane when its second half finishes
+//    row L-1 (a select, no branch);
+//  - pairs start, finish and are abandoned only every 16 steps (claims,
+//    completion and the abandon test), at the same step for the whole warp.
+// Abandoning uses the staircase cut of the one-pair-per-warp kernel; it is
+// only tested while every computed row is below L (the drain after that
+// sweeps rows past the end, whose values are never used).
+#include <utility>
+
+#include "dtw32.cuh"
+
+namespace nndtw {
+namespace {
+
+__host__ __device__ constexpr int rowsg_min_blocks(int C) {
+    return C <= 12 ? 6 : C <= 15 ? 5 : C <= 25 ? 4 : C <= 38 ? 3 : 2;
+}
+
+// One step of one lane from Din to Dout: the first half of its columns
+// advances to row i0 = s - K gl, the second half to row i0 - 1.
+template <int C, int K, int C0>
+__device__ __forceinline__ void rowsg_step(const float (&Din)[C], float (&Dout)[C],
+                                           const float (&B)[C], float &a0, float &a1,
+                                           float &anext, float &diag_in, float &h0prev,
+                                           const float *ap, int s, int gl, int G, int L) {
+    const unsigned FULL = 0xffffffffu;
+    const float INF = inf_of<float>();
+    float a_in = __shfl_up_sync(FULL, K == 2 ? a1 : a0, 1, G);
+    if (gl == 0) a_in = anext;                 // query value a[s]
+    anext = ap[min(s + 1, L - 1)];             // the next one (clamped)
+    if (K == 2) a1 = a0;
+    a0 = a_in;
+    float left0 = __shfl_up_sync(FULL, Din[C - 1], 1, G);
+    const int i0 = s - K * gl;
+    float diag0 = diag_in;
+    if (gl == 0) {
+        left0 = INF;
+        diag0 = (i0 == 0) ? 0.f : INF;
+    }
+    diag_in = left0;
+    const float left1 = Din[C0 - 1];
+    const float diag1 = h0prev;
+    if (K == 2) h0prev = left1;
+#pragma unroll
+    for (int c = 0; c < C0; c++) {
+        {
+            const float d = a0 - B[c];
+            Dout[c] = fmaf(d, d, min3f(Din[c], c == 0 ? left0 : Dout[c - 1],
+                                       c == 0 ? diag0 : Din[c - 1]));
+        }
+        if (K == 2 && C0 + c < C) {
+            const int e = C0 + c;
+            const float d = a1 - B[e];
+            Dout[e] = fmaf(d, d, min3f(Din[e], c == 0 ? left1 : Dout[e - 1],
+                                       c == 0 ? diag1 : Din[e - 1]));
+        }
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(128, rowsg_min_blocks(C))
+dtw32_rowsg_kernel(DtwJob32 job, int G) {
+    constexpr int K = C >= 4 ? 2 : 1;
+    constexpr int C0 = K == 2 ? (C + 1) / 2 : C;
+    const float INF = inf_of<float>();
+    const float APAD = -Pad<float>::v;   // query before the start: delta = +inf
+    const float BPAD = Pad<float>::v;    // columns in front of column 0
+    const unsigned FULL = 0xffffffffu;
+    const int L = job.L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int off = G * C - L;                 // padding columns before column 0
+    const int steps_total = L + K * G - 1;     // the last half finishes row L-1 at step steps_total-1
+    const int s_final = steps_total - 1;
+    const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
+                                       : job.n_seed;
+    const long long n_groups = (long long)gridDim.x * (blockDim.x / G);
+    const bool check_bsf = job.abandon && job.bsf;
+
+    // claims two pairs ahead per group (see the diagonal-layout kernel)
+    long long nxt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    long long p1;
+    if (job.head) {
+        unsigned long long v = 0;
+        if (gl == 0) v = atomicAdd(job.head, 1ull);
+        p1 = (long long)__shfl_sync(FULL, v, 0, G);
+        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+    } else {
+        p1 = nxt;
+        nxt += n_groups;
+    }
+    uint2 w1 = work_item(job, p1, n_work);
+
+    float B[C], D[C], E[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) { B[c] = BPAD; D[c] = INF; }
+    long long pid = -1;
+    int q = 0, t = 0, ws = 0, w = 0;
+    bool done = true, finished = false;
+    float ub = INF, res = INF;
+    unsigned kb = ~0u;
+    const float *ap = job.test;
+    float a0 = APAD, a1 = APAD, anext = 0.f, diag_in = INF, h0prev = INF;
+
+    while (true) {
+        // ---- start pairs (every 16 steps) ----------------------------------
+        const bool need = done && !finished;
+        if (__any_sync(FULL, need)) {
+            if (need) {
+                if (p1 >= n_work) {
+                    finished = true;
+                    pid = -1;
+                } else {
+                    pid = p1;
+                    q = (int)w1.x; t = (int)w1.y;
+                    if (job.head) {
+                        p1 = __shfl_sync(gmask, nxt, 0, G);
+                        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+                    } else {
+                        p1 = nxt;
+                        nxt += n_groups;
+                    }
+                    w1 = work_item(job, p1, n_work);
+                    ap = job.test + (long long)q * L;
+                    const float *bp = job.train + (long long)t * L;
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        const int j = gl * C + c - off;
+                        B[c] = j >= 0 ? bp[j] : (j == -1 ? APAD : BPAD);
+                        D[c] = j == -1 ? 0.f : INF;
+                    }
+                    a0 = APAD; a1 = APAD;
+                    anext = ap[0];
+                    diag_in = INF; h0prev = INF;
+                    res = INF; ub = INF;
+                    kb = check_bsf ? bsf_dist_bits(job.bsf, q) : ~0u;
+                    ws = w;
+                    done = false;
+                    if (job.counters && gl == 0) atomicAdd(job.counters + C_STARTED, 1ull);
+                }
+            }
+        }
+        if (__all_sync(FULL, finished)) break;
+
+        // ---- 16 steps, two per iteration (D -> E -> D) ---------------------
+#pragma unroll 1
+        for (int it = 0; it < 8; it++) {
+            const int s = w - ws;
+            rowsg_step<C, K, C0>(D, E, B, a0, a1, anext, diag_in, h0prev, ap, s, gl, G, L);
+            res = s == s_final ? E[C - 1] : res;
+            rowsg_step<C, K, C0>(E, D, B, a0, a1, anext, diag_in, h0prev, ap, s + 1, gl, G, L);
+            res = s + 1 == s_final ? D[C - 1] : res;
+            w += 2;
+        }
+        const int sd = w - ws;     // steps done in the current pair
+
+        // ---- completion -----------------------------------------------------
+        if (!done && sd >= steps_total) {
+            const float r = __shfl_sync(gmask, res, G - 1, G);
+            if (gl == 0) {
+                if (job.out) job.out[pid] = r;
+                if (job.bsf) {
+                    const unsigned long long key = pack_key(r, (uint32_t)t);
+                    const unsigned long long old = atomicMin(job.bsf + q, key);
+                    const unsigned long long cur = old < key ? old : key;
+                    const float ubn = upper32(key_dist(cur), job.dtw_hi, job.abs32);
+                    if (job.cand && lower32(r, job.dtw_lo, job.abs32) <= ubn) {
+                        const unsigned long long slot = atomicAdd(job.cand_count, 1ull);
+                        Cand cd;
+                        cd.q = q; cd.t = t; cd.d = r; cd.pad = 0;
+                        job.cand[slot] = cd;
+                    }
+                }
+                if (job.counters) atomicAdd(job.counters + C_CELLS, (unsigned long long)L * L);
+            }
+            done = true;
+        }
+
+        // ---- early abandoning (selects per group) ---------------------------
+        if (job.abandon) {
+            float mn = fminf(diag_in, h0prev);
+#pragma unroll
+            for (int c = 0; c < C; c++) mn = fminf(mn, D[c]);
+            for (int o = 1; o < G; o <<= 1) mn = fminf(mn, __shfl_xor_sync(FULL, mn, o, G));
+            const bool live = !done && sd <= L;    // every computed row is below L
+            const unsigned kbn = check_bsf ? bsf_dist_bits(job.bsf, q) : ~0u;
+            const float ubn = kb != ~0u ? upper32(__uint_as_float(kb), job.dtw_hi, job.abs32) : ub;
+            ub = live ? ubn : ub;
+            kb = live ? kbn : kb;
+            const bool drop = live && lower32(mn, job.dtw_lo, job.abs32) > ub;
+            if (drop && gl == 0 && job.counters) {
+                // half-block h of lane g has finished rows 0 .. sd-1 - (K g + h)
+                long long cells = 0;
+                for (int g = 0; g < G; g++) {
+                    for (int h = 0; h < K; h++) {
+                        const int lo = max(g * C + (h ? C0 : 0) - off, 0);
+                        const int hi = min(g * C + (h ? C : C0) - off, L);
+                        const int rows = min(sd - 1 - (K * g + h), L - 1) + 1;
+                        if (rows > 0 && hi > lo) cells += (long long)(hi - lo) * rows;
+                    }
+                }
+                atomicAdd(job.counters + C_ABANDONED, 1ull);
+                atomicAdd(job.counters + C_CELLS, (unsigned long long)cells);
+            }
+            done = done || drop;
+        }
+    }
+}
+
+using RowsGFn = void (*)(DtwJob32, int);
+template <int C> RowsGFn rowsg_fn() { return &dtw32_rowsg_kernel<C>; }
+template <int... Cs> RowsGFn pick_rowsg(int c, std::integer_sequence<int, Cs...>) {
+    RowsGFn fns[] = {rowsg_fn<Cs + 1>()...};
+    return (c >= 1 && c <= (int)sizeof...(Cs)) ? fns[c - 1] : nullptr;
+}
+
+}  // namespace
+
+bool dtw32_rowsg_ok(int L, int W, int G) {
+    return (G == 8 || G == 16) && W >= L - 1 && L >= 1 && L <= 64 * G;
+}
+
+cudaError_t launch_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, cudaStream_t s) {
+    if (!dtw32_rowsg_ok(job.L, job.W, G)) return cudaErrorNotSupported;
+    const int C = (job.L + G - 1) / G;
+    RowsGFn fn = pick_rowsg(C, std::make_integer_sequence<int, 64>{});
+    if (!fn) return cudaErrorNotSupported;
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    long long grid = (long long)sm_count * bps;
+    if (!job.pairs || !job.count) {
+        const long long n = job.pairs ? job.n_pairs : job.n_seed;
+        if (n <= 0) return cudaSuccess;
+        const long long per_block = 128 / G;
+        const long long need = (n + per_block - 1) / per_block;
+        if (need < grid) grid = need;
+    }
+    fn<<<(unsigned)grid, 128, 0, s>>>(job, G);
+    return cudaGetLastError();
+}
+
+}  // namespace nndtw

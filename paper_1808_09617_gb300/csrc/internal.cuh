@@ -117,8 +117,11 @@ struct DtwJob32 {
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_rows(const DtwJob32 &job, int sm_count, cudaStream_t s);
+bool dtw32_rowsg_ok(int L, int W, int G);
+cudaError_t launch_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, cudaStream_t s);
 bool dtw32_rows_ok(int L, int W);   // full window and L small enough for the row kernel
 constexpr int kRowsGroup = 64;      // DtwJob32::group value selecting the row kernel
+// kRowsGroup + 1 / + 2: the row layout with 16 / 8 lanes per pair
 bool dtw32_supported(int W);   // window W (<= L-1) fits the FP32 DTW kernel
 int dtw32_wide_group(int W);   // widest lanes-per-pair choice for W (latency-bound passes)
 

@@ -466,7 +466,7 @@ using namespace nndtw;
 
 extern "C" {
 
-int nn_dtw_version(void) { return 101; }
+int nn_dtw_version(void) { return 102; }
 
 int nn_dtw_stage_times(float *h_ms) {
     if (!h_ms || t_last_dev < 0) return NNDTW_EINVAL;
@@ -541,7 +541,10 @@ int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pai
 
 static int group_from_flags(unsigned flags) {
     const unsigned v = (flags & NNDTW_DTW_GROUP_MASK) >> 8;
-    if (v == 7) return kRowsGroup;
+    if (v == 7) {
+        const unsigned lanes = (flags & NNDTW_DTW_ROWS_LANES_MASK) >> 12;
+        return kRowsGroup + (lanes <= 2 ? (int)lanes : 0);
+    }
     return v ? 1 << (v - 1) : 0;
 }
 

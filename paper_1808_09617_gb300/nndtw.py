@@ -30,15 +30,26 @@ CHECK_FINITE = 1 << 5
 TIME_STAGES = 1 << 6
 
 
-ROWS_GROUP = 64        # tuning value meaning "row layout, one pair per warp"
+# Tuning values for full windows: the row layout with 32 lanes per pair (one
+# pair per warp), 16 lanes (L <= 1024) or 8 lanes (L <= 512).
+ROWS_GROUP = 64
+ROWS16_GROUP = 65
+ROWS8_GROUP = 66
 DTW_ROWS = 7 << 8
+DTW_ROWS_LANES16 = 1 << 12
+DTW_ROWS_LANES8 = 2 << 12
 
 
 def DTW_GROUP(g: int) -> int:
     """Flag selecting G lanes per pair in the FP32 DTW kernel's diagonal layout
-    (G = 1..32), or the row layout for full windows (G = ROWS_GROUP)."""
+    (G = 1..32), or the row layout for full windows (G = ROWS_GROUP,
+    ROWS16_GROUP or ROWS8_GROUP)."""
     if g == ROWS_GROUP:
         return DTW_ROWS
+    if g == ROWS16_GROUP:
+        return DTW_ROWS | DTW_ROWS_LANES16
+    if g == ROWS8_GROUP:
+        return DTW_ROWS | DTW_ROWS_LANES8
     if g < 1 or g > 32 or g & (g - 1):
         raise ValueError("G must be a power of two in 1..32")
     return (g.bit_length()) << 8

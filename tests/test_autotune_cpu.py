@@ -10,7 +10,9 @@ def test_admissible_groups():
     assert autotune.admissible_groups(1023) == [32]
     assert autotune.admissible_groups(1024) == []
     assert autotune.admissible_groups(100)[0] == 4
-    assert autotune.admissible_groups(255, 256)[-1] == 64    # full window: row layout too
+    assert autotune.admissible_groups(255, 256)[-3:] == [64, 65, 66]  # full window: row layouts
+    assert autotune.admissible_groups(599, 600)[-2:] == [64, 65]     # 8 lanes hold L <= 512
+    assert 65 not in autotune.admissible_groups(1999, 2000)          # 16 lanes hold L <= 1024
     assert 64 not in autotune.admissible_groups(100, 256)
     assert 64 not in autotune.admissible_groups(3000, 3001)  # beyond the row kernel's 2048
 

@@ -268,7 +268,7 @@ def test_dtw_every_group_width_same_values(lib, orc, L, W):
     rng = np.random.default_rng(W)
     pairs = np.stack([rng.integers(0, 6, 40), rng.integers(0, 11, 40)], 1).astype(np.int32)
     ref = orc.dtw_pairs(test, train, W, pairs=pairs)
-    for g in (1, 2, 4, 8, 16, 32, lib.ROWS_GROUP):
+    for g in (1, 2, 4, 8, 16, 32, lib.ROWS_GROUP, lib.ROWS16_GROUP, lib.ROWS8_GROUP):
         got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W,
                                flags=lib.DTW_GROUP(g)).cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0, err_msg=f"G={g}")
@@ -287,6 +287,37 @@ def test_dtw_full_window_row_layout(lib, orc, L):
     np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0)
     big = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W + 1000).cpu().numpy()
     np.testing.assert_array_equal(big, got)
+
+
+@pytest.mark.parametrize("L", [1, 3, 4, 7, 8, 9, 16, 17, 100, 128, 129, 300, 512, 513, 1000, 1024])
+def test_dtw_full_window_grouped_rows(lib, orc, L):
+    """The row layout with 16 or 8 lanes per pair (L <= 64 G) gives the oracle's
+    values; longer series fall back to the one-pair-per-warp kernel."""
+    W = L - 1 if L > 1 else 0
+    test = _series(1900 + L, 5, L)
+    train = _series(1901 + L, 9, L)
+    rng = np.random.default_rng(L)
+    pairs = np.stack([rng.integers(0, 5, 70), rng.integers(0, 9, 70)], 1).astype(np.int32)
+    ref = orc.dtw_pairs(test, train, W, pairs=pairs)
+    for g in (lib.ROWS16_GROUP, lib.ROWS8_GROUP):
+        got = lib.dtw_windowed(_t(test), _t(train), _t(pairs), W,
+                               flags=lib.DTW_GROUP(g)).cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0, err_msg=f"G={g}")
+
+
+@pytest.mark.parametrize("g", ["rows16", "rows8"])
+@pytest.mark.parametrize("L,N,Q", [(200, 300, 120), (37, 500, 200), (500, 90, 40)])
+def test_search_grouped_rows(lib, orc, g, L, N, Q):
+    """Full-window searches with the grouped row layout (seeds, abandoning, best
+    updates, ties) return the exhaustive FP64 nearest neighbours."""
+    rng = np.random.default_rng(L + N)
+    train = synth.znormed_walks(rng, N, L).astype(np.float32)
+    test = synth.znormed_walks(rng, Q, L).astype(np.float32)
+    test[:3] = train[:3]                       # exact matches, distance 0
+    labels = rng.integers(0, 5, N).astype(np.int32)
+    brute = orc.nn_brute(train, labels, test, L - 1)
+    grp = lib.ROWS16_GROUP if g == "rows16" else lib.ROWS8_GROUP
+    _check_search(lib, orc, train, labels, test, L - 1, 3, flags=lib.DTW_GROUP(grp), brute=brute)
 
 
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
