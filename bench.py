@@ -170,7 +170,8 @@ def source_sha(paths):
 
 
 _DTW_SOURCES = ["paper_1808_09617_gb300/csrc/dtw32.cuh", "paper_1808_09617_gb300/csrc/dtw32_launch.cu",
-                "paper_1808_09617_gb300/csrc/dtw32_rows.cu", "paper_1808_09617_gb300/csrc/dtw32_wide.cu"]
+                "paper_1808_09617_gb300/csrc/dtw32_rows.cu", "paper_1808_09617_gb300/csrc/dtw32_rowsg.cu",
+                "paper_1808_09617_gb300/csrc/dtw32_wide.cu"]
 STAGE_SOURCES = {
     "dtw": _DTW_SOURCES,
     "seed": _DTW_SOURCES,
