@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "exact NN-DTW queries/s + DTW GCUPS on 1 GB300: batched FP32 vs plain FP64 form"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_SEARCH = 11  # envelopes, lb, dtw(seed), compact x2, dtw, filter, collect, dtw64, ties, final
+KERNELS_PER_SEARCH = 12  # envelopes, norms, lb, dtw(seed), compact x2, dtw, filter, collect, dtw64, ties, final
 INSTR_PER_CELL = 3       # FADD + 3-input FMNMX + FFMA
-INSTR_PER_LB_ELEM = 6    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FADD + FFMA
+INSTR_PER_LB_ELEM = 5    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FFMA (dot product)
 FP32_LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
 STAGES = ("envelopes", "lb", "seed", "compact", "dtw", "recheck", "final", "total")
@@ -227,6 +227,38 @@ def roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, wor
     r["share_of_step"] = stage_ms[dom] / stage_ms["total"] if stage_ms["total"] else None
     r["traffic"] = traffic_for(dom, workload_name)
     return r
+
+
+# ------------------------------------------------------------------ tightness
+
+def tightness_pairs(dev):
+    """Mean tightness LB/DTW over all 250,000 pairs of the 500 x 500 pairs
+    workload (L=256, W=26) for LB_Enhanced^V, V in {1, 2, 5}, and LB_Keogh
+    (pairs with DTW = 0 excluded), with the search's pruning per V."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw, synth
+    ds = synth.make_pairs(5)
+    train = torch.from_numpy(ds.train).to(dev)
+    test = torch.from_numpy(ds.test).to(dev)
+    labels = torch.from_numpy(ds.train_labels).to(dev)
+    Q, N = test.shape[0], train.shape[0]
+    q = torch.arange(Q, device=dev, dtype=torch.int32).repeat_interleave(N)
+    t = torch.arange(N, device=dev, dtype=torch.int32).repeat(Q)
+    pairs = torch.stack([q, t], 1).contiguous()
+    dtw = nndtw.dtw_windowed(test, train, pairs, ds.W).double()
+    env = nndtw.nn_dtw_build_envelopes(train, ds.W)
+    keep = dtw > 0
+    out = {"pairs": Q * N, "pairs_dtw_zero": int((~keep).sum().item()), "W": ds.W, "L": ds.L}
+    lbk = nndtw.lb_enhanced(test, train, env, ds.W, 1, keogh=True).double().reshape(-1)
+    out["LB_Keogh"] = float((lbk[keep] / dtw[keep]).mean().item())
+    for V in (1, 2, 5):
+        lb = nndtw.lb_enhanced(test, train, env, ds.W, V).double().reshape(-1)
+        st = nndtw.nn_dtw_search(train, labels, test, ds.W, V, stats=True).stats
+        out[f"LB_Enhanced^{V}"] = {
+            "tightness": float((lb[keep] / dtw[keep]).mean().item()),
+            "lb_pruned_frac": st["lb_pruned"] / st["pairs"],
+            "dtw_abandoned_frac_of_started": st["dtw_abandoned"] / max(1, st["dtw_started"])}
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -624,6 +656,7 @@ def main():
                         "rechecked": sum(c["rechecked"] for c in counts),
                         "recheck_queries": sum(c["recheck_queries"] for c in counts)},
             "fp64_plain": fp64,
+            "tightness_pairs_workload": tightness_pairs(dev),
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -89,10 +89,12 @@ struct Cand64 {
 template <typename T>
 cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s);
 
+// With seed_keys, also the Euclidean-nearest series of every query; `norms`
+// is then scratch for Q + N squared norms.
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
-                      T *lb_out, unsigned long long *seed_keys, cudaStream_t s);
+                      T *lb_out, unsigned long long *seed_keys, T *norms, cudaStream_t s);
 
 // FP32 DTW over a work list.  Pairs come from `pairs` ([count] of (q, t)) or,
 // when pairs == nullptr, from seed keys (pair p = (p, key_idx(seed_keys[p]))).

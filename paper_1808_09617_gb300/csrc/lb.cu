@@ -17,11 +17,12 @@
 // Outputs: the bound per pair (raw, or scaled down by the rounding margin)
 // and, for the search, per query the packed key (distance, index) of its
 // nearest training series in squared Euclidean distance, fused into the same
-// pass (2 more operations per pair-element over the same staged values): the
-// search's first DTW candidate, as in the paper's protocol of starting from
-// the candidate nearest in Euclidean distance (Sec. 4).  ED = DTW_0 is an
-// upper bound of DTW_W, and that candidate is usually far closer to the
-// nearest neighbour than the one with the smallest bound.
+// pass: the search's first DTW candidate, as in the paper's protocol of
+// starting from the candidate nearest in Euclidean distance (Sec. 4).  The
+// distance is formed as |a|^2 + |b|^2 - 2 a.b from precomputed squared norms
+// (one multiply-add per pair-element); it only picks that first candidate,
+// whose exact DTW then bounds the query, so its rounding never changes a
+// result.
 #include "internal.cuh"
 
 namespace nndtw {
@@ -65,17 +66,62 @@ __device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) 
     return v > 0.0 ? v : 0.0;
 }
 
+// The two ends and the V-1 left and right bands of Eq. 7 for one pair:
+// element i of A and B is Ap[i], Bp[i] for i < nb, and Ap[last - k],
+// Bp[last - k] for the k-th element from the end.  Inlined at each call site
+// so that the loads keep the pointers' address space.
+template <typename T>
+__device__ __forceinline__ T band_terms(const T *Ap, const T *Bp, int last, int nb, int W) {
+    T res = dsq(Ap[0], Bp[0]) + dsq(Ap[last], Bp[last]);
+    for (int ii = 1; ii < nb; ii++) {
+        const int ri = last - ii;
+        const T ai = Ap[ii], bi = Bp[ii], ar = Ap[ri], br = Bp[ri];
+        T mL = dsq(ai, bi);
+        T mR = dsq(ar, br);
+        const int jlo = ii - W > 0 ? ii - W : 0;
+        for (int jj = jlo; jj < ii; jj++) {
+            const int rj = last - jj;
+            mL = tmin3(mL, dsq(ai, Bp[jj]), dsq(Ap[jj], bi));
+            mR = tmin3(mR, dsq(ar, Bp[rj]), dsq(Ap[rj], br));
+        }
+        res = res + mL + mR;
+    }
+    return res;
+}
+
+// Squared norm of every row of a and of b (one warp per row).
+template <typename T>
+__global__ void sqnorm_kernel(const T *__restrict__ a, int64_t na, const T *__restrict__ b,
+                              int64_t nb, int L, T *__restrict__ out_a, T *__restrict__ out_b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na + nb;
+         r += warps) {
+        const T *x = r < na ? a + r * L : b + (r - na) * L;
+        T acc = T(0);
+        for (int i = lane; i < L; i += 32) acc = fma(x[i], x[i], acc);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            if (r < na) out_a[r] = acc;
+            else out_b[r - na] = acc;
+        }
+    }
+}
+
 template <typename T, bool ED, int MR, int MC>
 __global__ void __launch_bounds__(kThreads)
 lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
           const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
-          T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys) {
+          T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys,
+          const T *__restrict__ nq, const T *__restrict__ nt) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // offsets from the shared array itself (not through integer casts), so
+    // that every access compiles to a shared-memory load
+    constexpr size_t kEsOff = (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16;
     T *As = reinterpret_cast<T *>(smem_raw);                      // [kLC][kQT+1]
-    T2 *Es = reinterpret_cast<T2 *>(As + kLC * (kQT + 1) + 1);    // [kLC][kNT+1] (aligned below)
-    Es = reinterpret_cast<T2 *>((reinterpret_cast<uintptr_t>(Es) + 15) & ~uintptr_t(15));
+    T2 *Es = reinterpret_cast<T2 *>(smem_raw + kEsOff);           // [kLC][kNT+1], 16-byte aligned
     T *Bs = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kLC][kNT+1] (ED only)
     // band staging, rows padded to an odd stride so that the 16 series a
     // warp reads at once fall in distinct banks
@@ -142,10 +188,7 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
 #pragma unroll
                 for (int r = 0; r < MR; r++)
 #pragma unroll
-                    for (int c = 0; c < MC; c++) {
-                        const T d = a[r] - b[c];
-                        ed[r][c] = fma(d, d, ed[r][c]);
-                    }
+                    for (int c = 0; c < MC; c++) ed[r][c] = fma(a[r], b[c], ed[r][c]);
             }
         }
         __syncthreads();
@@ -173,33 +216,16 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
 #pragma unroll
         for (int r = 0; r < MR; r++) {
             const int64_t q = q0 + ty + 16 * r;
-            const T *Ag = test + (q < Q ? q : 0) * L;
-            const T *Asg = Ab + (ty + 16 * r) * bstride;
 #pragma unroll
             for (int c = 0; c < MC; c++) {
                 const int64_t t = t0 + tx + 16 * c;
-                const T *Bg = train + (t < N ? t : 0) * L;
-                const T *Bsg = Bb + (tx + 16 * c) * bstride;
-                // element i (0-based, in the first or last nb) of A and B:
                 // staged copies hold the first nb then the last nb elements
-                const T *Ap = staged ? Asg : Ag;
-                const T *Bp = staged ? Bsg : Bg;
-                const int sh = staged ? L - 2 * nb : 0;   // offset of the last nb
-                const int last = L - 1 - sh;
-                T res = dsq(Ap[0], Bp[0]) + dsq(Ap[last], Bp[last]);
-                for (int ii = 1; ii < nb; ii++) {
-                    const int ri = last - ii;
-                    const T ai = Ap[ii], bi = Bp[ii], ar = Ap[ri], br = Bp[ri];
-                    T mL = dsq(ai, bi);
-                    T mR = dsq(ar, br);
-                    const int jlo = ii - W > 0 ? ii - W : 0;
-                    for (int jj = jlo; jj < ii; jj++) {
-                        const int rj = last - jj;
-                        mL = tmin3(mL, dsq(ai, Bp[jj]), dsq(Ap[jj], bi));
-                        mR = tmin3(mR, dsq(ar, Bp[rj]), dsq(Ap[rj], br));
-                    }
-                    res = res + mL + mR;
-                }
+                // (offset of the last nb: L - 2 nb); otherwise read the series
+                const T res = staged
+                    ? band_terms(Ab + (ty + 16 * r) * bstride, Bb + (tx + 16 * c) * bstride,
+                                 2 * nb - 1, nb, W)
+                    : band_terms(test + (q < Q ? q : 0) * L, train + (t < N ? t : 0) * L, L - 1,
+                                 nb, W);
                 acc[r][c] = res + acc[r][c];
             }
         }
@@ -218,7 +244,11 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             if (q < Q && t < N) {
                 if (lb_out) lb_out[q * N + t] = safe ? sv : raw;
                 if (ED) {
-                    const unsigned long long k = pack_key(to_key_float(ed[r][c]), (uint32_t)t);
+                    // squared distance from the norms and the dot product
+                    // (clamped: rounding may take it slightly below 0)
+                    T e = nq[q] + nt[t] - T(2) * ed[r][c];
+                    e = e > T(0) ? e : T(0);
+                    const unsigned long long k = pack_key(to_key_float(e), (uint32_t)t);
                     best = k < best ? k : best;
                 }
             }
@@ -237,11 +267,12 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
 template <typename T, int MR, int MC>
 cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                            int L, int Weff, int nb, bool keogh, bool safe, T lb_lo, T abs_slack,
-                           T *lb_out, unsigned long long *seed_keys, cudaStream_t s) {
+                           T *lb_out, unsigned long long *seed_keys, const T *nq, const T *nt,
+                           cudaStream_t s) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     const bool ed = seed_keys != nullptr;
-    size_t smem = sizeof(T) * (kLC * (kQT + 1) + 1) + 16 + sizeof(T2) * kLC * (kNT + 1);
+    size_t smem = (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16 + sizeof(T2) * kLC * (kNT + 1);
     if (ed) smem += sizeof(T) * kLC * (kNT + 1);
     if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * (2 * nb + 1);
     auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
@@ -250,7 +281,7 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
-                                    lb_lo, abs_slack, lb_out, seed_keys);
+                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt);
     return cudaGetLastError();
 }
 
@@ -259,8 +290,19 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                       int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
-                      unsigned long long *seed_keys, cudaStream_t s) {
+                      unsigned long long *seed_keys, T *norms, cudaStream_t s) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
+    if (seed_keys) {
+        // squared norms of the queries (norms[0..Q)) and training series
+        // (norms[Q..Q+N)) for the fused Euclidean distance
+        if (!norms) return cudaErrorInvalidValue;
+        const int64_t rows = Q + N;
+        const unsigned grid = (unsigned)((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096);
+        sqnorm_kernel<T><<<grid, 256, 0, s>>>(test, Q, train, N, L, norms, norms + Q);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const T *nq = seed_keys ? norms : nullptr, *nt = seed_keys ? norms + Q : nullptr;
     int nb = L / 2 < V ? L / 2 : V;
     if (nb < 1) nb = 1;
     const int Weff = W > L - 1 ? L - 1 : W;
@@ -268,16 +310,16 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
     const int sms = device_sm_count();
     const bool small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
     if (small) return launch_lb_tile<T, 2, 2>(test, Q, train, env, N, L, Weff, nb, keogh, safe,
-                                              lb_lo, abs_slack, lb_out, seed_keys, s);
+                                              lb_lo, abs_slack, lb_out, seed_keys, nq, nt, s);
     return launch_lb_tile<T, 4, 4>(test, Q, train, env, N, L, Weff, nb, keogh, safe, lb_lo,
-                                   abs_slack, lb_out, seed_keys, s);
+                                   abs_slack, lb_out, seed_keys, nq, nt, s);
 }
 
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                       int, int, int, bool, bool, float, float, float *,
-                                      unsigned long long *, cudaStream_t);
+                                      unsigned long long *, float *, cudaStream_t);
 template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
                                        int64_t, int, int, int, bool, bool, double, double,
-                                       double *, unsigned long long *, cudaStream_t);
+                                       double *, unsigned long long *, double *, cudaStream_t);
 
 }  // namespace nndtw

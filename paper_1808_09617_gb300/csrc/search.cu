@@ -297,7 +297,7 @@ struct Carve {
 struct Layout32 {
     unsigned long long *counters, *bsf, *seed, *best64, *buckets;
     int32_t *rcount, *bestidx;
-    float *env, *lb;
+    float *env, *lb, *norms;
     uint2 *queue, *rlist;
     Cand *cand;
     double *d64;
@@ -317,6 +317,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<float>((size_t)N * L * 2);
     l.lb = c.take<float>((size_t)Q * N);
+    l.norms = c.take<float>((size_t)Q + (size_t)N);
     l.queue = c.take<uint2>((size_t)Q * N);
     l.cand = c.take<Cand>(cap);
     l.rlist = c.take<uint2>(cap);
@@ -328,7 +329,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
 struct Layout64 {
     unsigned long long *counters, *bsf64, *seed, *buckets;
     int32_t *bestidx;
-    double *env, *lb;
+    double *env, *lb, *norms;
     uint2 *queue;
     Cand64 *cand;
     size_t bytes;
@@ -345,6 +346,7 @@ Layout64 layout64(void *base, int64_t N, int64_t Q, int L) {
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<double>((size_t)N * L * 2);
     l.lb = c.take<double>((size_t)Q * N);
+    l.norms = c.take<double>((size_t)Q + (size_t)N);
     l.queue = c.take<uint2>((size_t)Q * N);
     l.cand = c.take<Cand64>(cap);
     l.bytes = c.off + 256;
@@ -517,7 +519,7 @@ int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const floa
     const Margins m = make_margins(L);
     CK(launch_lb<float>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                         (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out, nullptr,
-                        (cudaStream_t)stream));
+                        nullptr, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -530,7 +532,7 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
     const Margins m = make_margins(L);
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
-                         (cudaStream_t)stream));
+                         nullptr, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -639,7 +641,7 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     CK(tm.mark(1));
     // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
     CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
-                        ws.lb, ws.seed, s));
+                        ws.lb, ws.seed, ws.norms, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     // S4 on the first candidate of every query: initial upper bounds
@@ -753,7 +755,7 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     }
     CK(tm.mark(1));
     CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
-                         m.abs64, ws.lb, ws.seed, s));
+                         m.abs64, ws.lb, ws.seed, ws.norms, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     DtwJob64 j{};
