@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "exact NN-DTW queries/s + DTW GCUPS on 1 GB300: batched FP32 vs plain FP64 form"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_SEARCH = 12  # envelopes, norms, lb, dtw(seed), compact x2, dtw, filter, collect, dtw64, ties, final
+KERNELS_PER_SEARCH = 14  # envelopes x2 (train, queries), norms, lb, dtw(seed), compact x2, reverse bound, dtw, filter, collect, dtw64, ties, final
 INSTR_PER_CELL = 3       # FADD + 3-input FMNMX + FFMA
 INSTR_PER_LB_ELEM = 5    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FFMA (dot product)
 FP32_LANES_PER_SM = 128
@@ -461,10 +461,11 @@ def main():
     elif not args.no_tune:
         for i, (d, s) in enumerate(zip(dsets, sets)):
             if d.N * d.Q >= 50_000:
+                s["flags"] = autotune.tune_search_flags(s["train"], s["labels"], s["test"], d.W,
+                                                        d.V, reps=2)
                 g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)
-                if g:
-                    s["flags"] = nndtw.DTW_GROUP(g)
-                    tuned[i] = g
+                if g or s["flags"] & nndtw.REVERSE:
+                    tuned[i] = {"group": g, "reverse": bool(s["flags"] & nndtw.REVERSE)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # counting pass (untimed): pruning and cells per dataset
@@ -634,7 +635,7 @@ def main():
                        "l2": "flushed before every step (256 MiB write, outside the step's events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "launch": "CUDA graph replay" if not args.no_graph else "direct launches",
-                       "dtw_group_autotuned": {str(k): v for k, v in tuned.items()}},
+                       "autotuned": {str(k): v for k, v in tuned.items()}},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world * Qtot / (e2e_ms / 1000.0), "unit": UNIT,

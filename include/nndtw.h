@@ -66,6 +66,8 @@ extern "C" {
 #define NNDTW_NO_ABANDON (1u << 4)   /* search: no early abandoning inside DTW      */
 #define NNDTW_CHECK_FINITE (1u << 5) /* search: reject non-finite or huge inputs     */
 #define NNDTW_TIME_STAGES (1u << 6)  /* search: record stage events (see below)      */
+#define NNDTW_NO_REVERSE (1u << 7)   /* search: skip the reverse bound LB_Enh(B, A)  */
+#define NNDTW_REVERSE (1u << 14)     /* FP32 search: test the reverse bound LB_Enh(B, A) */
 /* search / dtw_windowed: lanes per pair of the FP32 DTW kernel, a tuning
  * choice that never changes results: NNDTW_DTW_GROUP(log2 G) with
  * G = 1, 2, 4, ..., 32; 0 (the default) lets the library choose.  A G that
@@ -106,6 +108,8 @@ typedef struct nndtw_stats {
     int64_t rechecked;      /* FP64 re-evaluations of near-tie candidates       */
     int64_t recheck_queries;/* queries that needed at least one                 */
     int64_t seed_cells;     /* of dtw_cells, those of the first-candidate pass  */
+    int64_t lb_pruned_reverse; /* survivors dropped by the reverse bound
+                                  LB_Enhanced(B, A) when their DTW was due     */
 } nndtw_stats;
 
 /*
@@ -165,7 +169,12 @@ NNDTW_API size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V
 /*
  * Exact 1-NN classification of Q test series against N labelled training
  * series under DTW_W: the lower-bound search of Sec. 4 with LB_Enhanced^V
- * (Algorithm 1) as the bound.  For every query q:
+ * (Algorithm 1) as the bound, cascaded with the reverse bound
+ * LB_Enhanced^V(B, A) (the same bound with the series exchanged, over the
+ * query's envelope) on the pairs that survive it: by default in the FP64
+ * form, with NNDTW_REVERSE in the FP32 form (a tuning choice: it saves DTW
+ * work but reads each surviving pair's training series once more);
+ * NNDTW_NO_REVERSE leaves it out.  For every query q:
  *   d_nn_idx[q]   = argmin_t DTW_W(test_q, train_t), ties to the lowest t;
  *   d_nn_label[q] = d_train_labels[d_nn_idx[q]];
  *   d_nn_dist[q]  = that distance (squared units).

@@ -1,13 +1,15 @@
 """Autotuner for the search's launch shapes.
 
-The only shape with a large effect is G, the number of lanes that share one
+The shape with the largest effect is G, the number of lanes that share one
 (query, train) pair in the FP32 DTW kernel: G = 1 gives every lane its own
 pair (no shuffles, but many concurrent pairs, so uneven early-abandoning
 leaves lanes idle when work is scarce); larger G sweeps each pair faster with
-more exchange per cell.  The tuner times ``nn_dtw_search`` with every
-admissible G on the caller's data (results never depend on G) and keeps the
-fastest, cached in memory and optionally in a JSON file keyed by device, L,
-W, V and power-of-two buckets of N and Q.
+more exchange per cell; full windows also have the row layouts.  The tuner
+times ``nn_dtw_search`` with every admissible G on the caller's data
+(results never depend on G) and keeps the fastest, cached in memory and
+optionally in a JSON file keyed by device, L, W, V and power-of-two buckets
+of N and Q.  ``tune_search_flags`` then also decides whether the cascade's
+reverse bound (``nndtw.REVERSE``) pays off on that data.
 """
 from __future__ import annotations
 
@@ -59,6 +61,20 @@ def _load(path):
         return {}
 
 
+def _median_ms(train, labels, test, W, V, flags, workspace, out, reps):
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nndtw.nn_dtw_search(train, labels, test, W, V, flags=flags, workspace=workspace, out=out)
+    times = []
+    for _ in range(reps):
+        s.record()
+        nndtw.nn_dtw_search(train, labels, test, W, V, flags=flags, workspace=workspace, out=out)
+        e.record()
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+    return sorted(times)[len(times) // 2]
+
+
 def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, reps: int = 3,
                 cache_path: str | None = None) -> int:
     """Return the fastest lanes-per-pair G for this search (0 if nothing to tune)."""
@@ -85,18 +101,8 @@ def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, r
                torch.empty(Q, dtype=torch.int32, device=train.device),
                torch.empty(Q, dtype=torch.float64, device=train.device))
     best, best_ms = groups[0], float("inf")
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for g in groups:
-        f = nndtw.DTW_GROUP(g)
-        nndtw.nn_dtw_search(train, labels, test, W, V, flags=f, workspace=workspace, out=out)
-        times = []
-        for _ in range(reps):
-            s.record()
-            nndtw.nn_dtw_search(train, labels, test, W, V, flags=f, workspace=workspace, out=out)
-            e.record()
-            e.synchronize()
-            times.append(s.elapsed_time(e))
-        ms = sorted(times)[len(times) // 2]
+        ms = _median_ms(train, labels, test, W, V, nndtw.DTW_GROUP(g), workspace, out, reps)
         if ms < best_ms:
             best, best_ms = g, ms
     with _lock:
@@ -109,3 +115,29 @@ def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, r
                 json.dump(d, f, indent=1, sort_keys=True)
             os.replace(tmp, cache_path)
     return best
+
+
+def tune_search_flags(train, labels, test, W: int, V: int, reps: int = 3,
+                      cache_path: str | None = None) -> int:
+    """Search flags for this data: the fastest lanes-per-pair choice, plus
+    ``nndtw.REVERSE`` when the cascade's reverse bound makes the search
+    faster (results never depend on either)."""
+    import torch
+    g = tune_search(train, labels, test, W, V, reps=reps, cache_path=cache_path)
+    base = nndtw.DTW_GROUP(g) if g else 0
+    N, L = train.shape
+    Q = test.shape[0]
+    k = "reverse|" + key(torch.cuda.get_device_name(train.device), N, Q, L, min(W, L - 1), V)
+    with _lock:
+        if k in _mem:
+            return base | (nndtw.REVERSE if _mem[k] else 0)
+    workspace = torch.empty(nndtw.nn_dtw_workspace_size(N, Q, L, W, V), dtype=torch.uint8,
+                            device=train.device)
+    out = (torch.empty(Q, dtype=torch.int32, device=train.device),
+           torch.empty(Q, dtype=torch.int32, device=train.device),
+           torch.empty(Q, dtype=torch.float64, device=train.device))
+    off = _median_ms(train, labels, test, W, V, base, workspace, out, reps)
+    on = _median_ms(train, labels, test, W, V, base | nndtw.REVERSE, workspace, out, reps)
+    with _lock:
+        _mem[k] = on < off
+    return base | (nndtw.REVERSE if on < off else 0)

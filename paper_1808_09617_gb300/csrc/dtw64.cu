@@ -20,7 +20,11 @@
 // Early abandoning (FP64 search): the minimum over all slots is at most the
 // minimum over anti-diagonals t-1 and t, which every path crosses, so it is a
 // lower bound of D(L,L); it is compared (strictly) with the query's exact
-// current best.
+// current best.  Before a pair's sweep, the reverse bound LB_Enhanced(B, A)
+// (the pair's stored ends and bands plus the LB_Keogh bridge of the training
+// series against the query's envelope, scaled down by the bound's rounding
+// margin) is compared with the same best, and the pair is dropped when it is
+// larger.
 #include "internal.cuh"
 
 namespace nndtw {
@@ -63,6 +67,32 @@ dtw64_kernel(DtwJob64 job) {
             q = (int)pr.x; t = (int)pr.y;
         } else {
             q = (int)p; t = (int)key_idx(job.seed_keys[p]);
+        }
+        if (!F32IN && job.envq) {
+            const double2 *eq = job.envq + (long long)q * L;
+            const double *bp = job.train + (long long)t * L;
+            double part = 0.0;
+            for (int j = job.nb + tid; j < L - job.nb; j += nthr) {
+                const double b = bp[j];
+                const double d = b - fmin(fmax(b, eq[j].y), eq[j].x);
+                part = fma(d, d, part);
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if ((tid & 31) == 0) red[tid >> 5] = __double_as_longlong(part);
+            __syncthreads();
+            if (tid == 0) {
+                double tot = job.ends_bands[(long long)q * job.N + t];
+                for (int w = 0; w < (nthr >> 5); w++) tot += __longlong_as_double(red[w]);
+                double safe = __dmul_rd(tot, job.lb_lo) - job.lb_abs;
+                safe = safe > 0.0 ? safe : 0.0;
+                const long long ubits = (long long)*((volatile unsigned long long *)job.bsf64 + q);
+                bcast = __double_as_longlong(safe) > ubits;   // strict
+                if (bcast && job.counters) atomicAdd(job.counters + C_REVPRUNED, 1ull);
+            }
+            __syncthreads();
+            const bool drop = bcast != 0;
+            __syncthreads();
+            if (drop) continue;
         }
         for (int i = tid; i < L; i += nthr) {
             As[i] = F32IN ? (double)job.test32[(long long)q * L + i] : job.test[(long long)q * L + i];

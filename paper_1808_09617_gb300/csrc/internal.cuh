@@ -71,6 +71,8 @@ enum Counter : int {
     C_RQUERIES,      // queries with a recheck
     C_SEEDHEAD,      // next seed pair to claim
     C_BAD,           // non-finite input elements found
+    C_REVPRUNED,     // pairs dropped by the reverse bound LB_Enhanced(B, A)
+    C_QUEUE2,        // survivors of the reverse bound (FP32 search)
     C_COUNT
 };
 
@@ -90,11 +92,14 @@ template <typename T>
 cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s);
 
 // With seed_keys, also the Euclidean-nearest series of every query; `norms`
-// is then scratch for Q + N squared norms.
+// is then scratch for Q + N squared norms.  With ends_out, also the raw sum
+// of the two ends and the bands of every pair ([Q][N]): the part of Eq. 7
+// that LB_Enhanced(B, A) shares with LB_Enhanced(A, B).
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
-                      T *lb_out, unsigned long long *seed_keys, T *norms, cudaStream_t s);
+                      T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
+                      cudaStream_t s);
 
 // FP32 DTW over a work list.  Pairs come from `pairs` ([count] of (q, t)) or,
 // when pairs == nullptr, from seed keys (pair p = (p, key_idx(seed_keys[p]))).
@@ -145,8 +150,26 @@ struct DtwJob64 {
     double *out;                        // out[p] = DTW (nullptr: none)
     unsigned long long *counters;
     int abandon;
+    // Reverse bound at the start of every pair (nullptr: none):
+    // LB_Enhanced(B, A) = ends_bands[q N + t] + the LB_Keogh bridge of the
+    // training series against the query's envelope envq ([Q][L] (U, Lo))
+    // over [nb, L - nb), scaled down by lb_lo and lb_abs like every bound.
+    const double2 *envq;
+    const double *ends_bands;
+    long long N;
+    int nb;
+    double lb_lo, lb_abs;
 };
 cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
+
+// The reverse bound LB_Enhanced(B, A) over a queue of pairs (FP32): the
+// survivors of in[0 .. *in_count) are appended to out (count in *out_count).
+cudaError_t launch_rev_filter(const uint2 *in, const unsigned long long *in_count,
+                              const float *train, const float2 *envq, const float *ends,
+                              long long N, int L, int nb, const unsigned long long *bsf,
+                              float lb_lo, float lb_abs, float dtw_hi, float abs32, uint2 *out,
+                              unsigned long long *out_count, unsigned long long *counters,
+                              long long max_pairs, int sm_count, cudaStream_t s);
 
 int device_sm_count();
 void set_last_cuda_error(cudaError_t e);

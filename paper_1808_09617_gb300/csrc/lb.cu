@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads)
 lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
           const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
           T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys,
-          const T *__restrict__ nq, const T *__restrict__ nt) {
+          const T *__restrict__ nq, const T *__restrict__ nt, T *__restrict__ ends_out) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -227,6 +227,8 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
                     : band_terms(test + (q < Q ? q : 0) * L, train + (t < N ? t : 0) * L, L - 1,
                                  nb, W);
                 acc[r][c] = res + acc[r][c];
+                // the ends and bands alone: they are the same for LB(B, A)
+                if (ends_out && q < Q && t < N) ends_out[q * N + t] = res;
             }
         }
     }
@@ -268,7 +270,7 @@ template <typename T, int MR, int MC>
 cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                            int L, int Weff, int nb, bool keogh, bool safe, T lb_lo, T abs_slack,
                            T *lb_out, unsigned long long *seed_keys, const T *nq, const T *nt,
-                           cudaStream_t s) {
+                           T *ends_out, cudaStream_t s) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     const bool ed = seed_keys != nullptr;
@@ -281,7 +283,7 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
-                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt);
+                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt, ends_out);
     return cudaGetLastError();
 }
 
@@ -290,7 +292,7 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                       int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
-                      unsigned long long *seed_keys, T *norms, cudaStream_t s) {
+                      unsigned long long *seed_keys, T *norms, T *ends_out, cudaStream_t s) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
     if (seed_keys) {
         // squared norms of the queries (norms[0..Q)) and training series
@@ -310,16 +312,19 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
     const int sms = device_sm_count();
     const bool small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
     if (small) return launch_lb_tile<T, 2, 2>(test, Q, train, env, N, L, Weff, nb, keogh, safe,
-                                              lb_lo, abs_slack, lb_out, seed_keys, nq, nt, s);
+                                              lb_lo, abs_slack, lb_out, seed_keys, nq, nt,
+                                              keogh ? nullptr : ends_out, s);
     return launch_lb_tile<T, 4, 4>(test, Q, train, env, N, L, Weff, nb, keogh, safe, lb_lo,
-                                   abs_slack, lb_out, seed_keys, nq, nt, s);
+                                   abs_slack, lb_out, seed_keys, nq, nt,
+                                   keogh ? nullptr : ends_out, s);
 }
 
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                       int, int, int, bool, bool, float, float, float *,
-                                      unsigned long long *, float *, cudaStream_t);
+                                      unsigned long long *, float *, float *, cudaStream_t);
 template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
                                        int64_t, int, int, int, bool, bool, double, double,
-                                       double *, unsigned long long *, double *, cudaStream_t);
+                                       double *, unsigned long long *, double *, double *,
+                                       cudaStream_t);
 
 }  // namespace nndtw

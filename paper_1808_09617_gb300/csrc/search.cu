@@ -297,7 +297,7 @@ struct Carve {
 struct Layout32 {
     unsigned long long *counters, *bsf, *seed, *best64, *buckets;
     int32_t *rcount, *bestidx;
-    float *env, *lb, *norms;
+    float *env, *envq, *lb, *ends, *norms;
     uint2 *queue, *rlist;
     Cand *cand;
     double *d64;
@@ -316,7 +316,9 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
     l.rcount = c.take<int32_t>(Q);
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<float>((size_t)N * L * 2);
+    l.envq = c.take<float>((size_t)Q * L * 2);
     l.lb = c.take<float>((size_t)Q * N);
+    l.ends = c.take<float>((size_t)Q * N);
     l.norms = c.take<float>((size_t)Q + (size_t)N);
     l.queue = c.take<uint2>((size_t)Q * N);
     l.cand = c.take<Cand>(cap);
@@ -329,7 +331,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
 struct Layout64 {
     unsigned long long *counters, *bsf64, *seed, *buckets;
     int32_t *bestidx;
-    double *env, *lb, *norms;
+    double *env, *envq, *lb, *ends, *norms;
     uint2 *queue;
     Cand64 *cand;
     size_t bytes;
@@ -345,7 +347,9 @@ Layout64 layout64(void *base, int64_t N, int64_t Q, int L) {
     l.seed = c.take<unsigned long long>(Q);
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<double>((size_t)N * L * 2);
+    l.envq = c.take<double>((size_t)Q * L * 2);
     l.lb = c.take<double>((size_t)Q * N);
+    l.ends = c.take<double>((size_t)Q * N);
     l.norms = c.take<double>((size_t)Q + (size_t)N);
     l.queue = c.take<uint2>((size_t)Q * N);
     l.cand = c.take<Cand64>(cap);
@@ -382,6 +386,13 @@ dim3 grid_compact(int64_t Q, int64_t N) {
         if (e_ != cudaSuccess) { set_last_cuda_error(e_); return NNDTW_ECUDA; } \
     } while (0)
 
+// First index of the LB_Keogh bridge of Eq. 7 (the number of bands,
+// min(L/2, V), at least 1), as in the bound kernel.
+int bridge_start(int L, int V) {
+    const int nb = L / 2 < V ? L / 2 : V;
+    return nb < 1 ? 1 : nb;
+}
+
 void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t Q, int L,
                 int W, bool counted) {
     std::memset(st, 0, sizeof(*st));
@@ -394,6 +405,7 @@ void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t
         st->dtw_abandoned = (int64_t)h[C_ABANDONED];
         st->dtw_cells = (int64_t)h[C_CELLS];
         st->seed_cells = Q * band_cells(L, W);
+        st->lb_pruned_reverse = (int64_t)h[C_REVPRUNED];
     }
 }
 
@@ -468,7 +480,7 @@ using namespace nndtw;
 
 extern "C" {
 
-int nn_dtw_version(void) { return 102; }
+int nn_dtw_version(void) { return 103; }
 
 int nn_dtw_stage_times(float *h_ms) {
     if (!h_ms || t_last_dev < 0) return NNDTW_EINVAL;
@@ -519,7 +531,7 @@ int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const floa
     const Margins m = make_margins(L);
     CK(launch_lb<float>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                         (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out, nullptr,
-                        nullptr, (cudaStream_t)stream));
+                        nullptr, nullptr, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -532,7 +544,7 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
     const Margins m = make_margins(L);
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
-                         nullptr, (cudaStream_t)stream));
+                         nullptr, nullptr, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -638,10 +650,15 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
         CK(launch_envelopes<float>(d_train, N, L, Weff, ws.env, s));
         env = ws.env;
     }
+    // the query envelopes, for the reverse bound LB_Enhanced(B, A) (asked for
+    // with NNDTW_REVERSE: whether reading every surviving pair's training
+    // series once more pays off depends on the data, so the tuner decides)
+    const bool rev = (flags & NNDTW_REVERSE) && !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
+    if (rev) CK(launch_envelopes<float>(d_test, Q, L, Weff, ws.envq, s));
     CK(tm.mark(1));
     // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
     CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
-                        ws.lb, ws.seed, ws.norms, s));
+                        ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     // S4 on the first candidate of every query: initial upper bounds
@@ -669,9 +686,18 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
             CK(cudaGetLastError());
         }
     }
+    // the cascade's reverse bound on the survivors (into the recheck list's
+    // storage, which S5 fills only after the DTW pass)
+    if (rev) {
+        CK(launch_rev_filter(ws.queue, ws.counters + C_QUEUE, d_train,
+                             reinterpret_cast<const float2 *>(ws.envq), ws.ends, N, L,
+                             bridge_start(L, V), ws.bsf, m.lb_lo, m.abs32, m.dtw_hi, m.abs32,
+                             ws.rlist, ws.counters + C_QUEUE2, cnt, Q * N, sms, s));
+    }
     CK(tm.mark(4));
     // S4 on the survivors, with early abandoning
-    j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
+    j.pairs = rev ? ws.rlist : ws.queue; j.seed_keys = nullptr;
+    j.count = ws.counters + (rev ? C_QUEUE2 : C_QUEUE);
     j.head = ws.counters + C_HEAD;
     j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
     CK(launch_dtw32(j, sms, s));
@@ -753,9 +779,11 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
         CK(launch_envelopes<double>(d_train, N, L, Weff, ws.env, s));
         env = ws.env;
     }
+    const bool rev = !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
+    if (rev) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
     CK(tm.mark(1));
     CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
-                         m.abs64, ws.lb, ws.seed, ws.norms, s));
+                         m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     DtwJob64 j{};
@@ -778,6 +806,14 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     CK(tm.mark(4));
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
     j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
+    if (rev) {
+        j.envq = reinterpret_cast<const double2 *>(ws.envq);
+        j.ends_bands = ws.ends;
+        j.N = N;
+        j.nb = bridge_start(L, V);
+        j.lb_lo = m.lb_lo64;
+        j.lb_abs = m.abs64;
+    }
     CK(launch_dtw64(j, sms, s));
     CK(tm.mark(5));
     const long long cap = (long long)Q * N + Q;

@@ -28,6 +28,8 @@ NO_PRUNE = 1 << 3
 NO_ABANDON = 1 << 4
 CHECK_FINITE = 1 << 5
 TIME_STAGES = 1 << 6
+NO_REVERSE = 1 << 7
+REVERSE = 1 << 14
 
 
 # Tuning values for full windows: the row layout with 32 lanes per pair (one
@@ -84,7 +86,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("lb_pruned", ctypes.c_int64),
                 ("dtw_started", ctypes.c_int64), ("dtw_abandoned", ctypes.c_int64),
                 ("dtw_cells", ctypes.c_int64), ("rechecked", ctypes.c_int64),
-                ("recheck_queries", ctypes.c_int64), ("seed_cells", ctypes.c_int64)]
+                ("recheck_queries", ctypes.c_int64), ("seed_cells", ctypes.c_int64),
+                ("lb_pruned_reverse", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -177,6 +177,31 @@ def pin_lb_enhanced_bounds_dtw_larger(orc, trials=40):
         assert orc.lb_enhanced(a, b, U, Lo, W, 1) >= lbk * (1 - 1e-12)
 
 
+def pin_reverse_bound(orc, trials=40):
+    """The cascade's reverse bound: LB_Enhanced^V(B, A), computed over A's
+    envelope, bounds DTW_W(A, B) as well (DTW_W is symmetric); its two ends
+    and its bands equal those of LB_Enhanced^V(A, B) (each band takes the
+    minimum over the cells (i, j) and (j, i)), so the two bounds differ only
+    in their LB_Keogh bridges over [n_b, L - n_b)."""
+    rng = _rng(12)
+    for _ in range(trials):
+        L = int(rng.integers(4, 120))
+        W = int(rng.integers(0, L))
+        V = int(rng.integers(1, min(12, L // 2) + 1))
+        a, b = _series(rng, L), _series(rng, L)
+        Ub, Lb = orc.envelope(b, W)
+        Ua, La = orc.envelope(a, W)
+        ab = orc.lb_enhanced(a, b, Ub, Lb, W, V)
+        ba = orc.lb_enhanced(b, a, Ua, La, W, V)
+        d = orc.dtw(a, b, W)
+        assert max(ab, ba) <= d * (1 + 1e-12), (L, W, V, ab, ba, d)
+        nb = min(L // 2, V)
+        mid = slice(nb, L - nb)
+        bridge_ab = math.fsum((a[mid] - np.clip(a[mid], Lb[mid], Ub[mid])) ** 2)
+        bridge_ba = math.fsum((b[mid] - np.clip(b[mid], La[mid], Ua[mid])) ** 2)
+        assert abs((ab - bridge_ab) - (ba - bridge_ba)) <= 1e-12 * max(ab, ba, 1.0), (L, W, V)
+
+
 def pin_lb_enhanced_w0_is_euclidean(orc, trials=30):
     """At W=0 every band is the single diagonal cell and U = Lo = B, so
     LB_Enhanced^V = DTW_0 = the Euclidean distance for every V."""
@@ -288,6 +313,7 @@ ALL_PINS = [
     pin_theorems_1_and_2,
     pin_lb_enhanced_bounds_dtw_larger,
     pin_lb_enhanced_w0_is_euclidean,
+    pin_reverse_bound,
     pin_algorithm1_abandon,
     pin_nn_brute_by_paths,
     pin_nn_w0_is_euclidean_nn,

@@ -320,6 +320,56 @@ def test_search_grouped_rows(lib, orc, g, L, N, Q):
     _check_search(lib, orc, train, labels, test, L - 1, 3, flags=lib.DTW_GROUP(grp), brute=brute)
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_search_reverse_bound(lib, orc, fp64):
+    """The cascade's reverse bound drops survivors without changing any
+    result: every queue pair is either dropped by it or has its DTW started,
+    and with NNDTW_NO_REVERSE every one is started."""
+    ds = synth.make_pairs(5)
+    dt = np.float64 if fp64 else np.float32
+    train, labels, test = ds.train[:300].astype(dt), ds.train_labels[:300], ds.test[:150].astype(dt)
+    brute = orc.nn_brute(train, labels, test, ds.W)
+    on = _check_search(lib, orc, train, labels, test, ds.W, 5, flags=lib.REVERSE, brute=brute)
+    off = _check_search(lib, orc, train, labels, test, ds.W, 5, flags=lib.NO_REVERSE, brute=brute)
+    assert on["lb_pruned_reverse"] > 0 and off["lb_pruned_reverse"] == 0
+    assert on["lb_pruned"] == off["lb_pruned"]
+    assert on["dtw_started"] + on["lb_pruned_reverse"] == off["dtw_started"]
+
+
+@pytest.mark.parametrize("g", [2, 8, 32, "rows", "rows16", "rows8"])
+def test_search_reverse_bound_layouts(lib, orc, g):
+    """The reverse bound in every DTW layout (diagonal groups, rows with 32, 16
+    and 8 lanes) on a full-window search."""
+    rng = np.random.default_rng(77)
+    L, N, Q = 160, 400, 120
+    train = synth.znormed_walks(rng, N, L).astype(np.float32)
+    test = synth.znormed_walks(rng, Q, L).astype(np.float32)
+    labels = rng.integers(0, 4, N).astype(np.int32)
+    W = L - 1 if isinstance(g, str) else 40
+    brute = orc.nn_brute(train, labels, test, W)
+    grp = {"rows": lib.ROWS_GROUP, "rows16": lib.ROWS16_GROUP, "rows8": lib.ROWS8_GROUP}.get(g, g)
+    on = _check_search(lib, orc, train, labels, test, W, 4, flags=lib.DTW_GROUP(grp) | lib.REVERSE,
+                       brute=brute)
+    off = _check_search(lib, orc, train, labels, test, W, 4, flags=lib.DTW_GROUP(grp) | lib.NO_REVERSE,
+                        brute=brute)
+    assert on["lb_pruned_reverse"] > 0 and off["lb_pruned_reverse"] == 0
+    assert on["dtw_started"] + on["lb_pruned_reverse"] == off["dtw_started"]
+
+
+def test_search_reverse_bound_defaults(lib, orc):
+    """The FP64 form tests the reverse bound by default, the FP32 form only
+    when asked (NNDTW_REVERSE)."""
+    rng = np.random.default_rng(78)
+    L, N, Q = 200, 300, 80
+    train = synth.znormed_walks(rng, N, L)
+    test = synth.znormed_walks(rng, Q, L)
+    labels = rng.integers(0, 4, N).astype(np.int32)
+    brute = orc.nn_brute(train, labels, test, 30)
+    f64 = _check_search(lib, orc, train, labels, test, 30, 4, brute=brute)
+    f32 = _check_search(lib, orc, train.astype(np.float32), labels, test.astype(np.float32), 30, 4)
+    assert f64["lb_pruned_reverse"] > 0 and f32["lb_pruned_reverse"] == 0
+
+
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
 def test_search_group_override(lib, orc, g):
     ds = synth.make_pairs(5)
