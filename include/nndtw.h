@@ -68,6 +68,9 @@ extern "C" {
 #define NNDTW_TIME_STAGES (1u << 6)  /* search: record stage events (see below)      */
 #define NNDTW_NO_REVERSE (1u << 7)   /* search: skip the reverse bound LB_Enh(B, A)  */
 #define NNDTW_REVERSE (1u << 14)     /* FP32 search: test the reverse bound LB_Enh(B, A) */
+/* search: leave-one-out over a training set (test == train, Q == N >= 2):
+ * query i never matches training series i (window learning, Sec. 1, 4). */
+#define NNDTW_LEAVE_ONE_OUT (1u << 15)
 /* search / dtw_windowed: lanes per pair of the FP32 DTW kernel, a tuning
  * choice that never changes results: NNDTW_DTW_GROUP(log2 G) with
  * G = 1, 2, 4, ..., 32; 0 (the default) lets the library choose.  A G that
@@ -249,6 +252,27 @@ typedef struct nndtw_dataset {
     double *d_nn_dist;
     unsigned flags;                /* per-dataset flags, OR-ed with the call's */
 } nndtw_dataset;
+
+/*
+ * Window learning by leave-one-out 1-NN on a training set (Sec. 1, Sec. 4):
+ * for each candidate window h_windows[k] (host array, k < n_windows) the FP32
+ * search runs with NNDTW_LEAVE_ONE_OUT (every training series against all the
+ * others), all windows at once as one batch, and d_correct[k] (device) gets
+ * the number of training series whose leave-one-out nearest neighbour has the
+ * same label.  Accuracy = d_correct[k] / N; the paper keeps the window with
+ * the highest accuracy (among equal ones this library's reading keeps the
+ * smallest window; the choice is left to the caller).  flags: search flags
+ * applied to every window (tuning choices, NNDTW_REVERSE, ...).  d_workspace:
+ * nn_dtw_learn_window_workspace_size() bytes, 256-byte aligned.  Errors:
+ * NNDTW_EINVAL for N < 2, no windows, a negative window, null pointers or
+ * invalid sizes; NNDTW_ENOSPACE; NNDTW_ECUDA.  Asynchronous on `stream`.
+ */
+NNDTW_API size_t nn_dtw_learn_window_workspace_size(int64_t N, int L, const int32_t *h_windows,
+                                                    int n_windows, int V);
+NNDTW_API int nn_dtw_learn_window(const float *d_train, const int32_t *d_train_labels,
+                                  int64_t N, int L, const int32_t *h_windows, int n_windows,
+                                  int V, unsigned flags, int64_t *d_correct, void *d_workspace,
+                                  size_t workspace_bytes, void *stream);
 
 /* Bytes of device workspace nn_dtw_search_batched needs for these datasets
  * (host array of n descriptors).  0 if any dataset has invalid sizes. */

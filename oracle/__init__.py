@@ -79,6 +79,9 @@ def _declare(lib):
     lib.oracle_nn_brute.argtypes = [_d, _i32, ctypes.c_int64, _d, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, _i32, _i32, _d, ctypes.c_int]
     lib.oracle_nn_brute.restype = None
+    lib.oracle_nn_loo.argtypes = [_d, _i32, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _i32,
+                                  _i32, _d, ctypes.c_int]
+    lib.oracle_nn_loo.restype = None
     lib.oracle_nn_pruned.argtypes = [_d, _i32, _d, _d, ctypes.c_int64, _d, ctypes.c_int64,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32, _i32, _d,
                                      _i64, ctypes.c_int]
@@ -194,6 +197,23 @@ class Oracle:
                                  _p(idx, _i32), _p(lab, _i32), _p(dist),
                                  threads or default_threads())
         return idx, lab, dist
+
+    def nn_loo(self, train, labels, W, threads=None):
+        """Leave-one-out 1-NN of every training series among the others."""
+        train = _f64(train)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        N, L = train.shape
+        idx = np.empty(N, np.int32); lab = np.empty(N, np.int32); dist = np.empty(N)
+        self.lib.oracle_nn_loo(_p(train), _p(labels, _i32), N, L, int(W), _p(idx, _i32),
+                               _p(lab, _i32), _p(dist), threads or default_threads())
+        return idx, lab, dist
+
+    def loo_correct(self, train, labels, windows, threads=None):
+        """Window learning: for each W, the number of training series whose
+        leave-one-out nearest neighbour has the same label."""
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        return np.array([int((self.nn_loo(train, labels, W, threads)[1] == labels).sum())
+                         for W in windows], np.int64)
 
     def nn_pruned(self, train, labels, test, W, V, env=None, threads=None):
         """Returns (idx, label, dist, stats) with stats = (lb_pruned, abandoned, completed)."""

@@ -176,6 +176,7 @@ typedef struct {
     int32_t *nn_idx, *nn_label;
     double *nn_dist;
     int64_t *stats; /* per-thread slot of 3 counters */
+    int exclude_self; /* leave-one-out: query q never matches training series q */
 } job_t;
 
 static void *lb_matrix_worker(void *p) {
@@ -213,6 +214,7 @@ static void *nn_brute_worker(void *p) {
         double best = INFINITY;
         int64_t bi = -1;
         for (int64_t t = 0; t < j->N; t++) {
+            if (j->exclude_self && t == q) continue;
             double d = oracle_dtw(A, j->train + t * j->L, j->L, j->W);
             if (d < best) { best = d; bi = t; }
         }
@@ -329,6 +331,18 @@ void oracle_nn_brute(const double *train, const int32_t *labels, int64_t N,
     b.test = test; b.train = train; b.labels = labels; b.Q = Q; b.N = N;
     b.L = L; b.W = W; b.nn_idx = nn_idx; b.nn_label = nn_label; b.nn_dist = nn_dist;
     run_threads(nn_brute_worker, &b, Q, nthreads);
+}
+
+/* Leave-one-out 1-NN on a training set (used to learn W, Sec. 1 and 4): the
+ * nearest neighbour of each training series among all the others, by brute
+ * force, ties to the lowest index. */
+void oracle_nn_loo(const double *train, const int32_t *labels, int64_t N, int L, int W,
+                   int32_t *nn_idx, int32_t *nn_label, double *nn_dist, int nthreads) {
+    job_t b = {0};
+    b.test = train; b.train = train; b.labels = labels; b.Q = N; b.N = N;
+    b.L = L; b.W = W; b.nn_idx = nn_idx; b.nn_label = nn_label; b.nn_dist = nn_dist;
+    b.exclude_self = 1;
+    run_threads(nn_brute_worker, &b, N, nthreads);
 }
 
 void oracle_nn_pruned(const double *train, const int32_t *labels, const double *U,

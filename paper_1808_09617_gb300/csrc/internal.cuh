@@ -94,12 +94,14 @@ cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cu
 // With seed_keys, also the Euclidean-nearest series of every query; `norms`
 // is then scratch for Q + N squared norms.  With ends_out, also the raw sum
 // of the two ends and the bands of every pair ([Q][N]): the part of Eq. 7
-// that LB_Enhanced(B, A) shares with LB_Enhanced(A, B).
+// that LB_Enhanced(B, A) shares with LB_Enhanced(A, B).  With loo (test ==
+// train, leave-one-out), pair (i, i) gets the bound +inf and is never a
+// first candidate.
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
                       T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
-                      cudaStream_t s);
+                      bool loo, cudaStream_t s);
 
 // FP32 DTW over a work list.  Pairs come from `pairs` ([count] of (q, t)) or,
 // when pairs == nullptr, from seed keys (pair p = (p, key_idx(seed_keys[p]))).

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kThreads)
 lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
           const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
           T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys,
-          const T *__restrict__ nq, const T *__restrict__ nt, T *__restrict__ ends_out) {
+          const T *__restrict__ nq, const T *__restrict__ nt, T *__restrict__ ends_out,
+          int loo) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -244,8 +245,10 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             const T raw = acc[r][c];
             const T sv = safe_scale(raw, lb_lo, abs_slack);
             if (q < Q && t < N) {
-                if (lb_out) lb_out[q * N + t] = safe ? sv : raw;
-                if (ED) {
+                // leave-one-out: a series is never its own candidate
+                const bool self = loo && q == t;
+                if (lb_out) lb_out[q * N + t] = self ? POS : (safe ? sv : raw);
+                if (ED && !self) {
                     // squared distance from the norms and the dot product
                     // (clamped: rounding may take it slightly below 0)
                     T e = nq[q] + nt[t] - T(2) * ed[r][c];
@@ -270,7 +273,7 @@ template <typename T, int MR, int MC>
 cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                            int L, int Weff, int nb, bool keogh, bool safe, T lb_lo, T abs_slack,
                            T *lb_out, unsigned long long *seed_keys, const T *nq, const T *nt,
-                           T *ends_out, cudaStream_t s) {
+                           T *ends_out, bool loo, cudaStream_t s) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     const bool ed = seed_keys != nullptr;
@@ -283,7 +286,8 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
-                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt, ends_out);
+                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt, ends_out,
+                                    loo ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -292,7 +296,8 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                       int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
-                      unsigned long long *seed_keys, T *norms, T *ends_out, cudaStream_t s) {
+                      unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
+                      cudaStream_t s) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
     if (seed_keys) {
         // squared norms of the queries (norms[0..Q)) and training series
@@ -313,18 +318,19 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
     const bool small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
     if (small) return launch_lb_tile<T, 2, 2>(test, Q, train, env, N, L, Weff, nb, keogh, safe,
                                               lb_lo, abs_slack, lb_out, seed_keys, nq, nt,
-                                              keogh ? nullptr : ends_out, s);
+                                              keogh ? nullptr : ends_out, loo, s);
     return launch_lb_tile<T, 4, 4>(test, Q, train, env, N, L, Weff, nb, keogh, safe, lb_lo,
                                    abs_slack, lb_out, seed_keys, nq, nt,
-                                   keogh ? nullptr : ends_out, s);
+                                   keogh ? nullptr : ends_out, loo, s);
 }
 
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                       int, int, int, bool, bool, float, float, float *,
-                                      unsigned long long *, float *, float *, cudaStream_t);
+                                      unsigned long long *, float *, float *, bool,
+                                      cudaStream_t);
 template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
                                        int64_t, int, int, int, bool, bool, double, double,
                                        double *, unsigned long long *, double *, double *,
-                                       cudaStream_t);
+                                       bool, cudaStream_t);
 
 }  // namespace nndtw

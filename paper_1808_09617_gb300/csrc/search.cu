@@ -531,7 +531,7 @@ int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const floa
     const Margins m = make_margins(L);
     CK(launch_lb<float>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                         (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out, nullptr,
-                        nullptr, nullptr, (cudaStream_t)stream));
+                        nullptr, nullptr, false, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -544,7 +544,7 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
     const Margins m = make_margins(L);
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
-                         nullptr, nullptr, (cudaStream_t)stream));
+                         nullptr, nullptr, false, (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -606,6 +606,7 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
                   unsigned flags, int32_t *d_nn_idx, int32_t *d_nn_label, double *d_nn_dist,
                   void *d_workspace, size_t workspace_bytes, nndtw_stats *stats, void *stream) {
     if (!search_sizes_ok(N, Q, L, W, V)) return NNDTW_EINVAL;
+    if ((flags & NNDTW_LEAVE_ONE_OUT) && (Q != N || N < 2)) return NNDTW_EINVAL;
     if (Q == 0) {
         if (stats) std::memset(stats, 0, sizeof(*stats));
         return NNDTW_OK;
@@ -658,7 +659,8 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     CK(tm.mark(1));
     // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
     CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
-                        ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr, s));
+                        ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
+                        (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     // S4 on the first candidate of every query: initial upper bounds
@@ -741,6 +743,7 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
                       void *d_workspace, size_t workspace_bytes, nndtw_stats *stats,
                       void *stream) {
     if (!search_sizes_ok(N, Q, L, W, V)) return NNDTW_EINVAL;
+    if ((flags & NNDTW_LEAVE_ONE_OUT) && (Q != N || N < 2)) return NNDTW_EINVAL;
     if (Q == 0) {
         if (stats) std::memset(stats, 0, sizeof(*stats));
         return NNDTW_OK;
@@ -783,7 +786,8 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     if (rev) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
     CK(tm.mark(1));
     CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
-                         m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr, s));
+                         m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
+                         (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
     CK(tm.mark(2));
     unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
     DtwJob64 j{};

@@ -30,6 +30,7 @@ CHECK_FINITE = 1 << 5
 TIME_STAGES = 1 << 6
 NO_REVERSE = 1 << 7
 REVERSE = 1 << 14
+LEAVE_ONE_OUT = 1 << 15
 
 
 # Tuning values for full windows: the row layout with 32 lanes per pair (one
@@ -137,6 +138,11 @@ def _declare(lib):
     lib.nn_dtw_batch_workspace_size.restype = _sz
     lib.nn_dtw_search_batched.argtypes = [ctypes.POINTER(DatasetDesc), _int, _vp, _sz, _uint, _vp]
     lib.nn_dtw_search_batched.restype = _int
+    lib.nn_dtw_learn_window_workspace_size.argtypes = [_i64, _int, _vp, _int, _int]
+    lib.nn_dtw_learn_window_workspace_size.restype = _sz
+    lib.nn_dtw_learn_window.argtypes = [_vp, _vp, _i64, _int, _vp, _int, _int, _uint, _vp, _vp,
+                                        _sz, _vp]
+    lib.nn_dtw_learn_window.restype = _int
     lib.nn_dtw_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float)]
     lib.nn_dtw_stage_times.restype = _int
     lib.nn_dtw_probe_sink_bytes.argtypes = []
@@ -332,6 +338,52 @@ def _descs(sets, outs):
             _dev(o[0], torch.int32, "nn_idx"), _dev(o[1], torch.int32, "nn_label"),
             _dev(o[2], torch.float64, "nn_dist"), int(d.get("flags", 0)))
     return arr
+
+
+def _windows_array(windows):
+    w = np.ascontiguousarray(np.asarray(windows, dtype=np.int32))
+    if w.ndim != 1 or w.size == 0:
+        raise ValueError("windows must be a non-empty 1-D list")
+    return w
+
+
+def nn_dtw_learn_window_workspace_size(N: int, L: int, windows, V: int) -> int:
+    w = _windows_array(windows)
+    return int(load().nn_dtw_learn_window_workspace_size(N, L, w.ctypes.data, w.size, V))
+
+
+def nn_dtw_learn_window(train, labels, windows, V: int, flags: int = 0, workspace=None,
+                        correct=None, stream=None):
+    """Window learning by leave-one-out 1-NN on a training set: for every
+    candidate window, the number of training series whose leave-one-out
+    nearest neighbour has the same label (int64 tensor [len(windows)])."""
+    import torch
+    lib = load()
+    N, L = train.shape
+    w = _windows_array(windows)
+    if workspace is None:
+        n = nn_dtw_learn_window_workspace_size(N, L, w, V)
+        if n == 0:
+            raise NnDtwError(EINVAL, "nn_dtw_learn_window_workspace_size")
+        workspace = torch.empty(n, dtype=torch.uint8, device=train.device)
+    if correct is None:
+        correct = torch.empty(w.size, dtype=torch.int64, device=train.device)
+    _check(lib.nn_dtw_learn_window(_dev(train, torch.float32, "train", 2),
+                                   _dev(labels, torch.int32, "labels"), N, L, w.ctypes.data,
+                                   w.size, int(V), int(flags), _dev(correct, torch.int64, "correct"),
+                                   workspace.data_ptr(), workspace.numel(), _stream(stream)),
+           "nn_dtw_learn_window")
+    return correct
+
+
+def learn_window(train, labels, windows, V: int, flags: int = 0):
+    """The learned window: the candidate with the highest leave-one-out
+    accuracy, the smallest such window among equals.  Returns (W, accuracies)."""
+    correct = nn_dtw_learn_window(train, labels, windows, V, flags).cpu().numpy()
+    acc = correct / float(train.shape[0])
+    w = _windows_array(windows)
+    best = max(range(w.size), key=lambda k: (acc[k], -w[k]))
+    return int(w[best]), acc
 
 
 def nn_dtw_batch_workspace_size(sets) -> int:

@@ -302,6 +302,33 @@ def pin_nn_pruned_equals_brute(orc):
         assert pi[0] == 0 and pl[0] == 7 and pd[0] == 0.0
 
 
+def pin_nn_loo_equals_removal(orc):
+    """Leave-one-out 1-NN (window learning): the neighbour of series q among
+    the others is the brute-force neighbour in the set with q removed; exact
+    duplicates find each other at distance 0."""
+    rng = _rng(13)
+    for trial in range(6):
+        N, L = int(rng.integers(3, 12)), int(rng.integers(4, 30))
+        W = int(rng.integers(0, L))
+        tr = rng.standard_normal((N, L))
+        if trial % 2:
+            tr[N - 1] = tr[0]                       # a duplicate pair
+        lab = rng.integers(0, 3, N).astype(np.int32)
+        li, ll, ld = orc.nn_loo(tr, lab, W)
+        for q in range(N):
+            keep = np.array([t for t in range(N) if t != q])
+            bi, bl, bd = orc.nn_brute(tr[keep], lab[keep], tr[q:q + 1], W)
+            assert li[q] == keep[bi[0]] and ll[q] == bl[0] and ld[q] == bd[0], (trial, q)
+        if trial % 2:
+            assert li[0] == N - 1 and ld[0] == 0.0 and li[N - 1] == 0 and ld[N - 1] == 0.0
+    # the counts of window learning follow from the neighbours' labels
+    tr = rng.standard_normal((8, 16))
+    lab = np.array([0, 0, 1, 1, 2, 2, 0, 1], np.int32)
+    c = orc.loo_correct(tr, lab, [0, 3, 15])
+    for k, W in enumerate([0, 3, 15]):
+        assert c[k] == int((orc.nn_loo(tr, lab, W)[1] == lab).sum())
+
+
 ALL_PINS = [
     pin_dtw_w0_is_squared_euclidean,
     pin_dtw_equals_min_over_all_paths,
@@ -318,4 +345,5 @@ ALL_PINS = [
     pin_nn_brute_by_paths,
     pin_nn_w0_is_euclidean_nn,
     pin_nn_pruned_equals_brute,
+    pin_nn_loo_equals_removal,
 ]

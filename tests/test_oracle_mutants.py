@@ -39,6 +39,7 @@ MUTANTS = {
         "for (int i = n_bands; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])"),
     "lbenh_abandon_wrong_way": ("if (res >= D) return INFINITY;", "if (res < D) return INFINITY;"),
     "nn_ties_to_highest_index": ("if (d < best) { best = d; bi = t; }", "if (d <= best) { best = d; bi = t; }"),
+    "loo_keeps_the_query_itself": ("if (j->exclude_self && t == q) continue;", ""),
     "pruned_search_drops_tie_update": (
         "if (d < D || (d == D && t < bi)) { D = d; bi = t; }",
         "if (d < D) { D = d; bi = t; }"),
