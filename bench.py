@@ -336,6 +336,75 @@ def run_reference(args, dsets, desc):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ window learning
+
+def run_window(args):
+    """Window learning on the 500-series training set of the pairs workload
+    (L=256): leave-one-out 1-NN accuracy for W = 0, 1 %, ..., 100 % of L (the
+    paper's protocol), all windows in one batched call per step."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw, synth
+    ds = synth.make_pairs(5)
+    L, N, V = ds.L, ds.N, ds.V
+    windows = sorted({int(np.floor(r / 100.0 * L + 0.5)) for r in range(101)})
+    windows = [min(w, L - 1) for w in windows]
+    windows = sorted(set(windows))
+    dev = torch.device("cuda", 0)
+    nndtw.load()
+    train = torch.from_numpy(ds.train).to(dev)
+    labels = torch.from_numpy(ds.train_labels).to(dev)
+    ws = torch.empty(nndtw.nn_dtw_learn_window_workspace_size(N, L, windows, V),
+                     dtype=torch.uint8, device=dev)
+    correct = torch.empty(len(windows), dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    run = lambda: nndtw.nn_dtw_learn_window(train, labels, windows, V, workspace=ws,
+                                            correct=correct)
+    for _ in range(args.warmup):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sel = device_selector(torch, dev, 0)
+    with ClockSampler(sel) as clk:
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            run()
+            b.record()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    acc = correct.cpu().numpy() / float(N)
+    best = max(range(len(windows)), key=lambda k: (acc[k], -windows[k]))
+    # the oracle on the host cores, a bounded sample: three of the windows
+    from oracle import get as oracle_get, default_threads
+    orc = oracle_get()
+    sample_w = [windows[0], windows[len(windows) // 10], windows[len(windows) // 5]]
+    t0 = time.perf_counter()
+    ref = orc.loo_correct(ds.train, ds.train_labels, sample_w)
+    cpu_s = time.perf_counter() - t0
+    got = {w: int(correct[windows.index(w)].item()) for w in sample_w}
+    queries = N * len(windows)
+    line = {"metric": "window learning: leave-one-out 1-NN queries/s over candidate windows",
+            "value": queries / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"window learning: train {N}, L={L}, V={V}, "
+                                   f"{len(windows)} windows (0..100 % of L in 1 % steps)",
+                       "l2": "flushed before every step (256 MiB write, outside the events)"},
+            "learned_window": windows[best], "learned_accuracy": float(acc[best]),
+            "accuracy_by_window": {str(w): float(a) for w, a in zip(windows, acc)},
+            "oracle_check": {"windows": sample_w, "gpu_correct": [got[w] for w in sample_w],
+                             "oracle_correct": [int(c) for c in ref]},
+            "cpu_baseline": {"value": N * len(sample_w) / cpu_s, "unit": "queries/s",
+                             "cores": default_threads(), "kind": "oracle",
+                             "sample": f"leave-one-out brute force for W in {sample_w}, "
+                                       f"{cpu_s:.1f} s"},
+            "gpu_launches": (KERNELS_PER_SEARCH * len(windows) + 1) * args.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 def run_serving(args):
@@ -425,6 +494,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             run_serving(args)
+        return
+    if args.workload == "window":
+        if rank == 0:
+            run_window(args)
         return
     if args.workload == "batched":
         dsets, desc = batched_workload()
