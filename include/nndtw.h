@@ -77,9 +77,10 @@ extern "C" {
  * cannot hold the window (more than 64 diagonals per lane) is ignored. */
 #define NNDTW_DTW_GROUP(log2g) ((unsigned)((log2g) + 1) << 8)
 #define NNDTW_DTW_GROUP_MASK (7u << 8)
-/* search / dtw_windowed: for full windows (W >= L-1, L <= 2048) sweep DTW by
- * rows, one pair per warp (the default for such windows when no
- * NNDTW_DTW_GROUP is given); ignored for other windows.  Combined with
+/* search / dtw_windowed: for full windows (W >= L-1) sweep DTW by rows, one
+ * pair per warp for L <= 2048 and one pair per 128-thread CTA for L <= 4096
+ * (the default for such windows when no NNDTW_DTW_GROUP is given); ignored
+ * for other windows.  Combined with
  * NNDTW_DTW_ROWS_LANES16 (L <= 1024) or NNDTW_DTW_ROWS_LANES8 (L <= 512) a
  * pair takes 16 or 8 lanes instead (a tuning choice; results never change;
  * ignored where L is too long). */

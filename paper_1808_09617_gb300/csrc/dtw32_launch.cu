@@ -70,6 +70,8 @@ cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
         return launch_dtw32_rowsg(job, 8, sm_count, s);
     if ((job.group == 0 || job.group >= kRowsGroup) && dtw32_rows_ok(job.L, job.W))
         return launch_dtw32_rows(job, sm_count, s);
+    if ((job.group == 0 || job.group >= kRowsGroup) && dtw32_rowsc_ok(job.L, job.W))
+        return launch_dtw32_rowsc(job, sm_count, s);
     int G = 0, H = 0;
     if (!dtw32_shape(job.W, job.group, &G, &H)) return launch_dtw32_wide(job, sm_count, s);
     Dtw32Fn fn = pick_fn(H);

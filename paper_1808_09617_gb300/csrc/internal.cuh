@@ -127,6 +127,8 @@ cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_rows(const DtwJob32 &job, int sm_count, cudaStream_t s);
 bool dtw32_rowsg_ok(int L, int W, int G);
+bool dtw32_rowsc_ok(int L, int W);   // full window, 2048 < L <= 4096: a CTA per pair
+cudaError_t launch_dtw32_rowsc(const DtwJob32 &job, int sm_count, cudaStream_t s);
 cudaError_t launch_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, cudaStream_t s);
 bool dtw32_rows_ok(int L, int W);   // full window and L small enough for the row kernel
 constexpr int kRowsGroup = 64;      // DtwJob32::group value selecting the row kernel

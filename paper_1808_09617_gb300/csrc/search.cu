@@ -673,7 +673,8 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     j.pairs = nullptr; j.seed_keys = ws.seed; j.n_seed = Q; j.head = nullptr; j.abandon = 0;
     // one pair per query: latency-bound, so spread each pair over the widest group
     const int main_group = j.group;
-    j.group = dtw32_rows_ok(L, Weff) ? kRowsGroup : dtw32_wide_group(Weff);
+    j.group = (dtw32_rows_ok(L, Weff) || dtw32_rowsc_ok(L, Weff)) ? kRowsGroup
+                                                                : dtw32_wide_group(Weff);
     CK(launch_dtw32(j, sms, s));
     j.group = main_group;
     CK(tm.mark(3));

@@ -274,7 +274,8 @@ def test_dtw_every_group_width_same_values(lib, orc, L, W):
         np.testing.assert_allclose(got, ref, rtol=RTOL32, atol=0, err_msg=f"G={g}")
 
 
-@pytest.mark.parametrize("L", [1, 2, 5, 31, 32, 33, 64, 100, 1000, 2047, 2048])
+@pytest.mark.parametrize("L", [1, 2, 5, 31, 32, 33, 64, 100, 1000, 2047, 2048, 2049, 2600, 3001,
+                               4095, 4096])
 def test_dtw_full_window_row_layout(lib, orc, L):
     """Full windows (W >= L-1) use the row layout by default; the diagonal layout
     (forced by a group width) must agree."""
@@ -368,6 +369,18 @@ def test_search_reverse_bound_defaults(lib, orc):
     f64 = _check_search(lib, orc, train, labels, test, 30, 4, brute=brute)
     f32 = _check_search(lib, orc, train.astype(np.float32), labels, test.astype(np.float32), 30, 4)
     assert f64["lb_pruned_reverse"] > 0 and f32["lb_pruned_reverse"] == 0
+
+
+@pytest.mark.parametrize("L,N,Q", [(3000, 40, 12), (4096, 20, 6)])
+def test_search_long_full_window(lib, orc, L, N, Q):
+    """Full windows of series longer than 2048 (a CTA per pair in the row
+    layout): the exhaustive FP64 nearest neighbours, ties included."""
+    rng = np.random.default_rng(L)
+    train = synth.znormed_walks(rng, N, L).astype(np.float32)
+    test = synth.znormed_walks(rng, Q, L).astype(np.float32)
+    test[0] = train[5]
+    labels = rng.integers(0, 3, N).astype(np.int32)
+    _check_search(lib, orc, train, labels, test, L - 1, 4)
 
 
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
