@@ -475,6 +475,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each step's kernels directly instead of replaying a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the lanes-per-pair autotuner")
+    ap.add_argument("--reverse", action="store_true",
+                    help="test the cascade's reverse bound in every dataset (with --dtw-group "
+                         "or --no-tune; the tuner decides otherwise)")
     ap.add_argument("--dtw-group", type=int, default=0,
                     help="lanes per pair for every dataset (1..32, or 64 for the row layout); "
                          "implies --no-tune")
@@ -529,8 +532,12 @@ def main():
     tuned = {}
     if args.dtw_group:
         for i, s in enumerate(sets):
-            s["flags"] = nndtw.DTW_GROUP(args.dtw_group)
-            tuned[i] = args.dtw_group
+            s["flags"] = nndtw.DTW_GROUP(args.dtw_group) | (nndtw.REVERSE if args.reverse else 0)
+            tuned[i] = {"group": args.dtw_group, "reverse": bool(args.reverse)}
+    elif args.no_tune and args.reverse:
+        for i, s in enumerate(sets):
+            s["flags"] = nndtw.REVERSE
+            tuned[i] = {"group": 0, "reverse": True}
     elif not args.no_tune:
         for i, (d, s) in enumerate(zip(dsets, sets)):
             if d.N * d.Q >= 50_000:
