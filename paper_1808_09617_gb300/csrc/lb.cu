@@ -114,7 +114,7 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
           const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
           T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys,
           const T *__restrict__ nq, const T *__restrict__ nt, T *__restrict__ ends_out,
-          int loo) {
+          int loo, int qfast) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,7 +131,10 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     T *Bb = Ab + kQT * (nb <= kNBMax ? bstride : 0);               // [kNT][2nb+1]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t q0 = (int64_t)blockIdx.y * kQT, t0 = (int64_t)blockIdx.x * kNT;
+    // query tiles vary fastest (qfast), so the CTAs resident at one time share
+    // a few training tiles (series and envelopes read from DRAM about once)
+    const int64_t q0 = (int64_t)(qfast ? blockIdx.x : blockIdx.y) * kQT;
+    const int64_t t0 = (int64_t)(qfast ? blockIdx.y : blockIdx.x) * kNT;
 
     T acc[MR][MC], ed[MR][MC];
 #pragma unroll
@@ -283,11 +286,13 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((N + kNT - 1) / kNT), (unsigned)((Q + kQT - 1) / kQT));
+    const long long qt = (Q + kQT - 1) / kQT, nt_tiles = (N + kNT - 1) / kNT;
+    const int qfast = nt_tiles <= 65535 ? 1 : 0;   // grid.y holds at most 65535 tiles
+    dim3 grid(qfast ? (unsigned)qt : (unsigned)nt_tiles, qfast ? (unsigned)nt_tiles : (unsigned)qt);
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
                                     lb_lo, abs_slack, lb_out, seed_keys, nq, nt, ends_out,
-                                    loo ? 1 : 0);
+                                    loo ? 1 : 0, qfast);
     return cudaGetLastError();
 }
 

@@ -64,11 +64,12 @@ template <> struct UbOf<double> {
     }
 };
 
+// Bucket of a kept pair: kBuckets equal slices of bound / upper bound
+// (inv = kBuckets / ub, computed once per query; only the order of the
+// queue depends on it).
 template <typename T>
-__device__ __forceinline__ int bucket_of(T lb, T ub) {
-    if (!(ub > T(0))) return 0;
-    const T r = lb / ub;
-    int b = (int)(r * T(kBuckets));
+__device__ __forceinline__ int bucket_of(T lb, T inv) {
+    const int b = (int)(lb * inv);
     return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
 }
 
@@ -76,6 +77,8 @@ __device__ __forceinline__ int bucket_of(T lb, T ub) {
 // pass 2 (scatter == 1): write them at bucket offset + position.
 // Both passes aggregate per block in shared memory: one global atomic per
 // bucket per block-iteration (pass 2) or per block (pass 1).
+constexpr int kCompactE = 8;   // pairs per thread per compaction round
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
@@ -99,22 +102,36 @@ compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
         }
     }
     __syncthreads();
+    // each round covers kCompactE * 256 consecutive pairs of a row; element e
+    // of thread tid is t0 + e * 256 + tid (coalesced loads)
+    constexpr int E = kCompactE;
     for (int64_t q = blockIdx.y; q < Q; q += gridDim.y) {
         const T ub = ubof(bsf[q]);
+        const T inv = ub > T(0) && ub < inf_of<T>() ? T(kBuckets) / ub : T(0);
         const uint32_t st = key_idx(seed[q]);
         const T *row = lb + q * N;
-        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < N;
-             t0 += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t t = t0 + tid;
-            bool keep = false;
-            int b = 0;
-            if (t < N) {
-                const T v = row[t];
-                keep = (no_prune || v <= ub) && (uint32_t)t != st;
-                b = bucket_of(v, ub);
+        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x * E; t0 < N;
+             t0 += (int64_t)gridDim.x * blockDim.x * E) {
+            unsigned keepm = 0;
+            unsigned pos[E];
+            int bk[E];
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int64_t t = t0 + (int64_t)e * blockDim.x + tid;
+                bool keep = false;
+                bk[e] = 0;
+                pos[e] = 0;
+                if (t < N) {
+                    const T v = row[t];
+                    // (a leave-one-out pair (q, q) has the bound +inf: never kept)
+                    keep = (no_prune ? v < inf_of<T>() : v <= ub) && (uint32_t)t != st;
+                    if (keep) bk[e] = bucket_of(v, inv);
+                }
+                if (keep) {
+                    keepm |= 1u << e;
+                    pos[e] = atomicAdd(&scount[bk[e]], 1u);
+                }
             }
-            unsigned int pos = 0;
-            if (keep) pos = atomicAdd(&scount[b], 1u);
             if (!scatter) continue;
             __syncthreads();
             if (tid < kBuckets) {
@@ -122,7 +139,11 @@ compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
                 sbase[tid] = c ? atomicAdd(bcursor + tid, (unsigned long long)c) : 0ull;
             }
             __syncthreads();
-            if (keep) queue[boff[b] + sbase[b] + pos] = make_uint2((uint32_t)q, (uint32_t)t);
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                if ((keepm >> e) & 1u)
+                    queue[boff[bk[e]] + sbase[bk[e]] + pos[e]] =
+                        make_uint2((uint32_t)q, (uint32_t)(t0 + (int64_t)e * blockDim.x + tid));
             __syncthreads();
             if (tid < kBuckets) scount[tid] = 0;
             __syncthreads();
@@ -373,7 +394,8 @@ unsigned grid_small(long long n) {
 }
 
 dim3 grid_compact(int64_t Q, int64_t N) {
-    long long gx = (N + kSmallThreads - 1) / kSmallThreads;
+    const long long per_block = (long long)kSmallThreads * kCompactE;
+    long long gx = (N + per_block - 1) / per_block;
     if (gx > 64) gx = 64;
     long long gy = Q < 65535 ? Q : 65535;
     if (gy < 1) gy = 1;

@@ -43,6 +43,19 @@ def test_loo_search_matches_oracle(lib, orc, fp64, N, L, W, V):
         assert idx[0] == N - 1 and idx[N - 1] == 0 and dist[0] == 0.0
 
 
+@pytest.mark.parametrize("extra", ["NO_PRUNE", "NO_ABANDON", "REVERSE"])
+def test_loo_search_with_flags(lib, orc, extra):
+    """Leave-one-out with the bound or the abandoning switched off, or the
+    reverse bound on: the same neighbours, never the query itself."""
+    x, lab = _set(5, 70, 48)
+    x = x.astype(np.float32)
+    ri, rl, rd = orc.nn_loo(x, lab, 9)
+    r = lib.nn_dtw_search(_t(x), _t(lab), _t(x), 9, 3,
+                          flags=lib.LEAVE_ONE_OUT | getattr(lib, extra))
+    np.testing.assert_array_equal(r.nn_idx.cpu().numpy(), ri)
+    np.testing.assert_array_equal(r.nn_label.cpu().numpy(), rl)
+
+
 def test_loo_needs_a_square_set(lib):
     x, lab = _set(3, 20, 16)
     x = x.astype(np.float32)
