@@ -66,6 +66,21 @@ __device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) 
     return v > 0.0 ? v : 0.0;
 }
 
+// Asynchronous copy of one element (4, 8 or 16 bytes) from global to shared
+// memory; when !valid nothing is read and the element is zero-filled.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n"
+                 :: "r"(sa), "l"(gmem), "n"(BYTES), "r"(valid ? BYTES : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
 // The two ends and the V-1 left and right bands of Eq. 7 for one pair:
 // element i of A and B is Ap[i], Bp[i] for i < nb, and Ap[last - k],
 // Bp[last - k] for the k-th element from the end.  Inlined at each call site
@@ -87,6 +102,19 @@ __device__ __forceinline__ T band_terms(const T *Ap, const T *Bp, int last, int 
         res = res + mL + mR;
     }
     return res;
+}
+
+// Shared-memory layout of one stage of chunk tiles: queries [kLC][kQT+1],
+// then (16-byte aligned) envelope pairs [kLC][kNT+1], then training values
+// [kLC][kNT+1] when the Euclidean seed is fused in.
+template <typename T, int kQT>
+__host__ __device__ constexpr size_t lb_es_offset() {
+    return (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16;
+}
+template <typename T, int kQT, int kNT, bool ED>
+__host__ __device__ constexpr size_t lb_stage_bytes() {
+    return (lb_es_offset<T, kQT>() + 2 * sizeof(T) * kLC * (kNT + 1) +
+            (ED ? sizeof(T) * kLC * (kNT + 1) : 0) + 15) / 16 * 16;
 }
 
 // Squared norm of every row of a and of b (one warp per row).
@@ -118,16 +146,19 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // offsets from the shared array itself (not through integer casts), so
-    // that every access compiles to a shared-memory load
-    constexpr size_t kEsOff = (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16;
-    T *As = reinterpret_cast<T *>(smem_raw);                      // [kLC][kQT+1]
-    T2 *Es = reinterpret_cast<T2 *>(smem_raw + kEsOff);           // [kLC][kNT+1], 16-byte aligned
-    T *Bs = reinterpret_cast<T *>(Es + kLC * (kNT + 1));           // [kLC][kNT+1] (ED only)
+    // Two stages of chunk tiles (the next chunk is copied in while the
+    // current one is used), then the band staging.  Offsets are taken from
+    // the shared array itself (not through integer casts), so that every
+    // access compiles to a shared-memory load.
+    constexpr size_t kEsOff = lb_es_offset<T, kQT>();
+    constexpr size_t kStage = lb_stage_bytes<T, kQT, kNT, ED>();
+    T *As0 = reinterpret_cast<T *>(smem_raw);                     // [kLC][kQT+1]
+    T2 *Es0 = reinterpret_cast<T2 *>(smem_raw + kEsOff);          // [kLC][kNT+1], 16-byte aligned
+    T *Bs0 = reinterpret_cast<T *>(Es0 + kLC * (kNT + 1));         // [kLC][kNT+1] (ED only)
     // band staging, rows padded to an odd stride so that the 16 series a
     // warp reads at once fall in distinct banks
     const int bstride = 2 * nb + 1;
-    T *Ab = Bs + (ED ? kLC * (kNT + 1) : 0);                       // [kQT][2nb+1]
+    T *Ab = reinterpret_cast<T *>(smem_raw + 2 * kStage);          // [kQT][2nb+1]
     T *Bb = Ab + kQT * (nb <= kNBMax ? bstride : 0);               // [kNT][2nb+1]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -146,33 +177,48 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     const T POS = inf_of<T>();
 
     const int cbeg = ED ? 0 : (mlo / kLC) * kLC, cend = ED ? L : mhi;
-    for (int c0 = cbeg; c0 < cend; c0 += kLC) {
+    // copy the tiles of the chunk starting at c0 into stage st
+    auto stage = [&](int c0, int st) {
+        T *As = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(As0) + st * kStage);
+        T2 *Es = reinterpret_cast<T2 *>(reinterpret_cast<unsigned char *>(Es0) + st * kStage);
+        T *Bs = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(Bs0) + st * kStage);
         for (int idx = tid; idx < kQT * kLC; idx += kThreads) {
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
             const int64_t q = q0 + row;
-            T v = T(0);
-            if (q < Q && i < L) v = test[q * L + i];
-            As[col * (kQT + 1) + row] = v;
+            const bool ok = q < Q && i < L;
+            cp_async<sizeof(T)>(&As[col * (kQT + 1) + row], ok ? test + q * L + i : test, ok);
         }
         if (ED) {
             for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
                 const int row = idx / kLC, col = idx % kLC, i = c0 + col;
                 const int64_t t = t0 + row;
-                Bs[col * (kNT + 1) + row] = (t < N && i < L) ? train[t * L + i] : T(0);
+                const bool ok = t < N && i < L;
+                cp_async<sizeof(T)>(&Bs[col * (kNT + 1) + row], ok ? train + t * L + i : train, ok);
             }
         }
         for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
             const int64_t t = t0 + row;
-            T2 e;
-            e.x = POS; e.y = -POS;
             if (t < N && i >= mlo && i < mhi) {
-                const T *p = env + 2 * (t * L + i);
-                e.x = p[0]; e.y = p[1];
+                cp_async<sizeof(T2)>(&Es[col * (kNT + 1) + row], env + 2 * (t * L + i), true);
+            } else {
+                T2 e;
+                e.x = POS; e.y = -POS;   // outside the bridge: the term is 0
+                Es[col * (kNT + 1) + row] = e;
             }
-            Es[col * (kNT + 1) + row] = e;
         }
+    };
+    if (cbeg < cend) stage(cbeg, 0);
+    cp_async_commit();
+    int st = 0;
+    for (int c0 = cbeg; c0 < cend; c0 += kLC, st ^= 1) {
+        if (c0 + kLC < cend) stage(c0 + kLC, st ^ 1);
+        cp_async_commit();
+        cp_async_wait_1();       // this chunk's copies have landed
         __syncthreads();
+        const T *As = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(As0) + st * kStage);
+        const T2 *Es = reinterpret_cast<const T2 *>(reinterpret_cast<unsigned char *>(Es0) + st * kStage);
+        const T *Bs = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(Bs0) + st * kStage);
 #pragma unroll 4
         for (int col = 0; col < kLC; col++) {
             T a[MR];
@@ -280,8 +326,7 @@ cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *en
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     const bool ed = seed_keys != nullptr;
-    size_t smem = (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16 + sizeof(T2) * kLC * (kNT + 1);
-    if (ed) smem += sizeof(T) * kLC * (kNT + 1);
+    size_t smem = 2 * (ed ? lb_stage_bytes<T, kQT, kNT, true>() : lb_stage_bytes<T, kQT, kNT, false>());
     if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * (2 * nb + 1);
     auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
