@@ -46,6 +46,25 @@ FALLBACK_HBM_GBS = 6800.0
 STAGES = ("envelopes", "lb", "seed", "compact", "dtw", "recheck", "final", "total")
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); ``dist`` is
+    torch.distributed or None for a single process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms: float) -> float:
+    """Units per second of the whole job: every rank (an independent replica)
+    processes units_per_rank units in the slowest rank's ms."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 # ------------------------------------------------------------------ workloads
 
 def single_workload(name: str):
@@ -626,12 +645,8 @@ def main():
         if dist:
             dist.barrier()
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * Qtot / (ms / 1000.0)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
+    value = whole_job_rate(world, Qtot, ms)
     clocks = clk.summary()
 
     stage_ms = {k: sum(d[k] for d in stages) / len(stages) for k in STAGES}
@@ -693,11 +708,7 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
     if not batched:
         nndtw.nn_dtw_stage_times()
-    e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1000.0 * sum(e2e_t) / len(e2e_t), dist, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -718,7 +729,7 @@ def main():
                        "autotuned": {str(k): v for k, v in tuned.items()}},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * Qtot / (e2e_ms / 1000.0), "unit": UNIT,
+            "e2e": {"value": whole_job_rate(world, Qtot, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(d.train.nbytes + d.test.nbytes +
                                                   d.train_labels.nbytes for d in dsets)),
                     "d2h_bytes_per_step": int(Qtot * (4 + 4 + 8)), "ms_per_step": e2e_ms},
