@@ -69,6 +69,9 @@ def _declare(lib):
     lib.oracle_lb_enhanced.argtypes = [_d, _d, _d, _d, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double]
     lib.oracle_lb_enhanced.restype = ctypes.c_double
+    lib.oracle_lb_enhanced_improved.argtypes = [_d, _d, _d, _d, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int]
+    lib.oracle_lb_enhanced_improved.restype = ctypes.c_double
     lib.oracle_lb_matrix.argtypes = [_d, ctypes.c_int64, _d, _d, _d, ctypes.c_int64,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      _d, ctypes.c_int]
@@ -149,6 +152,12 @@ class Oracle:
         return self.lib.oracle_lb_enhanced(_p(a), _p(b), _p(U), _p(Lo), a.shape[0],
                                            int(W), int(V), float(D))
 
+    def lb_enhanced_improved(self, a, b, U, Lo, W, V):
+        """LB_Enhanced^V with the LB_Improved bridge (Sec. 5, Sec. 2.2.4)."""
+        a = _f64(a); b = _f64(b); U = _f64(U); Lo = _f64(Lo)
+        return self.lib.oracle_lb_enhanced_improved(_p(a), _p(b), _p(U), _p(Lo), a.shape[0],
+                                                    int(W), int(V))
+
     # -- batched drivers ----------------------------------------------------
     def envelopes(self, train, W):
         train = _f64(train)
@@ -164,7 +173,7 @@ class Oracle:
         U, Lo = env if env is not None else self.envelopes(train, W)
         U = _f64(U); Lo = _f64(Lo)
         out = np.empty((Q, N))
-        k = {"enhanced": 0, "keogh": 1}[kind]
+        k = {"enhanced": 0, "keogh": 1, "improved": 2}[kind]
         self.lib.oracle_lb_matrix(_p(test), Q, _p(train), _p(U), _p(Lo), N, L, int(W),
                                   int(V), k, _p(out), threads or default_threads())
         return out

@@ -162,6 +162,40 @@ double oracle_lb_enhanced(const double *A, const double *B, const double *U,
 #undef b
 }
 
+/*
+ * LB_Enhanced^V_W(A, B) with its LB_Keogh bridge replaced by LB_Improved, the
+ * combination that the conclusion (Sec. 5) proposes.  LB_Improved (Sec. 2.2.4)
+ * adds to LB_Keogh(A, B) a second LB_Keogh: that of B against the envelope of
+ * A', the projection of A onto B's envelope (Eq. 5).  Here both passes run
+ * over the bridge only, i = n_bands+1 .. L-n_bands, so that the bands stay
+ * as in Algorithm 1:
+ *   res = LB_Enhanced^V_W(A, B)                 (ends, bands, first pass)
+ *   A'_i = U_i if A_i > U_i, Lo_i if A_i < Lo_i, A_i otherwise, i = 1..L
+ *   (U', Lo') = envelopes of A' over the window W (Eq. 3-4)
+ *   res += sum_{j = n_bands+1 .. L-n_bands} LB_Keogh term of B_j against (U'_j, Lo'_j).
+ * Requires L >= 2.
+ */
+double oracle_lb_enhanced_improved(const double *A, const double *B, const double *U,
+                                   const double *Lo, int L, int W, int V) {
+    double res = oracle_lb_enhanced(A, B, U, Lo, L, W, V, INFINITY);
+    const int nb = imin(L / 2, V);   /* n_bands of Algorithm 1 */
+    double *Ap = malloc(3 * sizeof(double) * (size_t)L);
+    if (!Ap) return NAN;
+    double *Up = Ap + L, *Lp = Ap + 2 * L;
+    for (int i = 0; i < L; i++) {
+        if (A[i] > U[i]) Ap[i] = U[i];
+        else if (A[i] < Lo[i]) Ap[i] = Lo[i];
+        else Ap[i] = A[i];
+    }
+    oracle_envelope(Ap, L, W, Up, Lp);
+    for (int j = nb + 1; j <= L - nb; j++) {
+        if (B[j - 1] > Up[j - 1]) res = res + delta(B[j - 1], Up[j - 1]);
+        else if (B[j - 1] < Lp[j - 1]) res = res + delta(B[j - 1], Lp[j - 1]);
+    }
+    free(Ap);
+    return res;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Threaded drivers over many pairs / queries (plain loops per item).        */
 
@@ -188,6 +222,7 @@ static void *lb_matrix_worker(void *p) {
         const double *U = j->U + t * j->L, *Lo = j->Lo + t * j->L;
         double v;
         if (j->kind == 1) v = oracle_lb_keogh(A, U, Lo, j->L);
+        else if (j->kind == 2) v = oracle_lb_enhanced_improved(A, B, U, Lo, j->L, j->W, j->V);
         else v = oracle_lb_enhanced(A, B, U, Lo, j->L, j->W, j->V, INFINITY);
         j->out[f] = v;
     }
@@ -303,7 +338,8 @@ void oracle_envelopes(const double *train, int64_t N, int L, int W, double *U, d
         oracle_envelope(train + t * L, L, W, U + t * L, Lo + t * L);
 }
 
-/* out[q*N + t] = LB(test_q, train_t); kind 0 = LB_Enhanced^V, 1 = LB_Keogh. */
+/* out[q*N + t] = LB(test_q, train_t); kind 0 = LB_Enhanced^V, 1 = LB_Keogh,
+ * 2 = LB_Enhanced^V with the LB_Improved bridge. */
 void oracle_lb_matrix(const double *test, int64_t Q, const double *train,
                       const double *U, const double *Lo, int64_t N, int L, int W,
                       int V, int kind, double *out, int nthreads) {

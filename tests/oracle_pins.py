@@ -202,6 +202,66 @@ def pin_reverse_bound(orc, trials=40):
         assert abs((ab - bridge_ab) - (ba - bridge_ba)) <= 1e-12 * max(ab, ba, 1.0), (L, W, V)
 
 
+def pin_lb_improved_bridge_bounds_dtw(orc, max_L=8):
+    """LB_Enhanced^V with the LB_Improved bridge (Sec. 5, Sec. 2.2.4) never
+    exceeds DTW_W, taken here as the minimum over every warping path, and never
+    falls below LB_Enhanced^V; at W = 0 it is the Euclidean distance (B's
+    envelope is B, so A' = B and the second pass adds nothing); with
+    2 n_b = L (even L) its bridge is empty and it equals LB_Enhanced^V.  Integer-valued
+    series give ties between cells and envelope values."""
+    rng = _rng(13)
+    tol = 1 + 1e-12
+    for L in range(2, max_L + 1):
+        for W in range(0, L + 1):
+            for V in range(1, L // 2 + 1):
+                for kind in range(2):
+                    if kind:
+                        a = rng.integers(-2, 3, L).astype(float)
+                        b = rng.integers(-2, 3, L).astype(float)
+                    else:
+                        a, b = _series(rng, L), _series(rng, L)
+                    U, Lo = orc.envelope(b, W)
+                    lbi = orc.lb_enhanced_improved(a, b, U, Lo, W, V)
+                    lbe = orc.lb_enhanced(a, b, U, Lo, W, V)
+                    d = paths.dtw_by_paths(a, b, W)
+                    assert lbe <= lbi * tol and lbi <= d * tol, (L, W, V, lbe, lbi, d)
+                    if W == 0:
+                        assert _rel_close(lbi, math.fsum((a - b) ** 2), 1e-13)
+                    if 2 * min(L // 2, V) >= L:
+                        assert lbi == lbe, (L, W, V)
+                    assert orc.lb_enhanced_improved(a, a, *orc.envelope(a, W), W, V) == 0.0
+
+
+def pin_lb_improved_bridge_closed_form(orc, trials=60):
+    """The second pass of the LB_Improved bridge in closed form.  For |i - j|
+    <= W the envelope of B satisfies Lo_i <= B_j <= U_i, so the projection A'
+    (Eq. 5) exceeds B_j somewhere in j's window exactly when max(A_i, Lo_i)
+    does, and otherwise its window maximum is max(U^A_j, max_i Lo_i), with
+    U^A the envelope of A; the lower side mirrors this.  The term of B_j is
+    therefore its distance to [min(L^A_j, min_i U_i), max(U^A_j, max_i Lo_i)]
+    (window minima and maxima by scipy's filters), summed over the bridge
+    n_b < j <= L - n_b."""
+    rng = _rng(14)
+    for _ in range(trials):
+        L = int(rng.integers(2, 150))
+        W = int(rng.integers(0, L + 2))
+        V = int(rng.integers(1, max(1, min(10, L // 2)) + 1))
+        a, b = _series(rng, L), _series(rng, L)
+        size = 2 * W + 1
+        f_max = lambda x: maximum_filter1d(x, size=size, mode="nearest")
+        f_min = lambda x: minimum_filter1d(x, size=size, mode="nearest")
+        Ub, Lb = f_max(b), f_min(b)
+        Ua, La = f_max(a), f_min(a)
+        hi = np.maximum(Ua, f_max(Lb))
+        lo = np.minimum(La, f_min(Ub))
+        nb = min(L // 2, V)
+        mid = slice(nb, L - nb)
+        second = math.fsum((b[mid] - np.clip(b[mid], lo[mid], hi[mid])) ** 2)
+        U, Lo = orc.envelope(b, W)
+        got = orc.lb_enhanced_improved(a, b, U, Lo, W, V) - orc.lb_enhanced(a, b, U, Lo, W, V)
+        assert abs(got - second) <= 1e-12 * max(abs(second), 1.0), (L, W, V, got, second)
+
+
 def pin_lb_enhanced_w0_is_euclidean(orc, trials=30):
     """At W=0 every band is the single diagonal cell and U = Lo = B, so
     LB_Enhanced^V = DTW_0 = the Euclidean distance for every V."""
@@ -341,6 +401,8 @@ ALL_PINS = [
     pin_lb_enhanced_bounds_dtw_larger,
     pin_lb_enhanced_w0_is_euclidean,
     pin_reverse_bound,
+    pin_lb_improved_bridge_bounds_dtw,
+    pin_lb_improved_bridge_closed_form,
     pin_algorithm1_abandon,
     pin_nn_brute_by_paths,
     pin_nn_w0_is_euclidean_nn,

@@ -31,11 +31,13 @@ def test_hand_worked_examples(orc):
             got = [orc.lb_keogh(a, U, Lo)]
         elif qty == "lb_enhanced":
             got = [orc.lb_enhanced(a, b, U, Lo, W, V)]
+        elif qty == "lb_enh_improved":
+            got = [orc.lb_enhanced_improved(a, b, U, Lo, W, V)]
         else:
             raise AssertionError(qty)
         assert got == val, (name, qty, got, val)
         n += 1
-    assert n == 13
+    assert n == 22
 
 
 def test_tiny_golden_regression(orc):

@@ -38,6 +38,15 @@ MUTANTS = {
         "for (int i = n_bands + 1; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])",
         "for (int i = n_bands; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])"),
     "lbenh_abandon_wrong_way": ("if (res >= D) return INFINITY;", "if (res < D) return INFINITY;"),
+    "lbimp_second_pass_without_projection": (
+        "if (A[i] > U[i]) Ap[i] = U[i];\n        else if (A[i] < Lo[i]) Ap[i] = Lo[i];\n        else Ap[i] = A[i];",
+        "Ap[i] = A[i];"),
+    "lbimp_second_pass_overlaps_bands": (
+        "for (int j = nb + 1; j <= L - nb; j++) {",
+        "for (int j = nb; j <= L - nb; j++) {"),
+    "lbimp_second_pass_lower_uses_upper": (
+        "else if (B[j - 1] < Lp[j - 1]) res = res + delta(B[j - 1], Lp[j - 1]);",
+        "else if (B[j - 1] < Lp[j - 1]) res = res + delta(B[j - 1], Up[j - 1]);"),
     "nn_ties_to_highest_index": ("if (d < best) { best = d; bi = t; }", "if (d <= best) { best = d; bi = t; }"),
     "loo_keeps_the_query_itself": ("if (j->exclude_self && t == q) continue;", ""),
     "pruned_search_drops_tie_update": (
