@@ -38,7 +38,20 @@ sys.path.insert(0, ROOT)
 METRIC = "exact NN-DTW queries/s + DTW GCUPS on 1 GB300: batched FP32 vs plain FP64 form"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_SEARCH = 14  # envelopes x2 (train, queries), norms, lb, dtw(seed), compact x2, reverse bound, dtw, filter, collect, dtw64, ties, final
+def kernels_per_search(flags: int, nndtw) -> int:
+    """Kernels one FP32 search launches: envelopes, norms, bounds, DTW of the
+    first candidates, compaction (two passes), DTW, recheck filter and collect,
+    FP64 recheck, ties, final (12); with a cascade second stage also the query
+    envelopes and the filter; with the LB_Improved bridge also the second
+    envelopes and their packing."""
+    n = 12
+    rev = bool(flags & nndtw.REVERSE) and not flags & (nndtw.NO_PRUNE | nndtw.NO_REVERSE)
+    imp = bool(flags & nndtw.IMPROVED) and not flags & nndtw.NO_PRUNE
+    if rev or imp:
+        n += 2
+    if imp:
+        n += 2
+    return n
 INSTR_PER_CELL = 3       # FADD + 3-input FMNMX + FFMA
 INSTR_PER_LB_ELEM = 5    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FFMA (dot product)
 FP32_LANES_PER_SM = 128
@@ -252,8 +265,9 @@ def roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, wor
 
 def tightness_pairs(dev):
     """Mean tightness LB/DTW over all 250,000 pairs of the 500 x 500 pairs
-    workload (L=256, W=26) for LB_Enhanced^V, V in {1, 2, 5}, and LB_Keogh
-    (pairs with DTW = 0 excluded), with the search's pruning per V."""
+    workload (L=256, W=26) for LB_Enhanced^V, V in {1, 2, 5}, with and
+    without the LB_Improved bridge, and LB_Keogh (pairs with DTW = 0
+    excluded), with the search's pruning per V."""
     import torch
     from paper_1808_09617_gb300 import nndtw, synth
     ds = synth.make_pairs(5)
@@ -270,13 +284,24 @@ def tightness_pairs(dev):
     out = {"pairs": Q * N, "pairs_dtw_zero": int((~keep).sum().item()), "W": ds.W, "L": ds.L}
     lbk = nndtw.lb_enhanced(test, train, env, ds.W, 1, keogh=True).double().reshape(-1)
     out["LB_Keogh"] = float((lbk[keep] / dtw[keep]).mean().item())
+    tenv = nndtw.nn_dtw_build_envelopes(test, ds.W)
+    env2 = nndtw.nn_dtw_build_second_envelopes(env, ds.W)
     for V in (1, 2, 5):
         lb = nndtw.lb_enhanced(test, train, env, ds.W, V).double().reshape(-1)
         st = nndtw.nn_dtw_search(train, labels, test, ds.W, V, stats=True).stats
+        lbi = nndtw.lb_enhanced_improved(test, tenv, train, env, env2, ds.W, V).double().reshape(-1)
+        sti = nndtw.nn_dtw_search(train, labels, test, ds.W, V, flags=nndtw.IMPROVED,
+                                  stats=True).stats
         out[f"LB_Enhanced^{V}"] = {
             "tightness": float((lb[keep] / dtw[keep]).mean().item()),
             "lb_pruned_frac": st["lb_pruned"] / st["pairs"],
-            "dtw_abandoned_frac_of_started": st["dtw_abandoned"] / max(1, st["dtw_started"])}
+            "dtw_abandoned_frac_of_started": st["dtw_abandoned"] / max(1, st["dtw_started"]),
+            # the same bound with the LB_Improved bridge (Sec. 5), and the
+            # search with it as the cascade's second stage
+            "with_improved_bridge": {
+                "tightness": float((lbi[keep] / dtw[keep]).mean().item()),
+                "pruned_frac": (sti["lb_pruned"] + sti["lb_pruned_improved"]) / sti["pairs"],
+                "dtw_started": sti["dtw_started"], "dtw_started_without": st["dtw_started"]}}
     return out
 
 
@@ -419,7 +444,8 @@ def run_window(args):
                              "cores": default_threads(), "kind": "oracle",
                              "sample": f"leave-one-out brute force for W in {sample_w}, "
                                        f"{cpu_s:.1f} s"},
-            "gpu_launches": (KERNELS_PER_SEARCH * len(windows) + 1) * args.steps,
+            "gpu_launches": (kernels_per_search(nndtw.LEAVE_ONE_OUT, nndtw) * len(windows) + 1)
+                            * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -497,6 +523,9 @@ def main():
     ap.add_argument("--reverse", action="store_true",
                     help="test the cascade's reverse bound in every dataset (with --dtw-group "
                          "or --no-tune; the tuner decides otherwise)")
+    ap.add_argument("--improved", action="store_true",
+                    help="test the bound with the LB_Improved bridge in every dataset (with "
+                         "--dtw-group or --no-tune; the tuner decides otherwise)")
     ap.add_argument("--dtw-group", type=int, default=0,
                     help="lanes per pair for every dataset (1..32, or 64 for the row layout); "
                          "implies --no-tune")
@@ -549,22 +578,27 @@ def main():
     Qtot = sum(d.Q for d in dsets)
     # lanes-per-pair per dataset (datasets with enough pairs to matter)
     tuned = {}
+    cascade = (nndtw.REVERSE if args.reverse else 0) | (nndtw.IMPROVED if args.improved else 0)
+
+    def record(g, flags):
+        return {"group": g, "reverse": bool(flags & nndtw.REVERSE),
+                "improved": bool(flags & nndtw.IMPROVED)}
     if args.dtw_group:
         for i, s in enumerate(sets):
-            s["flags"] = nndtw.DTW_GROUP(args.dtw_group) | (nndtw.REVERSE if args.reverse else 0)
-            tuned[i] = {"group": args.dtw_group, "reverse": bool(args.reverse)}
-    elif args.no_tune and args.reverse:
+            s["flags"] = nndtw.DTW_GROUP(args.dtw_group) | cascade
+            tuned[i] = record(args.dtw_group, cascade)
+    elif args.no_tune and cascade:
         for i, s in enumerate(sets):
-            s["flags"] = nndtw.REVERSE
-            tuned[i] = {"group": 0, "reverse": True}
+            s["flags"] = cascade
+            tuned[i] = record(0, cascade)
     elif not args.no_tune:
         for i, (d, s) in enumerate(zip(dsets, sets)):
             if d.N * d.Q >= 50_000:
                 s["flags"] = autotune.tune_search_flags(s["train"], s["labels"], s["test"], d.W,
                                                         d.V, reps=2)
                 g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)
-                if g or s["flags"] & nndtw.REVERSE:
-                    tuned[i] = {"group": g, "reverse": bool(s["flags"] & nndtw.REVERSE)}
+                if g or s["flags"] & (nndtw.REVERSE | nndtw.IMPROVED):
+                    tuned[i] = record(g, s["flags"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # counting pass (untimed): pruning and cells per dataset
@@ -660,8 +694,13 @@ def main():
     work = {"dtw": main_cells, "seed": seed_cells,
             "lb": sum(d.N * d.Q * d.L for d in dsets),
             "envelopes": sum(12 * d.N * d.L for d in dsets)}
-    launches = {"dtw": nds, "seed": nds, "lb": nds, "envelopes": nds, "compact": 2 * nds,
-                "recheck": 4 * nds, "final": nds}
+    # kernels per stage: the cascade's second stage adds the query envelopes
+    # (and, with the LB_Improved bridge, the second envelopes and their
+    # packing) to the envelope stage and its filter to the compaction stage
+    second = sum(1 for s in sets if kernels_per_search(s["flags"], nndtw) > 12)
+    packed = sum(1 for s in sets if kernels_per_search(s["flags"], nndtw) > 14)
+    launches = {"dtw": nds, "seed": nds, "lb": nds, "envelopes": nds + second + 2 * packed,
+                "compact": 2 * nds + second, "recheck": 4 * nds, "final": nds}
     roof = roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, args.workload)
     if batched:
         roof["stage_timing"] = ("per-dataset searches run one after another with stage events "
@@ -733,7 +772,7 @@ def main():
                     "h2d_bytes_per_step": int(sum(d.train.nbytes + d.test.nbytes +
                                                   d.train_labels.nbytes for d in dsets)),
                     "d2h_bytes_per_step": int(Qtot * (4 + 4 + 8)), "ms_per_step": e2e_ms},
-            "gpu_launches": KERNELS_PER_SEARCH * nds * args.steps,
+            "gpu_launches": sum(kernels_per_search(s["flags"], nndtw) for s in sets) * args.steps,
             "clocks": clocks,
             "gcups_effective": eff_cells / (ms * 1e-3) / 1e9,
             "gcups_dtw_kernel": (main_cells / (stage_ms["dtw"] * 1e-3) / 1e9
@@ -742,6 +781,8 @@ def main():
             "pruning": {"pairs": pairs,
                         "lb_pruned": sum(c["lb_pruned"] for c in counts),
                         "lb_pruned_frac": sum(c["lb_pruned"] for c in counts) / pairs,
+                        "lb_pruned_reverse": sum(c["lb_pruned_reverse"] for c in counts),
+                        "lb_pruned_improved": sum(c["lb_pruned_improved"] for c in counts),
                         "dtw_started": sum(c["dtw_started"] for c in counts),
                         "dtw_abandoned": sum(c["dtw_abandoned"] for c in counts),
                         "dtw_cells": main_cells + seed_cells,

@@ -71,6 +71,12 @@ extern "C" {
 /* search: leave-one-out over a training set (test == train, Q == N >= 2):
  * query i never matches training series i (window learning, Sec. 1, 4). */
 #define NNDTW_LEAVE_ONE_OUT (1u << 15)
+/* search: also test, on the pairs that survive LB_Enhanced^V(A, B), that bound
+ * with its LB_Keogh bridge replaced by LB_Improved (the combination Sec. 5
+ * proposes; see lb_enhanced_improved).  A tuning choice: it never changes
+ * results, and it saves DTW work at the price of one more pass over each
+ * surviving pair's training series. */
+#define NNDTW_IMPROVED (1u << 16)
 /* search / dtw_windowed: lanes per pair of the FP32 DTW kernel, a tuning
  * choice that never changes results: NNDTW_DTW_GROUP(log2 G) with
  * G = 1, 2, 4, ..., 32; 0 (the default) lets the library choose.  A G that
@@ -114,6 +120,9 @@ typedef struct nndtw_stats {
     int64_t seed_cells;     /* of dtw_cells, those of the first-candidate pass  */
     int64_t lb_pruned_reverse; /* survivors dropped by the reverse bound
                                   LB_Enhanced(B, A) when their DTW was due     */
+    int64_t lb_pruned_improved;/* survivors dropped by the bound with the
+                                  LB_Improved bridge (NNDTW_IMPROVED) then;
+                                  a pair both drop counts here only           */
 } nndtw_stats;
 
 /*
@@ -127,6 +136,18 @@ NNDTW_API int nn_dtw_build_envelopes(const float *d_train, int64_t N, int L, int
                            void *stream);
 NNDTW_API int nn_dtw_build_envelopes_f64(const double *d_train, int64_t N, int L, int W,
                                double *d_env, void *stream);
+
+/*
+ * Second envelopes, the training-series side of the LB_Improved bridge
+ * (lb_enhanced_improved): from the envelopes d_env ([N][L][2] (U, Lo), as
+ * written by nn_dtw_build_envelopes with the same W),
+ *   d_env2[t][i] = (max Lo_j, min U_j) over max(1, i-W) <= j <= min(L, i+W).
+ * Exact (min/max only).  Errors as nn_dtw_build_envelopes.
+ */
+NNDTW_API int nn_dtw_build_second_envelopes(const float *d_env, int64_t N, int L, int W,
+                                            float *d_env2, void *stream);
+NNDTW_API int nn_dtw_build_second_envelopes_f64(const double *d_env, int64_t N, int L, int W,
+                                                double *d_env2, void *stream);
 
 /*
  * LB_Enhanced^V_W(A, B) (Sec. 3.1, Eq. 7; Algorithm 1 with D = +inf) for every
@@ -148,6 +169,31 @@ NNDTW_API int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, 
 NNDTW_API int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train,
                     const double *d_env, int64_t N, int L, int W, int V, unsigned flags,
                     double *d_lb_out, void *stream);
+
+/*
+ * LB_Enhanced^V_W(A, B) with its LB_Keogh bridge replaced by LB_Improved
+ * (Sec. 2.2.4, Eq. 5), the combination proposed in Sec. 5: the value of
+ * lb_enhanced plus the second pass of LB_Improved over the bridge,
+ *   sum_{j=n+1..L-n} LB_Keogh term of B_j against the envelope of A',
+ * with A' the projection of A onto B's envelope (Eq. 5) and n =
+ * min(floor(L/2), V).  For |i-j| <= W, Lo_i <= B_j <= U_i, so wherever the
+ * term is non-zero the window maximum of A' equals max(U^A_j, env2_j.x) and
+ * its minimum min(Lo^A_j, env2_j.y): each term is computed against those,
+ * with U^A, Lo^A the query's envelopes and env2 the training series'
+ * second envelopes.  d_test_env: [Q][L][2] (nn_dtw_build_envelopes on the
+ * test set, same W); d_env2: [N][L][2] (nn_dtw_build_second_envelopes);
+ * other arguments as lb_enhanced.  flags: NNDTW_LB_SAFE (both parts scaled
+ * down, the sum rounded down); NNDTW_LB_KEOGH is an error.
+ * Errors: those of lb_enhanced, and NNDTW_EINVAL for NNDTW_LB_KEOGH.
+ */
+NNDTW_API int lb_enhanced_improved(const float *d_test, const float *d_test_env, int64_t Q,
+                                   const float *d_train, const float *d_env, const float *d_env2,
+                                   int64_t N, int L, int W, int V, unsigned flags,
+                                   float *d_lb_out, void *stream);
+NNDTW_API int lb_enhanced_improved_f64(const double *d_test, const double *d_test_env, int64_t Q,
+                                       const double *d_train, const double *d_env,
+                                       const double *d_env2, int64_t N, int L, int W, int V,
+                                       unsigned flags, double *d_lb_out, void *stream);
 
 /*
  * DTW_W(test_q, train_t) (Sec. 2.1, Eq. 1; D(L,L) in squared units) for P
@@ -178,7 +224,10 @@ NNDTW_API size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V
  * query's envelope) on the pairs that survive it: by default in the FP64
  * form, with NNDTW_REVERSE in the FP32 form (a tuning choice: it saves DTW
  * work but reads each surviving pair's training series once more);
- * NNDTW_NO_REVERSE leaves it out.  For every query q:
+ * NNDTW_NO_REVERSE leaves it out.  NNDTW_IMPROVED adds, in the same stage,
+ * LB_Enhanced^V(A, B) with the LB_Improved bridge (lb_enhanced_improved);
+ * the training series' second envelopes are then built into the workspace.
+ * For every query q:
  *   d_nn_idx[q]   = argmin_t DTW_W(test_q, train_t), ties to the lowest t;
  *   d_nn_label[q] = d_train_labels[d_nn_idx[q]];
  *   d_nn_dist[q]  = that distance (squared units).

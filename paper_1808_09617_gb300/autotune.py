@@ -8,8 +8,9 @@ more exchange per cell; full windows also have the row layouts.  The tuner
 times ``nn_dtw_search`` with every admissible G on the caller's data
 (results never depend on G) and keeps the fastest, cached in memory and
 optionally in a JSON file keyed by device, L, W, V and power-of-two buckets
-of N and Q.  ``tune_search_flags`` then also decides whether the cascade's
-reverse bound (``nndtw.REVERSE``) pays off on that data.
+of N and Q.  ``tune_search_flags`` then also picks the cascade's second
+stage for that data: none, the reverse bound (``nndtw.REVERSE``) or the bound
+with the LB_Improved bridge (``nndtw.IMPROVED``).
 """
 from __future__ import annotations
 
@@ -21,6 +22,9 @@ from . import nndtw
 
 _lock = threading.Lock()
 _mem: dict = {}
+
+# the cascade's second stage: none, the reverse bound, the LB_Improved bridge
+CASCADE_CHOICES = (0, nndtw.REVERSE, nndtw.IMPROVED)
 
 
 def _bucket(n: int) -> int:
@@ -120,25 +124,29 @@ def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, r
 
 def tune_search_flags(train, labels, test, W: int, V: int, reps: int = 3,
                       cache_path: str | None = None) -> int:
-    """Search flags for this data: the fastest lanes-per-pair choice, plus
-    ``nndtw.REVERSE`` when the cascade's reverse bound makes the search
-    faster (results never depend on either)."""
+    """Search flags for this data: the fastest lanes-per-pair choice, plus the
+    cascade's second stage that makes the search fastest: none, the reverse
+    bound (``nndtw.REVERSE``) or the bound with the LB_Improved bridge
+    (``nndtw.IMPROVED``).  Results never depend on any of them."""
     import torch
     g = tune_search(train, labels, test, W, V, reps=reps, cache_path=cache_path)
     base = nndtw.DTW_GROUP(g) if g else 0
     N, L = train.shape
     Q = test.shape[0]
-    k = "reverse|" + key(torch.cuda.get_device_name(train.device), N, Q, L, min(W, L - 1), V)
+    k = "cascade|" + key(torch.cuda.get_device_name(train.device), N, Q, L, min(W, L - 1), V)
     with _lock:
         if k in _mem:
-            return base | (nndtw.REVERSE if _mem[k] else 0)
+            return base | _mem[k]
     workspace = torch.empty(nndtw.nn_dtw_workspace_size(N, Q, L, W, V), dtype=torch.uint8,
                             device=train.device)
     out = (torch.empty(Q, dtype=torch.int32, device=train.device),
            torch.empty(Q, dtype=torch.int32, device=train.device),
            torch.empty(Q, dtype=torch.float64, device=train.device))
-    off = _median_ms(train, labels, test, W, V, base, workspace, out, reps)
-    on = _median_ms(train, labels, test, W, V, base | nndtw.REVERSE, workspace, out, reps)
+    best, best_ms = 0, None
+    for extra in CASCADE_CHOICES:
+        ms = _median_ms(train, labels, test, W, V, base | extra, workspace, out, reps)
+        if best_ms is None or ms < best_ms:
+            best, best_ms = extra, ms
     with _lock:
-        _mem[k] = on < off
-    return base | (nndtw.REVERSE if on < off else 0)
+        _mem[k] = best
+    return base | best

@@ -69,25 +69,53 @@ dtw64_kernel(DtwJob64 job) {
             q = (int)p; t = (int)key_idx(job.seed_keys[p]);
         }
         if (!F32IN && job.envq) {
+            // the cascade's second stage: the reverse bound (job.rev) and the
+            // bound with the LB_Improved bridge (job.env2), over [nb, L - nb)
             const double2 *eq = job.envq + (long long)q * L;
+            const double2 *e2 = job.env2 ? job.env2 + (long long)t * L : nullptr;
             const double *bp = job.train + (long long)t * L;
-            double part = 0.0;
+            double pr = 0.0, pi = 0.0;
             for (int j = job.nb + tid; j < L - job.nb; j += nthr) {
                 const double b = bp[j];
-                const double d = b - fmin(fmax(b, eq[j].y), eq[j].x);
-                part = fma(d, d, part);
+                const double2 e = eq[j];
+                const double d = b - fmin(fmax(b, e.y), e.x);
+                pr = fma(d, d, pr);
+                if (e2) {
+                    const double2 o = e2[j];
+                    const double di = b - fmin(fmax(b, fmin(e.y, o.y)), fmax(e.x, o.x));
+                    pi = fma(di, di, pi);
+                }
             }
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            if ((tid & 31) == 0) red[tid >> 5] = __double_as_longlong(part);
+            for (int off = 16; off > 0; off >>= 1) {
+                pr += __shfl_xor_sync(0xffffffffu, pr, off);
+                pi += __shfl_xor_sync(0xffffffffu, pi, off);
+            }
+            if ((tid & 31) == 0) {
+                red[tid >> 5] = __double_as_longlong(pr);
+                red[16 + (tid >> 5)] = __double_as_longlong(pi);
+            }
             __syncthreads();
             if (tid == 0) {
-                double tot = job.ends_bands[(long long)q * job.N + t];
-                for (int w = 0; w < (nthr >> 5); w++) tot += __longlong_as_double(red[w]);
-                double safe = __dmul_rd(tot, job.lb_lo) - job.lb_abs;
-                safe = safe > 0.0 ? safe : 0.0;
+                const long long pq = (long long)q * job.N + t;
                 const long long ubits = (long long)*((volatile unsigned long long *)job.bsf64 + q);
-                bcast = __double_as_longlong(safe) > ubits;   // strict
-                if (bcast && job.counters) atomicAdd(job.counters + C_REVPRUNED, 1ull);
+                bool by_imp = false, by_rev = false;
+                if (e2) {
+                    double tot = 0.0;
+                    for (int w = 0; w < (nthr >> 5); w++) tot += __longlong_as_double(red[16 + w]);
+                    double si = __dsub_rd(__dmul_rd(tot, job.lb_lo), job.lb_abs);
+                    si = si > 0.0 ? si : 0.0;
+                    by_imp = __double_as_longlong(__dadd_rd(job.lb[pq], si)) > ubits;   // strict
+                }
+                if (job.rev && !by_imp) {
+                    double tot = job.ends_bands[pq];
+                    for (int w = 0; w < (nthr >> 5); w++) tot += __longlong_as_double(red[w]);
+                    double safe = __dsub_rd(__dmul_rd(tot, job.lb_lo), job.lb_abs);
+                    safe = safe > 0.0 ? safe : 0.0;
+                    by_rev = __double_as_longlong(safe) > ubits;   // strict
+                }
+                bcast = by_imp || by_rev;
+                if (job.counters && by_imp) atomicAdd(job.counters + C_IMPPRUNED, 1ull);
+                if (job.counters && by_rev) atomicAdd(job.counters + C_REVPRUNED, 1ull);
             }
             __syncthreads();
             const bool drop = bcast != 0;

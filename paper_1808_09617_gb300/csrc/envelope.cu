@@ -11,6 +11,10 @@
 // With T > W/2 at most three tiles lie between; with T = 32 a sparse table
 // over tile maxima answers the middle range with two lookups.  min/max are
 // exact, so the result is bit-identical to a naive scan.
+//
+// The same kernel gives the second envelopes used by the LB_Improved bridge:
+// fed with a series' envelopes (U, Lo) instead of the series, it takes the
+// window maximum of Lo and the window minimum of U.
 #include "internal.cuh"
 
 namespace nndtw {
@@ -25,8 +29,10 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
 template <typename T>
 __global__ void __launch_bounds__(kEnvThreads)
-envelope_kernel(const T *__restrict__ train, int64_t N, int L, int W, T *__restrict__ env,
-                int T_tile, int levels) {
+envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64_t N, int L,
+                int W, T *__restrict__ env, int T_tile, int levels) {
+    // env_in == nullptr: envelopes of train; else the second envelopes of
+    // env_in ([N][L] (U, Lo)): window max of Lo and window min of U
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Pmax = reinterpret_cast<T *>(smem_raw);
     T *Pmin = Pmax + L;
@@ -41,21 +47,24 @@ envelope_kernel(const T *__restrict__ train, int64_t N, int L, int W, T *__restr
     const T NEG = -inf_of<T>(), POS = inf_of<T>();
 
     for (int64_t s = blockIdx.x; s < N; s += gridDim.x) {
-        const T *x = train + s * (int64_t)L;
+        const T *x = env_in ? nullptr : train + s * (int64_t)L;
+        const T *ein = env_in ? env_in + s * 2 * (int64_t)L : nullptr;
         T *out = env + s * 2 * (int64_t)L;
         if (W == 0) {
             for (int i = tid; i < L; i += kEnvThreads) {
-                T v = x[i];
-                out[2 * i] = v;
-                out[2 * i + 1] = v;
+                out[2 * i] = ein ? ein[2 * i + 1] : x[i];
+                out[2 * i + 1] = ein ? ein[2 * i] : x[i];
             }
             continue;
         }
         // tile prefix / suffix scans
         for (int base = 0; base < L; base += kEnvThreads) {
             const int k = base + tid;
-            const T v = k < L ? x[k] : T(0);
-            T pmx = k < L ? v : NEG, pmn = k < L ? v : POS;
+            T pmx = NEG, pmn = POS;
+            if (k < L) {
+                pmx = ein ? ein[2 * k + 1] : x[k];
+                pmn = ein ? ein[2 * k] : x[k];
+            }
             T smx = pmx, smn = pmn;
             for (int d = 1; d < T_tile; d <<= 1) {
                 T a = __shfl_up_sync(0xffffffffu, pmx, d);
@@ -109,10 +118,9 @@ envelope_kernel(const T *__restrict__ train, int64_t N, int L, int W, T *__restr
     }
 }
 
-}  // namespace
-
 template <typename T>
-cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s) {
+cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, int L, int W,
+                                   T *env, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     int Weff = W > L - 1 ? L - 1 : W;
     int T_tile = 1, levels = 0;
@@ -130,14 +138,31 @@ cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cu
     if (e != cudaSuccess) return e;
     const int sms = device_sm_count();
     int64_t grid = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
-    envelope_kernel<T><<<(unsigned)grid, kEnvThreads, smem, s>>>(train, N, L, Weff, env, T_tile,
-                                                                  levels);
+    envelope_kernel<T><<<(unsigned)grid, kEnvThreads, smem, s>>>(train, env_in, N, L, Weff, env,
+                                                                  T_tile, levels);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s) {
+    return launch_envelope_kernel<T>(train, nullptr, N, L, W, env, s);
+}
+
+template <typename T>
+cudaError_t launch_second_envelopes(const T *env, int64_t N, int L, int W, T *env2,
+                                    cudaStream_t s) {
+    return launch_envelope_kernel<T>(nullptr, env, N, L, W, env2, s);
 }
 
 template cudaError_t launch_envelopes<float>(const float *, int64_t, int, int, float *,
                                              cudaStream_t);
 template cudaError_t launch_envelopes<double>(const double *, int64_t, int, int, double *,
                                               cudaStream_t);
+template cudaError_t launch_second_envelopes<float>(const float *, int64_t, int, int, float *,
+                                                    cudaStream_t);
+template cudaError_t launch_second_envelopes<double>(const double *, int64_t, int, int, double *,
+                                                     cudaStream_t);
 
 }  // namespace nndtw

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libnndtw.so.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,7 +73,8 @@ enum Counter : int {
     C_SEEDHEAD,      // next seed pair to claim
     C_BAD,           // non-finite input elements found
     C_REVPRUNED,     // pairs dropped by the reverse bound LB_Enhanced(B, A)
-    C_QUEUE2,        // survivors of the reverse bound (FP32 search)
+    C_QUEUE2,        // survivors of the cascade's second stage (FP32 search)
+    C_IMPPRUNED,     // pairs dropped by LB_Enhanced with the LB_Improved bridge
     C_COUNT
 };
 
@@ -90,6 +92,12 @@ struct Cand64 {
 // ---- launchers implemented in the .cu files --------------------------------
 template <typename T>
 cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s);
+// Second envelopes from envelopes env ([N][L] (U, Lo)): env2[t][i] =
+// (max of Lo, min of U) over the window of i, the training side of the
+// LB_Improved bridge's second pass.
+template <typename T>
+cudaError_t launch_second_envelopes(const T *env, int64_t N, int L, int W, T *env2,
+                                    cudaStream_t s);
 
 // With seed_keys, also the Euclidean-nearest series of every query; `norms`
 // is then scratch for Q + N squared norms.  With ends_out, also the raw sum
@@ -163,17 +171,56 @@ struct DtwJob64 {
     long long N;
     int nb;
     double lb_lo, lb_abs;
+    // With envq: rev tests the reverse bound above; env2 (nullptr: none) the
+    // bound with the LB_Improved bridge, lb[q N + t] (the pair's safe
+    // LB_Enhanced(A, B)) plus the second pass of the bridge: the LB_Keogh
+    // terms of the training series against [min(Lo^A, env2.y), max(U^A,
+    // env2.x)] over [nb, L - nb), scaled down like every bound.
+    bool rev;
+    const double2 *env2;
+    const double *lb;
 };
 cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
 
-// The reverse bound LB_Enhanced(B, A) over a queue of pairs (FP32): the
-// survivors of in[0 .. *in_count) are appended to out (count in *out_count).
-cudaError_t launch_rev_filter(const uint2 *in, const unsigned long long *in_count,
-                              const float *train, const float2 *envq, const float *ends,
-                              long long N, int L, int nb, const unsigned long long *bsf,
-                              float lb_lo, float lb_abs, float dtw_hi, float abs32, uint2 *out,
-                              unsigned long long *out_count, unsigned long long *counters,
-                              long long max_pairs, int sm_count, cudaStream_t s);
+// The cascade's second stage over a queue of pairs (FP32): with ends, the
+// reverse bound LB_Enhanced(B, A); with env2 and lb, LB_Enhanced(A, B) with
+// the LB_Improved bridge.  The survivors of in[0 .. *in_count) are appended
+// to out (count in *out_count).
+// A training element with its gaps to the second envelopes, (B_j -
+// env2_j.x, env2_j.y - B_j) rounded down to half precision: the training
+// side of the LB_Improved bridge in the FP32 search.
+struct __align__(8) BGap {
+    float b;
+    __half2 g;
+};
+cudaError_t launch_pack_bgap(const float *train, float *env2, long long n, cudaStream_t s);
+
+struct CascadeJob {
+    const uint2 *in;
+    const unsigned long long *in_count;
+    const float *train;
+    const float2 *envq;    // query envelopes [Q][L] (U, Lo)
+    const float *ends;     // [Q][N] ends + bands (raw), or nullptr: no reverse bound
+    const BGap *bgap;      // [N][L] training elements and gaps, or nullptr: no
+                           // LB_Improved bridge
+    const float *lb;       // [Q][N] safe LB_Enhanced(A, B) (with bgap)
+    long long N;
+    int L, nb;
+    const unsigned long long *bsf;
+    float lb_lo, lb_abs, dtw_hi, abs32;
+    uint2 *out;
+    unsigned long long *out_count, *counters;
+};
+cudaError_t launch_cascade_filter(const CascadeJob &job, long long max_pairs, int sm_count,
+                                  cudaStream_t s);
+
+// Adds the second pass of the LB_Improved bridge to every pair's LB_Enhanced
+// value in lb[Q][N] (raw, or with safe: both parts scaled down and the sum
+// rounded down).
+template <typename T>
+cudaError_t launch_improved_terms(const T *train, const T *envq, const T *env2, int64_t Q,
+                                  int64_t N, int L, int nb, bool safe, T lb_lo, T lb_abs, T *lb,
+                                  cudaStream_t s);
 
 int device_sm_count();
 void set_last_cuda_error(cudaError_t e);

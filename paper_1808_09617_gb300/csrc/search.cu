@@ -318,7 +318,7 @@ struct Carve {
 struct Layout32 {
     unsigned long long *counters, *bsf, *seed, *best64, *buckets;
     int32_t *rcount, *bestidx;
-    float *env, *envq, *lb, *ends, *norms;
+    float *env, *envq, *env2, *lb, *ends, *norms;
     uint2 *queue, *rlist;
     Cand *cand;
     double *d64;
@@ -338,6 +338,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<float>((size_t)N * L * 2);
     l.envq = c.take<float>((size_t)Q * L * 2);
+    l.env2 = c.take<float>((size_t)N * L * 2);
     l.lb = c.take<float>((size_t)Q * N);
     l.ends = c.take<float>((size_t)Q * N);
     l.norms = c.take<float>((size_t)Q + (size_t)N);
@@ -352,7 +353,7 @@ Layout32 layout32(void *base, int64_t N, int64_t Q, int L) {
 struct Layout64 {
     unsigned long long *counters, *bsf64, *seed, *buckets;
     int32_t *bestidx;
-    double *env, *envq, *lb, *ends, *norms;
+    double *env, *envq, *env2, *lb, *ends, *norms;
     uint2 *queue;
     Cand64 *cand;
     size_t bytes;
@@ -369,6 +370,7 @@ Layout64 layout64(void *base, int64_t N, int64_t Q, int L) {
     l.bestidx = c.take<int32_t>(Q);
     l.env = c.take<double>((size_t)N * L * 2);
     l.envq = c.take<double>((size_t)Q * L * 2);
+    l.env2 = c.take<double>((size_t)N * L * 2);
     l.lb = c.take<double>((size_t)Q * N);
     l.ends = c.take<double>((size_t)Q * N);
     l.norms = c.take<double>((size_t)Q + (size_t)N);
@@ -428,6 +430,7 @@ void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t
         st->dtw_cells = (int64_t)h[C_CELLS];
         st->seed_cells = Q * band_cells(L, W);
         st->lb_pruned_reverse = (int64_t)h[C_REVPRUNED];
+        st->lb_pruned_improved = (int64_t)h[C_IMPPRUNED];
     }
 }
 
@@ -502,7 +505,7 @@ using namespace nndtw;
 
 extern "C" {
 
-int nn_dtw_version(void) { return 103; }
+int nn_dtw_version(void) { return 104; }
 
 int nn_dtw_stage_times(float *h_ms) {
     if (!h_ms || t_last_dev < 0) return NNDTW_EINVAL;
@@ -545,6 +548,24 @@ int nn_dtw_build_envelopes_f64(const double *d_train, int64_t N, int L, int W, d
     return NNDTW_OK;
 }
 
+int nn_dtw_build_second_envelopes(const float *d_env, int64_t N, int L, int W, float *d_env2,
+                                  void *stream) {
+    if (N < 0 || L < 1 || L > NNDTW_MAX_L || W < 0) return NNDTW_EINVAL;
+    if (N == 0) return NNDTW_OK;
+    if (!d_env || !d_env2) return NNDTW_EINVAL;
+    CK(launch_second_envelopes<float>(d_env, N, L, W, d_env2, (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
+int nn_dtw_build_second_envelopes_f64(const double *d_env, int64_t N, int L, int W,
+                                      double *d_env2, void *stream) {
+    if (N < 0 || L < 1 || L > NNDTW_MAX_L || W < 0) return NNDTW_EINVAL;
+    if (N == 0) return NNDTW_OK;
+    if (!d_env || !d_env2) return NNDTW_EINVAL;
+    CK(launch_second_envelopes<double>(d_env, N, L, W, d_env2, (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
 int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const float *d_env,
                 int64_t N, int L, int W, int V, unsigned flags, float *d_lb_out, void *stream) {
     if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
@@ -567,6 +588,39 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
                          nullptr, nullptr, false, (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
+int lb_enhanced_improved(const float *d_test, const float *d_test_env, int64_t Q,
+                         const float *d_train, const float *d_env, const float *d_env2, int64_t N,
+                         int L, int W, int V, unsigned flags, float *d_lb_out, void *stream) {
+    if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
+    if (flags & NNDTW_LB_KEOGH) return NNDTW_EINVAL;
+    if (Q == 0 || N == 0) return NNDTW_OK;
+    if (!d_test || !d_test_env || !d_train || !d_env || !d_env2 || !d_lb_out) return NNDTW_EINVAL;
+    const int rc = lb_enhanced(d_test, Q, d_train, d_env, N, L, W, V, flags, d_lb_out, stream);
+    if (rc != NNDTW_OK) return rc;
+    const Margins m = make_margins(L);
+    CK(launch_improved_terms<float>(d_train, d_test_env, d_env2, Q, N, L, bridge_start(L, V),
+                                    (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out,
+                                    (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
+int lb_enhanced_improved_f64(const double *d_test, const double *d_test_env, int64_t Q,
+                             const double *d_train, const double *d_env, const double *d_env2,
+                             int64_t N, int L, int W, int V, unsigned flags, double *d_lb_out,
+                             void *stream) {
+    if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
+    if (flags & NNDTW_LB_KEOGH) return NNDTW_EINVAL;
+    if (Q == 0 || N == 0) return NNDTW_OK;
+    if (!d_test || !d_test_env || !d_train || !d_env || !d_env2 || !d_lb_out) return NNDTW_EINVAL;
+    const int rc = lb_enhanced_f64(d_test, Q, d_train, d_env, N, L, W, V, flags, d_lb_out, stream);
+    if (rc != NNDTW_OK) return rc;
+    const Margins m = make_margins(L);
+    CK(launch_improved_terms<double>(d_train, d_test_env, d_env2, Q, N, L, bridge_start(L, V),
+                                     (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out,
+                                     (cudaStream_t)stream));
     return NNDTW_OK;
 }
 
@@ -677,7 +731,14 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     // with NNDTW_REVERSE: whether reading every surviving pair's training
     // series once more pays off depends on the data, so the tuner decides)
     const bool rev = (flags & NNDTW_REVERSE) && !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
-    if (rev) CK(launch_envelopes<float>(d_test, Q, L, Weff, ws.envq, s));
+    // and the training series' second envelopes, for the bound with the
+    // LB_Improved bridge (asked for with NNDTW_IMPROVED, also a tuning choice)
+    const bool imp = (flags & NNDTW_IMPROVED) && !(flags & NNDTW_NO_PRUNE);
+    if (rev || imp) CK(launch_envelopes<float>(d_test, Q, L, Weff, ws.envq, s));
+    if (imp) {
+        CK(launch_second_envelopes<float>(env, N, L, Weff, ws.env2, s));
+        CK(launch_pack_bgap(d_train, ws.env2, N * L, s));
+    }
     CK(tm.mark(1));
     // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
     CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
@@ -711,18 +772,26 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
             CK(cudaGetLastError());
         }
     }
-    // the cascade's reverse bound on the survivors (into the recheck list's
+    // the cascade's second stage on the survivors (into the recheck list's
     // storage, which S5 fills only after the DTW pass)
-    if (rev) {
-        CK(launch_rev_filter(ws.queue, ws.counters + C_QUEUE, d_train,
-                             reinterpret_cast<const float2 *>(ws.envq), ws.ends, N, L,
-                             bridge_start(L, V), ws.bsf, m.lb_lo, m.abs32, m.dtw_hi, m.abs32,
-                             ws.rlist, ws.counters + C_QUEUE2, cnt, Q * N, sms, s));
+    const bool second = rev || imp;
+    if (second) {
+        CascadeJob cj{};
+        cj.in = ws.queue; cj.in_count = ws.counters + C_QUEUE;
+        cj.train = d_train; cj.envq = reinterpret_cast<const float2 *>(ws.envq);
+        cj.ends = rev ? ws.ends : nullptr;
+        cj.bgap = imp ? reinterpret_cast<const BGap *>(ws.env2) : nullptr;
+        cj.lb = ws.lb;
+        cj.N = N; cj.L = L; cj.nb = bridge_start(L, V);
+        cj.bsf = ws.bsf;
+        cj.lb_lo = m.lb_lo; cj.lb_abs = m.abs32; cj.dtw_hi = m.dtw_hi; cj.abs32 = m.abs32;
+        cj.out = ws.rlist; cj.out_count = ws.counters + C_QUEUE2; cj.counters = cnt;
+        CK(launch_cascade_filter(cj, Q * N, sms, s));
     }
     CK(tm.mark(4));
     // S4 on the survivors, with early abandoning
-    j.pairs = rev ? ws.rlist : ws.queue; j.seed_keys = nullptr;
-    j.count = ws.counters + (rev ? C_QUEUE2 : C_QUEUE);
+    j.pairs = second ? ws.rlist : ws.queue; j.seed_keys = nullptr;
+    j.count = ws.counters + (second ? C_QUEUE2 : C_QUEUE);
     j.head = ws.counters + C_HEAD;
     j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
     CK(launch_dtw32(j, sms, s));
@@ -806,7 +875,9 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
         env = ws.env;
     }
     const bool rev = !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
-    if (rev) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
+    const bool imp = (flags & NNDTW_IMPROVED) && !(flags & NNDTW_NO_PRUNE);
+    if (rev || imp) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
+    if (imp) CK(launch_second_envelopes<double>(env, N, L, Weff, ws.env2, s));
     CK(tm.mark(1));
     CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
                          m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
@@ -833,9 +904,12 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     CK(tm.mark(4));
     j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
     j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
-    if (rev) {
+    if (rev || imp) {
         j.envq = reinterpret_cast<const double2 *>(ws.envq);
+        j.rev = rev;
         j.ends_bands = ws.ends;
+        j.env2 = imp ? reinterpret_cast<const double2 *>(ws.env2) : nullptr;
+        j.lb = ws.lb;
         j.N = N;
         j.nb = bridge_start(L, V);
         j.lb_lo = m.lb_lo64;

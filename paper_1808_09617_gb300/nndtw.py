@@ -31,6 +31,7 @@ TIME_STAGES = 1 << 6
 NO_REVERSE = 1 << 7
 REVERSE = 1 << 14
 LEAVE_ONE_OUT = 1 << 15
+IMPROVED = 1 << 16
 
 
 # Tuning values for full windows: the row layout with 32 lanes per pair (one
@@ -88,7 +89,7 @@ class Stats(ctypes.Structure):
                 ("dtw_started", ctypes.c_int64), ("dtw_abandoned", ctypes.c_int64),
                 ("dtw_cells", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("recheck_queries", ctypes.c_int64), ("seed_cells", ctypes.c_int64),
-                ("lb_pruned_reverse", ctypes.c_int64)]
+                ("lb_pruned_reverse", ctypes.c_int64), ("lb_pruned_improved", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -108,6 +109,12 @@ def _declare(lib):
         "nn_dtw_build_envelopes_f64": [_vp, _i64, _int, _int, _vp, _vp],
         "lb_enhanced": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
         "lb_enhanced_f64": [_vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint, _vp, _vp],
+        "nn_dtw_build_second_envelopes": [_vp, _i64, _int, _int, _vp, _vp],
+        "nn_dtw_build_second_envelopes_f64": [_vp, _i64, _int, _int, _vp, _vp],
+        "lb_enhanced_improved": [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _int, _int, _uint,
+                                 _vp, _vp],
+        "lb_enhanced_improved_f64": [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _int, _int,
+                                     _uint, _vp, _vp],
         "dtw_windowed": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
         "dtw_windowed_ex": [_vp, _vp, _vp, _i64, _int, _int, _uint, _vp, _vp],
         "dtw_windowed_f64": [_vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
@@ -227,6 +234,41 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
     _check(fn(_dev(test, test.dtype, "test", 2), Q, _dev(train, test.dtype, "train", 2),
               _dev(env, test.dtype, "env"), N, L, int(W), int(V), flags,
               _dev(out, test.dtype, "out"), _stream(stream)), "lb_enhanced")
+    return out
+
+
+def nn_dtw_build_second_envelopes(env, W: int, env2=None, stream=None):
+    """Second envelopes (window max of Lo, window min of U) of every training
+    series, from its envelopes [N, L, 2]: tensor [N, L, 2]."""
+    import torch
+    lib = load()
+    f64 = _fp(env)
+    N, L = env.shape[0], env.shape[1]
+    if env2 is None:
+        env2 = torch.empty_like(env)
+    fn = lib.nn_dtw_build_second_envelopes_f64 if f64 else lib.nn_dtw_build_second_envelopes
+    _check(fn(_dev(env, env.dtype, "env"), N, L, int(W), _dev(env2, env.dtype, "env2"),
+              _stream(stream)), "nn_dtw_build_second_envelopes")
+    return env2
+
+
+def lb_enhanced_improved(test, test_env, train, env, env2, W: int, V: int, safe: bool = False,
+                         out=None, stream=None):
+    """LB_Enhanced^V with the LB_Improved bridge (Sec. 5) for all pairs:
+    tensor [Q, N].  test_env: envelopes of the test set; env, env2: the
+    training series' envelopes and second envelopes, all with the same W."""
+    import torch
+    lib = load()
+    f64 = _fp(test)
+    Q, L = test.shape
+    N = train.shape[0]
+    if out is None:
+        out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
+    fn = lib.lb_enhanced_improved_f64 if f64 else lib.lb_enhanced_improved
+    _check(fn(_dev(test, test.dtype, "test", 2), _dev(test_env, test.dtype, "test_env"), Q,
+              _dev(train, test.dtype, "train", 2), _dev(env, test.dtype, "env"),
+              _dev(env2, test.dtype, "env2"), N, L, int(W), int(V), LB_SAFE if safe else 0,
+              _dev(out, test.dtype, "out"), _stream(stream)), "lb_enhanced_improved")
     return out
 
 

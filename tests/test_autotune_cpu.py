@@ -22,3 +22,38 @@ def test_key_buckets():
     k2 = autotune.key("GB300", 400, 300, 256, 26, 5)
     assert k1 == k2
     assert autotune.key("GB300", 500, 500, 256, 300, 5) == autotune.key("GB300", 500, 500, 256, 255, 5)
+
+
+def test_tune_search_flags_picks_fastest_cascade(monkeypatch):
+    """The cascade's second stage is the fastest of none / reverse bound /
+    LB_Improved bridge, chosen once per data key and then remembered (timings
+    faked: no GPU here)."""
+    import torch
+
+    from paper_1808_09617_gb300 import nndtw
+    calls = []
+    fake_ms = {0: 5.0, nndtw.REVERSE: 4.0, nndtw.IMPROVED: 3.0}
+
+    def median_ms(train, labels, test, W, V, flags, workspace, out, reps):
+        calls.append(flags)
+        return fake_ms[flags & (nndtw.REVERSE | nndtw.IMPROVED)]
+
+    monkeypatch.setattr(autotune, "tune_search", lambda *a, **k: 8)
+    monkeypatch.setattr(autotune, "_median_ms", median_ms)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda dev=None: "fake-gpu")
+    monkeypatch.setattr(nndtw, "nn_dtw_workspace_size", lambda *a: 64)
+    monkeypatch.setattr(autotune, "_mem", {})
+    train = torch.zeros((100, 32))
+    test = torch.zeros((40, 32))
+    labels = torch.zeros(100, dtype=torch.int32)
+    f = autotune.tune_search_flags(train, labels, test, 3, 2, reps=1)
+    assert f == nndtw.DTW_GROUP(8) | nndtw.IMPROVED
+    cascade = nndtw.REVERSE | nndtw.IMPROVED
+    assert sorted(c & cascade for c in calls) == sorted(autotune.CASCADE_CHOICES)
+    assert all(c & ~cascade == nndtw.DTW_GROUP(8) for c in calls)
+    n = len(calls)
+    assert autotune.tune_search_flags(train, labels, test, 3, 2, reps=1) == f
+    assert len(calls) == n                       # remembered
+    fake_ms[nndtw.IMPROVED] = 9.0
+    f2 = autotune.tune_search_flags(train, labels, test[:3], 3, 2, reps=1)   # another Q bucket
+    assert f2 == nndtw.DTW_GROUP(8) | nndtw.REVERSE
