@@ -60,6 +60,12 @@ __device__ __forceinline__ double add_rd(double a, double b) { return __dadd_rd(
 __device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+// max(a, b, c) in one three-input instruction
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 
 // The LB_Keogh term of b against [lo, hi] (squared distance to the interval).
@@ -114,10 +120,10 @@ __global__ void __launch_bounds__(256) cascade_filter_kernel(CascadeJob job) {
                         const float2 g = __half22float2(r.g);
                         const float up = r.b - ej.x, dn = ej.y - r.b;
                         if (REV) {
-                            const float d = fmaxf(fmaxf(up, dn), 0.f);
+                            const float d = max3f(up, dn, 0.f);
                             pr = fmaf(d, d, pr);
                         }
-                        const float d = fmaxf(fmaxf(fminf(up, g.x), fminf(dn, g.y)), 0.f);
+                        const float d = max3f(fminf(up, g.x), fminf(dn, g.y), 0.f);
                         pi = fmaf(d, d, pi);
                     }
                 } else {
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(256) cascade_filter_kernel(CascadeJob job) {
                     for (int j = nb + gl; j < L - nb; j += G) {
                         const float bj = b[j];
                         const float2 ej = e[j];
-                        const float d = fmaxf(fmaxf(bj - ej.x, ej.y - bj), 0.f);
+                        const float d = max3f(bj - ej.x, ej.y - bj, 0.f);
                         pr = fmaf(d, d, pr);
                     }
                 }
