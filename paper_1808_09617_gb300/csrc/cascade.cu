@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) cascade_filter_kernel(CascadeJob job) {
                 const float2 *e = job.envq + (long long)q * L;
                 if (IMP) {
                     const BGap *bg = job.bgap + (long long)t * L;
-#pragma unroll 4
+#pragma unroll 8
                     for (int j = nb + gl; j < L - nb; j += G) {
                         const BGap r = bg[j];
                         const float2 ej = e[j];
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) cascade_filter_kernel(CascadeJob job) {
                     }
                 } else {
                     const float *b = job.train + (long long)t * L;
-#pragma unroll 4
+#pragma unroll 8
                     for (int j = nb + gl; j < L - nb; j += G) {
                         const float bj = b[j];
                         const float2 ej = e[j];

@@ -108,17 +108,54 @@ __device__ __forceinline__ T band_terms(const T *Ap, const T *Bp, int last, int 
     return res;
 }
 
-// Shared-memory layout of one stage of chunk tiles: queries [kLC][kQT+1],
-// then (16-byte aligned) envelope pairs [kLC][kNT+1], then training values
-// [kLC][kNT+1] when the Euclidean seed is fused in.
+// Shared-memory layout of one stage of chunk tiles: queries [kLC][kQT+4],
+// then envelope pairs [kLC][kNT+2], then training values [kLC][kNT+2] when
+// the Euclidean seed is fused in.  The row strides keep every row 16-byte
+// aligned, so that a thread reads its MR queries, and its column pairs'
+// envelopes and values, with vector loads.
+constexpr int kPadA = 4, kPadN = 2;
 template <typename T, int kQT>
 __host__ __device__ constexpr size_t lb_es_offset() {
-    return (sizeof(T) * (kLC * (kQT + 1)) + 15) / 16 * 16;
+    return (sizeof(T) * (kLC * (kQT + kPadA)) + 15) / 16 * 16;
 }
 template <typename T, int kQT, int kNT, bool ED>
 __host__ __device__ constexpr size_t lb_stage_bytes() {
-    return (lb_es_offset<T, kQT>() + 2 * sizeof(T) * kLC * (kNT + 1) +
-            (ED ? sizeof(T) * kLC * (kNT + 1) : 0) + 15) / 16 * 16;
+    return (lb_es_offset<T, kQT>() + 2 * sizeof(T) * kLC * (kNT + kPadN) +
+            (ED ? sizeof(T) * kLC * (kNT + kPadN) : 0) + 15) / 16 * 16;
+}
+
+// Vector loads from shared memory: n consecutive values (16-byte aligned).
+__device__ __forceinline__ void lds4(float (&d)[4], const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+__device__ __forceinline__ void lds4(double (&d)[4], const double *p) {
+    const double2 v0 = reinterpret_cast<const double2 *>(p)[0];
+    const double2 v1 = reinterpret_cast<const double2 *>(p)[1];
+    d[0] = v0.x; d[1] = v0.y; d[2] = v1.x; d[3] = v1.y;
+}
+__device__ __forceinline__ void lds2(float (&d)[2], const float *p) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    d[0] = v.x; d[1] = v.y;
+}
+__device__ __forceinline__ void lds2(double (&d)[2], const double *p) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    d[0] = v.x; d[1] = v.y;
+}
+__device__ __forceinline__ void lds2(float2 (&d)[2], const float2 *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    d[0] = make_float2(v.x, v.y); d[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void lds2(double2 (&d)[2], const double2 *p) {
+    d[0] = p[0]; d[1] = p[1];
+}
+template <typename T, int N> __device__ __forceinline__ void ldsn(T (&d)[N], const T *p) {
+    if constexpr (N == 4) lds4(d, p);
+    else if constexpr (N == 2) lds2(d, p);
+    else {
+#pragma unroll
+        for (int k = 0; k < N; k++) d[k] = p[k];
+    }
 }
 
 // Squared norm of every row of a and of b (one warp per row).
@@ -156,9 +193,9 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     // access compiles to a shared-memory load.
     constexpr size_t kEsOff = lb_es_offset<T, kQT>();
     constexpr size_t kStage = lb_stage_bytes<T, kQT, kNT, ED>();
-    T *As0 = reinterpret_cast<T *>(smem_raw);                     // [kLC][kQT+1]
-    T2 *Es0 = reinterpret_cast<T2 *>(smem_raw + kEsOff);          // [kLC][kNT+1], 16-byte aligned
-    T *Bs0 = reinterpret_cast<T *>(Es0 + kLC * (kNT + 1));         // [kLC][kNT+1] (ED only)
+    T *As0 = reinterpret_cast<T *>(smem_raw);                     // [kLC][kQT+kPadA]
+    T2 *Es0 = reinterpret_cast<T2 *>(smem_raw + kEsOff);          // [kLC][kNT+kPadN], 16-byte aligned
+    T *Bs0 = reinterpret_cast<T *>(Es0 + kLC * (kNT + kPadN));     // [kLC][kNT+kPadN] (ED only)
     // band staging, rows padded to an odd stride so that the 16 series a
     // warp reads at once fall in distinct banks
     const int bstride = 2 * nb + 1;
@@ -166,6 +203,11 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     T *Bb = Ab + kQT * (nb <= kNBMax ? bstride : 0);               // [kNT][2nb+1]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // thread (tx, ty) owns the tile's query rows ty MR .. ty MR + MR-1 and the
+    // training columns 2 tx, 2 tx + 1 of each group of 32 (MC / 2 groups)
+    static_assert(MC % 2 == 0, "training columns come in pairs");
+    auto row_of = [&](int r) { return ty * MR + r; };
+    auto col_of = [&](int c) { return (c >> 1) * 32 + 2 * tx + (c & 1); };
     // query tiles vary fastest (qfast), so the CTAs resident at one time share
     // a few training tiles (series and envelopes read from DRAM about once)
     const int64_t q0 = (int64_t)(qfast ? blockIdx.x : blockIdx.y) * kQT;
@@ -190,25 +232,25 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
             const int64_t q = q0 + row;
             const bool ok = q < Q && i < L;
-            cp_async<sizeof(T)>(&As[col * (kQT + 1) + row], ok ? test + q * L + i : test, ok);
+            cp_async<sizeof(T)>(&As[col * (kQT + kPadA) + row], ok ? test + q * L + i : test, ok);
         }
         if (ED) {
             for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
                 const int row = idx / kLC, col = idx % kLC, i = c0 + col;
                 const int64_t t = t0 + row;
                 const bool ok = t < N && i < L;
-                cp_async<sizeof(T)>(&Bs[col * (kNT + 1) + row], ok ? train + t * L + i : train, ok);
+                cp_async<sizeof(T)>(&Bs[col * (kNT + kPadN) + row], ok ? train + t * L + i : train, ok);
             }
         }
         for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
             const int row = idx / kLC, col = idx % kLC, i = c0 + col;
             const int64_t t = t0 + row;
             if (t < N && i >= mlo && i < mhi) {
-                cp_async<sizeof(T2)>(&Es[col * (kNT + 1) + row], env + 2 * (t * L + i), true);
+                cp_async<sizeof(T2)>(&Es[col * (kNT + kPadN) + row], env + 2 * (t * L + i), true);
             } else {
                 T2 e;
                 e.x = POS; e.y = -POS;   // outside the bridge: the term is 0
-                Es[col * (kNT + 1) + row] = e;
+                Es[col * (kNT + kPadN) + row] = e;
             }
         }
     };
@@ -227,10 +269,13 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
         for (int col = 0; col < kLC; col++) {
             T a[MR];
             T2 e[MC];
+            ldsn<T, MR>(a, As + col * (kQT + kPadA) + ty * MR);
 #pragma unroll
-            for (int r = 0; r < MR; r++) a[r] = As[col * (kQT + 1) + ty + 16 * r];
-#pragma unroll
-            for (int c = 0; c < MC; c++) e[c] = Es[col * (kNT + 1) + tx + 16 * c];
+            for (int g = 0; g < MC / 2; g++) {
+                T2 eg[2];
+                lds2(eg, Es + col * (kNT + kPadN) + g * 32 + 2 * tx);
+                e[2 * g] = eg[0]; e[2 * g + 1] = eg[1];
+            }
 #pragma unroll
             for (int r = 0; r < MR; r++)
 #pragma unroll
@@ -238,7 +283,11 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
             if (ED) {
                 T b[MC];
 #pragma unroll
-                for (int c = 0; c < MC; c++) b[c] = Bs[col * (kNT + 1) + tx + 16 * c];
+                for (int g = 0; g < MC / 2; g++) {
+                    T bg[2];
+                    lds2(bg, Bs + col * (kNT + kPadN) + g * 32 + 2 * tx);
+                    b[2 * g] = bg[0]; b[2 * g + 1] = bg[1];
+                }
 #pragma unroll
                 for (int r = 0; r < MR; r++)
 #pragma unroll
@@ -269,14 +318,14 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
         }
 #pragma unroll
         for (int r = 0; r < MR; r++) {
-            const int64_t q = q0 + ty + 16 * r;
+            const int64_t q = q0 + row_of(r);
 #pragma unroll
             for (int c = 0; c < MC; c++) {
-                const int64_t t = t0 + tx + 16 * c;
+                const int64_t t = t0 + col_of(c);
                 // staged copies hold the first nb then the last nb elements
                 // (offset of the last nb: L - 2 nb); otherwise read the series
                 const T res = staged
-                    ? band_terms(Ab + (ty + 16 * r) * bstride, Bb + (tx + 16 * c) * bstride,
+                    ? band_terms(Ab + row_of(r) * bstride, Bb + col_of(c) * bstride,
                                  2 * nb - 1, nb, W)
                     : band_terms(test + (q < Q ? q : 0) * L, train + (t < N ? t : 0) * L, L - 1,
                                  nb, W);
@@ -290,11 +339,11 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     // outputs
 #pragma unroll
     for (int r = 0; r < MR; r++) {
-        const int64_t q = q0 + ty + 16 * r;
+        const int64_t q = q0 + row_of(r);
         unsigned long long best = ~0ull;
 #pragma unroll
         for (int c = 0; c < MC; c++) {
-            const int64_t t = t0 + tx + 16 * c;
+            const int64_t t = t0 + col_of(c);
             const T raw = acc[r][c];
             const T sv = safe_scale(raw, lb_lo, abs_slack);
             if (q < Q && t < N) {
