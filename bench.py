@@ -526,6 +526,10 @@ def main():
     ap.add_argument("--improved", action="store_true",
                     help="test the bound with the LB_Improved bridge in every dataset (with "
                          "--dtw-group or --no-tune; the tuner decides otherwise)")
+    ap.add_argument("--tuned-flags", default=None,
+                    help="JSON file of per-dataset search flags: read if it exists (no tuning), "
+                         "else written after tuning, so that a profiled run repeats the choices "
+                         "of a plain one")
     ap.add_argument("--dtw-group", type=int, default=0,
                     help="lanes per pair for every dataset (1..32, or 64 for the row layout); "
                          "implies --no-tune")
@@ -591,6 +595,14 @@ def main():
         for i, s in enumerate(sets):
             s["flags"] = cascade
             tuned[i] = record(0, cascade)
+    elif args.tuned_flags and os.path.exists(args.tuned_flags):
+        with open(args.tuned_flags) as f:
+            saved = json.load(f)
+        if len(saved["flags"]) != len(sets):
+            raise SystemExit(f"{args.tuned_flags}: {len(saved['flags'])} datasets, expected {len(sets)}")
+        for i, s in enumerate(sets):
+            s["flags"] = int(saved["flags"][i])
+        tuned = {int(k): v for k, v in saved["tuned"].items()}
     elif not args.no_tune:
         for i, (d, s) in enumerate(zip(dsets, sets)):
             if d.N * d.Q >= 50_000:
@@ -599,6 +611,9 @@ def main():
                 g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)
                 if g or s["flags"] & (nndtw.REVERSE | nndtw.IMPROVED):
                     tuned[i] = record(g, s["flags"])
+        if args.tuned_flags and rank == 0:
+            with open(args.tuned_flags, "w") as f:
+                json.dump({"flags": [s["flags"] for s in sets], "tuned": tuned}, f)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # counting pass (untimed): pruning and cells per dataset

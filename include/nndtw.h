@@ -48,7 +48,7 @@ extern "C" {
 #define NNDTW_API
 #endif
 
-#define NNDTW_MAX_L 4096
+#define NNDTW_MAX_L 8192
 
 /* status codes */
 #define NNDTW_OK 0
@@ -84,7 +84,8 @@ extern "C" {
 #define NNDTW_DTW_GROUP(log2g) ((unsigned)((log2g) + 1) << 8)
 #define NNDTW_DTW_GROUP_MASK (7u << 8)
 /* search / dtw_windowed: for full windows (W >= L-1) sweep DTW by rows, one
- * pair per warp for L <= 2048 and one pair per 128-thread CTA for L <= 4096
+ * pair per warp for L <= 2048 and one pair per CTA of 128 threads for L <=
+ * 4096 and of 256 threads for L <= 8192
  * (the default for such windows when no NNDTW_DTW_GROUP is given); ignored
  * for other windows.  Combined with
  * NNDTW_DTW_ROWS_LANES16 (L <= 1024) or NNDTW_DTW_ROWS_LANES8 (L <= 512) a

@@ -41,15 +41,15 @@ def key(device_name: str, N: int, Q: int, L: int, W: int, V: int) -> str:
 def admissible_groups(W: int, L: int | None = None):
     """Lanes-per-pair choices of the diagonal layout for window W, plus the
     row layouts when the window is full (W >= L-1): 32 lanes per pair for
-    L <= 2048 (a CTA of 128 lanes per pair up to 4096), 16 for L <= 1024,
-    8 for L <= 512."""
+    L <= 2048 (a CTA of 128 lanes per pair up to 4096, of 256 up to 8192),
+    16 for L <= 1024, 8 for L <= 512."""
     out = []
     for g in (1, 2, 4, 8, 16, 32):
         h = (W + g) // g
         if h <= 32 and not (h == 1 and g != W + 1):
             out.append(g)
     if L is not None and W >= L - 1:
-        if L <= 4096:
+        if L <= nndtw.NNDTW_MAX_L:
             out.append(nndtw.ROWS_GROUP)
         if L <= 1024:
             out.append(nndtw.ROWS16_GROUP)

@@ -1,6 +1,7 @@
 // FP32 DTW (Sec. 2.1, Eq. 1) for full windows of long series, 2048 < L <=
-// 4096: the row layout of the one-pair-per-warp kernel spread over a CTA of
-// four warps (128 lanes, C = ceil(L / 128) columns each).
+// 8192: the row layout of the one-pair-per-warp kernel spread over a CTA of
+// NW warps (four up to L = 4096, eight beyond; 32 NW lanes, C = ceil(L / (32
+// NW)) columns each).
 //
 // Inside a warp the lanes exchange values by shuffles exactly as in that
 // kernel: the query streams from lane to lane, and each lane needs the last
@@ -18,9 +19,10 @@
 namespace nndtw {
 namespace {
 
-constexpr int kWarps = 4, kLanes = 32 * kWarps;
-
-__host__ __device__ constexpr int rowsc_min_blocks(int C) { return C <= 20 ? 4 : 3; }
+// resident CTAs per SM (of NW warps) for C columns per lane
+__host__ __device__ constexpr int rowsc_min_blocks(int C, int NW) {
+    return (C <= 20 ? 4 : 3) * 4 / NW > 0 ? (C <= 20 ? 4 : 3) * 4 / NW : 1;
+}
 
 // One step of one lane (global lane g of the CTA), from Din to Dout: as in
 // the one-pair-per-warp kernel, with the first lane of warps 1..3 taking its
@@ -73,9 +75,10 @@ __device__ __forceinline__ void rowsc_advance(const float (&Din)[C], float (&Dou
     }
 }
 
-template <int C>
-__global__ void __launch_bounds__(kLanes, rowsc_min_blocks(C))
+template <int C, int NW>
+__global__ void __launch_bounds__(32 * NW, rowsc_min_blocks(C, NW))
 dtw32_rowsc_kernel(DtwJob32 job) {
+    constexpr int kWarps = NW, kLanes = 32 * NW;
     constexpr int K = C >= 4 ? 2 : 1;
     constexpr int C0 = K == 2 ? (C + 1) / 2 : C;
     const float INF = inf_of<float>();
@@ -223,21 +226,28 @@ dtw32_rowsc_kernel(DtwJob32 job) {
     }
 }
 
+// C = 17 .. 32 columns per lane: L in (2048, 4096] over 4 warps, (4096, 8192]
+// over 8 warps
+constexpr int kCMin = 17, kCMax = 32;
 using RowsCFn = void (*)(DtwJob32);
-template <int C> RowsCFn rowsc_fn() { return &dtw32_rowsc_kernel<C>; }
-template <int... Cs> RowsCFn pick_rowsc(int c, std::integer_sequence<int, Cs...>) {
-    RowsCFn fns[] = {rowsc_fn<Cs + 1>()...};
-    return (c >= 1 && c <= (int)sizeof...(Cs)) ? fns[c - 1] : nullptr;
+template <int C, int NW> RowsCFn rowsc_fn() { return &dtw32_rowsc_kernel<C, NW>; }
+template <int NW, int... Cs> RowsCFn pick_rowsc(int c, std::integer_sequence<int, Cs...>) {
+    RowsCFn fns[] = {rowsc_fn<Cs + kCMin, NW>()...};
+    return (c >= kCMin && c <= kCMax) ? fns[c - kCMin] : nullptr;
 }
+
+int rowsc_warps(int L) { return L > 32 * 4 * kCMax ? 8 : 4; }
 
 }  // namespace
 
-bool dtw32_rowsc_ok(int L, int W) { return W >= L - 1 && L > 32 * 64 && L <= kLanes * 32; }
+bool dtw32_rowsc_ok(int L, int W) { return W >= L - 1 && L > 32 * 64 && L <= 32 * 8 * kCMax; }
 
 cudaError_t launch_dtw32_rowsc(const DtwJob32 &job, int sm_count, cudaStream_t s) {
     if (!dtw32_rowsc_ok(job.L, job.W)) return cudaErrorNotSupported;
+    const int NW = rowsc_warps(job.L), kLanes = 32 * NW;
     const int C = (job.L + kLanes - 1) / kLanes;
-    RowsCFn fn = pick_rowsc(C, std::make_integer_sequence<int, 32>{});
+    using Seq = std::make_integer_sequence<int, kCMax - kCMin + 1>;
+    RowsCFn fn = NW == 8 ? pick_rowsc<8>(C, Seq{}) : pick_rowsc<4>(C, Seq{});
     if (!fn) return cudaErrorNotSupported;
     int bps = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kLanes, 0);

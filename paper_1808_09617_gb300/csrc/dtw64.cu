@@ -9,7 +9,10 @@
 // bit patterns as 64-bit integers (D is never negative, and +inf orders
 // last), which keeps it off GB300's narrow FP64 pipe.
 //
-// Both series are staged in shared memory; the band is kept by diagonals
+// Both series are staged in shared memory (FP32 inputs of the recheck as
+// FP32, converted exactly when used; FP64 series only while the two of them
+// and the band fit, else they are read from global memory, where L2 holds
+// them); the band is kept by diagonals
 // k = j - i + W in shared memory, one slot per diagonal plus two +inf
 // sentinels.  Anti-diagonal t updates the diagonals of its parity that hold a
 // cell inside the L x L matrix, spread over the CTA's threads, reading only
@@ -25,10 +28,14 @@
 // series against the query's envelope, scaled down by the bound's rounding
 // margin) is compared with the same best, and the pair is dropped when it is
 // larger.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace nndtw {
 namespace {
+
+constexpr size_t kDtw64SmemCap = 227 * 1024;
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
@@ -38,9 +45,11 @@ dtw64_kernel(DtwJob64 job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = job.L, W = job.W;
     const int nslot = 2 * W + 3;
+    using ST = typename std::conditional<F32IN, float, double>::type;
     long long *Rs = reinterpret_cast<long long *>(smem_raw);  // Rs[k+1]: double bits
-    double *As = reinterpret_cast<double *>(Rs + nslot);
-    double *Bs = As + L;
+    ST *As = reinterpret_cast<ST *>(Rs + nslot);
+    ST *Bs = As + L;
+    const bool staged = F32IN || job.stage_series;
     __shared__ long long red[32];
     __shared__ long long claim;
     __shared__ int bcast;
@@ -122,9 +131,17 @@ dtw64_kernel(DtwJob64 job) {
             __syncthreads();
             if (drop) continue;
         }
-        for (int i = tid; i < L; i += nthr) {
-            As[i] = F32IN ? (double)job.test32[(long long)q * L + i] : job.test[(long long)q * L + i];
-            Bs[i] = F32IN ? (double)job.train32[(long long)t * L + i] : job.train[(long long)t * L + i];
+        const ST *Ap, *Bp;
+        if (F32IN) {
+            Ap = reinterpret_cast<const ST *>(job.test32 + (long long)q * L);
+            Bp = reinterpret_cast<const ST *>(job.train32 + (long long)t * L);
+        } else {
+            Ap = reinterpret_cast<const ST *>(job.test + (long long)q * L);
+            Bp = reinterpret_cast<const ST *>(job.train + (long long)t * L);
+        }
+        if (staged) {
+            for (int i = tid; i < L; i += nthr) { As[i] = Ap[i]; Bs[i] = Bp[i]; }
+            Ap = As; Bp = Bs;
         }
         for (int k = tid; k < nslot; k += nthr) Rs[k] = INFB;
         __syncthreads();
@@ -168,7 +185,7 @@ dtw64_kernel(DtwJob64 job) {
             for (int k = klo + 2 * tid; k <= khi; k += 2 * nthr) {
                 const int i = (s + W - k) >> 1, j = s - i;
                 const long long m = lmin(lmin(Rs[k + 1], Rs[k]), Rs[k + 2]);
-                const double d = __dsub_rn(As[i], Bs[j]);
+                const double d = __dsub_rn((double)Ap[i], (double)Bp[j]);
                 const double tt = __dmul_rn(d, d);
                 Rs[k + 1] = __double_as_longlong(__dadd_rn(tt, __longlong_as_double(m)));
             }
@@ -200,9 +217,14 @@ dtw64_kernel(DtwJob64 job) {
 
 }  // namespace
 
-cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s) {
-    if (!job.count && job.n_pairs <= 0) return cudaSuccess;
-    const size_t smem = sizeof(long long) * (size_t)(2 * job.W + 3) + sizeof(double) * 2 * (size_t)job.L;
+cudaError_t launch_dtw64(const DtwJob64 &job_in, int sm_count, cudaStream_t s) {
+    if (!job_in.count && job_in.n_pairs <= 0) return cudaSuccess;
+    DtwJob64 job = job_in;
+    const size_t band = sizeof(long long) * (size_t)(2 * job.W + 3);
+    const size_t series = (job.test32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)job.L;
+    job.stage_series = band + series <= kDtw64SmemCap;
+    if (job.test32 && !job.stage_series) return cudaErrorInvalidValue;
+    const size_t smem = band + (job.stage_series ? series : 0);
     // threads: enough for the widest anti-diagonal (W+1 cells), 32..256
     int threads = ((job.W / 2 + 1) + 31) / 32 * 32;
     if (threads > 256) threads = 256;

@@ -32,19 +32,19 @@ __global__ void __launch_bounds__(kEnvThreads)
 envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64_t N, int L,
                 int W, T *__restrict__ env, int T_tile, int levels) {
     // env_in == nullptr: envelopes of train; else the second envelopes of
-    // env_in ([N][L] (U, Lo)): window max of Lo and window min of U
+    // env_in ([N][L] (U, Lo)): window max of Lo and window min of U.
+    // Two passes per series: the window maximum (pass 0), then the window
+    // minimum as the negated maximum of the negated values (pass 1; negation
+    // is exact), each over tile prefixes P, suffixes S and the tile table M.
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Pmax = reinterpret_cast<T *>(smem_raw);
-    T *Pmin = Pmax + L;
-    T *Smax = Pmin + L;
-    T *Smin = Smax + L;
-    T *Mmax = Smin + L;                       // [levels+1][nt]
+    T *P = reinterpret_cast<T *>(smem_raw);
+    T *S = P + L;
+    T *M = S + L;                              // [levels+1][nt]
     const int nt = (L + T_tile - 1) / T_tile;
-    T *Mmin = Mmax + (size_t)(levels + 1) * nt;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int r = lane & (T_tile - 1);
-    const T NEG = -inf_of<T>(), POS = inf_of<T>();
+    const T NEG = -inf_of<T>();
 
     for (int64_t s = blockIdx.x; s < N; s += gridDim.x) {
         const T *x = env_in ? nullptr : train + s * (int64_t)L;
@@ -57,64 +57,58 @@ envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64
             }
             continue;
         }
-        // tile prefix / suffix scans
-        for (int base = 0; base < L; base += kEnvThreads) {
-            const int k = base + tid;
-            T pmx = NEG, pmn = POS;
-            if (k < L) {
-                pmx = ein ? ein[2 * k + 1] : x[k];
-                pmn = ein ? ein[2 * k] : x[k];
+        for (int pass = 0; pass < 2; pass++) {
+            // the values whose window maximum this pass takes
+            auto value = [&](int k) -> T {
+                if (pass == 0) return ein ? ein[2 * k + 1] : x[k];
+                return -(ein ? ein[2 * k] : x[k]);
+            };
+            // tile prefix / suffix scans
+            for (int base = 0; base < L; base += kEnvThreads) {
+                const int k = base + tid;
+                T pm = k < L ? value(k) : NEG;
+                T sm = pm;
+                for (int d = 1; d < T_tile; d <<= 1) {
+                    const T a = __shfl_up_sync(0xffffffffu, pm, d);
+                    const T c = __shfl_down_sync(0xffffffffu, sm, d);
+                    if (r >= d) pm = tmax(pm, a);
+                    if (r + d < T_tile) sm = tmax(sm, c);
+                }
+                if (k < L) {
+                    P[k] = pm; S[k] = sm;
+                    if (r == 0) M[k / T_tile] = sm;
+                }
             }
-            T smx = pmx, smn = pmn;
-            for (int d = 1; d < T_tile; d <<= 1) {
-                T a = __shfl_up_sync(0xffffffffu, pmx, d);
-                T b = __shfl_up_sync(0xffffffffu, pmn, d);
-                T c = __shfl_down_sync(0xffffffffu, smx, d);
-                T e = __shfl_down_sync(0xffffffffu, smn, d);
-                if (r >= d) { pmx = tmax(pmx, a); pmn = tmin(pmn, b); }
-                if (r + d < T_tile) { smx = tmax(smx, c); smn = tmin(smn, e); }
+            __syncthreads();
+            // sparse table over tile maxima (level j covers 2^j tiles)
+            for (int j = 1; j <= levels; j++) {
+                const int half = 1 << (j - 1);
+                const int cnt = nt - (1 << j) + 1;
+                const T *pm = M + (size_t)(j - 1) * nt;
+                T *cm = M + (size_t)j * nt;
+                for (int t = tid; t < cnt; t += kEnvThreads) cm[t] = tmax(pm[t], pm[t + half]);
+                __syncthreads();
             }
-            if (k < L) {
-                Pmax[k] = pmx; Pmin[k] = pmn; Smax[k] = smx; Smin[k] = smn;
-                if (r == 0) { Mmax[k / T_tile] = smx; Mmin[k / T_tile] = smn; }
-            }
-        }
-        __syncthreads();
-        // sparse table over tile extremes (level j covers 2^j tiles)
-        for (int j = 1; j <= levels; j++) {
-            const int half = 1 << (j - 1);
-            const int cnt = nt - (1 << j) + 1;
-            const T *pmx = Mmax + (size_t)(j - 1) * nt, *pmn = Mmin + (size_t)(j - 1) * nt;
-            T *cmx = Mmax + (size_t)j * nt, *cmn = Mmin + (size_t)j * nt;
-            for (int t = tid; t < cnt; t += kEnvThreads) {
-                cmx[t] = tmax(pmx[t], pmx[t + half]);
-                cmn[t] = tmin(pmn[t], pmn[t + half]);
+            for (int i = tid; i < L; i += kEnvThreads) {
+                const int lo = i - W < 0 ? 0 : i - W;
+                const int hi = i + W > L - 1 ? L - 1 : i + W;
+                const int tlo = lo / T_tile, thi = hi / T_tile;
+                T u = tmax(S[lo], P[hi]);
+                const int a = tlo + 1, b = thi - 1;
+                if (b >= a) {
+                    if (levels == 0) {
+                        for (int t = a; t <= b; t++) u = tmax(u, M[t]);
+                    } else {
+                        const int len = b - a + 1;
+                        const int j = 31 - __clz(len);
+                        const T *mx = M + (size_t)j * nt;
+                        u = tmax(u, tmax(mx[a], mx[b - (1 << j) + 1]));
+                    }
+                }
+                out[2 * i + pass] = pass == 0 ? u : -u;
             }
             __syncthreads();
         }
-        for (int i = tid; i < L; i += kEnvThreads) {
-            const int lo = i - W < 0 ? 0 : i - W;
-            const int hi = i + W > L - 1 ? L - 1 : i + W;
-            const int tlo = lo / T_tile, thi = hi / T_tile;
-            T u = tmax(Smax[lo], Pmax[hi]);
-            T l = tmin(Smin[lo], Pmin[hi]);
-            const int a = tlo + 1, b = thi - 1;
-            if (b >= a) {
-                if (levels == 0) {
-                    for (int t = a; t <= b; t++) { u = tmax(u, Mmax[t]); l = tmin(l, Mmin[t]); }
-                } else {
-                    const int len = b - a + 1;
-                    const int j = 31 - __clz(len);
-                    const T *mx = Mmax + (size_t)j * nt, *mn = Mmin + (size_t)j * nt;
-                    const int b2 = b - (1 << j) + 1;
-                    u = tmax(u, tmax(mx[a], mx[b2]));
-                    l = tmin(l, tmin(mn[a], mn[b2]));
-                }
-            }
-            out[2 * i] = u;
-            out[2 * i + 1] = l;
-        }
-        __syncthreads();
     }
 }
 
@@ -132,7 +126,7 @@ cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, i
         while (T_tile * 2 <= Weff) T_tile *= 2;
     }
     const int nt = (L + T_tile - 1) / T_tile;
-    const size_t smem = sizeof(T) * (4 * (size_t)L + 2 * (size_t)(levels + 1) * nt);
+    const size_t smem = sizeof(T) * (2 * (size_t)L + (size_t)(levels + 1) * nt);
     cudaError_t e = cudaFuncSetAttribute(envelope_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

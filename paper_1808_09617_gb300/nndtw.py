@@ -19,7 +19,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libnndtw.so")
 
-NNDTW_MAX_L = 4096
+NNDTW_MAX_L = 8192
 OK, EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED, ENONFINITE = 0, 1, 2, 3, 4, 5
 LB_KEOGH = 1 << 0
 LB_SAFE = 1 << 1

@@ -46,7 +46,8 @@ def test_host_only_calls(clib):
     # invalid sizes give 0 bytes
     assert nndtw.nn_dtw_workspace_size(0, 5, 256, 26, 5) == 0
     assert nndtw.nn_dtw_workspace_size(5, 5, 1, 0, 5) == 0
-    assert nndtw.nn_dtw_workspace_size(5, 5, 8192, 0, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, nndtw.NNDTW_MAX_L + 1, 0, 5) == 0
+    assert nndtw.nn_dtw_workspace_size(5, 5, nndtw.NNDTW_MAX_L, 0, 5) > 0
     assert nndtw.nn_dtw_workspace_size(5, 5, 64, -1, 5) == 0
     assert nndtw.nn_dtw_workspace_size(5, 5, 64, 3, 0) == 0
     assert nndtw.nn_dtw_host_buffer_size(10, 4, 64, 6, 2) > nndtw.nn_dtw_workspace_size(

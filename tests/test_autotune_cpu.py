@@ -14,7 +14,8 @@ def test_admissible_groups():
     assert autotune.admissible_groups(599, 600)[-2:] == [64, 65]     # 8 lanes hold L <= 512
     assert 65 not in autotune.admissible_groups(1999, 2000)          # 16 lanes hold L <= 1024
     assert 64 not in autotune.admissible_groups(100, 256)
-    assert 64 in autotune.admissible_groups(3000, 3001)      # a CTA per pair up to 4096
+    assert 64 in autotune.admissible_groups(3000, 3001)      # a CTA per pair up to 8192
+    assert 64 in autotune.admissible_groups(8191, 8192)
 
 
 def test_key_buckets():

@@ -28,7 +28,8 @@ def _series(seed, n, L, dtype=np.float32):
 
 ENV_CASES = [(2, 0), (2, 1), (3, 1), (5, 2), (17, 3), (100, 13), (256, 26), (300, 31),
              (300, 32), (300, 33), (129, 1), (24, 24), (1024, 102), (1024, 512), (1024, 1023),
-             (1024, 5000), (4096, 409), (4096, 100), (4096, 4095), (33, 7)]
+             (1024, 5000), (4096, 409), (4096, 100), (4096, 4095), (33, 7), (8192, 819),
+             (8192, 8191), (6000, 31), (5000, 2500)]
 
 
 @pytest.mark.parametrize("L,W", ENV_CASES)
@@ -40,7 +41,7 @@ def test_envelopes_bit_exact(lib, orc, L, W):
     np.testing.assert_array_equal(env[..., 1], Lo.astype(np.float32))
 
 
-@pytest.mark.parametrize("L,W", [(128, 13), (7, 3), (1000, 999)])
+@pytest.mark.parametrize("L,W", [(128, 13), (7, 3), (1000, 999), (8192, 100), (8192, 8191)])
 def test_envelopes_f64_bit_exact(lib, orc, L, W):
     x = _series(L + W, 11, L, np.float64)
     env = lib.nn_dtw_build_envelopes(_t(x), W).cpu().numpy()
@@ -52,7 +53,7 @@ def test_envelopes_f64_bit_exact(lib, orc, L, W):
 # ---------------------------------------------------------------- bounds
 
 LB_CASES = [(256, 26, 1), (256, 26, 2), (256, 26, 5), (100, 0, 3), (57, 56, 20), (200, 50, 64),
-            (2, 1, 1), (5, 2, 2), (1024, 102, 5), (130, 3, 7), (31, 30, 15)]
+            (2, 1, 1), (5, 2, 2), (1024, 102, 5), (130, 3, 7), (31, 30, 15), (8192, 819, 5)]
 
 
 @pytest.mark.parametrize("L,W,V", LB_CASES)
@@ -275,7 +276,7 @@ def test_dtw_every_group_width_same_values(lib, orc, L, W):
 
 
 @pytest.mark.parametrize("L", [1, 2, 5, 31, 32, 33, 64, 100, 1000, 2047, 2048, 2049, 2600, 3001,
-                               4095, 4096])
+                               4095, 4096, 4097, 6000, 8192])
 def test_dtw_full_window_row_layout(lib, orc, L):
     """Full windows (W >= L-1) use the row layout by default; the diagonal layout
     (forced by a group width) must agree."""
@@ -371,16 +372,30 @@ def test_search_reverse_bound_defaults(lib, orc):
     assert f64["lb_pruned_reverse"] > 0 and f32["lb_pruned_reverse"] == 0
 
 
-@pytest.mark.parametrize("L,N,Q", [(3000, 40, 12), (4096, 20, 6)])
+@pytest.mark.parametrize("L,N,Q", [(3000, 40, 12), (4096, 20, 6), (8192, 8, 3)])
 def test_search_long_full_window(lib, orc, L, N, Q):
     """Full windows of series longer than 2048 (a CTA per pair in the row
-    layout): the exhaustive FP64 nearest neighbours, ties included."""
+    layout; the FP64 recheck of the tie on FP32 series staged as FP32): the
+    exhaustive FP64 nearest neighbours, ties included."""
     rng = np.random.default_rng(L)
     train = synth.znormed_walks(rng, N, L).astype(np.float32)
     test = synth.znormed_walks(rng, Q, L).astype(np.float32)
     test[0] = train[5]
     labels = rng.integers(0, 3, N).astype(np.int32)
     _check_search(lib, orc, train, labels, test, L - 1, 4)
+
+
+@pytest.mark.parametrize("L,W,N,Q", [(8192, 8191, 6, 2), (6000, 600, 10, 3), (8192, 5000, 5, 2)])
+def test_search_f64_long_series(lib, orc, L, W, N, Q):
+    """The FP64 form on series up to 8192: the FP64 kernel reads the series
+    from global memory when the two series and the band do not fit in shared
+    memory (L = 8192, W = 8191); results bit-identical to the oracle."""
+    rng = np.random.default_rng(L + W)
+    train = synth.znormed_walks(rng, N, L)
+    test = synth.znormed_walks(rng, Q, L)
+    test[0] = train[N - 1]
+    labels = rng.integers(0, 3, N).astype(np.int32)
+    _check_search(lib, orc, train, labels, test, W, 3)
 
 
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
@@ -391,7 +406,8 @@ def test_search_group_override(lib, orc, g):
                   flags=lib.DTW_GROUP(g), brute=brute)
 
 
-@pytest.mark.parametrize("N,Q,L,W", [(12, 5, 2048, 1500), (9, 4, 1100, 1099), (7, 3, 2048, 1024)])
+@pytest.mark.parametrize("N,Q,L,W", [(12, 5, 2048, 1500), (9, 4, 1100, 1099), (7, 3, 2048, 1024),
+                                     (5, 2, 8192, 5000), (6, 3, 6000, 1023)])
 def test_search_wide_windows(lib, orc, N, Q, L, W):
     """Windows beyond the register kernel (W >= 1024) use the shared-memory band kernel."""
     train = _series(31 + L, N, L)
