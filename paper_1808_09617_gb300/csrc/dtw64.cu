@@ -9,10 +9,11 @@
 // bit patterns as 64-bit integers (D is never negative, and +inf orders
 // last), which keeps it off GB300's narrow FP64 pipe.
 //
-// Both series are staged in shared memory (FP32 inputs of the recheck as
-// FP32, converted exactly when used; FP64 series only while the two of them
-// and the band fit, else they are read from global memory, where L2 holds
-// them); the band is kept by diagonals
+// Both series are staged in shared memory as FP64 while they fit next to the
+// band (FP32 inputs of the recheck converted once, exactly); beyond that the
+// recheck stages its FP32 inputs as FP32 and converts them in every cell,
+// and FP64 series are read from global memory, where L2 holds them.  The
+// band is kept by diagonals
 // k = j - i + W in shared memory, one slot per diagonal plus two +inf
 // sentinels.  Anti-diagonal t updates the diagonals of its parity that hold a
 // cell inside the L x L matrix, spread over the CTA's threads, reading only
@@ -39,17 +40,17 @@ constexpr size_t kDtw64SmemCap = 227 * 1024;
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
-template <bool F32IN>
+template <bool F32IN, bool F32STAGE, bool STAGED>
 __global__ void __launch_bounds__(256)
 dtw64_kernel(DtwJob64 job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = job.L, W = job.W;
     const int nslot = 2 * W + 3;
-    using ST = typename std::conditional<F32IN, float, double>::type;
+    using ST = typename std::conditional<F32STAGE, float, double>::type;   // staged type
+    using IT = typename std::conditional<F32IN, float, double>::type;      // input type
     long long *Rs = reinterpret_cast<long long *>(smem_raw);  // Rs[k+1]: double bits
     ST *As = reinterpret_cast<ST *>(Rs + nslot);
     ST *Bs = As + L;
-    const bool staged = F32IN || job.stage_series;
     __shared__ long long red[32];
     __shared__ long long claim;
     __shared__ int bcast;
@@ -131,18 +132,21 @@ dtw64_kernel(DtwJob64 job) {
             __syncthreads();
             if (drop) continue;
         }
-        const ST *Ap, *Bp;
+        const IT *Ag, *Bg;
         if (F32IN) {
-            Ap = reinterpret_cast<const ST *>(job.test32 + (long long)q * L);
-            Bp = reinterpret_cast<const ST *>(job.train32 + (long long)t * L);
+            Ag = reinterpret_cast<const IT *>(job.test32 + (long long)q * L);
+            Bg = reinterpret_cast<const IT *>(job.train32 + (long long)t * L);
         } else {
-            Ap = reinterpret_cast<const ST *>(job.test + (long long)q * L);
-            Bp = reinterpret_cast<const ST *>(job.train + (long long)t * L);
+            Ag = reinterpret_cast<const IT *>(job.test + (long long)q * L);
+            Bg = reinterpret_cast<const IT *>(job.train + (long long)t * L);
         }
-        if (staged) {
-            for (int i = tid; i < L; i += nthr) { As[i] = Ap[i]; Bs[i] = Bp[i]; }
-            Ap = As; Bp = Bs;
+        // staged copies (shared-memory loads in the sweep), or (FP64 inputs
+        // only) the series in global memory
+        if (STAGED) {
+            for (int i = tid; i < L; i += nthr) { As[i] = (ST)Ag[i]; Bs[i] = (ST)Bg[i]; }
         }
+        const ST *Ap = STAGED ? As : reinterpret_cast<const ST *>(Ag);
+        const ST *Bp = STAGED ? Bs : reinterpret_cast<const ST *>(Bg);
         for (int k = tid; k < nslot; k += nthr) Rs[k] = INFB;
         __syncthreads();
         if (tid == 0) {
@@ -215,43 +219,43 @@ dtw64_kernel(DtwJob64 job) {
     }
 }
 
-}  // namespace
 
-cudaError_t launch_dtw64(const DtwJob64 &job_in, int sm_count, cudaStream_t s) {
-    if (!job_in.count && job_in.n_pairs <= 0) return cudaSuccess;
-    DtwJob64 job = job_in;
-    const size_t band = sizeof(long long) * (size_t)(2 * job.W + 3);
-    const size_t series = (job.test32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)job.L;
-    job.stage_series = band + series <= kDtw64SmemCap;
-    if (job.test32 && !job.stage_series) return cudaErrorInvalidValue;
-    const size_t smem = band + (job.stage_series ? series : 0);
+template <bool F32IN, bool F32STAGE, bool STAGED>
+cudaError_t launch_dtw64_as(const DtwJob64 &job, size_t smem, int sm_count, cudaStream_t s) {
+    auto fn = dtw64_kernel<F32IN, F32STAGE, STAGED>;
     // threads: enough for the widest anti-diagonal (W+1 cells), 32..256
     int threads = ((job.W / 2 + 1) + 31) / 32 * 32;
     if (threads > 256) threads = 256;
     if (threads < 32) threads = 32;
-    cudaError_t e;
-    if (job.test32)
-        e = cudaFuncSetAttribute(dtw64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-    else
-        e = cudaFuncSetAttribute(dtw64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int bps = 0;
-    if (job.test32)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dtw64_kernel<true>, threads, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dtw64_kernel<false>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     const long long cap = (long long)sm_count * bps;
     long long grid = job.count ? cap : (job.n_pairs < cap ? job.n_pairs : cap);
     if (grid < 1) grid = 1;
-    if (job.test32)
-        dtw64_kernel<true><<<(unsigned)grid, threads, smem, s>>>(job);
-    else
-        dtw64_kernel<false><<<(unsigned)grid, threads, smem, s>>>(job);
+    fn<<<(unsigned)grid, threads, smem, s>>>(job);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_dtw64(const DtwJob64 &job_in, int sm_count, cudaStream_t s) {
+    if (!job_in.count && job_in.n_pairs <= 0) return cudaSuccess;
+    const DtwJob64 &job = job_in;
+    const size_t band = sizeof(long long) * (size_t)(2 * job.W + 3);
+    const size_t as_f64 = sizeof(double) * 2 * (size_t)job.L;
+    const size_t as_f32 = sizeof(float) * 2 * (size_t)job.L;
+    if (band + as_f64 <= kDtw64SmemCap)
+        return job.test32 ? launch_dtw64_as<true, false, true>(job, band + as_f64, sm_count, s)
+                          : launch_dtw64_as<false, false, true>(job, band + as_f64, sm_count, s);
+    if (job.test32) {
+        if (band + as_f32 > kDtw64SmemCap) return cudaErrorInvalidValue;
+        return launch_dtw64_as<true, true, true>(job, band + as_f32, sm_count, s);
+    }
+    return launch_dtw64_as<false, false, false>(job, band, sm_count, s);
 }
 
 }  // namespace nndtw

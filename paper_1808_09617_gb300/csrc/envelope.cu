@@ -27,20 +27,24 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
-template <typename T>
+// Channel 0 is the window maximum of the series (of Lo for the second
+// envelopes), channel 1 the window minimum of the series (of U), taken as
+// the negated maximum of the negated values (negation is exact).  NP = 2
+// computes both channels in one pass over tile prefixes P, suffixes S and
+// tile tables M ([NP][L], [NP][L], [NP][levels+1][nt]); NP = 1 runs one
+// channel per pass in half the shared memory (the longest FP64 series).
+template <typename T, int NP>
 __global__ void __launch_bounds__(kEnvThreads)
 envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64_t N, int L,
                 int W, T *__restrict__ env, int T_tile, int levels) {
     // env_in == nullptr: envelopes of train; else the second envelopes of
-    // env_in ([N][L] (U, Lo)): window max of Lo and window min of U.
-    // Two passes per series: the window maximum (pass 0), then the window
-    // minimum as the negated maximum of the negated values (pass 1; negation
-    // is exact), each over tile prefixes P, suffixes S and the tile table M.
+    // env_in ([N][L] (U, Lo)): window max of Lo and window min of U
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *P = reinterpret_cast<T *>(smem_raw);
-    T *S = P + L;
-    T *M = S + L;                              // [levels+1][nt]
     const int nt = (L + T_tile - 1) / T_tile;
+    T *P = reinterpret_cast<T *>(smem_raw);                 // [NP][L]
+    T *S = P + (size_t)NP * L;                              // [NP][L]
+    T *M = S + (size_t)NP * L;                              // [NP][levels+1][nt]
+    const size_t mstride = (size_t)(levels + 1) * nt;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int r = lane & (T_tile - 1);
@@ -57,26 +61,30 @@ envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64
             }
             continue;
         }
-        for (int pass = 0; pass < 2; pass++) {
-            // the values whose window maximum this pass takes
-            auto value = [&](int k) -> T {
-                if (pass == 0) return ein ? ein[2 * k + 1] : x[k];
+        for (int pass = 0; pass < 2 / NP; pass++) {
+            // the values whose window maximum channel ch takes
+            auto value = [&](int ch, int k) -> T {
+                if (ch == 0) return ein ? ein[2 * k + 1] : x[k];
                 return -(ein ? ein[2 * k] : x[k]);
             };
             // tile prefix / suffix scans
             for (int base = 0; base < L; base += kEnvThreads) {
                 const int k = base + tid;
-                T pm = k < L ? value(k) : NEG;
-                T sm = pm;
-                for (int d = 1; d < T_tile; d <<= 1) {
-                    const T a = __shfl_up_sync(0xffffffffu, pm, d);
-                    const T c = __shfl_down_sync(0xffffffffu, sm, d);
-                    if (r >= d) pm = tmax(pm, a);
-                    if (r + d < T_tile) sm = tmax(sm, c);
-                }
-                if (k < L) {
-                    P[k] = pm; S[k] = sm;
-                    if (r == 0) M[k / T_tile] = sm;
+#pragma unroll
+                for (int c = 0; c < NP; c++) {
+                    const int ch = pass * NP + c;
+                    T pm = k < L ? value(ch, k) : NEG;
+                    T sm = pm;
+                    for (int d = 1; d < T_tile; d <<= 1) {
+                        const T a = __shfl_up_sync(0xffffffffu, pm, d);
+                        const T b = __shfl_down_sync(0xffffffffu, sm, d);
+                        if (r >= d) pm = tmax(pm, a);
+                        if (r + d < T_tile) sm = tmax(sm, b);
+                    }
+                    if (k < L) {
+                        P[(size_t)c * L + k] = pm; S[(size_t)c * L + k] = sm;
+                        if (r == 0) M[c * mstride + k / T_tile] = sm;
+                    }
                 }
             }
             __syncthreads();
@@ -84,28 +92,34 @@ envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64
             for (int j = 1; j <= levels; j++) {
                 const int half = 1 << (j - 1);
                 const int cnt = nt - (1 << j) + 1;
-                const T *pm = M + (size_t)(j - 1) * nt;
-                T *cm = M + (size_t)j * nt;
-                for (int t = tid; t < cnt; t += kEnvThreads) cm[t] = tmax(pm[t], pm[t + half]);
+                for (int idx = tid; idx < NP * cnt; idx += kEnvThreads) {
+                    const int c = idx / cnt, t = idx % cnt;
+                    const T *pm = M + c * mstride + (size_t)(j - 1) * nt;
+                    M[c * mstride + (size_t)j * nt + t] = tmax(pm[t], pm[t + half]);
+                }
                 __syncthreads();
             }
             for (int i = tid; i < L; i += kEnvThreads) {
                 const int lo = i - W < 0 ? 0 : i - W;
                 const int hi = i + W > L - 1 ? L - 1 : i + W;
-                const int tlo = lo / T_tile, thi = hi / T_tile;
-                T u = tmax(S[lo], P[hi]);
-                const int a = tlo + 1, b = thi - 1;
-                if (b >= a) {
-                    if (levels == 0) {
-                        for (int t = a; t <= b; t++) u = tmax(u, M[t]);
-                    } else {
-                        const int len = b - a + 1;
-                        const int j = 31 - __clz(len);
-                        const T *mx = M + (size_t)j * nt;
-                        u = tmax(u, tmax(mx[a], mx[b - (1 << j) + 1]));
+                const int a = lo / T_tile + 1, b = hi / T_tile - 1;
+#pragma unroll
+                for (int c = 0; c < NP; c++) {
+                    const int ch = pass * NP + c;
+                    const T *Pc = P + (size_t)c * L, *Sc = S + (size_t)c * L, *Mc = M + c * mstride;
+                    T u = tmax(Sc[lo], Pc[hi]);
+                    if (b >= a) {
+                        if (levels == 0) {
+                            for (int t = a; t <= b; t++) u = tmax(u, Mc[t]);
+                        } else {
+                            const int len = b - a + 1;
+                            const int j = 31 - __clz(len);
+                            const T *mx = Mc + (size_t)j * nt;
+                            u = tmax(u, tmax(mx[a], mx[b - (1 << j) + 1]));
+                        }
                     }
+                    out[2 * i + ch] = ch == 0 ? u : -u;
                 }
-                out[2 * i + pass] = pass == 0 ? u : -u;
             }
             __syncthreads();
         }
@@ -126,14 +140,16 @@ cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, i
         while (T_tile * 2 <= Weff) T_tile *= 2;
     }
     const int nt = (L + T_tile - 1) / T_tile;
-    const size_t smem = sizeof(T) * (2 * (size_t)L + (size_t)(levels + 1) * nt);
-    cudaError_t e = cudaFuncSetAttribute(envelope_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // both channels in one pass when they fit, else one channel per pass
+    const size_t per_channel = sizeof(T) * (2 * (size_t)L + (size_t)(levels + 1) * nt);
+    const bool one_pass = 2 * per_channel <= 200u * 1024u;
+    const size_t smem = one_pass ? 2 * per_channel : per_channel;
+    auto fn = one_pass ? envelope_kernel<T, 2> : envelope_kernel<T, 1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int sms = device_sm_count();
     int64_t grid = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
-    envelope_kernel<T><<<(unsigned)grid, kEnvThreads, smem, s>>>(train, env_in, N, L, Weff, env,
-                                                                  T_tile, levels);
+    fn<<<(unsigned)grid, kEnvThreads, smem, s>>>(train, env_in, N, L, Weff, env, T_tile, levels);
     return cudaGetLastError();
 }
 

@@ -179,9 +179,6 @@ struct DtwJob64 {
     bool rev;
     const double2 *env2;
     const double *lb;
-    // set by the launcher: the two series fit in shared memory next to the
-    // band (else the FP64 series are read from global memory)
-    bool stage_series;
 };
 cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
 
