@@ -24,7 +24,7 @@ def _series(seed, n, L, dtype=np.float32):
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("L,W", [(2, 0), (2, 1), (17, 3), (100, 13), (300, 33), (1024, 102),
-                                 (1024, 1023), (4096, 409), (129, 5000)])
+                                 (1024, 1023), (4096, 409), (129, 5000), (8192, 700)])
 def test_second_envelopes_bit_exact(lib, orc, dt, L, W):
     """(window max of Lo, window min of U), i.e. the oracle's envelope scan run
     on Lo and on U."""

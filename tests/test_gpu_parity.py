@@ -385,8 +385,10 @@ def test_search_long_full_window(lib, orc, L, N, Q):
     _check_search(lib, orc, train, labels, test, L - 1, 4)
 
 
-@pytest.mark.parametrize("L,W,N,Q", [(8192, 8191, 6, 2), (6000, 600, 10, 3), (8192, 5000, 5, 2)])
-def test_search_f64_long_series(lib, orc, L, W, N, Q):
+@pytest.mark.parametrize("L,W,N,Q,improved", [(8192, 8191, 6, 2, False), (6000, 600, 10, 3, False),
+                                               (8192, 5000, 5, 2, False), (6000, 600, 10, 3, True),
+                                               (8192, 8191, 6, 2, True)])
+def test_search_f64_long_series(lib, orc, L, W, N, Q, improved):
     """The FP64 form on series up to 8192: the FP64 kernel reads the series
     from global memory when the two series and the band do not fit in shared
     memory (L = 8192, W = 8191); results bit-identical to the oracle."""
@@ -395,7 +397,10 @@ def test_search_f64_long_series(lib, orc, L, W, N, Q):
     test = synth.znormed_walks(rng, Q, L)
     test[0] = train[N - 1]
     labels = rng.integers(0, 3, N).astype(np.int32)
-    _check_search(lib, orc, train, labels, test, W, 3)
+    _check_search(lib, orc, train, labels, test, W, 3, flags=lib.IMPROVED if improved else 0)
+    if improved:   # and the FP32 form on the same series
+        _check_search(lib, orc, train.astype(np.float32), labels, test.astype(np.float32), W, 3,
+                      flags=lib.IMPROVED | lib.REVERSE)
 
 
 @pytest.mark.parametrize("g", [1, 2, 4, 8])
