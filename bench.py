@@ -382,6 +382,73 @@ def run_reference(args, dsets, desc):
 
 # ------------------------------------------------------------------ window learning
 
+VSWEEP_V = (1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20)
+VSWEEP_W_ABS = (1, 3, 5, 7, 9)
+VSWEEP_W_REL = (0.1, 0.2, 0.3, 0.5, 1.0)
+
+
+def run_vsweep(args):
+    """The paper's study of the tightness parameter V (Sec. 4.1) on synthetic
+    data: for each window, the search time with LB_Enhanced^V as the bound,
+    V = 1..20, divided by the search time with LB_Keogh as the bound on the
+    same dataset, and the geometric mean of that ratio over the datasets.
+    Envelopes are built beforehand and passed in, so that, as in the paper,
+    their time is not counted; no cascade second stage; each time is the
+    median of `--steps` searches timed by the library's stage events."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw, synth
+    dev = torch.device("cuda", 0)
+    nndtw.load()
+    # twelve mid-sized datasets of the batched generator (its W and V ignored)
+    specs = [sp for sp in synth.batched_specs(64)]
+    picked = [i for i, sp in enumerate(specs)
+              if 20_000 <= sp["N"] * sp["Q"] <= 3_000_000 and sp["L"] <= 1024][:12]
+    dsets = [synth.make_batched_dataset(i, specs[i]) for i in picked]
+    reps = max(3, args.steps)
+
+    def timed(tr, lb, te, env, W, V, flags):
+        for _ in range(2):
+            nndtw.nn_dtw_search(tr, lb, te, W, V, env=env, flags=flags)
+        ts = []
+        for _ in range(reps):
+            nndtw.nn_dtw_search(tr, lb, te, W, V, env=env, flags=flags | nndtw.TIME_STAGES)
+            ts.append(nndtw.nn_dtw_stage_times()["total"])
+        return statistics.median(ts)
+
+    windows = [("W=%d" % w, lambda L, w=w: w) for w in VSWEEP_W_ABS] + \
+              [("W=%gL" % r, lambda L, r=r: int(np.floor(r * L + 0.5))) for r in VSWEEP_W_REL]
+    logs = {name: {V: [] for V in VSWEEP_V} for name, _ in windows}
+    base_flags = nndtw.NO_REVERSE
+    t0 = time.perf_counter()
+    for d in dsets:
+        tr = torch.from_numpy(d.train).to(dev)
+        te = torch.from_numpy(d.test).to(dev)
+        lb = torch.from_numpy(d.train_labels).to(dev)
+        for name, wf in windows:
+            W = min(wf(d.L), d.L - 1)
+            env = nndtw.nn_dtw_build_envelopes(tr, W)
+            tk = timed(tr, lb, te, env, W, 1, base_flags | nndtw.KEOGH_BOUND)
+            for V in VSWEEP_V:
+                logs[name][V].append(np.log(timed(tr, lb, te, env, W, V, base_flags) / tk))
+    wall = time.perf_counter() - t0
+    table = {name: {str(V): float(np.exp(np.mean(v))) for V, v in row.items()}
+             for name, row in logs.items()}
+    best = {name: int(min(row, key=lambda V: row[V])) for name, row in
+            ((n, {int(k): x for k, x in r.items()}) for n, r in table.items())}
+    line = {"metric": "search time with LB_Enhanced^V / with LB_Keogh (geometric mean over datasets)",
+            "value": table["W=0.1L"]["5"], "unit": "ratio at W=0.1L, V=5", "n_gpus": 1,
+            "steps": reps, "warmup": 2, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"V sweep: {len(dsets)} datasets of the batched generator "
+                                   f"(L {min(d.L for d in dsets)}..{max(d.L for d in dsets)}, "
+                                   f"train {min(d.N for d in dsets)}..{max(d.N for d in dsets)}), "
+                                   f"W in {[n for n, _ in windows]}, V in {list(VSWEEP_V)}",
+                       "timing": "median of the searches' stage events (envelopes supplied, "
+                                 "not counted), no cascade second stage"},
+            "ratio": table, "best_V": best, "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
 def run_window(args):
     """Window learning on the 500-series training set of the pairs workload
     (L=256): leave-one-out 1-NN accuracy for W = 0, 1 %, ..., 100 % of L (the
@@ -553,6 +620,10 @@ def main():
     if args.workload == "window":
         if rank == 0:
             run_window(args)
+        return
+    if args.workload == "vsweep":
+        if rank == 0:
+            run_vsweep(args)
         return
     if args.workload == "batched":
         dsets, desc = batched_workload()

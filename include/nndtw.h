@@ -77,6 +77,10 @@ extern "C" {
  * results, and it saves DTW work at the price of one more pass over each
  * surviving pair's training series. */
 #define NNDTW_IMPROVED (1u << 16)
+/* search: prune with LB_Keogh (Sec. 2.2.3) instead of LB_Enhanced^V, the
+ * baseline bound of the paper's study of V (Sec. 4.1); no cascade second
+ * stage.  Results never change. */
+#define NNDTW_KEOGH_BOUND (1u << 17)
 /* search / dtw_windowed: lanes per pair of the FP32 DTW kernel, a tuning
  * choice that never changes results: NNDTW_DTW_GROUP(log2 G) with
  * G = 1, 2, 4, ..., 32; 0 (the default) lets the library choose.  A G that

@@ -730,10 +730,13 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     // the query envelopes, for the reverse bound LB_Enhanced(B, A) (asked for
     // with NNDTW_REVERSE: whether reading every surviving pair's training
     // series once more pays off depends on the data, so the tuner decides)
-    const bool rev = (flags & NNDTW_REVERSE) && !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
+    // (LB_Keogh as the bound, NNDTW_KEOGH_BOUND, has no second stage)
+    const bool keogh = (flags & NNDTW_KEOGH_BOUND) != 0;
+    const bool rev = (flags & NNDTW_REVERSE) && !keogh &&
+                     !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
     // and the training series' second envelopes, for the bound with the
     // LB_Improved bridge (asked for with NNDTW_IMPROVED, also a tuning choice)
-    const bool imp = (flags & NNDTW_IMPROVED) && !(flags & NNDTW_NO_PRUNE);
+    const bool imp = (flags & NNDTW_IMPROVED) && !keogh && !(flags & NNDTW_NO_PRUNE);
     if (rev || imp) CK(launch_envelopes<float>(d_test, Q, L, Weff, ws.envq, s));
     if (imp) {
         CK(launch_second_envelopes<float>(env, N, L, Weff, ws.env2, s));
@@ -741,7 +744,7 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
     }
     CK(tm.mark(1));
     // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
-    CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo, m.abs32,
+    CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, keogh, true, m.lb_lo, m.abs32,
                         ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
                         (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
     CK(tm.mark(2));
@@ -874,12 +877,13 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
         CK(launch_envelopes<double>(d_train, N, L, Weff, ws.env, s));
         env = ws.env;
     }
-    const bool rev = !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
-    const bool imp = (flags & NNDTW_IMPROVED) && !(flags & NNDTW_NO_PRUNE);
+    const bool keogh = (flags & NNDTW_KEOGH_BOUND) != 0;
+    const bool rev = !keogh && !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
+    const bool imp = (flags & NNDTW_IMPROVED) && !keogh && !(flags & NNDTW_NO_PRUNE);
     if (rev || imp) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
     if (imp) CK(launch_second_envelopes<double>(env, N, L, Weff, ws.env2, s));
     CK(tm.mark(1));
-    CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, false, true, m.lb_lo64,
+    CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, keogh, true, m.lb_lo64,
                          m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
                          (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
     CK(tm.mark(2));

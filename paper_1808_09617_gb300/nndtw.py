@@ -32,6 +32,7 @@ NO_REVERSE = 1 << 7
 REVERSE = 1 << 14
 LEAVE_ONE_OUT = 1 << 15
 IMPROVED = 1 << 16
+KEOGH_BOUND = 1 << 17
 
 
 # Tuning values for full windows: the row layout with 32 lanes per pair (one

@@ -421,3 +421,20 @@ def test_search_wide_windows(lib, orc, N, Q, L, W):
     brute = orc.nn_brute(train, labels, test, W)
     _check_search(lib, orc, train, labels, test, W, 5, brute=brute)
     _check_search(lib, orc, train, labels, test, W, 5, flags=lib.EXACT_DIST, brute=brute)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_search_keogh_bound(lib, orc, fp64):
+    """LB_Keogh as the pruning bound (the baseline of the paper's V study):
+    the same neighbours, and never more pruning than LB_Enhanced^1, which is
+    at least LB_Keogh for every pair (same first candidates, same upper
+    bounds)."""
+    ds = synth.make_pairs(5)
+    dt = np.float64 if fp64 else np.float32
+    train, labels, test = ds.train[:300].astype(dt), ds.train_labels[:300], ds.test[:120].astype(dt)
+    brute = orc.nn_brute(train, labels, test, ds.W)
+    k = _check_search(lib, orc, train, labels, test, ds.W, 1,
+                      flags=lib.KEOGH_BOUND | lib.REVERSE | lib.IMPROVED, brute=brute)
+    e = _check_search(lib, orc, train, labels, test, ds.W, 1, flags=lib.NO_REVERSE, brute=brute)
+    assert k["lb_pruned_reverse"] == 0 and k["lb_pruned_improved"] == 0
+    assert 0 < k["lb_pruned"] <= e["lb_pruned"]
