@@ -186,7 +186,10 @@ def _stream(stream):
     return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _dev(t, dtype, name, ndim=None):
+def _dev(t, dtype, name, ndim=None, shape=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype, after
+    checking its rank and (with shape; None entries match any size) its
+    shape, so that no kernel reads or writes past a caller's buffer."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -196,6 +199,11 @@ def _dev(t, dtype, name, ndim=None):
         raise ValueError(f"{name} must be contiguous")
     if ndim is not None and t.dim() != ndim:
         raise ValueError(f"{name} must have {ndim} dimensions")
+    if shape is not None:
+        if t.dim() != len(shape) or any(w is not None and int(g) != int(w)
+                                        for g, w in zip(t.shape, shape)):
+            want = tuple("*" if w is None else int(w) for w in shape)
+            raise ValueError(f"{name} must have shape {want}, got {tuple(t.shape)}")
     return _vp(t.data_ptr())
 
 
@@ -216,7 +224,8 @@ def nn_dtw_build_envelopes(train, W: int, env=None, stream=None):
         env = torch.empty((N, L, 2), dtype=train.dtype, device=train.device)
     fn = lib.nn_dtw_build_envelopes_f64 if f64 else lib.nn_dtw_build_envelopes
     _check(fn(_dev(train, train.dtype, "train", 2), N, L, int(W),
-              _dev(env, train.dtype, "env"), _stream(stream)), "nn_dtw_build_envelopes")
+              _dev(env, train.dtype, "env", shape=(N, L, 2)), _stream(stream)),
+           "nn_dtw_build_envelopes")
     return env
 
 
@@ -232,9 +241,10 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
         out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
     flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0)
     fn = lib.lb_enhanced_f64 if f64 else lib.lb_enhanced
-    _check(fn(_dev(test, test.dtype, "test", 2), Q, _dev(train, test.dtype, "train", 2),
-              _dev(env, test.dtype, "env"), N, L, int(W), int(V), flags,
-              _dev(out, test.dtype, "out"), _stream(stream)), "lb_enhanced")
+    _check(fn(_dev(test, test.dtype, "test", 2), Q,
+              _dev(train, test.dtype, "train", shape=(N, L)),
+              _dev(env, test.dtype, "env", shape=(N, L, 2)), N, L, int(W), int(V), flags,
+              _dev(out, test.dtype, "out", shape=(Q, N)), _stream(stream)), "lb_enhanced")
     return out
 
 
@@ -248,8 +258,9 @@ def nn_dtw_build_second_envelopes(env, W: int, env2=None, stream=None):
     if env2 is None:
         env2 = torch.empty_like(env)
     fn = lib.nn_dtw_build_second_envelopes_f64 if f64 else lib.nn_dtw_build_second_envelopes
-    _check(fn(_dev(env, env.dtype, "env"), N, L, int(W), _dev(env2, env.dtype, "env2"),
-              _stream(stream)), "nn_dtw_build_second_envelopes")
+    _check(fn(_dev(env, env.dtype, "env", shape=(N, L, 2)), N, L, int(W),
+              _dev(env2, env.dtype, "env2", shape=(N, L, 2)), _stream(stream)),
+           "nn_dtw_build_second_envelopes")
     return env2
 
 
@@ -266,10 +277,13 @@ def lb_enhanced_improved(test, test_env, train, env, env2, W: int, V: int, safe:
     if out is None:
         out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
     fn = lib.lb_enhanced_improved_f64 if f64 else lib.lb_enhanced_improved
-    _check(fn(_dev(test, test.dtype, "test", 2), _dev(test_env, test.dtype, "test_env"), Q,
-              _dev(train, test.dtype, "train", 2), _dev(env, test.dtype, "env"),
-              _dev(env2, test.dtype, "env2"), N, L, int(W), int(V), LB_SAFE if safe else 0,
-              _dev(out, test.dtype, "out"), _stream(stream)), "lb_enhanced_improved")
+    _check(fn(_dev(test, test.dtype, "test", 2),
+              _dev(test_env, test.dtype, "test_env", shape=(Q, L, 2)), Q,
+              _dev(train, test.dtype, "train", shape=(N, L)),
+              _dev(env, test.dtype, "env", shape=(N, L, 2)),
+              _dev(env2, test.dtype, "env2", shape=(N, L, 2)), N, L, int(W), int(V),
+              LB_SAFE if safe else 0, _dev(out, test.dtype, "out", shape=(Q, N)),
+              _stream(stream)), "lb_enhanced_improved")
     return out
 
 
@@ -282,9 +296,9 @@ def dtw_windowed(test, train, pairs, W: int, out=None, stream=None, flags: int =
     P = pairs.shape[0]
     if out is None:
         out = torch.empty((P,), dtype=test.dtype, device=test.device)
-    args = (_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", 2),
-            _dev(pairs, torch.int32, "pairs", 2), P, L, int(W))
-    tail = (_dev(out, test.dtype, "out"), _stream(stream))
+    args = (_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", shape=(None, L)),
+            _dev(pairs, torch.int32, "pairs", shape=(P, 2)), P, L, int(W))
+    tail = (_dev(out, test.dtype, "out", shape=(P,)), _stream(stream))
     if f64:
         _check(lib.dtw_windowed_f64(*args, *tail), "dtw_windowed_f64")
     else:
@@ -324,11 +338,13 @@ def nn_dtw_search(train, labels, test, W: int, V: int, env=None, flags: int = 0,
     idx, lab, dist = out
     st = Stats() if stats else None
     fn = lib.nn_dtw_search_f64 if f64 else lib.nn_dtw_search
-    envp = _dev(env, train.dtype, "env") if env is not None else None
-    _check(fn(_dev(train, train.dtype, "train", 2), _dev(labels, torch.int32, "labels", 1), N,
-              _dev(test, train.dtype, "test", 2), Q, L, int(W), int(V), envp, int(flags),
-              _dev(idx, torch.int32, "nn_idx"), _dev(lab, torch.int32, "nn_label"),
-              _dev(dist, torch.float64, "nn_dist"), _dev(workspace, torch.uint8, "workspace"),
+    envp = _dev(env, train.dtype, "env", shape=(N, L, 2)) if env is not None else None
+    _check(fn(_dev(train, train.dtype, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
+              N, _dev(test, train.dtype, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
+              int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
+              _dev(lab, torch.int32, "nn_label", shape=(Q,)),
+              _dev(dist, torch.float64, "nn_dist", shape=(Q,)),
+              _dev(workspace, torch.uint8, "workspace"),
               workspace.numel(), ctypes.byref(st) if st is not None else None, _stream(stream)),
            "nn_dtw_search")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
@@ -350,12 +366,13 @@ def nn_dtw_search_noalloc(train, labels, test, W: int, V: int, env=None, flags: 
                torch.empty((Q,), dtype=torch.float64, device=train.device))
     idx, lab, dist = out
     st = Stats() if stats else None
-    envp = _dev(env, torch.float32, "env") if env is not None else None
+    envp = _dev(env, torch.float32, "env", shape=(N, L, 2)) if env is not None else None
     _check(lib.nn_dtw_search_noalloc(
-        _dev(train, torch.float32, "train", 2), _dev(labels, torch.int32, "labels", 1), N,
-        _dev(test, torch.float32, "test", 2), Q, L, int(W), int(V), envp, int(flags),
-        _dev(idx, torch.int32, "nn_idx"), _dev(lab, torch.int32, "nn_label"),
-        _dev(dist, torch.float64, "nn_dist"), ctypes.byref(st) if st is not None else None,
+        _dev(train, torch.float32, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
+        N, _dev(test, torch.float32, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
+        int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
+        _dev(lab, torch.int32, "nn_label", shape=(Q,)),
+        _dev(dist, torch.float64, "nn_dist", shape=(Q,)), ctypes.byref(st) if st is not None else None,
         _stream(stream)), "nn_dtw_search_noalloc")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
@@ -367,19 +384,25 @@ def nn_dtw_search_f64(train, labels, test, W: int, V: int, **kw) -> SearchResult
     return nn_dtw_search(train, labels, test, W, V, **kw)
 
 
-def _descs(sets, outs):
+def _descs(sets, outs, sizing=False):
+    """Descriptors of the datasets; with sizing (workspace-size queries, which
+    write nothing) the output tensors may be placeholders of any size."""
     import torch
     arr = (DatasetDesc * len(sets))()
     for i, (d, o) in enumerate(zip(sets, outs)):
         train, test = d["train"], d["test"]
         N, L = train.shape
+        Q = test.shape[0]
+        qs = None if sizing else (Q,)
         env = d.get("env")
         arr[i] = DatasetDesc(
-            _dev(train, torch.float32, "train", 2), _dev(d["labels"], torch.int32, "labels", 1), N,
-            _dev(test, torch.float32, "test", 2), test.shape[0], L, int(d["W"]), int(d["V"]),
-            _dev(env, torch.float32, "env") if env is not None else None,
-            _dev(o[0], torch.int32, "nn_idx"), _dev(o[1], torch.int32, "nn_label"),
-            _dev(o[2], torch.float64, "nn_dist"), int(d.get("flags", 0)))
+            _dev(train, torch.float32, "train", 2),
+            _dev(d["labels"], torch.int32, "labels", shape=(N,)), N,
+            _dev(test, torch.float32, "test", shape=(Q, L)), Q, L, int(d["W"]), int(d["V"]),
+            _dev(env, torch.float32, "env", shape=(N, L, 2)) if env is not None else None,
+            _dev(o[0], torch.int32, "nn_idx", shape=qs),
+            _dev(o[1], torch.int32, "nn_label", shape=qs),
+            _dev(o[2], torch.float64, "nn_dist", shape=qs), int(d.get("flags", 0)))
     return arr
 
 
@@ -412,9 +435,11 @@ def nn_dtw_learn_window(train, labels, windows, V: int, flags: int = 0, workspac
     if correct is None:
         correct = torch.empty(w.size, dtype=torch.int64, device=train.device)
     _check(lib.nn_dtw_learn_window(_dev(train, torch.float32, "train", 2),
-                                   _dev(labels, torch.int32, "labels"), N, L, w.ctypes.data,
-                                   w.size, int(V), int(flags), _dev(correct, torch.int64, "correct"),
-                                   workspace.data_ptr(), workspace.numel(), _stream(stream)),
+                                   _dev(labels, torch.int32, "labels", shape=(N,)), N, L,
+                                   w.ctypes.data, w.size, int(V), int(flags),
+                                   _dev(correct, torch.int64, "correct", shape=(w.size,)),
+                                   _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
+                                   _stream(stream)),
            "nn_dtw_learn_window")
     return correct
 
@@ -433,7 +458,7 @@ def nn_dtw_batch_workspace_size(sets) -> int:
     import torch
     dummy = [(torch.empty(0, dtype=torch.int32, device="cuda"),) * 2 +
              (torch.empty(0, dtype=torch.float64, device="cuda"),) for _ in sets]
-    arr = _descs(sets, dummy)
+    arr = _descs(sets, dummy, sizing=True)
     return int(load().nn_dtw_batch_workspace_size(arr, len(sets)))
 
 
@@ -508,9 +533,13 @@ def nn_dtw_host_buffer_size(N: int, Q: int, L: int, W: int, V: int) -> int:
     return int(load().nn_dtw_host_buffer_size(N, Q, L, W, V))
 
 
-def _host(a, dtype, name):
+def _host(a, dtype, name, shape=None):
+    """Host pointer of a C-contiguous numpy array of the given dtype and
+    (with shape) shape: the library copies exactly that many elements."""
     if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
         raise TypeError(f"{name} must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    if shape is not None and tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {a.shape}")
     return _vp(a.ctypes.data)
 
 
@@ -521,20 +550,22 @@ def nn_dtw_search_host(train, labels, test, W: int, V: int, flags: int = 0, buff
     lib = load()
     N, L = train.shape
     Q = test.shape[0]
+    if out is None:
+        out = (np.empty(Q, np.int32), np.empty(Q, np.int32), np.empty(Q, np.float64))
+    idx, lab, dist = out
+    # host arguments first: the library copies exactly these many elements
+    hp = (_host(train, np.float32, "train", (N, L)), _host(labels, np.int32, "labels", (N,)),
+          _host(test, np.float32, "test", (Q, L)), _host(idx, np.int32, "nn_idx", (Q,)),
+          _host(lab, np.int32, "nn_label", (Q,)), _host(dist, np.float64, "nn_dist", (Q,)))
     need = lib.nn_dtw_host_buffer_size(N, Q, L, int(W), int(V))
     if need == 0:
         raise NnDtwError(EINVAL, "nn_dtw_host_buffer_size")
     if buffer is None:
         buffer = torch.empty((need,), dtype=torch.uint8, device="cuda")
-    if out is None:
-        out = (np.empty(Q, np.int32), np.empty(Q, np.int32), np.empty(Q, np.float64))
-    idx, lab, dist = out
     st = Stats() if stats else None
     _check(lib.nn_dtw_search_host(
-        _host(train, np.float32, "train"), _host(labels, np.int32, "labels"), N,
-        _host(test, np.float32, "test"), Q, L, int(W), int(V), int(flags),
-        _host(idx, np.int32, "nn_idx"), _host(lab, np.int32, "nn_label"),
-        _host(dist, np.float64, "nn_dist"), _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
+        hp[0], hp[1], N, hp[2], Q, L, int(W), int(V), int(flags), hp[3], hp[4], hp[5],
+        _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
         ctypes.byref(st) if st is not None else None, _stream(stream)), "nn_dtw_search_host")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 

@@ -90,3 +90,24 @@ def test_binding_fails_loudly_without_library(tmp_path):
             nndtw.load(str(tmp_path / "missing.so"))
         finally:
             nndtw._lib = saved
+
+
+def test_host_entry_checks_shapes_before_any_copy():
+    """The host-buffer entry point copies exactly N*L, Q*L, N and Q elements:
+    the binding rejects arrays of any other shape before calling the library
+    (no GPU needed to see it)."""
+    import numpy as np
+    import pytest
+
+    from paper_1808_09617_gb300 import nndtw
+    train = np.zeros((10, 32), np.float32)
+    test = np.zeros((4, 32), np.float32)
+    with pytest.raises(ValueError, match="labels"):
+        nndtw.nn_dtw_search_host(train, np.zeros(9, np.int32), test, 3, 2)
+    with pytest.raises(ValueError, match="test"):
+        nndtw.nn_dtw_search_host(train, np.zeros(10, np.int32), np.zeros((4, 31), np.float32), 3, 2)
+    out = (np.empty(3, np.int32), np.empty(4, np.int32), np.empty(4, np.float64))
+    with pytest.raises(ValueError, match="nn_idx"):
+        nndtw.nn_dtw_search_host(train, np.zeros(10, np.int32), test, 3, 2, out=out)
+    with pytest.raises(TypeError, match="train"):
+        nndtw.nn_dtw_search_host(train.astype(np.float64), np.zeros(10, np.int32), test, 3, 2)

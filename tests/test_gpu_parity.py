@@ -438,3 +438,26 @@ def test_search_keogh_bound(lib, orc, fp64):
     e = _check_search(lib, orc, train, labels, test, ds.W, 1, flags=lib.NO_REVERSE, brute=brute)
     assert k["lb_pruned_reverse"] == 0 and k["lb_pruned_improved"] == 0
     assert 0 < k["lb_pruned"] <= e["lb_pruned"]
+
+
+def test_binding_rejects_mismatched_shapes(lib):
+    """The binding checks every device buffer's shape against the sizes it
+    passes, so that no kernel reads or writes past a caller's tensor."""
+    L, W = 32, 3
+    train = _t(_series(1, 10, L))
+    test = _t(_series(2, 4, L))
+    labels = _t(np.zeros(10, np.int32))
+    env = lib.nn_dtw_build_envelopes(train, W)
+    with pytest.raises(ValueError, match="env"):
+        lib.lb_enhanced(test, train, env[:9], W, 2)
+    with pytest.raises(ValueError, match="train"):
+        lib.lb_enhanced(test, _t(_series(3, 10, L + 1)), env, W, 2)
+    with pytest.raises(ValueError, match="labels"):
+        lib.nn_dtw_search(train, _t(np.zeros(9, np.int32)), test, W, 2)
+    with pytest.raises(ValueError, match="env"):
+        lib.nn_dtw_search(train, labels, test, W, 2, env=env[:, :16].contiguous())
+    with pytest.raises(ValueError, match="pairs"):
+        lib.dtw_windowed(test, train, _t(np.zeros((5, 3), np.int32)), W)
+    with pytest.raises(ValueError, match="test_env"):
+        env2 = lib.nn_dtw_build_second_envelopes(env, W)
+        lib.lb_enhanced_improved(test, env, train, env, env2, W, 2)
