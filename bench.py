@@ -602,7 +602,7 @@ def main():
                          "implies --no-tune")
     ap.add_argument("--serve-rates", type=float, nargs="*",
                     default=[1000, 5000, 10000, 20000, 50000])
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=512)
     args = ap.parse_args()

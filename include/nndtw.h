@@ -273,8 +273,9 @@ NNDTW_API int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_la
  *    fit) are rejected with NNDTW_ENOSPACE before any work is enqueued.
  *  - The array is part of the library's device image: every GPU that loads
  *    the library holds those 16 MiB until the process exits.
- *  - The first call on a device, with that device current, looks up the
- *    array's device address (cudaGetSymbolAddress); make that first call
+ *  - Every call looks up the array's device address in the current
+ *    device's context (cudaGetSymbolAddress); the first call in a context
+ *    also loads the library's device code there, so make that first call
  *    before any stream capture.
  *  - All calls share the one array.  Each call clears what must start at
  *    zero, so an earlier call's leftovers do no harm, but calls whose GPU
@@ -343,6 +344,10 @@ NNDTW_API size_t nn_dtw_batch_workspace_size(const nndtw_dataset *h_sets, int n)
  * as one CUDA graph.  h_sets: host array of n descriptors (read during the
  * call only); d_workspace: nn_dtw_batch_workspace_size() bytes, 256-byte
  * aligned.  flags apply to every dataset (NNDTW_TIME_STAGES is rejected).
+ * Concurrent calls (from several host threads, on any streams) are
+ * supported: calls on one device take a lock around the fork, the issue and
+ * the join, so their GPU work may overlap but their stream and event
+ * bookkeeping never interleaves.  Each call needs its own workspace.
  * Errors: NNDTW_EINVAL for invalid descriptors or sizes, NNDTW_ENOSPACE,
  * NNDTW_ECUDA.  On an error every forked stream is still joined.
  */

@@ -3,7 +3,8 @@
 // FP32 search (nn_dtw_search), all on the caller's stream:
 //   S1  envelopes of the training set (unless supplied)
 //   S2  LB_Enhanced^V for all Q x N pairs, scaled down by the rounding margin,
-//       and per query the pair with the smallest bound (the first candidate)
+//       and per query its Euclidean-nearest training series (the first
+//       candidate, the paper's starting point of the search, Sec. 4)
 //   S4  DTW of that candidate per query, which sets each query's upper bound
 //   S3  compaction: pairs whose bound does not exceed the upper bound
 //   S4  DTW of the survivors with early abandoning against the live bound;

@@ -20,6 +20,11 @@ constexpr int kBatchStreams = 16;
 
 struct DeviceStreams {
     bool ready = false;
+    // held for a whole call: the fork, the searches issued on the internal
+    // streams and the join use this device's one set of streams and events,
+    // so two calls must not interleave (one thread's fork event re-recorded
+    // by another before the first one's streams wait on it)
+    std::mutex call_mu;
     cudaStream_t s[kBatchStreams] = {};
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[kBatchStreams] = {};
@@ -94,6 +99,7 @@ int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
     cudaError_t e = device_streams(&ds);
     if (e != cudaSuccess) { set_last_cuda_error(e); return NNDTW_ECUDA; }
     cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> call_lock(ds->call_mu);
 
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);

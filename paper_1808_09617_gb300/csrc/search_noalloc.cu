@@ -1,8 +1,6 @@
 // nn_dtw_search_noalloc: the FP32 search with its scratch memory in a fixed
 // device array compiled into the library, for callers that cannot allocate
 // device memory themselves (the paper has no counterpart).
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace {
@@ -10,11 +8,8 @@ namespace {
 // The search's scratch.  It is part of the library's device image, so every
 // GPU that loads the library holds these NNDTW_NOALLOC_SCRATCH_BYTES until
 // the process exits.  In host code `g_noalloc_scratch` only names the symbol;
-// its device address comes from cudaGetSymbolAddress, per device.
+// its device address comes from cudaGetSymbolAddress in the current context.
 __device__ __align__(256) unsigned char g_noalloc_scratch[NNDTW_NOALLOC_SCRATCH_BYTES];
-
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
 
 }  // namespace
 
@@ -33,19 +28,16 @@ extern "C" int nn_dtw_search_noalloc(const float *d_train, const int32_t *d_trai
         return NNDTW_ECUDA;
     }
     if (dev < 0 || dev >= 64) return NNDTW_EUNSUPPORTED;
+    // The array's address in the current device's context, looked up on every
+    // call (a host-side table lookup once the library's device code is loaded
+    // in this context), so that no address outlives a device reset or is used
+    // in another context.  The first call in a context loads the module; that
+    // is why the first call must come before any stream capture.
     void *ptr = nullptr;
-    {
-        // first call on this device (which is current): look up the address
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                nndtw::set_last_cuda_error(e);
-                return NNDTW_ECUDA;
-            }
-            g_noalloc_addr[dev] = ptr;
-        }
-        ptr = g_noalloc_addr[dev];
+    e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        nndtw::set_last_cuda_error(e);
+        return NNDTW_ECUDA;
     }
     // The search clears every part of its scratch that must start at zero
     // (counters, best-so-far keys, per-query tallies) at the start of each

@@ -186,6 +186,32 @@ def _stream(stream):
     return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def one_device(devices, stream_device=None):
+    """The one CUDA device shared by every tensor argument of a call (and by
+    its stream, when it names one).  Tensors on two devices, or a stream of
+    another device, raise ValueError before anything reaches the library:
+    its kernels would run on the current device with another GPU's
+    pointers."""
+    devs = {(d.type, d.index) for d in devices if d is not None}
+    if len(devs) != 1:
+        raise ValueError(f"all tensor arguments must be on one CUDA device, got {sorted(devs)}")
+    typ, idx = devs.pop()
+    if typ != "cuda":
+        raise TypeError("tensor arguments must be CUDA tensors")
+    if stream_device is not None and (stream_device.type, stream_device.index) != (typ, idx):
+        raise ValueError(f"stream is on {stream_device}, tensors on cuda:{idx}")
+    return idx
+
+
+def _on(tensors, stream=None):
+    """Context in which a library call runs: the tensors' device made current
+    (the library launches on the current device), after one_device's check."""
+    import torch
+    sdev = getattr(stream, "device", None) if stream is not None else None
+    idx = one_device([t.device for t in tensors if isinstance(t, torch.Tensor)], sdev)
+    return torch.cuda.device(idx)
+
+
 def _dev(t, dtype, name, ndim=None, shape=None):
     """Device pointer of a contiguous CUDA tensor of the given dtype, after
     checking its rank and (with shape; None entries match any size) its
@@ -223,9 +249,10 @@ def nn_dtw_build_envelopes(train, W: int, env=None, stream=None):
     if env is None:
         env = torch.empty((N, L, 2), dtype=train.dtype, device=train.device)
     fn = lib.nn_dtw_build_envelopes_f64 if f64 else lib.nn_dtw_build_envelopes
-    _check(fn(_dev(train, train.dtype, "train", 2), N, L, int(W),
-              _dev(env, train.dtype, "env", shape=(N, L, 2)), _stream(stream)),
-           "nn_dtw_build_envelopes")
+    with _on([train, env], stream):
+        _check(fn(_dev(train, train.dtype, "train", 2), N, L, int(W),
+                _dev(env, train.dtype, "env", shape=(N, L, 2)), _stream(stream)),
+             "nn_dtw_build_envelopes")
     return env
 
 
@@ -241,10 +268,11 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
         out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
     flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0)
     fn = lib.lb_enhanced_f64 if f64 else lib.lb_enhanced
-    _check(fn(_dev(test, test.dtype, "test", 2), Q,
-              _dev(train, test.dtype, "train", shape=(N, L)),
-              _dev(env, test.dtype, "env", shape=(N, L, 2)), N, L, int(W), int(V), flags,
-              _dev(out, test.dtype, "out", shape=(Q, N)), _stream(stream)), "lb_enhanced")
+    with _on([test, train, env, out], stream):
+        _check(fn(_dev(test, test.dtype, "test", 2), Q,
+                _dev(train, test.dtype, "train", shape=(N, L)),
+                _dev(env, test.dtype, "env", shape=(N, L, 2)), N, L, int(W), int(V), flags,
+                _dev(out, test.dtype, "out", shape=(Q, N)), _stream(stream)), "lb_enhanced")
     return out
 
 
@@ -258,9 +286,10 @@ def nn_dtw_build_second_envelopes(env, W: int, env2=None, stream=None):
     if env2 is None:
         env2 = torch.empty_like(env)
     fn = lib.nn_dtw_build_second_envelopes_f64 if f64 else lib.nn_dtw_build_second_envelopes
-    _check(fn(_dev(env, env.dtype, "env", shape=(N, L, 2)), N, L, int(W),
-              _dev(env2, env.dtype, "env2", shape=(N, L, 2)), _stream(stream)),
-           "nn_dtw_build_second_envelopes")
+    with _on([env, env2], stream):
+        _check(fn(_dev(env, env.dtype, "env", shape=(N, L, 2)), N, L, int(W),
+                _dev(env2, env.dtype, "env2", shape=(N, L, 2)), _stream(stream)),
+             "nn_dtw_build_second_envelopes")
     return env2
 
 
@@ -277,13 +306,14 @@ def lb_enhanced_improved(test, test_env, train, env, env2, W: int, V: int, safe:
     if out is None:
         out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
     fn = lib.lb_enhanced_improved_f64 if f64 else lib.lb_enhanced_improved
-    _check(fn(_dev(test, test.dtype, "test", 2),
-              _dev(test_env, test.dtype, "test_env", shape=(Q, L, 2)), Q,
-              _dev(train, test.dtype, "train", shape=(N, L)),
-              _dev(env, test.dtype, "env", shape=(N, L, 2)),
-              _dev(env2, test.dtype, "env2", shape=(N, L, 2)), N, L, int(W), int(V),
-              LB_SAFE if safe else 0, _dev(out, test.dtype, "out", shape=(Q, N)),
-              _stream(stream)), "lb_enhanced_improved")
+    with _on([test, test_env, train, env, env2, out], stream):
+        _check(fn(_dev(test, test.dtype, "test", 2),
+                _dev(test_env, test.dtype, "test_env", shape=(Q, L, 2)), Q,
+                _dev(train, test.dtype, "train", shape=(N, L)),
+                _dev(env, test.dtype, "env", shape=(N, L, 2)),
+                _dev(env2, test.dtype, "env2", shape=(N, L, 2)), N, L, int(W), int(V),
+                LB_SAFE if safe else 0, _dev(out, test.dtype, "out", shape=(Q, N)),
+                _stream(stream)), "lb_enhanced_improved")
     return out
 
 
@@ -298,11 +328,12 @@ def dtw_windowed(test, train, pairs, W: int, out=None, stream=None, flags: int =
         out = torch.empty((P,), dtype=test.dtype, device=test.device)
     args = (_dev(test, test.dtype, "test", 2), _dev(train, test.dtype, "train", shape=(None, L)),
             _dev(pairs, torch.int32, "pairs", shape=(P, 2)), P, L, int(W))
-    tail = (_dev(out, test.dtype, "out", shape=(P,)), _stream(stream))
-    if f64:
-        _check(lib.dtw_windowed_f64(*args, *tail), "dtw_windowed_f64")
-    else:
-        _check(lib.dtw_windowed_ex(*args, int(flags), *tail), "dtw_windowed")
+    with _on([test, train, pairs, out], stream):
+        tail = (_dev(out, test.dtype, "out", shape=(P,)), _stream(stream))
+        if f64:
+            _check(lib.dtw_windowed_f64(*args, *tail), "dtw_windowed_f64")
+        else:
+            _check(lib.dtw_windowed_ex(*args, int(flags), *tail), "dtw_windowed")
     return out
 
 
@@ -339,14 +370,15 @@ def nn_dtw_search(train, labels, test, W: int, V: int, env=None, flags: int = 0,
     st = Stats() if stats else None
     fn = lib.nn_dtw_search_f64 if f64 else lib.nn_dtw_search
     envp = _dev(env, train.dtype, "env", shape=(N, L, 2)) if env is not None else None
-    _check(fn(_dev(train, train.dtype, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
-              N, _dev(test, train.dtype, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
-              int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
-              _dev(lab, torch.int32, "nn_label", shape=(Q,)),
-              _dev(dist, torch.float64, "nn_dist", shape=(Q,)),
-              _dev(workspace, torch.uint8, "workspace"),
-              workspace.numel(), ctypes.byref(st) if st is not None else None, _stream(stream)),
-           "nn_dtw_search")
+    with _on([train, labels, test, env, idx, lab, dist, workspace], stream):
+        _check(fn(_dev(train, train.dtype, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
+                N, _dev(test, train.dtype, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
+                int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
+                _dev(lab, torch.int32, "nn_label", shape=(Q,)),
+                _dev(dist, torch.float64, "nn_dist", shape=(Q,)),
+                _dev(workspace, torch.uint8, "workspace"),
+                workspace.numel(), ctypes.byref(st) if st is not None else None, _stream(stream)),
+             "nn_dtw_search")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
 
@@ -367,13 +399,14 @@ def nn_dtw_search_noalloc(train, labels, test, W: int, V: int, env=None, flags: 
     idx, lab, dist = out
     st = Stats() if stats else None
     envp = _dev(env, torch.float32, "env", shape=(N, L, 2)) if env is not None else None
-    _check(lib.nn_dtw_search_noalloc(
-        _dev(train, torch.float32, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
-        N, _dev(test, torch.float32, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
-        int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
-        _dev(lab, torch.int32, "nn_label", shape=(Q,)),
-        _dev(dist, torch.float64, "nn_dist", shape=(Q,)), ctypes.byref(st) if st is not None else None,
-        _stream(stream)), "nn_dtw_search_noalloc")
+    with _on([train, labels, test, env, idx, lab, dist], stream):
+        _check(lib.nn_dtw_search_noalloc(
+          _dev(train, torch.float32, "train", 2), _dev(labels, torch.int32, "labels", shape=(N,)),
+          N, _dev(test, torch.float32, "test", shape=(Q, L)), Q, L, int(W), int(V), envp,
+          int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
+          _dev(lab, torch.int32, "nn_label", shape=(Q,)),
+          _dev(dist, torch.float64, "nn_dist", shape=(Q,)), ctypes.byref(st) if st is not None else None,
+          _stream(stream)), "nn_dtw_search_noalloc")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
 
@@ -406,6 +439,14 @@ def _descs(sets, outs, sizing=False):
     return arr
 
 
+def _set_tensors(sets, outs):
+    """Every tensor of a batch's descriptors, for the one-device check."""
+    ts = []
+    for d, o in zip(sets, outs):
+        ts += [d["train"], d["labels"], d["test"], d.get("env"), *o]
+    return ts
+
+
 def _windows_array(windows):
     w = np.ascontiguousarray(np.asarray(windows, dtype=np.int32))
     if w.ndim != 1 or w.size == 0:
@@ -434,13 +475,14 @@ def nn_dtw_learn_window(train, labels, windows, V: int, flags: int = 0, workspac
         workspace = torch.empty(n, dtype=torch.uint8, device=train.device)
     if correct is None:
         correct = torch.empty(w.size, dtype=torch.int64, device=train.device)
-    _check(lib.nn_dtw_learn_window(_dev(train, torch.float32, "train", 2),
-                                   _dev(labels, torch.int32, "labels", shape=(N,)), N, L,
-                                   w.ctypes.data, w.size, int(V), int(flags),
-                                   _dev(correct, torch.int64, "correct", shape=(w.size,)),
-                                   _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
-                                   _stream(stream)),
-           "nn_dtw_learn_window")
+    with _on([train, labels, correct, workspace], stream):
+        _check(lib.nn_dtw_learn_window(_dev(train, torch.float32, "train", 2),
+                                     _dev(labels, torch.int32, "labels", shape=(N,)), N, L,
+                                     w.ctypes.data, w.size, int(V), int(flags),
+                                     _dev(correct, torch.int64, "correct", shape=(w.size,)),
+                                     _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
+                                     _stream(stream)),
+             "nn_dtw_learn_window")
     return correct
 
 
@@ -456,8 +498,9 @@ def learn_window(train, labels, windows, V: int, flags: int = 0):
 
 def nn_dtw_batch_workspace_size(sets) -> int:
     import torch
-    dummy = [(torch.empty(0, dtype=torch.int32, device="cuda"),) * 2 +
-             (torch.empty(0, dtype=torch.float64, device="cuda"),) for _ in sets]
+    dev = sets[0]["train"].device if sets else "cuda"
+    dummy = [(torch.empty(0, dtype=torch.int32, device=dev),) * 2 +
+             (torch.empty(0, dtype=torch.float64, device=dev),) for _ in sets]
     arr = _descs(sets, dummy, sizing=True)
     return int(load().nn_dtw_batch_workspace_size(arr, len(sets)))
 
@@ -478,10 +521,11 @@ def nn_dtw_search_batched(sets, workspace=None, outs=None, flags: int = 0, strea
     if need == 0:
         raise NnDtwError(EINVAL, "nn_dtw_batch_workspace_size")
     if workspace is None:
-        workspace = torch.empty((need,), dtype=torch.uint8, device="cuda")
-    _check(lib.nn_dtw_search_batched(arr, len(sets), _dev(workspace, torch.uint8, "workspace"),
-                                     workspace.numel(), int(flags), _stream(stream)),
-           "nn_dtw_search_batched")
+        workspace = torch.empty((need,), dtype=torch.uint8, device=sets[0]["train"].device)
+    with _on([workspace] + _set_tensors(sets, outs), stream):
+        _check(lib.nn_dtw_search_batched(arr, len(sets), _dev(workspace, torch.uint8, "workspace"),
+                                       workspace.numel(), int(flags), _stream(stream)),
+             "nn_dtw_search_batched")
     return [SearchResult(*o) for o in outs]
 
 
@@ -498,24 +542,26 @@ class BatchedSearch:
         import torch
         self.sets = sets
         self.flags = flags
-        self.outs = [(torch.empty(d["test"].shape[0], dtype=torch.int32, device="cuda"),
-                      torch.empty(d["test"].shape[0], dtype=torch.int32, device="cuda"),
-                      torch.empty(d["test"].shape[0], dtype=torch.float64, device="cuda"))
+        dev = sets[0]["train"].device
+        self.outs = [(torch.empty(d["test"].shape[0], dtype=torch.int32, device=dev),
+                      torch.empty(d["test"].shape[0], dtype=torch.int32, device=dev),
+                      torch.empty(d["test"].shape[0], dtype=torch.float64, device=dev))
                      for d in sets]
         self.workspace = torch.empty((nn_dtw_batch_workspace_size(sets),), dtype=torch.uint8,
-                                     device="cuda")
-        self._call()
-        torch.cuda.synchronize()
+                                     device=dev)
         self.graph = None
-        if graph:
-            self.graph = torch.cuda.CUDAGraph()
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s):
-                with torch.cuda.graph(self.graph, stream=s):
-                    self._call()
-            torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.device(dev):
+            self._call()
             torch.cuda.synchronize()
+            if graph:
+                self.graph = torch.cuda.CUDAGraph()
+                s = torch.cuda.Stream()
+                s.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(s):
+                    with torch.cuda.graph(self.graph, stream=s):
+                        self._call()
+                torch.cuda.current_stream().wait_stream(s)
+                torch.cuda.synchronize()
 
     def _call(self):
         return nn_dtw_search_batched(self.sets, workspace=self.workspace, outs=self.outs,
@@ -563,10 +609,11 @@ def nn_dtw_search_host(train, labels, test, W: int, V: int, flags: int = 0, buff
     if buffer is None:
         buffer = torch.empty((need,), dtype=torch.uint8, device="cuda")
     st = Stats() if stats else None
-    _check(lib.nn_dtw_search_host(
-        hp[0], hp[1], N, hp[2], Q, L, int(W), int(V), int(flags), hp[3], hp[4], hp[5],
-        _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
-        ctypes.byref(st) if st is not None else None, _stream(stream)), "nn_dtw_search_host")
+    with _on([buffer], stream):
+        _check(lib.nn_dtw_search_host(
+          hp[0], hp[1], N, hp[2], Q, L, int(W), int(V), int(flags), hp[3], hp[4], hp[5],
+          _dev(buffer, torch.uint8, "buffer"), buffer.numel(),
+          ctypes.byref(st) if st is not None else None, _stream(stream)), "nn_dtw_search_host")
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
 

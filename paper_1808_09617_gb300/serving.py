@@ -79,6 +79,13 @@ class Server:
         self.n_slots = n_slots
         self.max_batch = max_batch
         self.budget = memory_budget
+        # a set whose one-query batch does not fit the budget could never be
+        # served: refuse it here rather than let its queries wait forever
+        for sid, s in self.sets.items():
+            if self._batch_bytes(s, 1) > self.budget:
+                raise ValueError(f"training set {sid}: one query needs "
+                                 f"{self._batch_bytes(s, 1)} bytes, more than the memory "
+                                 f"budget of {self.budget}")
         self.in_use = 0
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(n_slots)]
         self.free_slots = list(range(n_slots))
@@ -219,6 +226,9 @@ class Server:
         torch.cuda.set_device(self.dev)
         while self.running or self.inflight or any(self.pending.values()):
             progressed = False
+            # cleared before the queues are scanned: a submit() after this
+            # point sets it again and ends the wait below at once
+            self.wake.clear()
             with self.lock:
                 # retire finished batches
                 for b in list(self.inflight):
@@ -238,4 +248,3 @@ class Server:
                     time.sleep(5e-5)
                 else:
                     self.wake.wait(0.01)
-                    self.wake.clear()

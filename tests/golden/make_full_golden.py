@@ -1,0 +1,123 @@
+"""Write the stored 1-NN results of the full-size workloads, for the parity
+tests that compare every query of the GPU search with the oracle.
+
+Calls only ``oracle/`` (the paper's pruned search, Sec. 4, in FP64; equal to
+the exhaustive 1-NN, which the oracle tests pin) and the seeded input
+generator for its inputs.  Run from the repository root:
+
+    python tests/golden/make_full_golden.py precision   # 3 windows x 2,000 queries
+    python tests/golden/make_full_golden.py batched     # 64 datasets, 35,843 queries
+    python tests/golden/make_full_golden.py serving     # 16 resident sets, 24 queries each
+
+Each file is gzip-compressed text, one query per line:
+``[dataset] query nn_index nn_label nn_dist(hex float)``.
+"""
+import gzip
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_1808_09617_gb300 import synth  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PRECISION_RATIOS = (0.1, 0.5, 1.0)
+SERVING_QUERIES_PER_SET = 24
+
+
+def precision_path(ratio):
+    return os.path.join(HERE, f"precision_r{int(round(ratio * 100)):03d}_nn.txt.gz")
+
+
+BATCHED_PATH = os.path.join(HERE, "batched_nn.txt.gz")
+SERVING_PATH = os.path.join(HERE, "serving_nn.txt.gz")
+
+
+def _write(path, header, rows):
+    tmp = path + ".tmp"
+    with gzip.open(tmp, "wt") as f:
+        for h in header:
+            f.write(f"# {h}\n")
+        for r in rows:
+            f.write(" ".join(r) + "\n")
+    os.replace(tmp, path)
+
+
+def _rows(prefix, idx, lab, dist, queries=None):
+    qs = range(len(idx)) if queries is None else queries
+    return [[*prefix, str(q), str(int(i)), str(int(l)), float(d).hex()]
+            for q, i, l, d in zip(qs, idx, lab, dist)]
+
+
+def make_precision(threads=None):
+    orc = oracle.get()
+    for r in PRECISION_RATIOS:
+        ds = synth.make_precision(r)
+        t0 = time.time()
+        idx, lab, dist, _ = orc.nn_pruned(ds.train, ds.train_labels, ds.test, ds.W, ds.V,
+                                          threads=threads)
+        _write(precision_path(r),
+               [f"1-NN of every query of the precision workload ({ds.N} x {ds.Q}, L={ds.L}, "
+                f"W={ds.W}, V={ds.V}), FP64 oracle (pruned search, ties to the lowest index)",
+                "written by tests/golden/make_full_golden.py",
+                "query nn_index nn_label nn_dist(hex float)"],
+               _rows([], idx, lab, dist))
+        print(f"precision W={ds.W}: {ds.Q} queries in {time.time() - t0:.0f} s", flush=True)
+
+
+def make_batched(threads=None):
+    orc = oracle.get()
+    rows = []
+    t0 = time.time()
+    for d, spec in enumerate(synth.batched_specs(64)):
+        ds = synth.make_batched_dataset(d, spec)
+        idx, lab, dist, _ = orc.nn_pruned(ds.train, ds.train_labels, ds.test, ds.W, ds.V,
+                                          threads=threads)
+        rows += _rows([str(d)], idx, lab, dist)
+    _write(BATCHED_PATH,
+           ["1-NN of every query of the 64 datasets of the batched workload, FP64 oracle "
+            "(pruned search, ties to the lowest index)",
+            "written by tests/golden/make_full_golden.py",
+            "dataset query nn_index nn_label nn_dist(hex float)"], rows)
+    print(f"batched: {len(rows)} queries in {time.time() - t0:.0f} s", flush=True)
+
+
+def make_serving(threads=None):
+    orc = oracle.get()
+    rows = []
+    t0 = time.time()
+    k = SERVING_QUERIES_PER_SET
+    for d, spec in enumerate(synth.serving_specs(16)):
+        ds = synth.make_serving_set(d, spec)
+        qs, _ = synth.serving_queries(d, spec, k, offset=0)
+        idx, lab, dist, _ = orc.nn_pruned(ds.train, ds.train_labels, qs, ds.W, ds.V,
+                                          threads=threads)
+        rows += _rows([str(d)], idx, lab, dist)
+    _write(SERVING_PATH,
+           [f"1-NN of serving queries 0..{k - 1} of each of the 16 resident sets of the serving "
+            "workload, FP64 oracle (pruned search, ties to the lowest index)",
+            "written by tests/golden/make_full_golden.py",
+            "set query nn_index nn_label nn_dist(hex float)"], rows)
+    print(f"serving: {len(rows)} queries in {time.time() - t0:.0f} s", flush=True)
+
+
+def read(path):
+    """Rows of a stored file as lists of ints, the distance as a float."""
+    out = []
+    with gzip.open(path, "rt") as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            parts = line.split()
+            out.append([int(x) for x in parts[:-1]] + [float.fromhex(parts[-1])])
+    return out
+
+
+if __name__ == "__main__":
+    what = sys.argv[1:] or ["precision", "batched", "serving"]
+    th = int(os.environ.get("ORACLE_THREADS", "0")) or None
+    for w in what:
+        {"precision": make_precision, "batched": make_batched, "serving": make_serving}[w](th)

@@ -111,3 +111,20 @@ def test_host_entry_checks_shapes_before_any_copy():
         nndtw.nn_dtw_search_host(train, np.zeros(10, np.int32), test, 3, 2, out=out)
     with pytest.raises(TypeError, match="train"):
         nndtw.nn_dtw_search_host(train.astype(np.float64), np.zeros(10, np.int32), test, 3, 2)
+
+
+def test_binding_requires_one_device():
+    """Tensors on two GPUs, or a stream of another GPU, are refused before any
+    pointer reaches the library (its kernels run on the current device)."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw
+    c0, c1 = torch.device("cuda", 0), torch.device("cuda", 1)
+    assert nndtw.one_device([c1, c1, None]) == 1
+    with pytest.raises(ValueError):
+        nndtw.one_device([c0, c1])
+    with pytest.raises(ValueError):
+        nndtw.one_device([c0, c0], stream_device=c1)
+    with pytest.raises(TypeError):
+        nndtw.one_device([torch.device("cpu")])
+    with pytest.raises(ValueError):
+        nndtw.one_device([])

@@ -48,18 +48,57 @@ def test_batched_graph_replay(lib, batch):
             np.testing.assert_array_equal(a, c)
 
 
-def test_batched_matches_oracle_on_samples(lib, orc, batch):
+@pytest.fixture(scope="module")
+def golden_batched():
+    """The oracle's 1-NN of every query of the 64 datasets, stored by
+    tests/golden/make_full_golden.py: {dataset: (idx, label, dist)}."""
+    from golden import make_full_golden as fg
+    rows = fg.read(fg.BATCHED_PATH)
+    out = {}
+    for d in sorted({r[0] for r in rows}):
+        rs = [r for r in rows if r[0] == d]
+        out[d] = (np.array([r[2] for r in rs], np.int32), np.array([r[3] for r in rs], np.int32),
+                  np.array([r[4] for r in rs], np.float64))
+    return out
+
+
+def _check_every_query(dsets, results, golden):
+    assert len(golden) == len(dsets)
+    for k, (d, r) in enumerate(zip(dsets, results)):
+        idx, lab, dist = r
+        gi, gl, gd = golden[k]
+        assert gi.shape[0] == d.Q, d.name
+        np.testing.assert_array_equal(idx, gi, err_msg=d.name)
+        np.testing.assert_array_equal(lab, gl, err_msg=d.name)
+        np.testing.assert_allclose(dist, gd, rtol=1e-4, atol=0, err_msg=d.name)
+
+
+def test_batched_matches_oracle_every_query(lib, batch, golden_batched):
+    """All 35,843 queries of the 64 datasets, in one batched call and in the
+    CUDA-graph replay the bench times, against the oracle's stored results."""
     dsets, sets = batch
-    res = lib.nn_dtw_search_batched(sets)
-    rng = np.random.default_rng(64)
-    for d, r in zip(dsets, res):
-        idx, lab, dist = _np(r)
-        k = min(2, d.Q)
-        sample = np.sort(rng.choice(d.Q, k, replace=False))
-        ri, rl, rd, _ = orc.nn_pruned(d.train, d.train_labels, d.test[sample], d.W, d.V)
-        np.testing.assert_array_equal(idx[sample], ri, err_msg=d.name)
-        np.testing.assert_array_equal(lab[sample], rl, err_msg=d.name)
-        np.testing.assert_allclose(dist[sample], rd, rtol=1e-4, atol=0, err_msg=d.name)
+    _check_every_query(dsets, [_np(r) for r in lib.nn_dtw_search_batched(sets)], golden_batched)
+    bs = lib.BatchedSearch(sets, graph=True)
+    bs.run()
+    _check_every_query(dsets, [_np(r) for r in bs.run()], golden_batched)
+
+
+def test_batched_other_flags_match_oracle(lib, batch, golden_batched):
+    """Every dataset with search flags the bench's tuner may choose (the
+    cascade's second stage and every admissible DTW layout, dealt out in
+    turn): still the oracle's results for every query."""
+    from paper_1808_09617_gb300 import autotune
+    dsets, sets = batch
+    cascade = (0, lib.REVERSE, lib.IMPROVED, lib.REVERSE | lib.IMPROVED)
+    other = []
+    for k, (d, s) in enumerate(zip(dsets, sets)):
+        groups = autotune.admissible_groups(min(d.W, d.L - 1), d.L)
+        g = groups[(k // 4) % len(groups)] if groups else 0
+        t = dict(s)
+        t["flags"] = cascade[k % 4] | (lib.DTW_GROUP(g) if g else 0)
+        other.append(t)
+    _check_every_query(dsets, [_np(r) for r in lib.nn_dtw_search_batched(other)],
+                       golden_batched)
 
 
 def test_batched_rejects_bad_descriptors(lib, batch):

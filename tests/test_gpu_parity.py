@@ -203,12 +203,43 @@ def test_search_ties_lowest_index(lib, orc):
     labels = np.arange(train.shape[0], dtype=np.int32) % 7
     test = np.concatenate([_series(9002, 30, L), base[:10]], axis=0)  # some queries equal a series
     brute = orc.nn_brute(train, labels, test, W)
-    _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+    st = _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+    # the queries equal to a duplicated series have two candidates at the same
+    # FP32 distance: the FP64 recheck must have run for them
+    assert st["rechecked"] >= 20 and st["recheck_queries"] >= 10
     _check_search(lib, orc, train, labels, test, W, V, flags=lib.EXACT_DIST, brute=brute)
     # all training series identical: every query's NN is index 0
     same = np.repeat(base[:1], 50, axis=0)
     idx, _, _, _ = _search(lib, same, labels[:50], test, W, V)
     assert np.all(idx == 0)
+
+
+def test_search_near_ties_recheck_fires(lib, orc):
+    """Planted near ties: each query has two training series whose DTW
+    distances differ by far less than the FP32 rounding margin (one is the
+    other with a few elements moved by one FP32 ulp).  Without EXACT_DIST the
+    search must re-evaluate both in FP64 and return the oracle's index, which
+    is the nudged copy for some queries and the original for others."""
+    L, W, V = 200, 20, 4
+    rng = np.random.default_rng(77)
+    test = _series(9101, 24, L)
+    train = [_series(9102, 150, L)]
+    for q in range(test.shape[0]):
+        near = (test[q] + 0.05 * rng.standard_normal(L)).astype(np.float32)
+        nudged = near.copy()
+        pos = rng.choice(L, 6, replace=False)
+        direction = np.inf if q % 2 else -np.inf
+        nudged[pos] = np.nextafter(nudged[pos], np.float32(direction))
+        # the nudged copy first for half of the queries: the lower index is
+        # not always the answer
+        train.append(np.stack([nudged, near] if q % 3 == 0 else [near, nudged]))
+    train = np.concatenate(train, axis=0)
+    labels = (np.arange(train.shape[0]) % 5).astype(np.int32)
+    brute = orc.nn_brute(train, labels, test, W)
+    assert np.all(brute[0] >= 150)
+    st = _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+    assert st["rechecked"] >= 2 * test.shape[0] - 4
+    assert st["recheck_queries"] >= test.shape[0] - 2
 
 
 @pytest.mark.parametrize("flag", ["NO_PRUNE", "NO_ABANDON", "EXACT_DIST", "CHECK_FINITE"])
@@ -249,16 +280,24 @@ def test_search_workspace_too_small(lib):
 
 
 @pytest.mark.parametrize("W_ratio", [0.1, 0.5, 1.0])
-def test_search_precision_workload_sampled(lib, orc, W_ratio):
-    """The full-size precision workload (10,000 x 2,000, L=1024) on the GPU,
-    checked on a sample of queries with the oracle's exact pruned search."""
+def test_search_precision_workload_every_query(lib, orc, W_ratio):
+    """The full-size precision workload (10,000 x 2,000, L=1024, W = 102, 512
+    and 1023) on the GPU: every query's index and label equal the oracle's
+    stored results (tests/golden/make_full_golden.py), distances within
+    1e-4, and the same with the cascade's second stage (LB_Improved bridge)."""
+    from golden import make_full_golden as fg
     ds = synth.make_precision(W_ratio)
-    idx, lab, dist, st = _search(lib, ds.train, ds.train_labels, ds.test, ds.W, ds.V, stats=True)
-    sample = np.random.default_rng(5).choice(ds.Q, 6, replace=False)
-    ri, rl, rd, _ = orc.nn_pruned(ds.train, ds.train_labels, ds.test[sample], ds.W, ds.V)
-    np.testing.assert_array_equal(idx[sample], ri)
-    np.testing.assert_array_equal(lab[sample], rl)
-    np.testing.assert_allclose(dist[sample], rd, rtol=RTOL32, atol=0)
+    rows = np.array(fg.read(fg.precision_path(W_ratio)), dtype=object)
+    assert rows.shape[0] == ds.Q
+    gi = rows[:, 1].astype(np.int32)
+    gl = rows[:, 2].astype(np.int32)
+    gd = rows[:, 3].astype(np.float64)
+    for flags in (0, lib.IMPROVED):
+        idx, lab, dist, st = _search(lib, ds.train, ds.train_labels, ds.test, ds.W, ds.V,
+                                     flags=flags, stats=True)
+        np.testing.assert_array_equal(idx, gi)
+        np.testing.assert_array_equal(lab, gl)
+        np.testing.assert_allclose(dist, gd, rtol=RTOL32, atol=0)
 
 
 @pytest.mark.parametrize("L,W", [(300, 26), (257, 63), (600, 200), (1024, 511), (64, 3), (90, 89)])

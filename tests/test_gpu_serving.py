@@ -72,3 +72,43 @@ def test_small_memory_budget_splits_batches(lib, sets):
     finally:
         srv.close()
     assert len(res) == 150 and st["batches"] > 2
+
+
+def test_set_larger_than_the_budget_is_refused(lib, sets):
+    """A set whose one-query batch cannot fit the memory budget would never be
+    served: the server refuses it at construction instead of hanging."""
+    from paper_1808_09617_gb300 import serving
+    with pytest.raises(ValueError):
+        serving.Server({0: sets[0][:4]}, memory_budget=1 << 16, tune=False)
+
+
+def test_serving_workload_full_size_matches_oracle(lib):
+    """The serving workload at its configured size: 16 resident training sets
+    (L in {128, 512, 1500}, 1,000-20,000 series each, W = 0.1 L, V = 5), 24
+    queries per set submitted in a shuffled mix; every result equals the
+    oracle's stored 1-NN (tests/golden/make_full_golden.py)."""
+    from golden import make_full_golden as fg
+    from paper_1808_09617_gb300 import serving
+    specs = synth.serving_specs(16)
+    resident = {}
+    for d, sp in enumerate(specs):
+        ds = synth.make_serving_set(d, sp)
+        resident[d] = (ds.train, ds.train_labels, sp["W"], sp["V"])
+    k = fg.SERVING_QUERIES_PER_SET
+    golden = {(r[0], r[1]): r[2:] for r in fg.read(fg.SERVING_PATH)}
+    assert len(golden) == 16 * k
+    order = [(d, j) for d in range(16) for j in range(k)]
+    np.random.default_rng(1500).shuffle(order)
+    srv = serving.Server(resident, n_slots=4, max_batch=128, tune=False)
+    try:
+        futs = []
+        for d, j in order:
+            q, _ = synth.serving_queries(d, specs[d], 1, offset=j)
+            futs.append(((d, j), srv.submit(q[0], d)))
+        got = [(key, f.result(timeout=300)) for key, f in futs]
+    finally:
+        srv.close()
+    for key, (idx, lab, dist) in got:
+        gi, gl, gd = golden[key]
+        assert (idx, lab) == (gi, gl), key
+        assert abs(dist - gd) <= 1e-4 * gd, key
