@@ -266,8 +266,9 @@ def roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, wor
 def tightness_pairs(dev):
     """Mean tightness LB/DTW over all 250,000 pairs of the 500 x 500 pairs
     workload (L=256, W=26) for LB_Enhanced^V, V in {1, 2, 5}, with and
-    without the LB_Improved bridge, and LB_Keogh (pairs with DTW = 0
-    excluded), with the search's pruning per V."""
+    without the LB_Improved bridge, and for the comparison bounds LB_Keogh,
+    LB_Improved and LB_New (pairs with DTW = 0 excluded), with the search's
+    pruning per V."""
     import torch
     from paper_1808_09617_gb300 import nndtw, synth
     ds = synth.make_pairs(5)
@@ -286,6 +287,11 @@ def tightness_pairs(dev):
     out["LB_Keogh"] = float((lbk[keep] / dtw[keep]).mean().item())
     tenv = nndtw.nn_dtw_build_envelopes(test, ds.W)
     env2 = nndtw.nn_dtw_build_second_envelopes(env, ds.W)
+    # the paper's comparison bounds (Sec. 2.2.4, 2.2.5)
+    lbim = nndtw.lb_improved(test, tenv, train, env, env2, ds.W).double().reshape(-1)
+    out["LB_Improved"] = float((lbim[keep] / dtw[keep]).mean().item())
+    lbn = nndtw.lb_new(test, train, ds.W).double().reshape(-1)
+    out["LB_New"] = float((lbn[keep] / dtw[keep]).mean().item())
     for V in (1, 2, 5):
         lb = nndtw.lb_enhanced(test, train, env, ds.W, V).double().reshape(-1)
         st = nndtw.nn_dtw_search(train, labels, test, ds.W, V, stats=True).stats

@@ -61,6 +61,9 @@ extern "C" {
 /* flags */
 #define NNDTW_LB_KEOGH (1u << 0)     /* lb_enhanced*: compute LB_Keogh instead       */
 #define NNDTW_LB_SAFE (1u << 1)      /* lb_enhanced*: write rounding-safe bounds     */
+/* lb_enhanced: compute LB_New (Sec. 2.2.5) instead; d_env is then not read
+ * and may be NULL */
+#define NNDTW_LB_NEW (1u << 18)
 #define NNDTW_EXACT_DIST (1u << 2)   /* search: FP64 distance for every query's NN   */
 #define NNDTW_NO_PRUNE (1u << 3)     /* search: run DTW on every pair (no LB prune)  */
 #define NNDTW_NO_ABANDON (1u << 4)   /* search: no early abandoning inside DTW      */
@@ -161,12 +164,17 @@ NNDTW_API int nn_dtw_build_second_envelopes_f64(const double *d_env, int64_t N, 
  *   + sum_{i=2..n} [min over the left band L^W_i + min over the right band]
  *   + sum_{i=n+1..L-n} LB_Keogh term of A_i against (U_i, Lo_i),
  * with n = min(floor(L/2), V).  flags & NNDTW_LB_KEOGH computes LB_Keogh
- * (Sec. 2.2.3) instead.  flags & NNDTW_LB_SAFE scales each value down by the
- * FP32 (or FP64) rounding margin so that it never exceeds the exact bound.
+ * (Sec. 2.2.3) instead.  flags & NNDTW_LB_NEW computes LB_New (Sec. 2.2.5)
+ * instead, one of the comparison bounds of the paper's tightness study:
+ *   delta(A_1,B_1) + delta(A_L,B_L)
+ *   + sum_{i=2..L-1} min over max(1,i-W) <= j <= min(L,i+W) of delta(A_i,B_j),
+ * O(L (2W+1)) per pair (d_env is not read and may be NULL).
+ * flags & NNDTW_LB_SAFE scales each value down by the FP32 (or FP64) rounding
+ * margin so that it never exceeds the exact bound.
  * d_test: [Q][L]; d_train: [N][L]; d_env: [N][L][2] from
  * nn_dtw_build_envelopes with the same W; d_lb_out: [Q][N], row-major.
  * Errors: NNDTW_EINVAL for null pointers, Q < 0, N < 0, L < 2 or > NNDTW_MAX_L,
- * W < 0, V < 1.
+ * W < 0, V < 1, or NNDTW_LB_KEOGH together with NNDTW_LB_NEW.
  */
 NNDTW_API int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const float *d_env,
                 int64_t N, int L, int W, int V, unsigned flags, float *d_lb_out,
@@ -188,8 +196,11 @@ NNDTW_API int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_t
  * second envelopes.  d_test_env: [Q][L][2] (nn_dtw_build_envelopes on the
  * test set, same W); d_env2: [N][L][2] (nn_dtw_build_second_envelopes);
  * other arguments as lb_enhanced.  flags: NNDTW_LB_SAFE (both parts scaled
- * down, the sum rounded down); NNDTW_LB_KEOGH is an error.
- * Errors: those of lb_enhanced, and NNDTW_EINVAL for NNDTW_LB_KEOGH.
+ * down, the sum rounded down).  With NNDTW_LB_KEOGH both passes run over the
+ * whole series, which is LB_Improved itself (Sec. 2.2.4, Eq. 5):
+ *   LB_Keogh(A, B) + sum_{j=1..L} LB_Keogh term of B_j against the envelope
+ *   of A' (V is then not used).
+ * Errors: those of lb_enhanced, and NNDTW_EINVAL for NNDTW_LB_NEW.
  */
 NNDTW_API int lb_enhanced_improved(const float *d_test, const float *d_test_env, int64_t Q,
                                    const float *d_train, const float *d_env, const float *d_env2,

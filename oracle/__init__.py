@@ -17,6 +17,8 @@ Functions and the passage of the paper each one follows:
 ``ed``                 DTW_0, squared Euclidean distance (Sec. 2.1)
 ``lb_keogh``           Sec. 2.2.3 (LB_Keogh)
 ``lb_enhanced``        Sec. 3.1, Eq. 7 / Algorithm 1
+``lb_improved``        Sec. 2.2.4, Eq. 5 (LB_Improved)
+``lb_new``             Sec. 2.2.5 (LB_New)
 ``nn_brute``           1-NN by exhaustive DTW (Sec. 1, the task itself)
 ``nn_pruned``          the paper's lower-bound search protocol (Sec. 4)
 =====================  ====================================================
@@ -72,6 +74,10 @@ def _declare(lib):
     lib.oracle_lb_enhanced_improved.argtypes = [_d, _d, _d, _d, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int]
     lib.oracle_lb_enhanced_improved.restype = ctypes.c_double
+    lib.oracle_lb_improved.argtypes = [_d, _d, _d, _d, ctypes.c_int, ctypes.c_int]
+    lib.oracle_lb_improved.restype = ctypes.c_double
+    lib.oracle_lb_new.argtypes = [_d, _d, ctypes.c_int, ctypes.c_int]
+    lib.oracle_lb_new.restype = ctypes.c_double
     lib.oracle_lb_matrix.argtypes = [_d, ctypes.c_int64, _d, _d, _d, ctypes.c_int64,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      _d, ctypes.c_int]
@@ -158,6 +164,17 @@ class Oracle:
         return self.lib.oracle_lb_enhanced_improved(_p(a), _p(b), _p(U), _p(Lo), a.shape[0],
                                                     int(W), int(V))
 
+    def lb_improved(self, a, b, U, Lo, W):
+        """LB_Improved (Sec. 2.2.4): LB_Keogh(A, B) + LB_Keogh(B, A')."""
+        a = _f64(a); b = _f64(b); U = _f64(U); Lo = _f64(Lo)
+        return self.lib.oracle_lb_improved(_p(a), _p(b), _p(U), _p(Lo), a.shape[0], int(W))
+
+    def lb_new(self, a, b, W):
+        """LB_New (Sec. 2.2.5)."""
+        a = _f64(a); b = _f64(b)
+        assert a.shape == b.shape and a.ndim == 1 and a.shape[0] >= 2
+        return self.lib.oracle_lb_new(_p(a), _p(b), a.shape[0], int(W))
+
     # -- batched drivers ----------------------------------------------------
     def envelopes(self, train, W):
         train = _f64(train)
@@ -173,7 +190,7 @@ class Oracle:
         U, Lo = env if env is not None else self.envelopes(train, W)
         U = _f64(U); Lo = _f64(Lo)
         out = np.empty((Q, N))
-        k = {"enhanced": 0, "keogh": 1, "improved": 2}[kind]
+        k = {"enhanced": 0, "keogh": 1, "improved": 2, "lb_improved": 3, "new": 4}[kind]
         self.lib.oracle_lb_matrix(_p(test), Q, _p(train), _p(U), _p(Lo), N, L, int(W),
                                   int(V), k, _p(out), threads or default_threads())
         return out

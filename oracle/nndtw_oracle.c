@@ -196,6 +196,52 @@ double oracle_lb_enhanced_improved(const double *A, const double *B, const doubl
     return res;
 }
 
+/*
+ * LB_Improved_W(A, B) (Sec. 2.2.4): LB_Keogh_W(A, B) plus LB_Keogh_W(B, A'),
+ * where A' is the projection of A onto B's envelope (Eq. 5) and the second
+ * LB_Keogh is taken against the envelope of A' over the same window
+ * (Eq. 3-4), both over i = 1..L:
+ *   res = LB_Keogh(A against (U, Lo))
+ *   A'_i = U_i if A_i > U_i, Lo_i if A_i < Lo_i, A_i otherwise
+ *   (U', Lo') = envelopes of A' over W
+ *   res += LB_Keogh(B against (U', Lo')).
+ */
+double oracle_lb_improved(const double *A, const double *B, const double *U,
+                          const double *Lo, int L, int W) {
+    double res = oracle_lb_keogh(A, U, Lo, L);
+    double *Ap = malloc(3 * sizeof(double) * (size_t)L);
+    if (!Ap) return NAN;
+    double *Up = Ap + L, *Lp = Ap + 2 * L;
+    for (int i = 0; i < L; i++) {
+        if (A[i] > U[i]) Ap[i] = U[i];
+        else if (A[i] < Lo[i]) Ap[i] = Lo[i];
+        else Ap[i] = A[i];
+    }
+    oracle_envelope(Ap, L, W, Up, Lp);
+    res = res + oracle_lb_keogh(B, Up, Lp, L);
+    free(Ap);
+    return res;
+}
+
+/*
+ * LB_New_W(A, B) (Sec. 2.2.5): the two ends, which every warping path
+ * contains (boundary condition), plus, for every i = 2..L-1, the smallest
+ * delta(A_i, B_j) over the window max(1, i-W) <= j <= min(L, i+W), since the
+ * path pairs A_i with at least one B_j there (continuity):
+ *   res = delta(A_1, B_1) + delta(A_L, B_L) + sum_{i=2}^{L-1} min_j delta(A_i, B_j).
+ * Naive scan of each window.  Requires L >= 2.
+ */
+double oracle_lb_new(const double *A, const double *B, int L, int W) {
+    double res = delta(A[0], B[0]) + delta(A[L - 1], B[L - 1]);
+    for (int i = 2; i <= L - 1; i++) {
+        int jlo = imax(1, i - W), jhi = imin(L, i + W);
+        double m = INFINITY;
+        for (int j = jlo; j <= jhi; j++) m = dmin(m, delta(A[i - 1], B[j - 1]));
+        res = res + m;
+    }
+    return res;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Threaded drivers over many pairs / queries (plain loops per item).        */
 
@@ -223,6 +269,8 @@ static void *lb_matrix_worker(void *p) {
         double v;
         if (j->kind == 1) v = oracle_lb_keogh(A, U, Lo, j->L);
         else if (j->kind == 2) v = oracle_lb_enhanced_improved(A, B, U, Lo, j->L, j->W, j->V);
+        else if (j->kind == 3) v = oracle_lb_improved(A, B, U, Lo, j->L, j->W);
+        else if (j->kind == 4) v = oracle_lb_new(A, B, j->L, j->W);
         else v = oracle_lb_enhanced(A, B, U, Lo, j->L, j->W, j->V, INFINITY);
         j->out[f] = v;
     }
@@ -339,7 +387,7 @@ void oracle_envelopes(const double *train, int64_t N, int L, int W, double *U, d
 }
 
 /* out[q*N + t] = LB(test_q, train_t); kind 0 = LB_Enhanced^V, 1 = LB_Keogh,
- * 2 = LB_Enhanced^V with the LB_Improved bridge. */
+ * 2 = LB_Enhanced^V with the LB_Improved bridge, 3 = LB_Improved, 4 = LB_New. */
 void oracle_lb_matrix(const double *test, int64_t Q, const double *train,
                       const double *U, const double *Lo, int64_t N, int L, int W,
                       int V, int kind, double *out, int nthreads) {

@@ -111,6 +111,12 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
                       T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
                       bool loo, cudaStream_t s);
 
+// LB_New (Sec. 2.2.5) of every (query, training series) pair into out[Q][N]
+// (raw, or with safe: scaled down by the rounding margin).
+template <typename T>
+cudaError_t launch_lb_new(const T *test, int64_t Q, const T *train, int64_t N, int L, int W,
+                          bool safe, T lb_lo, T lb_abs, T *out, cudaStream_t s);
+
 // FP32 DTW over a work list.  Pairs come from `pairs` ([count] of (q, t)) or,
 // when pairs == nullptr, from seed keys (pair p = (p, key_idx(seed_keys[p]))).
 struct DtwJob32 {

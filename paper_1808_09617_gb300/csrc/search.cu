@@ -570,9 +570,16 @@ int nn_dtw_build_second_envelopes_f64(const double *d_env, int64_t N, int L, int
 int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const float *d_env,
                 int64_t N, int L, int W, int V, unsigned flags, float *d_lb_out, void *stream) {
     if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
+    if ((flags & NNDTW_LB_KEOGH) && (flags & NNDTW_LB_NEW)) return NNDTW_EINVAL;
     if (Q == 0 || N == 0) return NNDTW_OK;
-    if (!d_test || !d_train || !d_env || !d_lb_out) return NNDTW_EINVAL;
+    const bool lbnew = (flags & NNDTW_LB_NEW) != 0;
+    if (!d_test || !d_train || (!d_env && !lbnew) || !d_lb_out) return NNDTW_EINVAL;
     const Margins m = make_margins(L);
+    if (lbnew) {
+        CK(launch_lb_new<float>(d_test, Q, d_train, N, L, W, (flags & NNDTW_LB_SAFE) != 0,
+                                m.lb_lo, m.abs32, d_lb_out, (cudaStream_t)stream));
+        return NNDTW_OK;
+    }
     CK(launch_lb<float>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                         (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out, nullptr,
                         nullptr, nullptr, false, (cudaStream_t)stream));
@@ -583,9 +590,16 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
                     int64_t N, int L, int W, int V, unsigned flags, double *d_lb_out,
                     void *stream) {
     if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
+    if ((flags & NNDTW_LB_KEOGH) && (flags & NNDTW_LB_NEW)) return NNDTW_EINVAL;
     if (Q == 0 || N == 0) return NNDTW_OK;
-    if (!d_test || !d_train || !d_env || !d_lb_out) return NNDTW_EINVAL;
+    const bool lbnew = (flags & NNDTW_LB_NEW) != 0;
+    if (!d_test || !d_train || (!d_env && !lbnew) || !d_lb_out) return NNDTW_EINVAL;
     const Margins m = make_margins(L);
+    if (lbnew) {
+        CK(launch_lb_new<double>(d_test, Q, d_train, N, L, W, (flags & NNDTW_LB_SAFE) != 0,
+                                 m.lb_lo64, m.abs64, d_lb_out, (cudaStream_t)stream));
+        return NNDTW_OK;
+    }
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
                          nullptr, nullptr, false, (cudaStream_t)stream));
@@ -596,13 +610,16 @@ int lb_enhanced_improved(const float *d_test, const float *d_test_env, int64_t Q
                          const float *d_train, const float *d_env, const float *d_env2, int64_t N,
                          int L, int W, int V, unsigned flags, float *d_lb_out, void *stream) {
     if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
-    if (flags & NNDTW_LB_KEOGH) return NNDTW_EINVAL;
+    if (flags & NNDTW_LB_NEW) return NNDTW_EINVAL;
     if (Q == 0 || N == 0) return NNDTW_OK;
     if (!d_test || !d_test_env || !d_train || !d_env || !d_env2 || !d_lb_out) return NNDTW_EINVAL;
     const int rc = lb_enhanced(d_test, Q, d_train, d_env, N, L, W, V, flags, d_lb_out, stream);
     if (rc != NNDTW_OK) return rc;
     const Margins m = make_margins(L);
-    CK(launch_improved_terms<float>(d_train, d_test_env, d_env2, Q, N, L, bridge_start(L, V),
+    // with NNDTW_LB_KEOGH the first pass is LB_Keogh over the whole series and
+    // so is the second: LB_Improved itself (Sec. 2.2.4)
+    const int nb = (flags & NNDTW_LB_KEOGH) ? 0 : bridge_start(L, V);
+    CK(launch_improved_terms<float>(d_train, d_test_env, d_env2, Q, N, L, nb,
                                     (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out,
                                     (cudaStream_t)stream));
     return NNDTW_OK;
@@ -613,13 +630,16 @@ int lb_enhanced_improved_f64(const double *d_test, const double *d_test_env, int
                              int64_t N, int L, int W, int V, unsigned flags, double *d_lb_out,
                              void *stream) {
     if (Q < 0 || N < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return NNDTW_EINVAL;
-    if (flags & NNDTW_LB_KEOGH) return NNDTW_EINVAL;
+    if (flags & NNDTW_LB_NEW) return NNDTW_EINVAL;
     if (Q == 0 || N == 0) return NNDTW_OK;
     if (!d_test || !d_test_env || !d_train || !d_env || !d_env2 || !d_lb_out) return NNDTW_EINVAL;
     const int rc = lb_enhanced_f64(d_test, Q, d_train, d_env, N, L, W, V, flags, d_lb_out, stream);
     if (rc != NNDTW_OK) return rc;
     const Margins m = make_margins(L);
-    CK(launch_improved_terms<double>(d_train, d_test_env, d_env2, Q, N, L, bridge_start(L, V),
+    // with NNDTW_LB_KEOGH the first pass is LB_Keogh over the whole series and
+    // so is the second: LB_Improved itself (Sec. 2.2.4)
+    const int nb = (flags & NNDTW_LB_KEOGH) ? 0 : bridge_start(L, V);
+    CK(launch_improved_terms<double>(d_train, d_test_env, d_env2, Q, N, L, nb,
                                      (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out,
                                      (cudaStream_t)stream));
     return NNDTW_OK;

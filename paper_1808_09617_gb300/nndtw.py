@@ -23,6 +23,7 @@ NNDTW_MAX_L = 8192
 OK, EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED, ENONFINITE = 0, 1, 2, 3, 4, 5
 LB_KEOGH = 1 << 0
 LB_SAFE = 1 << 1
+LB_NEW = 1 << 18
 EXACT_DIST = 1 << 2
 NO_PRUNE = 1 << 3
 NO_ABANDON = 1 << 4
@@ -276,6 +277,24 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
     return out
 
 
+def lb_new(test, train, W: int, safe: bool = False, out=None, stream=None):
+    """LB_New (Sec. 2.2.5) for all pairs: tensor [Q, N]."""
+    import torch
+    lib = load()
+    f64 = _fp(test)
+    Q, L = test.shape
+    N = train.shape[0]
+    if out is None:
+        out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
+    flags = LB_NEW | (LB_SAFE if safe else 0)
+    fn = lib.lb_enhanced_f64 if f64 else lib.lb_enhanced
+    with _on([test, train, out], stream):
+        _check(fn(_dev(test, test.dtype, "test", 2), Q,
+                  _dev(train, test.dtype, "train", shape=(N, L)), None, N, L, int(W), 1, flags,
+                  _dev(out, test.dtype, "out", shape=(Q, N)), _stream(stream)), "lb_new")
+    return out
+
+
 def nn_dtw_build_second_envelopes(env, W: int, env2=None, stream=None):
     """Second envelopes (window max of Lo, window min of U) of every training
     series, from its envelopes [N, L, 2]: tensor [N, L, 2]."""
@@ -314,6 +333,30 @@ def lb_enhanced_improved(test, test_env, train, env, env2, W: int, V: int, safe:
                 _dev(env2, test.dtype, "env2", shape=(N, L, 2)), N, L, int(W), int(V),
                 LB_SAFE if safe else 0, _dev(out, test.dtype, "out", shape=(Q, N)),
                 _stream(stream)), "lb_enhanced_improved")
+    return out
+
+
+def lb_improved(test, test_env, train, env, env2, W: int, safe: bool = False, out=None,
+                stream=None):
+    """LB_Improved (Sec. 2.2.4, Eq. 5) for all pairs: LB_Keogh plus the
+    second pass over the whole series (lb_enhanced_improved with
+    NNDTW_LB_KEOGH); tensor [Q, N]."""
+    import torch
+    lib = load()
+    f64 = _fp(test)
+    Q, L = test.shape
+    N = train.shape[0]
+    if out is None:
+        out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
+    fn = lib.lb_enhanced_improved_f64 if f64 else lib.lb_enhanced_improved
+    with _on([test, test_env, train, env, env2, out], stream):
+        _check(fn(_dev(test, test.dtype, "test", 2),
+                  _dev(test_env, test.dtype, "test_env", shape=(Q, L, 2)), Q,
+                  _dev(train, test.dtype, "train", shape=(N, L)),
+                  _dev(env, test.dtype, "env", shape=(N, L, 2)),
+                  _dev(env2, test.dtype, "env2", shape=(N, L, 2)), N, L, int(W), 1,
+                  LB_KEOGH | (LB_SAFE if safe else 0), _dev(out, test.dtype, "out", shape=(Q, N)),
+                  _stream(stream)), "lb_improved")
     return out
 
 

@@ -262,6 +262,93 @@ def pin_lb_improved_bridge_closed_form(orc, trials=60):
         assert abs(got - second) <= 1e-12 * max(abs(second), 1.0), (L, W, V, got, second)
 
 
+def pin_lb_improved_standalone(orc, max_L=8, trials=60):
+    """LB_Improved (Sec. 2.2.4): never above DTW_W (minimum over every warping
+    path), never below LB_Keogh, the Euclidean distance at W = 0 (A' = B), zero
+    for A = B; and equal to LB_Keogh plus its second pass in closed form:
+    B_j's distance to [min(L^A_j, min_i U_i), max(U^A_j, max_i Lo_i)] with
+    window extremes from scipy's filters, summed over all of j = 1..L (the
+    identity of the bridge pin above with an empty band set)."""
+    rng = _rng(15)
+    tol = 1 + 1e-12
+    for L in range(1, max_L + 1):
+        for W in range(0, L + 1):
+            for kind in range(2):
+                if kind:
+                    a = rng.integers(-2, 3, L).astype(float)
+                    b = rng.integers(-2, 3, L).astype(float)
+                else:
+                    a, b = _series(rng, L), _series(rng, L)
+                U, Lo = orc.envelope(b, W)
+                lbi = orc.lb_improved(a, b, U, Lo, W)
+                d = paths.dtw_by_paths(a, b, W)
+                assert orc.lb_keogh(a, U, Lo) <= lbi * tol and lbi <= d * tol, (L, W, lbi, d)
+                if W == 0:
+                    assert _rel_close(lbi, math.fsum((a - b) ** 2), 1e-13)
+                assert orc.lb_improved(a, a, *orc.envelope(a, W), W) == 0.0
+    for _ in range(trials):
+        L = int(rng.integers(2, 150))
+        W = int(rng.integers(0, L + 2))
+        a, b = _series(rng, L), _series(rng, L)
+        size = 2 * W + 1
+        f_max = lambda x: maximum_filter1d(x, size=size, mode="nearest")
+        f_min = lambda x: minimum_filter1d(x, size=size, mode="nearest")
+        Ub, Lb = f_max(b), f_min(b)
+        hi = np.maximum(f_max(a), f_max(Lb))
+        lo = np.minimum(f_min(a), f_min(Ub))
+        first = math.fsum((a - np.clip(a, Lb, Ub)) ** 2)
+        second = math.fsum((b - np.clip(b, lo, hi)) ** 2)
+        U, Lo = orc.envelope(b, W)
+        got = orc.lb_improved(a, b, U, Lo, W)
+        assert abs(got - (first + second)) <= 1e-12 * max(first + second, 1.0), (L, W)
+
+
+def pin_lb_new(orc, max_L=8, trials=60):
+    """LB_New (Sec. 2.2.5): never above DTW_W (every warping path), never below
+    LB_Keogh nor LB_Enhanced^1 (its interior terms are distances to points of
+    the window, the Keogh terms distances to the window's range), the
+    Euclidean distance at W = 0, zero for A = B; with W >= L-1 every interior
+    term is A_i's squared distance to the nearest value of all of B (a 1-D
+    nearest-neighbour query on sorted B), and for any W the window minima by
+    numpy's sliding windows."""
+    rng = _rng(16)
+    tol = 1 + 1e-12
+    for L in range(2, max_L + 1):
+        for W in range(0, L + 1):
+            for kind in range(2):
+                if kind:
+                    a = rng.integers(-2, 3, L).astype(float)
+                    b = rng.integers(-2, 3, L).astype(float)
+                else:
+                    a, b = _series(rng, L), _series(rng, L)
+                U, Lo = orc.envelope(b, W)
+                lbn = orc.lb_new(a, b, W)
+                d = paths.dtw_by_paths(a, b, W)
+                assert lbn <= d * tol, (L, W, lbn, d)
+                assert orc.lb_keogh(a, U, Lo) <= lbn * tol
+                assert orc.lb_enhanced(a, b, U, Lo, W, 1) <= lbn * tol
+                if W == 0:
+                    assert _rel_close(lbn, math.fsum((a - b) ** 2), 1e-13)
+                assert orc.lb_new(a, a, W) == 0.0
+    from numpy.lib.stride_tricks import sliding_window_view
+    for _ in range(trials):
+        L = int(rng.integers(2, 200))
+        W = int(rng.integers(0, L + 2))
+        a, b = _series(rng, L), _series(rng, L)
+        ends = (a[0] - b[0]) ** 2 + (a[-1] - b[-1]) ** 2
+        if W >= L - 1:
+            sb = np.sort(b)
+            k = np.clip(np.searchsorted(sb, a[1:-1]), 1, L - 1)
+            near = np.minimum(np.abs(a[1:-1] - sb[k - 1]), np.abs(a[1:-1] - sb[k]))
+        else:
+            padded = np.concatenate([np.full(W, np.inf), b, np.full(W, np.inf)])
+            win = sliding_window_view(padded, 2 * W + 1)[1:-1]
+            near = np.min(np.abs(win - a[1:-1, None]), axis=1)
+        exact = ends + math.fsum(near ** 2)
+        got = orc.lb_new(a, b, W)
+        assert _rel_close(got, exact, 1e-12), (L, W, got, exact)
+
+
 def pin_lb_enhanced_w0_is_euclidean(orc, trials=30):
     """At W=0 every band is the single diagonal cell and U = Lo = B, so
     LB_Enhanced^V = DTW_0 = the Euclidean distance for every V."""
@@ -403,6 +490,8 @@ ALL_PINS = [
     pin_reverse_bound,
     pin_lb_improved_bridge_bounds_dtw,
     pin_lb_improved_bridge_closed_form,
+    pin_lb_improved_standalone,
+    pin_lb_new,
     pin_algorithm1_abandon,
     pin_nn_brute_by_paths,
     pin_nn_w0_is_euclidean_nn,

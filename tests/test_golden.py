@@ -33,11 +33,15 @@ def test_hand_worked_examples(orc):
             got = [orc.lb_enhanced(a, b, U, Lo, W, V)]
         elif qty == "lb_enh_improved":
             got = [orc.lb_enhanced_improved(a, b, U, Lo, W, V)]
+        elif qty == "lb_improved":
+            got = [orc.lb_improved(a, b, U, Lo, W)]
+        elif qty == "lb_new":
+            got = [orc.lb_new(a, b, W)]
         else:
             raise AssertionError(qty)
         assert got == val, (name, qty, got, val)
         n += 1
-    assert n == 22
+    assert n == 30
 
 
 def test_tiny_golden_regression(orc):

@@ -39,14 +39,31 @@ MUTANTS = {
         "for (int i = n_bands; i <= L - n_bands; i++) {\n        if (a(i) > U[i - 1])"),
     "lbenh_abandon_wrong_way": ("if (res >= D) return INFINITY;", "if (res < D) return INFINITY;"),
     "lbimp_second_pass_without_projection": (
-        "if (A[i] > U[i]) Ap[i] = U[i];\n        else if (A[i] < Lo[i]) Ap[i] = Lo[i];\n        else Ap[i] = A[i];",
-        "Ap[i] = A[i];"),
+        "        else Ap[i] = A[i];\n    }\n    oracle_envelope(Ap, L, W, Up, Lp);\n    for (int j = nb + 1;",
+        "        Ap[i] = A[i];\n    }\n    oracle_envelope(Ap, L, W, Up, Lp);\n    for (int j = nb + 1;"),
+    "lbimproved_without_projection": (
+        "        else Ap[i] = A[i];\n    }\n    oracle_envelope(Ap, L, W, Up, Lp);\n    res = res +",
+        "        Ap[i] = A[i];\n    }\n    oracle_envelope(Ap, L, W, Up, Lp);\n    res = res +"),
     "lbimp_second_pass_overlaps_bands": (
         "for (int j = nb + 1; j <= L - nb; j++) {",
         "for (int j = nb; j <= L - nb; j++) {"),
     "lbimp_second_pass_lower_uses_upper": (
         "else if (B[j - 1] < Lp[j - 1]) res = res + delta(B[j - 1], Lp[j - 1]);",
         "else if (B[j - 1] < Lp[j - 1]) res = res + delta(B[j - 1], Up[j - 1]);"),
+    "lbimproved_skips_second_pass": (
+        "    res = res + oracle_lb_keogh(B, Up, Lp, L);\n", "\n"),
+    "lbimproved_second_pass_against_b_envelope": (
+        "    oracle_envelope(Ap, L, W, Up, Lp);\n    res = res + oracle_lb_keogh(B, Up, Lp, L);",
+        "    oracle_envelope(Ap, L, W, Up, Lp);\n    res = res + oracle_lb_keogh(B, U, Lo, L);"),
+    "lbnew_window_one_short": (
+        "        int jlo = imax(1, i - W), jhi = imin(L, i + W);\n        double m = INFINITY;",
+        "        int jlo = imax(1, i - W), jhi = imin(L, i + W - (W > 0));\n        double m = INFINITY;"),
+    "lbnew_drops_an_end": (
+        "    double res = delta(A[0], B[0]) + delta(A[L - 1], B[L - 1]);\n    for (int i = 2; i <= L - 1; i++) {",
+        "    double res = delta(A[0], B[0]);\n    for (int i = 2; i <= L - 1; i++) {"),
+    "lbnew_interior_runs_to_the_end": (
+        "    for (int i = 2; i <= L - 1; i++) {\n        int jlo",
+        "    for (int i = 2; i <= L; i++) {\n        int jlo"),
     "nn_ties_to_highest_index": ("if (d < best) { best = d; bi = t; }", "if (d <= best) { best = d; bi = t; }"),
     "loo_keeps_the_query_itself": ("if (j->exclude_self && t == q) continue;", ""),
     "pruned_search_drops_tie_update": (
