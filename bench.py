@@ -38,20 +38,32 @@ sys.path.insert(0, ROOT)
 METRIC = "exact NN-DTW queries/s + DTW GCUPS on 1 GB300: batched FP32 vs plain FP64 form"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
-def kernels_per_search(flags: int, nndtw) -> int:
-    """Kernels one FP32 search launches: envelopes, norms, bounds, DTW of the
-    first candidates, compaction (two passes), DTW, recheck filter and collect,
-    FP64 recheck, ties, final (12); with a cascade second stage also the query
-    envelopes and the filter; with the LB_Improved bridge also the second
-    envelopes and their packing."""
-    n = 12
-    rev = bool(flags & nndtw.REVERSE) and not flags & (nndtw.NO_PRUNE | nndtw.NO_REVERSE)
-    imp = bool(flags & nndtw.IMPROVED) and not flags & nndtw.NO_PRUNE
-    if rev or imp:
-        n += 2
-    if imp:
-        n += 2
-    return n
+def stage_bytes(shapes, flags_of, nndtw) -> dict:
+    """Algorithmic DRAM bytes per step of the two HBM-facing stages, from the
+    datasets' shapes (dicts with N, Q, L) and search flags.  Envelopes: each
+    training series read once (4 B/element) and its envelope pair written
+    (8 B); with the cascade's second stage the queries' envelopes too; with
+    the LB_Improved bridge the second envelopes (read 8, write 8) and their
+    packing (read 4 + 8, write 8).  Bounds: the squared norms read every
+    series once, the bound pass reads the queries, the training series and
+    their envelopes once (the compulsory traffic of a tiled pass) and writes
+    one FP32 bound per pair (and, with the reverse bound, one FP32 ends-and-
+    bands sum)."""
+    env = lb = 0
+    for d, f in zip(shapes, flags_of):
+        N, Q, L = d["N"], d["Q"], d["L"]
+        rev = bool(f & nndtw.REVERSE) and not f & (nndtw.NO_PRUNE | nndtw.NO_REVERSE |
+                                                     nndtw.KEOGH_BOUND)
+        imp = bool(f & nndtw.IMPROVED) and not f & (nndtw.NO_PRUNE | nndtw.KEOGH_BOUND)
+        env += 12 * N * L
+        if rev or imp:
+            env += 12 * Q * L
+        if imp:
+            env += (16 + 20) * N * L
+        lb += 4 * (Q + N) * L + 4 * (Q * L + 3 * N * L) + 4 * Q * N * (2 if rev else 1)
+    return {"envelopes": env, "lb": lb}
+
+
 INSTR_PER_CELL = 3       # FADD + 3-input FMNMX + FFMA
 INSTR_PER_LB_ELEM = 5    # bridge: FMNMX + FMNMX + FADD + FFMA; fused ED: FFMA (dot product)
 FP32_LANES_PER_SM = 128
@@ -480,6 +492,7 @@ def run_window(args):
         flush.zero_()
         run()
     torch.cuda.synchronize()
+    launches = nndtw.nn_dtw_last_call_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     sel = device_selector(torch, dev, 0)
@@ -517,8 +530,8 @@ def run_window(args):
                              "cores": default_threads(), "kind": "oracle",
                              "sample": f"leave-one-out brute force for W in {sample_w}, "
                                        f"{cpu_s:.1f} s"},
-            "gpu_launches": (kernels_per_search(nndtw.LEAVE_ONE_OUT, nndtw) * len(windows) + 1)
-                            * args.steps,
+            # the batched search's launches (library count) and the tally kernel
+            "gpu_launches": (launches + 1) * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -701,7 +714,8 @@ def main():
 
     # the timed step
     if batched:
-        bs = nndtw.BatchedSearch(sets, graph=not args.no_graph)
+        # stage events on the search's stream inside every timed step
+        bs = nndtw.BatchedSearch(sets, flags=nndtw.TIME_STAGES, graph=not args.no_graph)
         run = bs.run
         outs = bs.outs
     else:
@@ -734,9 +748,13 @@ def main():
     for _ in range(args.warmup):
         flush.zero_()
         run()
-        if not batched:
-            nndtw.nn_dtw_stage_times()
+        nndtw.nn_dtw_stage_times()
     torch.cuda.synchronize()
+    # kernel launches of one step, in all and per stage (library counts of the
+    # last search call this thread issued: the captured one when the step is a
+    # graph replay, which launches the same kernels)
+    launches_step = nndtw.nn_dtw_last_call_launches()
+    stage_launches = nndtw.nn_dtw_last_call_stage_launches()
 
     sel = device_selector(torch, dev, local)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -751,22 +769,8 @@ def main():
             ev_s[k].record(stream)
             run()
             ev_e[k].record(stream)
-            if not batched:
-                stages.append(nndtw.nn_dtw_stage_times())
-        torch.cuda.synchronize()
-        if batched:
-            # stage times of the same kernels: every dataset once more, one
-            # after another on this stream, with stage events (same inputs)
-            for _ in range(max(1, args.steps // 5)):
-                agg = dict.fromkeys(STAGES, 0.0)
-                flush.zero_()
-                for s in sets:
-                    nndtw.nn_dtw_search(s["train"], s["labels"], s["test"], s["W"], s["V"],
-                                        flags=s["flags"] | nndtw.TIME_STAGES)
-                    st = nndtw.nn_dtw_stage_times()
-                    for key in STAGES:
-                        agg[key] += st[key]
-                stages.append(agg)
+            # the step's own stage events (waits for this step to finish)
+            stages.append(nndtw.nn_dtw_stage_times())
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -786,17 +790,24 @@ def main():
     work = {"dtw": main_cells, "seed": seed_cells,
             "lb": sum(d.N * d.Q * d.L for d in dsets),
             "envelopes": sum(12 * d.N * d.L for d in dsets)}
-    # kernels per stage: the cascade's second stage adds the query envelopes
-    # (and, with the LB_Improved bridge, the second envelopes and their
-    # packing) to the envelope stage and its filter to the compaction stage
-    second = sum(1 for s in sets if kernels_per_search(s["flags"], nndtw) > 12)
-    packed = sum(1 for s in sets if kernels_per_search(s["flags"], nndtw) > 14)
-    launches = {"dtw": nds, "seed": nds, "lb": nds, "envelopes": nds + second + 2 * packed,
-                "compact": 2 * nds + second, "recheck": 4 * nds, "final": nds}
+    launches = {k: max(1, stage_launches.get(k, 1)) for k in STAGES[:7]}
     roof = roofline(stage_ms, launches, work, n_sm, sm_max, peaks, peak_src, probe, args.workload)
-    if batched:
-        roof["stage_timing"] = ("per-dataset searches run one after another with stage events "
-                                "(the timed step runs them concurrently in one graph)")
+    roof["stage_timing"] = ("CUDA events on the search's stream between its stages, in every "
+                            "timed step; each stage is one launch per kernel variant over all "
+                            "datasets, so a stage's time covers exactly its launches")
+    # achieved HBM bandwidth of the envelope and bound stages (algorithmic bytes)
+    sb = stage_bytes([dict(N=d.N, Q=d.Q, L=d.L) for d in dsets], [s["flags"] for s in sets],
+                     nndtw)
+    hbm_peak = float(peaks["hbm_gbs"])
+    hbm = {}
+    for key in ("envelopes", "lb"):
+        if stage_ms[key] > 0:
+            gbs = sb[key] / (stage_ms[key] * 1e-3) / 1e9
+            hbm[key] = {"algorithmic_bytes_per_step": sb[key], "ms_per_step": stage_ms[key],
+                        "launches_per_step": stage_launches.get(key, 0), "achieved_gbs": gbs,
+                        "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                        "peak_source": f"{peak_src} copy bandwidth"}
+    roof["hbm_stages"] = hbm
 
     # plain FP64 form, one dataset per call, same data promoted
     fp64 = None
@@ -817,29 +828,31 @@ def main():
                 "fp32_over_fp64": ms64 / ms, "form": "plain FP64, one dataset per call"}
         del t64
 
-    # end to end: host buffers in, the step, results out, every step
-    h_in = [(torch.from_numpy(d.train).pin_memory(), torch.from_numpy(d.test).pin_memory(),
-             torch.from_numpy(d.train_labels).pin_memory()) for d in dsets]
-    h_out = [tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in out)
-             for out in outs]
+    # end to end through the C ABI on host buffers: nn_dtw_search_batched_host
+    # copies every dataset's series and labels in from pinned memory, searches
+    # the batch and copies every result back, every step
+    pinned = []
+
+    def pin(x):
+        t = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        pinned.append(t)
+        return t.numpy()
+    hsets = [dict(train=pin(d.train), labels=pin(d.train_labels), test=pin(d.test), W=d.W,
+                  V=d.V, flags=s["flags"]) for d, s in zip(dsets, sets)]
+    houts = [(pin(np.empty(d.Q, np.int32)), pin(np.empty(d.Q, np.int32)),
+              pin(np.empty(d.Q, np.float64))) for d in dsets]
+    hb = nndtw.BatchedHostSearch(hsets, outs=houts, device=dev)
     e2e_t = []
     for k in range(args.steps + 2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for (tr, te, lab), s in zip(h_in, sets):
-            s["train"].copy_(tr, non_blocking=True)
-            s["test"].copy_(te, non_blocking=True)
-            s["labels"].copy_(lab, non_blocking=True)
-        run()
-        for ho, o in zip(h_out, outs):
-            for h, x in zip(ho, o):
-                h.copy_(x, non_blocking=True)
-        torch.cuda.synchronize()
+        hb.run()
         if k >= 2:
             e2e_t.append(time.perf_counter() - t0)
-    if not batched:
-        nndtw.nn_dtw_stage_times()
+    e2e_launches = nndtw.nn_dtw_last_call_launches()
     e2e_ms = max_over_ranks(1000.0 * sum(e2e_t) / len(e2e_t), dist, dev)
+    e2e_same = all(np.array_equal(h, o.cpu().numpy()) for ho, out in zip(houts, outs)
+                   for h, o in zip(ho, out))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -863,8 +876,13 @@ def main():
             "e2e": {"value": whole_job_rate(world, Qtot, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(d.train.nbytes + d.test.nbytes +
                                                   d.train_labels.nbytes for d in dsets)),
-                    "d2h_bytes_per_step": int(Qtot * (4 + 4 + 8)), "ms_per_step": e2e_ms},
-            "gpu_launches": sum(kernels_per_search(s["flags"], nndtw) for s in sets) * args.steps,
+                    "d2h_bytes_per_step": int(Qtot * (4 + 4 + 8)), "ms_per_step": e2e_ms,
+                    "call": "nn_dtw_search_batched_host (C ABI, pinned host buffers, direct "
+                            "launches)",
+                    "gpu_launches_per_step": e2e_launches,
+                    "results_equal_device_step": bool(e2e_same)},
+            "gpu_launches": launches_step * args.steps,
+            "gpu_launches_per_step_by_stage": stage_launches,
             "clocks": clocks,
             "gcups_effective": eff_cells / (ms * 1e-3) / 1e9,
             "gcups_dtw_kernel": (main_cells / (stage_ms["dtw"] * 1e-3) / 1e9

@@ -348,19 +348,22 @@ NNDTW_API size_t nn_dtw_batch_workspace_size(const nndtw_dataset *h_sets, int n)
 /*
  * Batched search (the paper's NN-DTW search, Sec. 4, over many independent
  * datasets at once): exactly the results of n separate nn_dtw_search calls.
- * The call records work on the caller's stream that forks onto the library's
- * internal streams (created once per device on first use), runs each
- * dataset's search there, largest first, and joins back into the caller's
- * stream, so datasets overlap on the GPU and the whole batch can be captured
- * as one CUDA graph.  h_sets: host array of n descriptors (read during the
- * call only); d_workspace: nn_dtw_batch_workspace_size() bytes, 256-byte
- * aligned.  flags apply to every dataset (NNDTW_TIME_STAGES is rejected).
- * Concurrent calls (from several host threads, on any streams) are
- * supported: calls on one device take a lock around the fork, the issue and
- * the join, so their GPU work may overlap but their stream and event
- * bookkeeping never interleaves.  Each call needs its own workspace.
- * Errors: NNDTW_EINVAL for invalid descriptors or sizes, NNDTW_ENOSPACE,
- * NNDTW_ECUDA.  On an error every forked stream is still joined.
+ * The datasets are searched together, stage by stage, all on `stream`: each
+ * stage of the search (envelopes, bounds, first candidates, compaction, the
+ * cascade's second stage, DTW, recheck, argmin) is one kernel launch over
+ * every dataset of the batch (one per kernel variant where datasets need
+ * different ones: tile shapes, DTW layouts), each dataset's CTAs working on
+ * its own descriptor, which travels in the launch's parameters; datasets with
+ * the most DTW work come first.  Batches of more than 64 datasets run as
+ * consecutive groups of 64.  The call allocates nothing, waits for nothing
+ * and can be captured in a CUDA graph.  h_sets: host array of n descriptors
+ * (read during the call only); d_workspace: nn_dtw_batch_workspace_size()
+ * bytes, 256-byte aligned.  flags apply to every dataset.  With
+ * NNDTW_TIME_STAGES (at most 64 datasets with Q > 0) the stage events span
+ * the whole batch (nn_dtw_stage_times).  Calls are independent of each
+ * other: several may run at once on different streams, each with its own
+ * workspace.  Errors: NNDTW_EINVAL for invalid descriptors or sizes,
+ * NNDTW_ENOSPACE, NNDTW_ECUDA.
  */
 NNDTW_API int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
                                     size_t workspace_bytes, unsigned flags, void *stream);
@@ -382,6 +385,42 @@ NNDTW_API int nn_dtw_search_host(const float *h_train, const int32_t *h_train_la
                        int32_t *h_nn_idx, int32_t *h_nn_label, double *h_nn_dist,
                        void *d_buffer, size_t buffer_bytes, nndtw_stats *stats,
                        void *stream);
+
+/*
+ * One dataset of nn_dtw_search_batched_host: the arguments of
+ * nn_dtw_search_host for one training set / test set pair (host buffers).
+ */
+typedef struct nndtw_host_dataset {
+    const float *h_train;          /* [N][L]                                   */
+    const int32_t *h_train_labels; /* [N]                                      */
+    int64_t N;
+    const float *h_test;           /* [Q][L]                                   */
+    int64_t Q;
+    int L, W, V;
+    int32_t *h_nn_idx;             /* [Q] outputs                              */
+    int32_t *h_nn_label;
+    double *h_nn_dist;
+    unsigned flags;                /* per-dataset flags, OR-ed with the call's */
+} nndtw_host_dataset;
+
+/* Bytes of device memory nn_dtw_search_batched_host needs for these
+ * datasets (every dataset's inputs and outputs plus the batched search's
+ * workspace).  0 if any dataset has invalid sizes. */
+NNDTW_API size_t nn_dtw_batch_host_buffer_size(const nndtw_host_dataset *h_sets, int n);
+
+/*
+ * nn_dtw_search_batched on HOST buffers (the batched search of Sec. 4 over
+ * many datasets, end to end): copies every dataset's training series, labels
+ * and test series into the caller's device buffer (one copy per array, in
+ * order on `stream`), runs nn_dtw_search_batched there, copies every
+ * dataset's results back to its host arrays and waits for the stream before
+ * returning.  Pinned host memory makes the copies asynchronous and faster;
+ * pageable memory also works.  d_buffer: nn_dtw_batch_host_buffer_size()
+ * bytes of device memory, 256-byte aligned.  Same results and errors as
+ * nn_dtw_search_batched (NNDTW_TIME_STAGES is rejected).
+ */
+NNDTW_API int nn_dtw_search_batched_host(const nndtw_host_dataset *h_sets, int n, void *d_buffer,
+                                         size_t buffer_bytes, unsigned flags, void *stream);
 
 /*
  * Measurement aid, not part of the method.  A search called with
@@ -406,6 +445,15 @@ NNDTW_API int nn_dtw_stage_times(float *h_ms);
 NNDTW_API size_t nn_dtw_probe_sink_bytes(void);
 NNDTW_API int nn_dtw_probe_cell_rate(void *d_sink, size_t sink_bytes, int iters,
                                      double *h_cells_per_s, void *stream);
+
+/* Measurement aid, not part of the method: the number of kernel launches
+ * that the calling thread's last FP32 search call (nn_dtw_search or
+ * nn_dtw_search_batched, and the calls built on them) issued. */
+NNDTW_API long long nn_dtw_last_call_launches(void);
+/* The same launches by stage: h_counts[k] (k < 7, NNDTW_STAGE_*) counts those
+ * issued between stage boundaries k and k+1 (the start of the search counts
+ * as stage 0, the cascade's second stage as compaction); h_counts[7] is 0. */
+NNDTW_API int nn_dtw_last_call_stage_launches(long long *h_counts);
 
 /* Static description of a status code.  Never NULL. */
 NNDTW_API const char *nn_dtw_strerror(int code);

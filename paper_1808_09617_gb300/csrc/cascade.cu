@@ -77,9 +77,15 @@ __device__ __forceinline__ T keogh_term(T b, T lo, T hi) {
 
 // bg[k] = (B_k, gaps to the second envelopes rounded down), in place over
 // env2 (each thread reads its element before writing it).
-__global__ void pack_bgap_kernel(const float *__restrict__ train, float2 *env2, long long n) {
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+template <typename Src>
+__global__ void pack_bgap_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const PackJob &job = src.get(bid, nblk);
+    const float *__restrict__ train = job.train;
+    float2 *env2 = reinterpret_cast<float2 *>(job.env2);
+    const long long n = job.n;
+    for (long long k = (long long)bid * blockDim.x + threadIdx.x; k < n;
+         k += (long long)nblk * blockDim.x) {
         const float b = train[k];
         const float2 o = env2[k];
         BGap r;
@@ -89,14 +95,16 @@ __global__ void pack_bgap_kernel(const float *__restrict__ train, float2 *env2, 
     }
 }
 
-template <bool REV, bool IMP>
-__global__ void __launch_bounds__(256) cascade_filter_kernel(CascadeJob job) {
+template <bool REV, bool IMP, typename Src>
+__global__ void __launch_bounds__(256) cascade_filter_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const CascadeJob &job = src.get(bid, nblk);
     constexpr int G = kGroup;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, gl = lane & (G - 1), grp = lane / G;
     const long long n = (long long)*job.in_count;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
+    const long long n_warps = ((long long)nblk * blockDim.x) >> 5;
     const int L = job.L, nb = job.nb;
     for (long long base = warp * 32; base < n; base += n_warps * 32) {
         const int m = (int)(n - base < 32 ? n - base : 32);
@@ -228,29 +236,60 @@ improved_terms_kernel(const T *__restrict__ train, const T2 *__restrict__ envq,
 
 }  // namespace
 
-cudaError_t launch_cascade_filter(const CascadeJob &job, long long max_pairs, int sm_count,
-                                  cudaStream_t s) {
-    if (max_pairs <= 0) return cudaSuccess;
-    const bool rev = job.ends != nullptr, imp = job.bgap != nullptr;
-    if (!rev && !imp) return cudaErrorInvalidValue;
+long long cascade_filter_blocks(long long max_pairs, int sm_count) {
+    if (max_pairs <= 0) return 0;
     // warps: enough for the largest possible queue, at most 64 per SM
     // (residency is what hides the load latency)
     long long warps = (max_pairs + 31) / 32;
     const long long cap = (long long)sm_count * 64;
     if (warps > cap) warps = cap;
-    const unsigned grid = (unsigned)((warps + 7) / 8);
-    if (rev && imp) cascade_filter_kernel<true, true><<<grid, 256, 0, s>>>(job);
-    else if (rev) cascade_filter_kernel<true, false><<<grid, 256, 0, s>>>(job);
-    else cascade_filter_kernel<false, true><<<grid, 256, 0, s>>>(job);
+    return (warps + 7) / 8;
+}
+
+CascadeFns cascade_filter_fns(bool rev, bool imp) {
+    CascadeFns f{};
+    if (rev && imp) {
+        f.fn1 = cascade_filter_kernel<true, true, Src1<CascadeJob>>;
+        f.fnN = cascade_filter_kernel<true, true, SrcN<CascadeJob>>;
+    } else if (rev) {
+        f.fn1 = cascade_filter_kernel<true, false, Src1<CascadeJob>>;
+        f.fnN = cascade_filter_kernel<true, false, SrcN<CascadeJob>>;
+    } else if (imp) {
+        f.fn1 = cascade_filter_kernel<false, true, Src1<CascadeJob>>;
+        f.fnN = cascade_filter_kernel<false, true, SrcN<CascadeJob>>;
+    }
+    return f;
+}
+
+cudaError_t launch_cascade_filter(const CascadeJob &job, long long max_pairs, int sm_count,
+                                  cudaStream_t s) {
+    const long long grid = cascade_filter_blocks(max_pairs, sm_count);
+    if (grid <= 0) return cudaSuccess;
+    const bool rev = job.ends != nullptr, imp = job.bgap != nullptr;
+    if (!rev && !imp) return cudaErrorInvalidValue;
+    cascade_filter_fns(rev, imp).fn1<<<(unsigned)grid, 256, 0, s>>>(Src1<CascadeJob>{job});
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_bgap(const float *train, float *env2, long long n, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+long long pack_bgap_blocks(long long n) {
+    if (n <= 0) return 0;
     long long blocks = (n + 255) / 256;
     const long long cap = (long long)device_sm_count() * 16;
-    if (blocks > cap) blocks = cap;
-    pack_bgap_kernel<<<(unsigned)blocks, 256, 0, s>>>(train, reinterpret_cast<float2 *>(env2), n);
+    return blocks > cap ? cap : blocks;
+}
+
+PackFns pack_bgap_fns() {
+    PackFns f;
+    f.fn1 = pack_bgap_kernel<Src1<PackJob>>;
+    f.fnN = pack_bgap_kernel<SrcN<PackJob>>;
+    return f;
+}
+
+cudaError_t launch_pack_bgap(const float *train, float *env2, long long n, cudaStream_t s) {
+    const long long blocks = pack_bgap_blocks(n);
+    if (blocks <= 0) return cudaSuccess;
+    PackJob j{train, env2, n};
+    pack_bgap_kernel<<<(unsigned)blocks, 256, 0, s>>>(Src1<PackJob>{j});
     return cudaGetLastError();
 }
 

@@ -88,9 +88,12 @@ __host__ __device__ constexpr int dtw32_min_blocks(int H) {
     return H <= 4 ? 8 : H <= 9 ? 6 : H <= 11 ? 5 : H <= 15 ? 4 : H <= 23 ? 3 : 2;
 }
 
-template <int H, int U>
+template <int H, int U, typename Src>
 __global__ void __launch_bounds__(128, dtw32_min_blocks(H))
-dtw32_kernel(DtwJob32 job, int G) {
+dtw32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob32 &job = src.get(bid, nblk);
+    const int G = job.lanes;
     constexpr int C = 2 * H;
     const float INF = __int_as_float(0x7f800000);
     const float APAD = Pad<float>::v, BPAD = -Pad<float>::v, EPAD = Pad<float>::v;
@@ -118,7 +121,7 @@ dtw32_kernel(DtwJob32 job, int G) {
 
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
-    const long long n_groups = (long long)gridDim.x * (blockDim.x / G);
+    const long long n_groups = (long long)nblk * (blockDim.x / G);
     const bool check_bsf = job.abandon && job.bsf;
     // abandon checks every 16 super-steps, at the same block for the whole warp
     constexpr int kCheckBlocks = 16 / U > 1 ? 16 / U : 1;
@@ -128,7 +131,7 @@ dtw32_kernel(DtwJob32 job, int G) {
     // group's next pair with its item w1 already requested.  `nxt` is the
     // next static index, or (dynamic claims) the claim after p1, still in
     // flight in the group's lane 0.
-    long long nxt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    long long nxt = ((long long)bid * blockDim.x + threadIdx.x) / G;
     long long p1;
     if (job.head) {
         unsigned long long v = 0;

@@ -8,14 +8,14 @@ namespace nndtw {
 
 namespace {
 
-Dtw32Fn pick_fn(int H) {
+bool pick_fn(int H, Dtw32Fn1 *f1, Dtw32FnN *fn) {
     switch (H) {
-#define C_(h) case h: return dtw32_fn<h>();
+#define C_(h) case h: *f1 = dtw32_fn<h>(); *fn = dtw32_fn_n<h>(); return true;
         C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13)
         C_(14) C_(15) C_(16) C_(17) C_(18) C_(19) C_(20) C_(21) C_(22) C_(23) C_(24) C_(25)
         C_(26) C_(27) C_(28) C_(29) C_(30) C_(31) C_(32)
 #undef C_
-        default: return nullptr;
+        default: return false;
     }
 }
 
@@ -62,20 +62,19 @@ int dtw32_wide_group(int W) {
 // L <= NNDTW_MAX_L) the shared-memory band kernel.
 bool dtw32_supported(int W) { return W >= 0 && W < NNDTW_MAX_L; }
 
-cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
-    // full windows: the row kernel, unless a diagonal group width is asked for
+cudaError_t plan_dtw32(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
+    // full windows: the row kernels, unless a diagonal group width is asked for
     if (job.group == kRowsGroup + 1 && dtw32_rowsg_ok(job.L, job.W, 16))
-        return launch_dtw32_rowsg(job, 16, sm_count, s);
+        return plan_dtw32_rowsg(job, 16, sm_count, p);
     if (job.group == kRowsGroup + 2 && dtw32_rowsg_ok(job.L, job.W, 8))
-        return launch_dtw32_rowsg(job, 8, sm_count, s);
+        return plan_dtw32_rowsg(job, 8, sm_count, p);
     if ((job.group == 0 || job.group >= kRowsGroup) && dtw32_rows_ok(job.L, job.W))
-        return launch_dtw32_rows(job, sm_count, s);
+        return plan_dtw32_rows(job, sm_count, p);
     if ((job.group == 0 || job.group >= kRowsGroup) && dtw32_rowsc_ok(job.L, job.W))
-        return launch_dtw32_rowsc(job, sm_count, s);
+        return plan_dtw32_rowsc(job, sm_count, p);
     int G = 0, H = 0;
-    if (!dtw32_shape(job.W, job.group, &G, &H)) return launch_dtw32_wide(job, sm_count, s);
-    Dtw32Fn fn = pick_fn(H);
-    if (!fn) return cudaErrorNotSupported;
+    if (!dtw32_shape(job.W, job.group, &G, &H)) return plan_dtw32_wide(job, sm_count, p);
+    if (!pick_fn(H, &p->fn1, &p->fnN)) return cudaErrorNotSupported;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -84,7 +83,7 @@ cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
         std::lock_guard<std::mutex> lk(g_occ.mu);
         if (dev < 64) bps = g_occ.blocks[H][dev];
         if (bps == 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, 128, 0);
             if (e != cudaSuccess) return e;
             if (bps < 1) bps = 1;
             if (dev < 64) g_occ.blocks[H][dev] = bps;
@@ -93,12 +92,25 @@ cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s) {
     long long grid = (long long)sm_count * bps;
     if (!job.pairs || !job.count) {
         const long long n = job.pairs ? job.n_pairs : job.n_seed;
-        if (n <= 0) return cudaSuccess;
         const long long groups_per_block = 128 / G;
-        const long long need = (n + groups_per_block - 1) / groups_per_block;
+        const long long need = n > 0 ? (n + groups_per_block - 1) / groups_per_block : 0;
         if (need < grid) grid = need;
     }
-    fn<<<(unsigned)grid, 128, 0, s>>>(job, G);
+    p->threads = 128;
+    p->smem = 0;
+    p->blocks = grid;
+    p->lanes = G;
+    return cudaSuccess;
+}
+
+cudaError_t launch_dtw32(const DtwJob32 &job_in, int sm_count, cudaStream_t s) {
+    Dtw32Plan p{};
+    cudaError_t e = plan_dtw32(job_in, sm_count, &p);
+    if (e != cudaSuccess) return e;
+    if (p.blocks <= 0) return cudaSuccess;
+    DtwJob32 job = job_in;
+    job.lanes = p.lanes;
+    p.fn1<<<(unsigned)p.blocks, p.threads, p.smem, s>>>(Src1<DtwJob32>{job});
     return cudaGetLastError();
 }
 

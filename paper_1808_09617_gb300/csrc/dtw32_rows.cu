@@ -114,9 +114,11 @@ __device__ __forceinline__ bool rows_cut_exceeds(const float (&D)[C], float diag
     return lower32(mn, job.dtw_lo, job.abs32) > ub;
 }
 
-template <int C>
+template <int C, typename Src>
 __global__ void __launch_bounds__(128, rows_min_blocks(C))
-dtw32_rows_kernel(DtwJob32 job) {
+dtw32_rows_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob32 &job = src.get(bid, nblk);
     // K independent dependency chains per lane: with K = 2 the lane's columns
     // are split into halves, the second half one row behind the first.
     constexpr int K = C >= 4 ? 2 : 1;
@@ -126,8 +128,8 @@ dtw32_rows_kernel(DtwJob32 job) {
     const unsigned FULL = 0xffffffffu;
     const int L = job.L;
     const int lane = threadIdx.x & 31;
-    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int warp_g = (bid * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (nblk * blockDim.x) >> 5;
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
     const int last_lane = (L - 1) / C, last_c = (L - 1) % C;
@@ -254,33 +256,39 @@ dtw32_rows_kernel(DtwJob32 job) {
 }
 
 namespace {
-using RowsFn = void (*)(DtwJob32);
-template <int C> RowsFn rows_fn() { return &dtw32_rows_kernel<C>; }
-template <int... Cs> RowsFn pick_rows(int c, std::integer_sequence<int, Cs...>) {
-    RowsFn fns[] = {rows_fn<Cs + 1>()...};
-    return (c >= 1 && c <= (int)sizeof...(Cs)) ? fns[c - 1] : nullptr;
+template <int C> Dtw32Fn1 rows_fn1() { return &dtw32_rows_kernel<C, Src1<DtwJob32>>; }
+template <int C> Dtw32FnN rows_fnn() { return &dtw32_rows_kernel<C, SrcN<DtwJob32>>; }
+template <int... Cs>
+void pick_rows(int c, std::integer_sequence<int, Cs...>, Dtw32Fn1 *f1, Dtw32FnN *fn) {
+    const Dtw32Fn1 a[] = {rows_fn1<Cs + 1>()...};
+    const Dtw32FnN b[] = {rows_fnn<Cs + 1>()...};
+    const bool ok = c >= 1 && c <= (int)sizeof...(Cs);
+    *f1 = ok ? a[c - 1] : nullptr;
+    *fn = ok ? b[c - 1] : nullptr;
 }
 }  // namespace
 
 bool dtw32_rows_ok(int L, int W) { return W >= L - 1 && L >= 1 && L <= 32 * 64; }
 
-cudaError_t launch_dtw32_rows(const DtwJob32 &job, int sm_count, cudaStream_t s) {
+cudaError_t plan_dtw32_rows(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
     const int C = (job.L + 31) / 32;
-    RowsFn fn = pick_rows(C, std::make_integer_sequence<int, 64>{});
-    if (!fn) return cudaErrorNotSupported;
+    pick_rows(C, std::make_integer_sequence<int, 64>{}, &p->fn1, &p->fnN);
+    if (!p->fn1) return cudaErrorNotSupported;
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, 128, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     long long grid = (long long)sm_count * bps;
     if (!job.pairs || !job.count) {
         const long long n = job.pairs ? job.n_pairs : job.n_seed;
-        if (n <= 0) return cudaSuccess;
-        const long long need = (n + 3) / 4;
+        const long long need = n > 0 ? (n + 3) / 4 : 0;
         if (need < grid) grid = need;
     }
-    fn<<<(unsigned)grid, 128, 0, s>>>(job);
-    return cudaGetLastError();
+    p->threads = 128;
+    p->smem = 0;
+    p->blocks = grid;
+    p->lanes = 32;
+    return cudaSuccess;
 }
 
 }  // namespace nndtw

@@ -75,9 +75,11 @@ __device__ __forceinline__ void rowsc_advance(const float (&Din)[C], float (&Dou
     }
 }
 
-template <int C, int NW>
+template <int C, int NW, typename Src>
 __global__ void __launch_bounds__(32 * NW, rowsc_min_blocks(C, NW))
-dtw32_rowsc_kernel(DtwJob32 job) {
+dtw32_rowsc_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob32 &job = src.get(bid, nblk);
     constexpr int kWarps = NW, kLanes = 32 * NW;
     constexpr int K = C >= 4 ? 2 : 1;
     constexpr int C0 = K == 2 ? (C + 1) / 2 : C;
@@ -97,7 +99,7 @@ dtw32_rowsc_kernel(DtwJob32 job) {
     __shared__ int stop;
     __shared__ float result;
 
-    long long next_static = blockIdx.x;
+    long long next_static = bid;
     while (true) {
         long long p;
         if (job.head) {
@@ -107,7 +109,7 @@ dtw32_rowsc_kernel(DtwJob32 job) {
             __syncthreads();
         } else {
             p = next_static;
-            next_static += gridDim.x;
+            next_static += nblk;
         }
         if (p >= n_work) break;
         const uint2 w1 = work_item(job, p, n_work);
@@ -229,10 +231,13 @@ dtw32_rowsc_kernel(DtwJob32 job) {
 // C = 17 .. 32 columns per lane: L in (2048, 4096] over 4 warps, (4096, 8192]
 // over 8 warps
 constexpr int kCMin = 17, kCMax = 32;
-using RowsCFn = void (*)(DtwJob32);
-template <int C, int NW> RowsCFn rowsc_fn() { return &dtw32_rowsc_kernel<C, NW>; }
-template <int NW, int... Cs> RowsCFn pick_rowsc(int c, std::integer_sequence<int, Cs...>) {
-    RowsCFn fns[] = {rowsc_fn<Cs + kCMin, NW>()...};
+// (one-dataset form only: series this long are rare in a batch, whose
+// planner then launches them on their own)
+template <int C, int NW> Dtw32Fn1 rowsc_fn() {
+    return &dtw32_rowsc_kernel<C, NW, Src1<DtwJob32>>;
+}
+template <int NW, int... Cs> Dtw32Fn1 pick_rowsc(int c, std::integer_sequence<int, Cs...>) {
+    Dtw32Fn1 fns[] = {rowsc_fn<Cs + kCMin, NW>()...};
     return (c >= kCMin && c <= kCMax) ? fns[c - kCMin] : nullptr;
 }
 
@@ -242,25 +247,28 @@ int rowsc_warps(int L) { return L > 32 * 4 * kCMax ? 8 : 4; }
 
 bool dtw32_rowsc_ok(int L, int W) { return W >= L - 1 && L > 32 * 64 && L <= 32 * 8 * kCMax; }
 
-cudaError_t launch_dtw32_rowsc(const DtwJob32 &job, int sm_count, cudaStream_t s) {
+cudaError_t plan_dtw32_rowsc(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
     if (!dtw32_rowsc_ok(job.L, job.W)) return cudaErrorNotSupported;
     const int NW = rowsc_warps(job.L), kLanes = 32 * NW;
     const int C = (job.L + kLanes - 1) / kLanes;
     using Seq = std::make_integer_sequence<int, kCMax - kCMin + 1>;
-    RowsCFn fn = NW == 8 ? pick_rowsc<8>(C, Seq{}) : pick_rowsc<4>(C, Seq{});
-    if (!fn) return cudaErrorNotSupported;
+    p->fn1 = NW == 8 ? pick_rowsc<8>(C, Seq{}) : pick_rowsc<4>(C, Seq{});
+    p->fnN = nullptr;
+    if (!p->fn1) return cudaErrorNotSupported;
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kLanes, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, kLanes, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     long long grid = (long long)sm_count * bps;
     if (!job.pairs || !job.count) {
         const long long n = job.pairs ? job.n_pairs : job.n_seed;
-        if (n <= 0) return cudaSuccess;
-        if (n < grid) grid = n;
+        if (n < grid) grid = n > 0 ? n : 0;
     }
-    fn<<<(unsigned)grid, kLanes, 0, s>>>(job);
-    return cudaGetLastError();
+    p->threads = kLanes;
+    p->smem = 0;
+    p->blocks = grid;
+    p->lanes = kLanes;
+    return cudaSuccess;
 }
 
 }  // namespace nndtw

@@ -76,9 +76,12 @@ __device__ __forceinline__ void rowsg_step(const float (&Din)[C], float (&Dout)[
     }
 }
 
-template <int C>
+template <int C, typename Src>
 __global__ void __launch_bounds__(128, rowsg_min_blocks(C))
-dtw32_rowsg_kernel(DtwJob32 job, int G) {
+dtw32_rowsg_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob32 &job = src.get(bid, nblk);
+    const int G = job.lanes;
     constexpr int K = C >= 4 ? 2 : 1;
     constexpr int C0 = K == 2 ? (C + 1) / 2 : C;
     const float INF = inf_of<float>();
@@ -94,11 +97,11 @@ dtw32_rowsg_kernel(DtwJob32 job, int G) {
     const int s_final = steps_total - 1;
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
-    const long long n_groups = (long long)gridDim.x * (blockDim.x / G);
+    const long long n_groups = (long long)nblk * (blockDim.x / G);
     const bool check_bsf = job.abandon && job.bsf;
 
     // claims two pairs ahead per group (see the diagonal-layout kernel)
-    long long nxt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    long long nxt = ((long long)bid * blockDim.x + threadIdx.x) / G;
     long long p1;
     if (job.head) {
         unsigned long long v = 0;
@@ -227,11 +230,15 @@ dtw32_rowsg_kernel(DtwJob32 job, int G) {
     }
 }
 
-using RowsGFn = void (*)(DtwJob32, int);
-template <int C> RowsGFn rowsg_fn() { return &dtw32_rowsg_kernel<C>; }
-template <int... Cs> RowsGFn pick_rowsg(int c, std::integer_sequence<int, Cs...>) {
-    RowsGFn fns[] = {rowsg_fn<Cs + 1>()...};
-    return (c >= 1 && c <= (int)sizeof...(Cs)) ? fns[c - 1] : nullptr;
+template <int C> Dtw32Fn1 rowsg_fn1() { return &dtw32_rowsg_kernel<C, Src1<DtwJob32>>; }
+template <int C> Dtw32FnN rowsg_fnn() { return &dtw32_rowsg_kernel<C, SrcN<DtwJob32>>; }
+template <int... Cs>
+void pick_rowsg(int c, std::integer_sequence<int, Cs...>, Dtw32Fn1 *f1, Dtw32FnN *fn) {
+    const Dtw32Fn1 a[] = {rowsg_fn1<Cs + 1>()...};
+    const Dtw32FnN b[] = {rowsg_fnn<Cs + 1>()...};
+    const bool ok = c >= 1 && c <= (int)sizeof...(Cs);
+    *f1 = ok ? a[c - 1] : nullptr;
+    *fn = ok ? b[c - 1] : nullptr;
 }
 
 }  // namespace
@@ -240,25 +247,27 @@ bool dtw32_rowsg_ok(int L, int W, int G) {
     return (G == 8 || G == 16) && W >= L - 1 && L >= 1 && L <= 64 * G;
 }
 
-cudaError_t launch_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, cudaStream_t s) {
+cudaError_t plan_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, Dtw32Plan *p) {
     if (!dtw32_rowsg_ok(job.L, job.W, G)) return cudaErrorNotSupported;
     const int C = (job.L + G - 1) / G;
-    RowsGFn fn = pick_rowsg(C, std::make_integer_sequence<int, 64>{});
-    if (!fn) return cudaErrorNotSupported;
+    pick_rowsg(C, std::make_integer_sequence<int, 64>{}, &p->fn1, &p->fnN);
+    if (!p->fn1) return cudaErrorNotSupported;
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, 128, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     long long grid = (long long)sm_count * bps;
     if (!job.pairs || !job.count) {
         const long long n = job.pairs ? job.n_pairs : job.n_seed;
-        if (n <= 0) return cudaSuccess;
         const long long per_block = 128 / G;
-        const long long need = (n + per_block - 1) / per_block;
+        const long long need = n > 0 ? (n + per_block - 1) / per_block : 0;
         if (need < grid) grid = need;
     }
-    fn<<<(unsigned)grid, 128, 0, s>>>(job, G);
-    return cudaGetLastError();
+    p->threads = 128;
+    p->smem = 0;
+    p->blocks = grid;
+    p->lanes = G;
+    return cudaSuccess;
 }
 
 }  // namespace nndtw

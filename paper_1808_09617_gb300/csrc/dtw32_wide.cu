@@ -16,8 +16,12 @@ namespace {
 
 constexpr int kWideWarps = 4;
 
+template <typename Src>
 __global__ void __launch_bounds__(32 * kWideWarps)
-dtw32_wide_kernel(DtwJob32 job, int warps_per_block) {
+dtw32_wide_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob32 &job = src.get(bid, nblk);
+    const int warps_per_block = job.lanes;   // this kernel's launch shape: warps per CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= warps_per_block) return;
@@ -27,8 +31,8 @@ dtw32_wide_kernel(DtwJob32 job, int warps_per_block) {
     const float INF = inf_of<float>();
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
-    const long long n_warps = (long long)gridDim.x * warps_per_block;
-    long long next_static = (long long)blockIdx.x * warps_per_block + warp;
+    const long long n_warps = (long long)nblk * warps_per_block;
+    long long next_static = (long long)bid * warps_per_block + warp;
 
     while (true) {
         unsigned long long p = 0;
@@ -110,23 +114,28 @@ dtw32_wide_kernel(DtwJob32 job, int warps_per_block) {
 
 }  // namespace
 
-cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s) {
+cudaError_t plan_dtw32_wide(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
     const long long n = job.pairs ? job.n_pairs : job.n_seed;
-    if ((!job.pairs || !job.count) && n <= 0) return cudaSuccess;
     const size_t per_warp = sizeof(float) * (size_t)(2 * job.W + 3);
     int wpb = (int)((200u * 1024u) / per_warp);
     if (wpb > kWideWarps) wpb = kWideWarps;
     if (wpb < 1) return cudaErrorInvalidValue;
     const size_t smem = per_warp * wpb;
-    cudaError_t e = cudaFuncSetAttribute(dtw32_wide_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    p->fn1 = &dtw32_wide_kernel<Src1<DtwJob32>>;
+    p->fnN = &dtw32_wide_kernel<SrcN<DtwJob32>>;
+    cudaError_t e = cudaFuncSetAttribute(p->fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(p->fnN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long cap = (long long)sm_count * 16;
-    long long grid = (job.pairs && job.count) ? cap : (n + wpb - 1) / wpb;
+    long long grid = (job.pairs && job.count) ? cap : (n > 0 ? (n + wpb - 1) / wpb : 0);
     if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    dtw32_wide_kernel<<<(unsigned)grid, 32 * kWideWarps, smem, s>>>(job, wpb);
-    return cudaGetLastError();
+    p->threads = 32 * kWideWarps;
+    p->smem = smem;
+    p->blocks = grid;
+    p->lanes = wpb;
+    return cudaSuccess;
 }
 
 }  // namespace nndtw

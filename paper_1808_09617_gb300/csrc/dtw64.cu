@@ -40,9 +40,11 @@ constexpr size_t kDtw64SmemCap = 227 * 1024;
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
-template <bool F32IN, bool F32STAGE, bool STAGED>
+template <bool F32IN, bool F32STAGE, bool STAGED, typename Src>
 __global__ void __launch_bounds__(256)
-dtw64_kernel(DtwJob64 job) {
+dtw64_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const DtwJob64 &job = src.get(bid, nblk);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = job.L, W = job.W;
     const int nslot = 2 * W + 3;
@@ -57,7 +59,7 @@ dtw64_kernel(DtwJob64 job) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long INFB = 0x7ff0000000000000ll;
     const long long n_work = job.count ? (long long)*job.count : job.n_pairs;
-    long long next_static = blockIdx.x;
+    long long next_static = bid;
 
     while (true) {
         long long p;
@@ -68,7 +70,7 @@ dtw64_kernel(DtwJob64 job) {
             __syncthreads();
         } else {
             p = next_static;
-            next_static += gridDim.x;
+            next_static += nblk;
         }
         if (p >= n_work) break;
         int q, t;
@@ -221,41 +223,54 @@ dtw64_kernel(DtwJob64 job) {
 
 
 template <bool F32IN, bool F32STAGE, bool STAGED>
-cudaError_t launch_dtw64_as(const DtwJob64 &job, size_t smem, int sm_count, cudaStream_t s) {
-    auto fn = dtw64_kernel<F32IN, F32STAGE, STAGED>;
+cudaError_t plan_dtw64_as(const DtwJob64 &job, size_t smem, int sm_count, Dtw64Plan *p) {
+    p->fn1 = dtw64_kernel<F32IN, F32STAGE, STAGED, Src1<DtwJob64>>;
+    p->fnN = dtw64_kernel<F32IN, F32STAGE, STAGED, SrcN<DtwJob64>>;
     // threads: enough for the widest anti-diagonal (W+1 cells), 32..256
     int threads = ((job.W / 2 + 1) + 31) / 32 * 32;
     if (threads > 256) threads = 256;
     if (threads < 32) threads = 32;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(p->fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(p->fnN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, threads, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     const long long cap = (long long)sm_count * bps;
     long long grid = job.count ? cap : (job.n_pairs < cap ? job.n_pairs : cap);
-    if (grid < 1) grid = 1;
-    fn<<<(unsigned)grid, threads, smem, s>>>(job);
-    return cudaGetLastError();
+    p->threads = threads;
+    p->smem = smem;
+    p->blocks = grid > 0 ? grid : 0;
+    return cudaSuccess;
 }
 
 }  // namespace
 
-cudaError_t launch_dtw64(const DtwJob64 &job_in, int sm_count, cudaStream_t s) {
-    if (!job_in.count && job_in.n_pairs <= 0) return cudaSuccess;
-    const DtwJob64 &job = job_in;
+cudaError_t plan_dtw64(const DtwJob64 &job, int sm_count, Dtw64Plan *p) {
     const size_t band = sizeof(long long) * (size_t)(2 * job.W + 3);
     const size_t as_f64 = sizeof(double) * 2 * (size_t)job.L;
     const size_t as_f32 = sizeof(float) * 2 * (size_t)job.L;
     if (band + as_f64 <= kDtw64SmemCap)
-        return job.test32 ? launch_dtw64_as<true, false, true>(job, band + as_f64, sm_count, s)
-                          : launch_dtw64_as<false, false, true>(job, band + as_f64, sm_count, s);
+        return job.test32 ? plan_dtw64_as<true, false, true>(job, band + as_f64, sm_count, p)
+                          : plan_dtw64_as<false, false, true>(job, band + as_f64, sm_count, p);
     if (job.test32) {
         if (band + as_f32 > kDtw64SmemCap) return cudaErrorInvalidValue;
-        return launch_dtw64_as<true, true, true>(job, band + as_f32, sm_count, s);
+        return plan_dtw64_as<true, true, true>(job, band + as_f32, sm_count, p);
     }
-    return launch_dtw64_as<false, false, false>(job, band, sm_count, s);
+    return plan_dtw64_as<false, false, false>(job, band, sm_count, p);
+}
+
+cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s) {
+    if (!job.count && job.n_pairs <= 0) return cudaSuccess;
+    Dtw64Plan p{};
+    cudaError_t e = plan_dtw64(job, sm_count, &p);
+    if (e != cudaSuccess) return e;
+    if (p.blocks <= 0) return cudaSuccess;
+    p.fn1<<<(unsigned)p.blocks, p.threads, p.smem, s>>>(Src1<DtwJob64>{job});
+    return cudaGetLastError();
 }
 
 }  // namespace nndtw

@@ -20,7 +20,7 @@
 namespace nndtw {
 namespace {
 
-constexpr int kEnvThreads = 256;
+constexpr int kEnvThreads = kEnvelopeThreads;
 
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
@@ -33,12 +33,18 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 // computes both channels in one pass over tile prefixes P, suffixes S and
 // tile tables M ([NP][L], [NP][L], [NP][levels+1][nt]); NP = 1 runs one
 // channel per pass in half the shared memory (the longest FP64 series).
-template <typename T, int NP>
+template <typename T, int NP, typename Src>
 __global__ void __launch_bounds__(kEnvThreads)
-envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64_t N, int L,
-                int W, T *__restrict__ env, int T_tile, int levels) {
+envelope_kernel(const __grid_constant__ Src src) {
     // env_in == nullptr: envelopes of train; else the second envelopes of
     // env_in ([N][L] (U, Lo)): window max of Lo and window min of U
+    int bid, nblk;
+    const EnvJob<T> &job = src.get(bid, nblk);
+    const T *__restrict__ train = job.train;
+    const T *__restrict__ env_in = job.env_in;
+    const int64_t N = job.N;
+    const int L = job.L, W = job.W, T_tile = job.T_tile, levels = job.levels;
+    T *__restrict__ env = job.env;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nt = (L + T_tile - 1) / T_tile;
     T *P = reinterpret_cast<T *>(smem_raw);                 // [NP][L]
@@ -50,7 +56,7 @@ envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64
     const int r = lane & (T_tile - 1);
     const T NEG = -inf_of<T>();
 
-    for (int64_t s = blockIdx.x; s < N; s += gridDim.x) {
+    for (int64_t s = bid; s < N; s += nblk) {
         const T *x = env_in ? nullptr : train + s * (int64_t)L;
         const T *ein = env_in ? env_in + s * 2 * (int64_t)L : nullptr;
         T *out = env + s * 2 * (int64_t)L;
@@ -126,11 +132,12 @@ envelope_kernel(const T *__restrict__ train, const T *__restrict__ env_in, int64
     }
 }
 
+}  // namespace
+
 template <typename T>
-cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, int L, int W,
-                                   T *env, cudaStream_t s) {
-    if (N <= 0) return cudaSuccess;
-    int Weff = W > L - 1 ? L - 1 : W;
+EnvPlan<T> plan_envelopes(const T *train, const T *env_in, int64_t N, int L, int W, T *env) {
+    EnvPlan<T> p{};
+    const int Weff = W > L - 1 ? L - 1 : W;
     int T_tile = 1, levels = 0;
     if (Weff >= 32) {
         T_tile = 32;
@@ -142,17 +149,49 @@ cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, i
     const int nt = (L + T_tile - 1) / T_tile;
     // both channels in one pass when they fit, else one channel per pass
     const size_t per_channel = sizeof(T) * (2 * (size_t)L + (size_t)(levels + 1) * nt);
-    const bool one_pass = 2 * per_channel <= 200u * 1024u;
-    const size_t smem = one_pass ? 2 * per_channel : per_channel;
-    auto fn = one_pass ? envelope_kernel<T, 2> : envelope_kernel<T, 1>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    p.one_pass = 2 * per_channel <= 200u * 1024u;
+    p.smem = p.one_pass ? 2 * per_channel : per_channel;
     const int sms = device_sm_count();
-    int64_t grid = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
-    fn<<<(unsigned)grid, kEnvThreads, smem, s>>>(train, env_in, N, L, Weff, env, T_tile, levels);
-    return cudaGetLastError();
+    p.blocks = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
+    p.job = EnvJob<T>{train, env_in, N, L, Weff, T_tile, levels, env};
+    return p;
 }
 
+template <typename T>
+EnvFns<T> envelope_fns(bool one_pass) {
+    EnvFns<T> f;
+    if (one_pass) {
+        f.fn1 = envelope_kernel<T, 2, Src1<EnvJob<T>>>;
+        f.fnN = envelope_kernel<T, 2, SrcN<EnvJob<T>>>;
+    } else {
+        f.fn1 = envelope_kernel<T, 1, Src1<EnvJob<T>>>;
+        f.fnN = envelope_kernel<T, 1, SrcN<EnvJob<T>>>;
+    }
+    return f;
+}
+
+template <typename T>
+cudaError_t set_envelope_smem(bool one_pass, size_t smem) {
+    const EnvFns<T> f = envelope_fns<T>(one_pass);
+    cudaError_t e = cudaFuncSetAttribute(f.fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f.fnN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+namespace {
+template <typename T>
+cudaError_t launch_envelope_kernel(const T *train, const T *env_in, int64_t N, int L, int W,
+                                   T *env, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const EnvPlan<T> p = plan_envelopes<T>(train, env_in, N, L, W, env);
+    cudaError_t e = set_envelope_smem<T>(p.one_pass, p.smem);
+    if (e != cudaSuccess) return e;
+    envelope_fns<T>(p.one_pass).fn1<<<(unsigned)p.blocks, kEnvThreads, p.smem, s>>>(
+        Src1<EnvJob<T>>{p.job});
+    return cudaGetLastError();
+}
 }  // namespace
 
 template <typename T>
@@ -174,5 +213,9 @@ template cudaError_t launch_second_envelopes<float>(const float *, int64_t, int,
                                                     cudaStream_t);
 template cudaError_t launch_second_envelopes<double>(const double *, int64_t, int, int, double *,
                                                      cudaStream_t);
+template EnvPlan<float> plan_envelopes<float>(const float *, const float *, int64_t, int, int,
+                                              float *);
+template EnvFns<float> envelope_fns<float>(bool);
+template cudaError_t set_envelope_smem<float>(bool, size_t);
 
 }  // namespace nndtw

@@ -89,6 +89,58 @@ struct Cand64 {
     double d;
 };
 
+// ---- the work of one kernel launch -----------------------------------------
+// Every kernel takes its arguments as a job structure, from one of two
+// sources: Src1 (one dataset for the whole grid: the single-dataset entry
+// points) or SrcN (a batch: CTAs [off[d], off[d+1]) work on dataset d with
+// jobs[d], so that one launch serves every dataset of a batch).  A kernel
+// reads its job and its CTA index / count within that job once, at the
+// start, through get(); the table lives in the launch's parameters
+// (__grid_constant__, at most 32 KB), so no device memory holds it.
+constexpr int kMaxSets = 64;
+
+template <typename Job> struct Src1 {
+    Job job;
+    __device__ __forceinline__ const Job &get(int &bid, int &nblk) const {
+        bid = (int)blockIdx.x;
+        nblk = (int)gridDim.x;
+        return job;
+    }
+};
+
+template <typename Job> struct SrcN {
+    int n;
+    int off[kMaxSets + 1];
+    Job jobs[kMaxSets];
+    __device__ __forceinline__ const Job &get(int &bid, int &nblk) const {
+        const int b = (int)blockIdx.x;
+        int lo = 0, hi = n - 1;   // the last d with off[d] <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        bid = b - off[lo];
+        nblk = off[lo + 1] - off[lo];
+        return jobs[lo];
+    }
+};
+
+// Host side: appends dataset jobs with their CTA counts to a SrcN.
+template <typename Job> struct SrcNBuilder {
+    SrcN<Job> src;
+    SrcNBuilder() { src.n = 0; src.off[0] = 0; }
+    bool full() const { return src.n == kMaxSets; }
+    int blocks() const { return src.off[src.n]; }
+    // the caller checks full() first
+    void add(const Job &j, int nblocks) {
+        if (nblocks <= 0 || src.n >= kMaxSets) return;
+        src.jobs[src.n] = j;
+        src.off[src.n + 1] = src.off[src.n] + nblocks;
+        src.n++;
+    }
+};
+
 // ---- launchers implemented in the .cu files --------------------------------
 template <typename T>
 cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cudaStream_t s);
@@ -98,6 +150,31 @@ cudaError_t launch_envelopes(const T *train, int64_t N, int L, int W, T *env, cu
 template <typename T>
 cudaError_t launch_second_envelopes(const T *env, int64_t N, int L, int W, T *env2,
                                     cudaStream_t s);
+
+// Envelope work of one set of series (the series themselves, or with env_in
+// their envelopes for the second envelopes), its launch shape, and the
+// kernel in its two forms (kEnvelopeThreads threads per CTA).
+constexpr int kEnvelopeThreads = 256;
+template <typename T> struct EnvJob {
+    const T *train, *env_in;
+    int64_t N;
+    int L, W, T_tile, levels;
+    T *env;
+};
+template <typename T> struct EnvPlan {
+    EnvJob<T> job;
+    bool one_pass;   // both channels per pass (a kernel variant)
+    size_t smem;
+    long long blocks;
+};
+template <typename T> struct EnvFns {
+    void (*fn1)(Src1<EnvJob<T>>);
+    void (*fnN)(SrcN<EnvJob<T>>);
+};
+template <typename T>
+EnvPlan<T> plan_envelopes(const T *train, const T *env_in, int64_t N, int L, int W, T *env);
+template <typename T> EnvFns<T> envelope_fns(bool one_pass);
+template <typename T> cudaError_t set_envelope_smem(bool one_pass, size_t smem);
 
 // With seed_keys, also the Euclidean-nearest series of every query; `norms`
 // is then scratch for Q + N squared norms.  With ends_out, also the raw sum
@@ -110,6 +187,54 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
                       T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
                       bool loo, cudaStream_t s);
+
+// The bound pass (and its squared norms) of one dataset as job structures,
+// for the batched search: launch_lb's arguments, its tile shape (small: 32 x
+// 32 tiles, else 64 x 64; a kernel variant, as is ed, the fused Euclidean
+// seed) and launch shape.  The kernel runs kLbThreads threads per CTA, the
+// norms 256.
+constexpr int kLbThreads = 256;
+template <typename T> struct LbJob {
+    const T *test;
+    int64_t Q;
+    const T *train, *env;
+    int64_t N;
+    int L, W, nb, keogh, safe;
+    T lb_lo, abs_slack;
+    T *lb_out;
+    unsigned long long *seed_keys;
+    const T *nq, *nt;
+    T *ends_out;
+    int loo, qfast, gx;
+};
+template <typename T> struct SqnormJob {
+    const T *a;
+    int64_t na;
+    const T *b;
+    int64_t nb;
+    int L;
+    T *out_a, *out_b;
+};
+template <typename T> struct LbPlan {
+    LbJob<T> job;
+    SqnormJob<T> sq;
+    bool small, ed;
+    size_t smem;
+    long long blocks, sq_blocks;
+};
+template <typename T> struct LbFns {
+    void (*fn1)(Src1<LbJob<T>>);
+    void (*fnN)(SrcN<LbJob<T>>);
+    void (*sq1)(Src1<SqnormJob<T>>);
+    void (*sqN)(SrcN<SqnormJob<T>>);
+};
+template <typename T>
+cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
+                    int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
+                    unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
+                    LbPlan<T> *p);
+template <typename T> LbFns<T> lb_fns(bool small, bool ed);
+template <typename T> cudaError_t set_lb_smem(bool small, bool ed, size_t smem);
 
 // LB_New (Sec. 2.2.5) of every (query, training series) pair into out[Q][N]
 // (raw, or with safe: scaled down by the rounding margin).
@@ -136,14 +261,32 @@ struct DtwJob32 {
     float dtw_lo, dtw_hi, abs32;        // margins
     int abandon;                        // 1: abandon against bsf
     int group;                          // lanes per pair (0: library's choice; kRowsGroup: rows)
+    int lanes;                          // resolved lanes per pair (set by the launcher)
 };
+// How one dataset's FP32 DTW pass is launched: the kernel in its one-dataset
+// and batch forms (every FP32 DTW kernel takes a DtwJob32 source), block
+// size, dynamic shared memory, CTAs for this dataset's work and the lanes per
+// pair to put in the job.  Datasets of a batch whose plans name the same
+// kernel share one launch.
+using Dtw32Fn1 = void (*)(Src1<DtwJob32>);
+using Dtw32FnN = void (*)(SrcN<DtwJob32>);
+struct Dtw32Plan {
+    Dtw32Fn1 fn1;
+    Dtw32FnN fnN;
+    int threads;
+    size_t smem;
+    long long blocks;
+    int lanes;
+};
+cudaError_t plan_dtw32(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+cudaError_t plan_dtw32_wide(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+cudaError_t plan_dtw32_rows(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+cudaError_t plan_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, Dtw32Plan *p);
+cudaError_t plan_dtw32_rowsc(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+// One dataset: plan and launch.
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
-cudaError_t launch_dtw32_wide(const DtwJob32 &job, int sm_count, cudaStream_t s);
-cudaError_t launch_dtw32_rows(const DtwJob32 &job, int sm_count, cudaStream_t s);
 bool dtw32_rowsg_ok(int L, int W, int G);
 bool dtw32_rowsc_ok(int L, int W);   // full window, 2048 < L <= 4096: a CTA per pair
-cudaError_t launch_dtw32_rowsc(const DtwJob32 &job, int sm_count, cudaStream_t s);
-cudaError_t launch_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, cudaStream_t s);
 bool dtw32_rows_ok(int L, int W);   // full window and L small enough for the row kernel
 constexpr int kRowsGroup = 64;      // DtwJob32::group value selecting the row kernel
 // kRowsGroup + 1 / + 2: the row layout with 16 / 8 lanes per pair
@@ -187,6 +330,16 @@ struct DtwJob64 {
     const double *lb;
 };
 cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
+using Dtw64Fn1 = void (*)(Src1<DtwJob64>);
+using Dtw64FnN = void (*)(SrcN<DtwJob64>);
+struct Dtw64Plan {
+    Dtw64Fn1 fn1;
+    Dtw64FnN fnN;
+    int threads;
+    size_t smem;
+    long long blocks;
+};
+cudaError_t plan_dtw64(const DtwJob64 &job, int sm_count, Dtw64Plan *p);
 
 // The cascade's second stage over a queue of pairs (FP32): with ends, the
 // reverse bound LB_Enhanced(B, A); with env2 and lb, LB_Enhanced(A, B) with
@@ -200,6 +353,17 @@ struct __align__(8) BGap {
     __half2 g;
 };
 cudaError_t launch_pack_bgap(const float *train, float *env2, long long n, cudaStream_t s);
+struct PackJob {
+    const float *train;
+    float *env2;
+    long long n;   // elements (N * L)
+};
+struct PackFns {
+    void (*fn1)(Src1<PackJob>);
+    void (*fnN)(SrcN<PackJob>);
+};
+PackFns pack_bgap_fns();
+long long pack_bgap_blocks(long long n);   // CTAs for n elements
 
 struct CascadeJob {
     const uint2 *in;
@@ -219,6 +383,12 @@ struct CascadeJob {
 };
 cudaError_t launch_cascade_filter(const CascadeJob &job, long long max_pairs, int sm_count,
                                   cudaStream_t s);
+struct CascadeFns {
+    void (*fn1)(Src1<CascadeJob>);
+    void (*fnN)(SrcN<CascadeJob>);
+};
+CascadeFns cascade_filter_fns(bool rev, bool imp);          // 256 threads per CTA
+long long cascade_filter_blocks(long long max_pairs, int sm_count);
 
 // Adds the second pass of the LB_Improved bridge to every pair's LB_Enhanced
 // value in lb[Q][N] (raw, or with safe: both parts scaled down and the sum

@@ -159,12 +159,19 @@ template <typename T, int N> __device__ __forceinline__ void ldsn(T (&d)[N], con
 }
 
 // Squared norm of every row of a and of b (one warp per row).
-template <typename T>
-__global__ void sqnorm_kernel(const T *__restrict__ a, int64_t na, const T *__restrict__ b,
-                              int64_t nb, int L, T *__restrict__ out_a, T *__restrict__ out_b) {
+template <typename T, typename Src>
+__global__ void sqnorm_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const SqnormJob<T> &job = src.get(bid, nblk);
+    const T *__restrict__ a = job.a;
+    const T *__restrict__ b = job.b;
+    const int64_t na = job.na, nb = job.nb;
+    const int L = job.L;
+    T *__restrict__ out_a = job.out_a;
+    T *__restrict__ out_b = job.out_b;
     const int lane = threadIdx.x & 31;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na + nb;
+    const int64_t warps = ((int64_t)nblk * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)bid * blockDim.x + threadIdx.x) >> 5; r < na + nb;
          r += warps) {
         const T *x = r < na ? a + r * L : b + (r - na) * L;
         T acc = T(0);
@@ -177,13 +184,25 @@ __global__ void sqnorm_kernel(const T *__restrict__ a, int64_t na, const T *__re
     }
 }
 
-template <typename T, bool ED, int MR, int MC>
+template <typename T, bool ED, int MR, int MC, typename Src>
 __global__ void __launch_bounds__(kThreads)
-lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
-          const T *__restrict__ env, int64_t N, int L, int W, int nb, int keogh, int safe,
-          T lb_lo, T abs_slack, T *__restrict__ lb_out, unsigned long long *seed_keys,
-          const T *__restrict__ nq, const T *__restrict__ nt, T *__restrict__ ends_out,
-          int loo, int qfast) {
+lb_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const LbJob<T> &job = src.get(bid, nblk);
+    const T *__restrict__ test = job.test;
+    const T *__restrict__ train = job.train;
+    const T *__restrict__ env = job.env;
+    const int64_t Q = job.Q, N = job.N;
+    const int L = job.L, W = job.W, nb = job.nb, keogh = job.keogh, safe = job.safe;
+    const T lb_lo = job.lb_lo, abs_slack = job.abs_slack;
+    T *__restrict__ lb_out = job.lb_out;
+    unsigned long long *seed_keys = job.seed_keys;
+    const T *__restrict__ nq = job.nq;
+    const T *__restrict__ nt = job.nt;
+    T *__restrict__ ends_out = job.ends_out;
+    const int loo = job.loo, qfast = job.qfast;
+    // the CTA's tile: bx along the fast dimension (gx tiles), by along the other
+    const int bx = bid % job.gx, by = bid / job.gx;
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -210,8 +229,8 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
     auto col_of = [&](int c) { return (c >> 1) * 32 + 2 * tx + (c & 1); };
     // query tiles vary fastest (qfast), so the CTAs resident at one time share
     // a few training tiles (series and envelopes read from DRAM about once)
-    const int64_t q0 = (int64_t)(qfast ? blockIdx.x : blockIdx.y) * kQT;
-    const int64_t t0 = (int64_t)(qfast ? blockIdx.y : blockIdx.x) * kNT;
+    const int64_t q0 = (int64_t)(qfast ? bx : by) * kQT;
+    const int64_t t0 = (int64_t)(qfast ? by : bx) * kNT;
 
     T acc[MR][MC], ed[MR][MC];
 #pragma unroll
@@ -372,29 +391,72 @@ lb_kernel(const T *__restrict__ test, int64_t Q, const T *__restrict__ train,
 }
 
 template <typename T, int MR, int MC>
-cudaError_t launch_lb_tile(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
-                           int L, int Weff, int nb, bool keogh, bool safe, T lb_lo, T abs_slack,
-                           T *lb_out, unsigned long long *seed_keys, const T *nq, const T *nt,
-                           T *ends_out, bool loo, cudaStream_t s) {
-    using T2 = typename V2<T>::type;
+size_t lb_smem(bool ed, bool keogh, int nb) {
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
-    const bool ed = seed_keys != nullptr;
-    size_t smem = 2 * (ed ? lb_stage_bytes<T, kQT, kNT, true>() : lb_stage_bytes<T, kQT, kNT, false>());
+    size_t smem = 2 * (ed ? lb_stage_bytes<T, kQT, kNT, true>()
+                          : lb_stage_bytes<T, kQT, kNT, false>());
     if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * (2 * nb + 1);
-    auto fn = ed ? lb_kernel<T, true, MR, MC> : lb_kernel<T, false, MR, MC>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const long long qt = (Q + kQT - 1) / kQT, nt_tiles = (N + kNT - 1) / kNT;
-    const int qfast = nt_tiles <= 65535 ? 1 : 0;   // grid.y holds at most 65535 tiles
-    dim3 grid(qfast ? (unsigned)qt : (unsigned)nt_tiles, qfast ? (unsigned)nt_tiles : (unsigned)qt);
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    fn<<<grid, kThreads, smem, s>>>(test, Q, train, env, N, L, Weff, nb, keogh ? 1 : 0, safe ? 1 : 0,
-                                    lb_lo, abs_slack, lb_out, seed_keys, nq, nt, ends_out,
-                                    loo ? 1 : 0, qfast);
-    return cudaGetLastError();
+    return smem;
 }
 
 }  // namespace
+
+template <typename T>
+cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
+                    int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
+                    unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
+                    LbPlan<T> *p) {
+    int nb = L / 2 < V ? L / 2 : V;
+    if (nb < 1) nb = 1;
+    const int Weff = W > L - 1 ? L - 1 : W;
+    // 64 x 64 tiles when they give at least two CTAs per SM, else 32 x 32
+    const int sms = device_sm_count();
+    p->small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
+    p->ed = seed_keys != nullptr;
+    const int kQT = p->small ? 32 : 64, kNT = kQT;
+    const long long qt = (Q + kQT - 1) / kQT, nt_tiles = (N + kNT - 1) / kNT;
+    LbJob<T> &j = p->job;
+    j.test = test; j.Q = Q; j.train = train; j.env = env; j.N = N; j.L = L; j.W = Weff;
+    j.nb = nb; j.keogh = keogh ? 1 : 0; j.safe = safe ? 1 : 0; j.lb_lo = lb_lo;
+    j.abs_slack = abs_slack; j.lb_out = lb_out; j.seed_keys = seed_keys;
+    j.nq = seed_keys ? norms : nullptr; j.nt = seed_keys ? norms + Q : nullptr;
+    j.ends_out = keogh ? nullptr : ends_out; j.loo = loo ? 1 : 0;
+    // query tiles vary fastest, so the CTAs resident at one time share a few
+    // training tiles
+    j.qfast = 1;
+    j.gx = (int)qt;
+    p->blocks = qt * nt_tiles;
+    p->smem = p->small ? lb_smem<T, 2, 2>(p->ed, keogh, nb) : lb_smem<T, 4, 4>(p->ed, keogh, nb);
+    p->sq = SqnormJob<T>{test, Q, train, N, L, norms, norms + Q};
+    const int64_t rows = Q + N;
+    p->sq_blocks = seed_keys ? ((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096) : 0;
+    return cudaSuccess;
+}
+
+template <typename T>
+LbFns<T> lb_fns(bool small, bool ed) {
+    LbFns<T> f;
+    if (small) {
+        f.fn1 = ed ? lb_kernel<T, true, 2, 2, Src1<LbJob<T>>> : lb_kernel<T, false, 2, 2, Src1<LbJob<T>>>;
+        f.fnN = ed ? lb_kernel<T, true, 2, 2, SrcN<LbJob<T>>> : lb_kernel<T, false, 2, 2, SrcN<LbJob<T>>>;
+    } else {
+        f.fn1 = ed ? lb_kernel<T, true, 4, 4, Src1<LbJob<T>>> : lb_kernel<T, false, 4, 4, Src1<LbJob<T>>>;
+        f.fnN = ed ? lb_kernel<T, true, 4, 4, SrcN<LbJob<T>>> : lb_kernel<T, false, 4, 4, SrcN<LbJob<T>>>;
+    }
+    f.sq1 = sqnorm_kernel<T, Src1<SqnormJob<T>>>;
+    f.sqN = sqnorm_kernel<T, SrcN<SqnormJob<T>>>;
+    return f;
+}
+
+template <typename T>
+cudaError_t set_lb_smem(bool small, bool ed, size_t smem) {
+    const LbFns<T> f = lb_fns<T>(small, ed);
+    cudaError_t e = cudaFuncSetAttribute(f.fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f.fnN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
 
 template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
@@ -402,29 +464,23 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
                       unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
                       cudaStream_t s) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
-    if (seed_keys) {
+    if (seed_keys && !norms) return cudaErrorInvalidValue;
+    LbPlan<T> p{};
+    cudaError_t e = plan_lb<T>(test, Q, train, env, N, L, W, V, keogh, safe, lb_lo, abs_slack,
+                               lb_out, seed_keys, norms, ends_out, loo, &p);
+    if (e != cudaSuccess) return e;
+    const LbFns<T> f = lb_fns<T>(p.small, p.ed);
+    if (p.sq_blocks > 0) {
         // squared norms of the queries (norms[0..Q)) and training series
         // (norms[Q..Q+N)) for the fused Euclidean distance
-        if (!norms) return cudaErrorInvalidValue;
-        const int64_t rows = Q + N;
-        const unsigned grid = (unsigned)((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096);
-        sqnorm_kernel<T><<<grid, 256, 0, s>>>(test, Q, train, N, L, norms, norms + Q);
-        cudaError_t e = cudaGetLastError();
+        f.sq1<<<(unsigned)p.sq_blocks, 256, 0, s>>>(Src1<SqnormJob<T>>{p.sq});
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const T *nq = seed_keys ? norms : nullptr, *nt = seed_keys ? norms + Q : nullptr;
-    int nb = L / 2 < V ? L / 2 : V;
-    if (nb < 1) nb = 1;
-    const int Weff = W > L - 1 ? L - 1 : W;
-    // 64 x 64 tiles when they give at least two CTAs per SM, else 32 x 32
-    const int sms = device_sm_count();
-    const bool small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
-    if (small) return launch_lb_tile<T, 2, 2>(test, Q, train, env, N, L, Weff, nb, keogh, safe,
-                                              lb_lo, abs_slack, lb_out, seed_keys, nq, nt,
-                                              keogh ? nullptr : ends_out, loo, s);
-    return launch_lb_tile<T, 4, 4>(test, Q, train, env, N, L, Weff, nb, keogh, safe, lb_lo,
-                                   abs_slack, lb_out, seed_keys, nq, nt,
-                                   keogh ? nullptr : ends_out, loo, s);
+    e = set_lb_smem<T>(p.small, p.ed, p.smem);
+    if (e != cudaSuccess) return e;
+    f.fn1<<<(unsigned)p.blocks, kThreads, p.smem, s>>>(Src1<LbJob<T>>{p.job});
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
@@ -435,5 +491,11 @@ template cudaError_t launch_lb<double>(const double *, int64_t, const double *, 
                                        int64_t, int, int, int, bool, bool, double, double,
                                        double *, unsigned long long *, double *, double *,
                                        bool, cudaStream_t);
+template cudaError_t plan_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
+                                    int, int, int, bool, bool, float, float, float *,
+                                    unsigned long long *, float *, float *, bool,
+                                    LbPlan<float> *);
+template LbFns<float> lb_fns<float>(bool, bool);
+template cudaError_t set_lb_smem<float>(bool, bool, size_t);
 
 }  // namespace nndtw

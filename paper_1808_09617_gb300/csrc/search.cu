@@ -14,9 +14,12 @@
 //       index; labels gathered.
 // The FP64 search is the same pipeline in FP64, where DTW values are exact
 // and no recheck is needed.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -80,14 +83,34 @@ __device__ __forceinline__ int bucket_of(T lb, T inv) {
 // bucket per block-iteration (pass 2) or per block (pass 1).
 constexpr int kCompactE = 8;   // pairs per thread per compaction round
 
-template <typename T>
+template <typename T> struct CompactJob {
+    const T *lb;
+    int64_t Q, N;
+    const unsigned long long *bsf, *seed;
+    UbOf<T> ubof;
+    int no_prune, gx;   // gx: CTAs along a row; the others stride over the rows
+    int scatter;        // 0: count the kept pairs per bucket; 1: write them
+    unsigned long long *bcount, *bcursor, *qcount;
+    uint2 *queue;
+};
+
+template <typename T, typename Src>
 __global__ void __launch_bounds__(256)
-compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
-               const unsigned long long *__restrict__ bsf,
-               const unsigned long long *__restrict__ seed, UbOf<T> ubof, int no_prune,
-               int scatter, unsigned long long *__restrict__ bcount,
-               unsigned long long *__restrict__ bcursor, uint2 *__restrict__ queue,
-               unsigned long long *__restrict__ qcount) {
+compact_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const CompactJob<T> &job = src.get(bid, nblk);
+    const int scatter = job.scatter;
+    const T *__restrict__ lb = job.lb;
+    const int64_t Q = job.Q, N = job.N;
+    const unsigned long long *__restrict__ bsf = job.bsf;
+    const unsigned long long *__restrict__ seed = job.seed;
+    const UbOf<T> ubof = job.ubof;
+    const int no_prune = job.no_prune;
+    unsigned long long *__restrict__ bcount = job.bcount;
+    unsigned long long *__restrict__ bcursor = job.bcursor;
+    uint2 *__restrict__ queue = job.queue;
+    unsigned long long *__restrict__ qcount = job.qcount;
+    const int bx = bid % job.gx, by = bid / job.gx, gy = nblk / job.gx;
     __shared__ unsigned long long boff[kBuckets];
     __shared__ unsigned int scount[kBuckets];
     __shared__ unsigned long long sbase[kBuckets];
@@ -98,7 +121,7 @@ compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
             unsigned long long o = 0;
             for (int k = 0; k < tid; k++) o += bcount[k];
             boff[tid] = o;
-            if (tid == kBuckets - 1 && blockIdx.x == 0 && blockIdx.y == 0)
+            if (tid == kBuckets - 1 && bid == 0)
                 *qcount = o + bcount[kBuckets - 1];
         }
     }
@@ -106,13 +129,13 @@ compact_kernel(const T *__restrict__ lb, int64_t Q, int64_t N,
     // each round covers kCompactE * 256 consecutive pairs of a row; element e
     // of thread tid is t0 + e * 256 + tid (coalesced loads)
     constexpr int E = kCompactE;
-    for (int64_t q = blockIdx.y; q < Q; q += gridDim.y) {
+    for (int64_t q = by; q < Q; q += gy) {
         const T ub = ubof(bsf[q]);
         const T inv = ub > T(0) && ub < inf_of<T>() ? T(kBuckets) / ub : T(0);
         const uint32_t st = key_idx(seed[q]);
         const T *row = lb + q * N;
-        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x * E; t0 < N;
-             t0 += (int64_t)gridDim.x * blockDim.x * E) {
+        for (int64_t t0 = (int64_t)bx * blockDim.x * E; t0 < N;
+             t0 += (int64_t)job.gx * blockDim.x * E) {
             unsigned keepm = 0;
             unsigned pos[E];
             int bk[E];
@@ -162,68 +185,112 @@ __device__ __forceinline__ bool in_recheck_set(const Cand &e, unsigned long long
     return lower32(e.d, lo, abs32) <= upper32(key_dist(kb), hi, abs32);
 }
 
-__global__ void filter32_kernel(const Cand *__restrict__ cand, const unsigned long long *ccount,
-                                const unsigned long long *__restrict__ bsf, float lo, float hi,
-                                float abs32, int32_t *__restrict__ rcount) {
-    const long long n = (long long)*ccount;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const Cand e = cand[i];
-        if (in_recheck_set(e, bsf[e.q], lo, hi, abs32)) atomicAdd(rcount + e.q, 1);
+// The per-query end of one FP32 search: the candidate list, the keys, the
+// recheck list and the outputs.
+struct FinishJob32 {
+    const Cand *cand;
+    const unsigned long long *ccount, *bsf;
+    float lo, hi, abs32;
+    int32_t *rcount;
+    int exact;
+    uint2 *rlist;
+    unsigned long long *counters;     // C_RECHECK (recheck list length), C_RQUERIES
+    const double *d64;
+    unsigned long long *best64;
+    int32_t *bestidx;
+    int64_t Q;
+    const int32_t *labels;
+    int32_t *nn_idx, *nn_label;
+    double *nn_dist;
+};
+
+template <typename Src>
+__global__ void filter32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const FinishJob32 &j = src.get(bid, nblk);
+    const long long n = (long long)*j.ccount;
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < n;
+         i += (long long)nblk * blockDim.x) {
+        const Cand e = j.cand[i];
+        if (in_recheck_set(e, j.bsf[e.q], j.lo, j.hi, j.abs32)) atomicAdd(j.rcount + e.q, 1);
     }
 }
 
-__global__ void collect32_kernel(const Cand *__restrict__ cand, const unsigned long long *ccount,
-                                 const unsigned long long *__restrict__ bsf, float lo, float hi,
-                                 float abs32, const int32_t *__restrict__ rcount, int exact,
-                                 uint2 *__restrict__ rlist, unsigned long long *counters) {
-    const long long n = (long long)*ccount;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const Cand e = cand[i];
-        const unsigned long long kb = bsf[e.q];
-        if (!in_recheck_set(e, kb, lo, hi, abs32)) continue;
-        const int rc = rcount[e.q];
-        if (!(exact || rc >= 2)) continue;
-        const unsigned long long slot = atomicAdd(counters + C_RECHECK, 1ull);
-        rlist[slot] = make_uint2((uint32_t)e.q, (uint32_t)e.t);
-        if ((uint32_t)e.t == key_idx(kb)) atomicAdd(counters + C_RQUERIES, 1ull);
+template <typename Src>
+__global__ void collect32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const FinishJob32 &j = src.get(bid, nblk);
+    const long long n = (long long)*j.ccount;
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < n;
+         i += (long long)nblk * blockDim.x) {
+        const Cand e = j.cand[i];
+        const unsigned long long kb = j.bsf[e.q];
+        if (!in_recheck_set(e, kb, j.lo, j.hi, j.abs32)) continue;
+        const int rc = j.rcount[e.q];
+        if (!(j.exact || rc >= 2)) continue;
+        const unsigned long long slot = atomicAdd(j.counters + C_RECHECK, 1ull);
+        j.rlist[slot] = make_uint2((uint32_t)e.q, (uint32_t)e.t);
+        if ((uint32_t)e.t == key_idx(kb)) atomicAdd(j.counters + C_RQUERIES, 1ull);
     }
 }
 
-__global__ void ties32_kernel(const uint2 *__restrict__ rlist, const unsigned long long *rcnt,
-                              const double *__restrict__ d64,
-                              const unsigned long long *__restrict__ best64,
-                              int32_t *__restrict__ bestidx) {
-    const long long n = (long long)*rcnt;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const uint2 e = rlist[i];
-        if (dbits(d64[i]) == best64[e.x]) atomicMin(bestidx + e.x, (int32_t)e.y);
+template <typename Src>
+__global__ void ties32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const FinishJob32 &j = src.get(bid, nblk);
+    const long long n = (long long)j.counters[C_RECHECK];
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < n;
+         i += (long long)nblk * blockDim.x) {
+        const uint2 e = j.rlist[i];
+        if (dbits(j.d64[i]) == j.best64[e.x]) atomicMin(j.bestidx + e.x, (int32_t)e.y);
     }
 }
 
-__global__ void finalize32_kernel(int64_t Q, const unsigned long long *__restrict__ bsf,
-                                  const int32_t *__restrict__ rcount,
-                                  const unsigned long long *__restrict__ best64,
-                                  const int32_t *__restrict__ bestidx, int exact,
-                                  const int32_t *__restrict__ labels, int32_t *__restrict__ nn_idx,
-                                  int32_t *__restrict__ nn_label, double *__restrict__ nn_dist) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long kb = bsf[q];
+template <typename Src>
+__global__ void finalize32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const FinishJob32 &j = src.get(bid, nblk);
+    for (int64_t q = (int64_t)bid * blockDim.x + threadIdx.x; q < j.Q;
+         q += (int64_t)nblk * blockDim.x) {
+        const unsigned long long kb = j.bsf[q];
         int32_t idx;
         double dist;
-        if (exact || rcount[q] >= 2) {
-            idx = bestidx[q];
-            dist = __longlong_as_double((long long)best64[q]);
+        if (j.exact || j.rcount[q] >= 2) {
+            idx = j.bestidx[q];
+            dist = __longlong_as_double((long long)j.best64[q]);
         } else {
             idx = (int32_t)key_idx(kb);
             dist = (double)key_dist(kb);
         }
-        nn_idx[q] = idx;
-        nn_label[q] = labels[idx];
-        nn_dist[q] = dist;
+        j.nn_idx[q] = idx;
+        j.nn_label[q] = j.labels[idx];
+        j.nn_dist[q] = dist;
+    }
+}
+
+// The search's starting values: counters and bucket tallies 0, query keys
+// and FP64 bests all ones (no candidate), recheck tallies 0, tie indices
+// INT_MAX (0x7f7f7f7f as written by a byte fill).
+struct InitJob32 {
+    unsigned long long *counters, *buckets, *bsf, *seed, *best64;
+    int32_t *rcount, *bestidx;
+    int64_t Q;
+};
+
+template <typename Src>
+__global__ void init32_kernel(const __grid_constant__ Src src) {
+    int bid, nblk;
+    const InitJob32 &j = src.get(bid, nblk);
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    const int64_t i0 = (int64_t)bid * blockDim.x + threadIdx.x;
+    for (int64_t i = i0; i < C_COUNT; i += stride) j.counters[i] = 0ull;
+    for (int64_t i = i0; i < 2 * kBuckets; i += stride) j.buckets[i] = 0ull;
+    for (int64_t q = i0; q < j.Q; q += stride) {
+        j.bsf[q] = ~0ull;
+        j.seed[q] = ~0ull;
+        j.best64[q] = ~0ull;
+        j.rcount[q] = 0;
+        j.bestidx[q] = 0x7f7f7f7f;
     }
 }
 
@@ -443,6 +510,467 @@ int check_finite(const T *x, int64_t n, T limit, unsigned long long *bad, cudaSt
     return NNDTW_OK;
 }
 
+int group_from_flags(unsigned flags) {
+    const unsigned v = (flags & NNDTW_DTW_GROUP_MASK) >> 8;
+    if (v == 7) {
+        const unsigned lanes = (flags & NNDTW_DTW_ROWS_LANES_MASK) >> 12;
+        return kRowsGroup + (lanes <= 2 ? (int)lanes : 0);
+    }
+    return v ? 1 << (v - 1) : 0;
+}
+
+// ------------------------------------------------------------ FP32 executor
+//
+// One FP32 search over one dataset or a batch of up to kMaxSets datasets,
+// stage by stage on the caller's stream: every stage is one launch over all
+// datasets of the batch (one per kernel variant where datasets need
+// different ones: tile shapes, DTW layouts), each dataset's CTAs working on
+// its own job (SrcN; a single dataset takes the Src1 form).  The datasets'
+// workspaces are separate, so no stage of one dataset reads another's data.
+
+struct Set32 {
+    const float *train;
+    const int32_t *labels;
+    int64_t N;
+    const float *test;
+    int64_t Q;
+    int L, W, V;
+    const float *env;   // nullptr: built into the workspace
+    unsigned flags;
+    int32_t *nn_idx, *nn_label;
+    double *nn_dist;
+    void *ws;           // nn_dtw_workspace_size() bytes, 256-byte aligned
+};
+
+// One kernel (its two forms, block size, largest dynamic shared memory) and
+// the datasets it serves in one launch.
+template <typename Job> struct Batch {
+    void (*fn1)(Src1<Job>) = nullptr;
+    void (*fnN)(SrcN<Job>) = nullptr;   // nullptr: no batch form, one launch per dataset
+    int threads = 0;
+    size_t smem = 0;
+    SrcNBuilder<Job> b;
+};
+
+// kernel launches issued by the calling thread's last FP32 search call, in
+// all and per stage (stage k: between stage boundaries k and k+1 of
+// nn_dtw_stage_times)
+thread_local long long t_launches = 0;
+thread_local long long t_stage_launches[8] = {};
+thread_local int t_stage = 0;
+
+void reset_launch_counts() {
+    t_launches = 0;
+    t_stage = 0;
+    for (auto &c : t_stage_launches) c = 0;
+}
+
+template <typename Job>
+cudaError_t launch_batch(const Batch<Job> &g, cudaStream_t s) {
+    const SrcN<Job> &src = g.b.src;
+    if (src.n == 0) return cudaSuccess;
+    const long long k = (src.n > 1 && g.fnN) ? 1 : src.n;
+    t_launches += k;
+    t_stage_launches[t_stage] += k;
+    if (g.smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(g.fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)g.smem);
+        if (e == cudaSuccess && g.fnN)
+            e = cudaFuncSetAttribute(g.fnN, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g.smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (src.n > 1 && g.fnN) {
+        g.fnN<<<(unsigned)src.off[src.n], g.threads, g.smem, s>>>(src);
+        return cudaGetLastError();
+    }
+    for (int d = 0; d < src.n; d++) {
+        g.fn1<<<(unsigned)(src.off[d + 1] - src.off[d]), g.threads, g.smem, s>>>(
+            Src1<Job>{src.jobs[d]});
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Batches keyed by kernel and block size (a handful per stage); a key with
+// more than kMaxSets jobs (a stage with two jobs per dataset) gets another
+// batch.
+template <typename Job> struct Batches {
+    std::vector<Batch<Job>> v;
+    Batch<Job> &of(void (*fn1)(Src1<Job>), void (*fnN)(SrcN<Job>), int threads) {
+        for (auto &g : v)
+            if (g.fn1 == fn1 && g.threads == threads && !g.b.full()) return g;
+        v.emplace_back();
+        Batch<Job> &g = v.back();
+        g.fn1 = fn1;
+        g.fnN = fnN;
+        g.threads = threads;
+        return g;
+    }
+    void add(void (*fn1)(Src1<Job>), void (*fnN)(SrcN<Job>), int threads, size_t smem,
+             const Job &job, long long blocks) {
+        if (blocks <= 0) return;
+        Batch<Job> &g = of(fn1, fnN, threads);
+        g.smem = std::max(g.smem, smem);
+        g.b.add(job, (int)blocks);
+    }
+    cudaError_t launch(cudaStream_t s) const {
+        for (const auto &g : v) {
+            const cudaError_t e = launch_batch(g, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+// Streams on which the variant launches of one stage (bounds, first
+// candidates, DTW) run side by side: a few per caller stream and device,
+// created on first use and kept, so that calls on different streams never
+// share them.  A stage forks from the caller's stream with an event, issues
+// its launches round-robin over them and joins back, so the stage events on
+// the caller's stream still bracket all of its launches (and a captured
+// graph holds the fork and the join).
+constexpr int kForkStreams = 4;
+struct ForkSet {
+    cudaStream_t st[kForkStreams] = {};
+    cudaEvent_t fork = nullptr, join[kForkStreams] = {};
+};
+std::mutex g_fork_mu;
+std::vector<std::pair<std::pair<int, cudaStream_t>, ForkSet *>> g_forks;
+
+cudaError_t fork_set(cudaStream_t s, ForkSet **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_fork_mu);
+    for (auto &kv : g_forks)
+        if (kv.first.first == dev && kv.first.second == s) {
+            *out = kv.second;
+            return cudaSuccess;
+        }
+    ForkSet *f = new ForkSet();
+    for (int k = 0; k < kForkStreams; k++) {
+        e = cudaStreamCreateWithFlags(&f->st[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    g_forks.push_back({{dev, s}, f});
+    *out = f;
+    return cudaSuccess;
+}
+
+// Launches a stage's batches: one batch on the caller's stream, several side
+// by side on the fork streams (always joined back, also after an error).
+template <typename Job>
+cudaError_t launch_forked(const Batches<Job> &g, cudaStream_t s) {
+    const int nb = (int)g.v.size();
+    if (nb <= 1) return g.launch(s);
+    ForkSet *f = nullptr;
+    cudaError_t e = fork_set(s, &f);
+    if (e != cudaSuccess) return e;
+    const int used = nb < kForkStreams ? nb : kForkStreams;
+    e = cudaEventRecord(f->fork, s);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < used; k++) {
+        e = cudaStreamWaitEvent(f->st[k], f->fork, 0);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t first = cudaSuccess;
+    for (int b = 0; b < nb && first == cudaSuccess; b++) first = launch_batch(g.v[b], f->st[b % used]);
+    for (int k = 0; k < used; k++) {
+        e = cudaEventRecord(f->join[k], f->st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, f->join[k], 0);
+        if (e != cudaSuccess && first == cudaSuccess) first = e;
+    }
+    return first;
+}
+
+struct Prep32 {
+    Layout32 ws;
+    int Weff;
+    Margins m;
+    bool keogh, rev, imp, second, loo, no_prune, exact;
+    const float *env;
+    unsigned long long *cnt;   // work counters (stats), or nullptr
+};
+
+// Blocks for a grid-stride pass over a dataset's candidate lists (at least
+// one candidate per query, typically a few): enough threads for about eight
+// per query, at most the small-kernel grid.
+long long finish_blocks(int64_t Q, int64_t N) {
+    const long long by_q = (8 * Q + kSmallThreads - 1) / kSmallThreads;
+    const long long cap = grid_small((long long)Q * N + Q);
+    return std::max(1ll, std::min(by_q, cap));
+}
+
+int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *stats,
+          StageTimer &tm, cudaStream_t s) {
+    const int sms = device_sm_count();
+    t_stage = 0;
+    std::vector<Prep32> P(n);
+    for (int d = 0; d < n; d++) {
+        const Set32 &x = sets[d];
+        Prep32 &p = P[d];
+        p.ws = layout32(x.ws, x.N, x.Q, x.L);
+        p.Weff = x.W > x.L - 1 ? x.L - 1 : x.W;
+        p.m = make_margins(x.L);
+        p.keogh = (x.flags & NNDTW_KEOGH_BOUND) != 0;
+        p.no_prune = (x.flags & NNDTW_NO_PRUNE) != 0;
+        // the cascade's second stage: the reverse bound (NNDTW_REVERSE) and/or
+        // the bound with the LB_Improved bridge (NNDTW_IMPROVED), tuning
+        // choices; LB_Keogh as the bound (NNDTW_KEOGH_BOUND) has none
+        p.rev = (x.flags & NNDTW_REVERSE) && !p.keogh &&
+                !(x.flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
+        p.imp = (x.flags & NNDTW_IMPROVED) && !p.keogh && !p.no_prune;
+        p.second = p.rev || p.imp;
+        p.loo = (x.flags & NNDTW_LEAVE_ONE_OUT) != 0;
+        p.exact = (x.flags & NNDTW_EXACT_DIST) != 0;
+        p.env = x.env ? x.env : p.ws.env;
+        p.cnt = (want_stats && !timing) ? p.ws.counters : nullptr;
+    }
+
+    // starting values of every dataset's counters, keys and tallies
+    {
+        Batches<InitJob32> g;
+        for (int d = 0; d < n; d++) {
+            const Layout32 &w = P[d].ws;
+            const InitJob32 j{w.counters, w.buckets, w.bsf, w.seed, w.best64, w.rcount, w.bestidx,
+                              sets[d].Q};
+            g.add(init32_kernel<Src1<InitJob32>>, init32_kernel<SrcN<InitJob32>>, kSmallThreads,
+                  0, j, std::min<long long>(grid_small(std::max<int64_t>(sets[d].Q, 64)), 64));
+        }
+        CK(g.launch(s));
+    }
+    // optional scan for non-finite inputs (waits for the stream)
+    {
+        bool any = false;
+        for (int d = 0; d < n; d++) {
+            if (!(sets[d].flags & NNDTW_CHECK_FINITE)) continue;
+            any = true;
+            unsigned long long *bad = P[d].ws.counters + C_BAD;
+            t_launches += 2;
+            t_stage_launches[t_stage] += 2;
+            int rc = check_finite<float>(sets[d].train, sets[d].N * sets[d].L, 1e15f, bad, s);
+            if (rc) return rc;
+            rc = check_finite<float>(sets[d].test, sets[d].Q * sets[d].L, 1e15f, bad, s);
+            if (rc) return rc;
+        }
+        if (any) {
+            std::vector<unsigned long long> h(n, 0ull);
+            for (int d = 0; d < n; d++)
+                if (sets[d].flags & NNDTW_CHECK_FINITE)
+                    CK(cudaMemcpyAsync(&h[d], P[d].ws.counters + C_BAD, sizeof(h[d]),
+                                       cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int d = 0; d < n; d++)
+                if (h[d]) return NNDTW_ENONFINITE;
+        }
+    }
+    // S1: training envelopes (unless supplied) and, for the cascade's second
+    // stage, the queries' envelopes; then the second envelopes and the packed
+    // training records of the LB_Improved bridge
+    {
+        Batches<EnvJob<float>> g;
+        auto add = [&](const float *src, const float *ein, int64_t cnt, int d, float *out) {
+            const EnvPlan<float> ep = plan_envelopes<float>(src, ein, cnt, sets[d].L, P[d].Weff, out);
+            const EnvFns<float> f = envelope_fns<float>(ep.one_pass);
+            g.add(f.fn1, f.fnN, kEnvelopeThreads, ep.smem, ep.job, ep.blocks);
+        };
+        for (int d = 0; d < n; d++) {
+            if (!sets[d].env) add(sets[d].train, nullptr, sets[d].N, d, P[d].ws.env);
+            if (P[d].second) add(sets[d].test, nullptr, sets[d].Q, d, P[d].ws.envq);
+        }
+        CK(g.launch(s));
+        Batches<EnvJob<float>> g2;
+        Batches<PackJob> gp;
+        const PackFns pf = pack_bgap_fns();
+        for (int d = 0; d < n; d++) {
+            if (!P[d].imp) continue;
+            const EnvPlan<float> ep = plan_envelopes<float>(nullptr, P[d].env, sets[d].N, sets[d].L,
+                                                            P[d].Weff, P[d].ws.env2);
+            const EnvFns<float> f = envelope_fns<float>(ep.one_pass);
+            g2.add(f.fn1, f.fnN, kEnvelopeThreads, ep.smem, ep.job, ep.blocks);
+            const long long ne = sets[d].N * sets[d].L;
+            gp.add(pf.fn1, pf.fnN, 256, 0, PackJob{sets[d].train, P[d].ws.env2, ne},
+                   pack_bgap_blocks(ne));
+        }
+        CK(g2.launch(s));
+        CK(gp.launch(s));
+    }
+    t_stage = 1;
+    CK(tm.mark(1));
+    // S2: squared norms, then the safe bounds of all pairs and each query's
+    // Euclidean-nearest training series (its first candidate)
+    {
+        Batches<SqnormJob<float>> gs;
+        Batches<LbJob<float>> gl;
+        for (int d = 0; d < n; d++) {
+            const Set32 &x = sets[d];
+            const Prep32 &p = P[d];
+            LbPlan<float> lp{};
+            CK(plan_lb<float>(x.test, x.Q, x.train, p.env, x.N, x.L, p.Weff, x.V, p.keogh, true,
+                              p.m.lb_lo, p.m.abs32, p.ws.lb, p.ws.seed, p.ws.norms,
+                              p.rev ? p.ws.ends : nullptr, p.loo, &lp));
+            const LbFns<float> f = lb_fns<float>(lp.small, lp.ed);
+            gs.add(f.sq1, f.sqN, 256, 0, lp.sq, lp.sq_blocks);
+            gl.add(f.fn1, f.fnN, kLbThreads, lp.smem, lp.job, lp.blocks);
+        }
+        CK(gs.launch(s));
+        CK(launch_forked(gl, s));
+    }
+    t_stage = 2;
+    CK(tm.mark(2));
+    // S4 on each query's first candidate (no abandoning): initial upper bounds
+    std::vector<DtwJob32> main_jobs(n);
+    {
+        Batches<DtwJob32> g;
+        for (int d = 0; d < n; d++) {
+            const Set32 &x = sets[d];
+            const Prep32 &p = P[d];
+            DtwJob32 j{};
+            j.test = x.test; j.train = x.train; j.L = x.L; j.W = p.Weff;
+            j.dtw_lo = p.m.dtw_lo; j.dtw_hi = p.m.dtw_hi; j.abs32 = p.m.abs32;
+            j.bsf = p.ws.bsf; j.cand = p.ws.cand; j.cand_count = p.ws.counters + C_CAND;
+            j.counters = p.cnt;
+            j.group = group_from_flags(x.flags);
+            main_jobs[d] = j;
+            // one pair per query: latency-bound, so each pair gets the widest group
+            j.pairs = nullptr; j.seed_keys = p.ws.seed; j.n_seed = x.Q; j.head = nullptr;
+            j.abandon = 0;
+            j.group = (dtw32_rows_ok(x.L, p.Weff) || dtw32_rowsc_ok(x.L, p.Weff))
+                          ? kRowsGroup : dtw32_wide_group(p.Weff);
+            Dtw32Plan pl{};
+            CK(plan_dtw32(j, sms, &pl));
+            j.lanes = pl.lanes;
+            g.add(pl.fn1, pl.fnN, pl.threads, pl.smem, j, pl.blocks);
+        }
+        CK(launch_forked(g, s));
+    }
+    t_stage = 3;
+    CK(tm.mark(3));
+    // S3: compaction against the upper bounds, two passes (count, scatter)
+    for (int pass = 0; pass < 2; pass++) {
+        Batches<CompactJob<float>> g;
+        for (int d = 0; d < n; d++) {
+            const Set32 &x = sets[d];
+            const Prep32 &p = P[d];
+            const dim3 gc = grid_compact(x.Q, x.N);
+            CompactJob<float> j{};
+            j.lb = p.ws.lb; j.Q = x.Q; j.N = x.N; j.bsf = p.ws.bsf; j.seed = p.ws.seed;
+            j.ubof = UbOf<float>{p.m.dtw_hi, p.m.abs32};
+            j.no_prune = p.no_prune ? 1 : 0;
+            j.gx = (int)gc.x;
+            j.scatter = pass;
+            j.bcount = p.ws.buckets; j.bcursor = p.ws.buckets + kBuckets;
+            j.qcount = p.ws.counters + C_QUEUE; j.queue = p.ws.queue;
+            g.add(compact_kernel<float, Src1<CompactJob<float>>>,
+                  compact_kernel<float, SrcN<CompactJob<float>>>, kSmallThreads, 0, j,
+                  (long long)gc.x * gc.y);
+        }
+        CK(g.launch(s));
+    }
+    // the cascade's second stage on the survivors (into the recheck list's
+    // storage, which S5 fills only after the DTW pass)
+    {
+        Batches<CascadeJob> g;
+        for (int d = 0; d < n; d++) {
+            const Set32 &x = sets[d];
+            const Prep32 &p = P[d];
+            if (!p.second) continue;
+            CascadeJob cj{};
+            cj.in = p.ws.queue; cj.in_count = p.ws.counters + C_QUEUE;
+            cj.train = x.train; cj.envq = reinterpret_cast<const float2 *>(p.ws.envq);
+            cj.ends = p.rev ? p.ws.ends : nullptr;
+            cj.bgap = p.imp ? reinterpret_cast<const BGap *>(p.ws.env2) : nullptr;
+            cj.lb = p.ws.lb;
+            cj.N = x.N; cj.L = x.L; cj.nb = bridge_start(x.L, x.V);
+            cj.bsf = p.ws.bsf;
+            cj.lb_lo = p.m.lb_lo; cj.lb_abs = p.m.abs32; cj.dtw_hi = p.m.dtw_hi;
+            cj.abs32 = p.m.abs32;
+            cj.out = p.ws.rlist; cj.out_count = p.ws.counters + C_QUEUE2; cj.counters = p.cnt;
+            const CascadeFns f = cascade_filter_fns(p.rev, p.imp);
+            g.add(f.fn1, f.fnN, 256, 0, cj, cascade_filter_blocks(x.Q * x.N, sms));
+        }
+        CK(g.launch(s));
+    }
+    t_stage = 4;
+    CK(tm.mark(4));
+    // S4 on the survivors, with early abandoning
+    {
+        Batches<DtwJob32> g;
+        for (int d = 0; d < n; d++) {
+            const Prep32 &p = P[d];
+            DtwJob32 j = main_jobs[d];
+            j.pairs = p.second ? p.ws.rlist : p.ws.queue; j.seed_keys = nullptr;
+            j.count = p.ws.counters + (p.second ? C_QUEUE2 : C_QUEUE);
+            j.head = p.ws.counters + C_HEAD;
+            j.abandon = (sets[d].flags & NNDTW_NO_ABANDON) ? 0 : 1;
+            Dtw32Plan pl{};
+            CK(plan_dtw32(j, sms, &pl));
+            j.lanes = pl.lanes;
+            g.add(pl.fn1, pl.fnN, pl.threads, pl.smem, j, pl.blocks);
+        }
+        CK(launch_forked(g, s));
+    }
+    t_stage = 5;
+    CK(tm.mark(5));
+    // S5: near-tie recheck in FP64 and the final argmin
+    std::vector<FinishJob32> fin(n);
+    for (int d = 0; d < n; d++) {
+        const Set32 &x = sets[d];
+        const Prep32 &p = P[d];
+        FinishJob32 &j = fin[d];
+        j.cand = p.ws.cand; j.ccount = p.ws.counters + C_CAND; j.bsf = p.ws.bsf;
+        j.lo = p.m.dtw_lo; j.hi = p.m.dtw_hi; j.abs32 = p.m.abs32;
+        j.rcount = p.ws.rcount; j.exact = p.exact ? 1 : 0; j.rlist = p.ws.rlist;
+        j.counters = p.ws.counters; j.d64 = p.ws.d64; j.best64 = p.ws.best64;
+        j.bestidx = p.ws.bestidx; j.Q = x.Q; j.labels = x.labels;
+        j.nn_idx = x.nn_idx; j.nn_label = x.nn_label; j.nn_dist = x.nn_dist;
+    }
+    auto finish = [&](void (*f1)(Src1<FinishJob32>), void (*fN)(SrcN<FinishJob32>), bool per_q) {
+        Batches<FinishJob32> g;
+        for (int d = 0; d < n; d++)
+            g.add(f1, fN, kSmallThreads, 0, fin[d],
+                  per_q ? (long long)grid_small(sets[d].Q) : finish_blocks(sets[d].Q, sets[d].N));
+        return g.launch(s);
+    };
+    CK(finish(filter32_kernel<Src1<FinishJob32>>, filter32_kernel<SrcN<FinishJob32>>, false));
+    CK(finish(collect32_kernel<Src1<FinishJob32>>, collect32_kernel<SrcN<FinishJob32>>, false));
+    {
+        Batches<DtwJob64> g;
+        for (int d = 0; d < n; d++) {
+            const Set32 &x = sets[d];
+            const Prep32 &p = P[d];
+            DtwJob64 r{};
+            r.test32 = x.test; r.train32 = x.train; r.L = x.L; r.W = p.Weff;
+            r.pairs = p.ws.rlist; r.count = p.ws.counters + C_RECHECK; r.head = nullptr;
+            r.bsf64 = p.ws.best64; r.out = p.ws.d64; r.abandon = 0;
+            Dtw64Plan pl{};
+            CK(plan_dtw64(r, sms, &pl));
+            // a few pairs per dataset at most unless every query is rechecked
+            const long long want = p.exact ? x.Q : std::max<long long>(4, (x.Q + 7) / 8);
+            g.add(pl.fn1, pl.fnN, pl.threads, pl.smem, r, std::min(pl.blocks, want));
+        }
+        CK(launch_forked(g, s));
+    }
+    CK(finish(ties32_kernel<Src1<FinishJob32>>, ties32_kernel<SrcN<FinishJob32>>, false));
+    t_stage = 6;
+    CK(tm.mark(6));
+    CK(finish(finalize32_kernel<Src1<FinishJob32>>, finalize32_kernel<SrcN<FinishJob32>>, true));
+    t_stage = 7;
+    CK(tm.mark(7));
+    if (stats && n == 1) {
+        unsigned long long h[C_COUNT];
+        CK(cudaMemcpyAsync(h, P[0].ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        fill_stats(stats, h, sets[0].N, sets[0].Q, sets[0].L, P[0].Weff, P[0].cnt != nullptr);
+    }
+    return NNDTW_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ helpers
@@ -530,6 +1058,14 @@ const char *nn_dtw_strerror(int code) {
 }
 
 const char *nn_dtw_last_cuda_error(void) { return g_cuda_err; }
+
+long long nn_dtw_last_call_launches(void) { return t_launches; }
+
+int nn_dtw_last_call_stage_launches(long long *h_counts) {
+    if (!h_counts) return NNDTW_EINVAL;
+    for (int k = 0; k < 8; k++) h_counts[k] = t_stage_launches[k];
+    return NNDTW_OK;
+}
 
 int nn_dtw_build_envelopes(const float *d_train, int64_t N, int L, int W, float *d_env,
                            void *stream) {
@@ -650,14 +1186,6 @@ int dtw_windowed(const float *d_test, const float *d_train, const int32_t *d_pai
     return dtw_windowed_ex(d_test, d_train, d_pairs, P, L, W, 0, d_out, stream);
 }
 
-static int group_from_flags(unsigned flags) {
-    const unsigned v = (flags & NNDTW_DTW_GROUP_MASK) >> 8;
-    if (v == 7) {
-        const unsigned lanes = (flags & NNDTW_DTW_ROWS_LANES_MASK) >> 12;
-        return kRowsGroup + (lanes <= 2 ? (int)lanes : 0);
-    }
-    return v ? 1 << (v - 1) : 0;
-}
 
 int dtw_windowed_ex(const float *d_test, const float *d_train, const int32_t *d_pairs, int64_t P,
                     int L, int W, unsigned flags, float *d_out, void *stream) {
@@ -713,144 +1241,15 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
         return NNDTW_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return NNDTW_EINVAL;
     if (!dtw32_supported(W > L - 1 ? L - 1 : W)) return NNDTW_EUNSUPPORTED;
-    const Layout32 ws = layout32(d_workspace, N, Q, L);
-    if (workspace_bytes < ws.bytes) return NNDTW_ENOSPACE;
+    if (workspace_bytes < layout32(nullptr, N, Q, L).bytes) return NNDTW_ENOSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    const int Weff = W > L - 1 ? L - 1 : W;
-    const Margins m = make_margins(L);
-    const int sms = device_sm_count();
-    const int exact = (flags & NNDTW_EXACT_DIST) ? 1 : 0;
-
     const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
+    reset_launch_counts();
     StageTimer tm;
     CK(tm.start(timing, s));
-    CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
-    CK(cudaMemsetAsync(ws.buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, s));
-    CK(cudaMemsetAsync(ws.bsf, 0xff, sizeof(unsigned long long) * Q, s));
-    CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
-    CK(cudaMemsetAsync(ws.best64, 0xff, sizeof(unsigned long long) * Q, s));
-    CK(cudaMemsetAsync(ws.rcount, 0, sizeof(int32_t) * Q, s));
-    CK(cudaMemsetAsync(ws.bestidx, 0x7f, sizeof(int32_t) * Q, s));
-
-    if (flags & NNDTW_CHECK_FINITE) {
-        int rc = check_finite<float>(d_train, N * L, 1e15f, ws.counters + C_BAD, s);
-        if (rc) return rc;
-        rc = check_finite<float>(d_test, Q * L, 1e15f, ws.counters + C_BAD, s);
-        if (rc) return rc;
-        unsigned long long bad = 0;
-        CK(cudaMemcpyAsync(&bad, ws.counters + C_BAD, sizeof(bad), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (bad) return NNDTW_ENONFINITE;
-    }
-
-    const float *env = d_env;
-    if (!env) {
-        CK(launch_envelopes<float>(d_train, N, L, Weff, ws.env, s));
-        env = ws.env;
-    }
-    // the query envelopes, for the reverse bound LB_Enhanced(B, A) (asked for
-    // with NNDTW_REVERSE: whether reading every surviving pair's training
-    // series once more pays off depends on the data, so the tuner decides)
-    // (LB_Keogh as the bound, NNDTW_KEOGH_BOUND, has no second stage)
-    const bool keogh = (flags & NNDTW_KEOGH_BOUND) != 0;
-    const bool rev = (flags & NNDTW_REVERSE) && !keogh &&
-                     !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
-    // and the training series' second envelopes, for the bound with the
-    // LB_Improved bridge (asked for with NNDTW_IMPROVED, also a tuning choice)
-    const bool imp = (flags & NNDTW_IMPROVED) && !keogh && !(flags & NNDTW_NO_PRUNE);
-    if (rev || imp) CK(launch_envelopes<float>(d_test, Q, L, Weff, ws.envq, s));
-    if (imp) {
-        CK(launch_second_envelopes<float>(env, N, L, Weff, ws.env2, s));
-        CK(launch_pack_bgap(d_train, ws.env2, N * L, s));
-    }
-    CK(tm.mark(1));
-    // S2: safe bounds, and per query the Euclidean-nearest series (first candidate)
-    CK(launch_lb<float>(d_test, Q, d_train, env, N, L, Weff, V, keogh, true, m.lb_lo, m.abs32,
-                        ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
-                        (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
-    CK(tm.mark(2));
-    unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
-    // S4 on the first candidate of every query: initial upper bounds
-    DtwJob32 j{};
-    j.test = d_test; j.train = d_train; j.L = L; j.W = Weff;
-    j.dtw_lo = m.dtw_lo; j.dtw_hi = m.dtw_hi; j.abs32 = m.abs32;
-    j.bsf = ws.bsf; j.cand = ws.cand; j.cand_count = ws.counters + C_CAND;
-    j.counters = cnt;
-    j.group = group_from_flags(flags);
-    j.pairs = nullptr; j.seed_keys = ws.seed; j.n_seed = Q; j.head = nullptr; j.abandon = 0;
-    // one pair per query: latency-bound, so spread each pair over the widest group
-    const int main_group = j.group;
-    j.group = (dtw32_rows_ok(L, Weff) || dtw32_rowsc_ok(L, Weff)) ? kRowsGroup
-                                                                : dtw32_wide_group(Weff);
-    CK(launch_dtw32(j, sms, s));
-    j.group = main_group;
-    CK(tm.mark(3));
-    // S3: compaction against the upper bounds
-    {
-        UbOf<float> ubf{m.dtw_hi, m.abs32};
-        const int np = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
-        for (int pass = 0; pass < 2; pass++) {
-            compact_kernel<float><<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
-                ws.lb, Q, N, ws.bsf, ws.seed, ubf, np, pass, ws.buckets, ws.buckets + kBuckets,
-                ws.queue, ws.counters + C_QUEUE);
-            CK(cudaGetLastError());
-        }
-    }
-    // the cascade's second stage on the survivors (into the recheck list's
-    // storage, which S5 fills only after the DTW pass)
-    const bool second = rev || imp;
-    if (second) {
-        CascadeJob cj{};
-        cj.in = ws.queue; cj.in_count = ws.counters + C_QUEUE;
-        cj.train = d_train; cj.envq = reinterpret_cast<const float2 *>(ws.envq);
-        cj.ends = rev ? ws.ends : nullptr;
-        cj.bgap = imp ? reinterpret_cast<const BGap *>(ws.env2) : nullptr;
-        cj.lb = ws.lb;
-        cj.N = N; cj.L = L; cj.nb = bridge_start(L, V);
-        cj.bsf = ws.bsf;
-        cj.lb_lo = m.lb_lo; cj.lb_abs = m.abs32; cj.dtw_hi = m.dtw_hi; cj.abs32 = m.abs32;
-        cj.out = ws.rlist; cj.out_count = ws.counters + C_QUEUE2; cj.counters = cnt;
-        CK(launch_cascade_filter(cj, Q * N, sms, s));
-    }
-    CK(tm.mark(4));
-    // S4 on the survivors, with early abandoning
-    j.pairs = second ? ws.rlist : ws.queue; j.seed_keys = nullptr;
-    j.count = ws.counters + (second ? C_QUEUE2 : C_QUEUE);
-    j.head = ws.counters + C_HEAD;
-    j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
-    CK(launch_dtw32(j, sms, s));
-    CK(tm.mark(5));
-    // S5: near-tie recheck in FP64 and the final argmin
-    const long long cap = (long long)Q * N + Q;
-    const unsigned gs = grid_small(cap);
-    filter32_kernel<<<gs, kSmallThreads, 0, s>>>(ws.cand, ws.counters + C_CAND, ws.bsf, m.dtw_lo,
-                                                 m.dtw_hi, m.abs32, ws.rcount);
-    CK(cudaGetLastError());
-    collect32_kernel<<<gs, kSmallThreads, 0, s>>>(ws.cand, ws.counters + C_CAND, ws.bsf,
-                                                  m.dtw_lo, m.dtw_hi, m.abs32, ws.rcount, exact,
-                                                  ws.rlist, ws.counters);
-    CK(cudaGetLastError());
-    DtwJob64 r{};
-    r.test32 = d_test; r.train32 = d_train; r.L = L; r.W = Weff;
-    r.pairs = ws.rlist; r.count = ws.counters + C_RECHECK; r.head = nullptr;
-    r.bsf64 = ws.best64; r.out = ws.d64; r.abandon = 0;
-    CK(launch_dtw64(r, sms, s));
-    ties32_kernel<<<gs, kSmallThreads, 0, s>>>(ws.rlist, ws.counters + C_RECHECK, ws.d64,
-                                               ws.best64, ws.bestidx);
-    CK(cudaGetLastError());
-    CK(tm.mark(6));
-    finalize32_kernel<<<grid_small(Q), kSmallThreads, 0, s>>>(
-        Q, ws.bsf, ws.rcount, ws.best64, ws.bestidx, exact, d_train_labels, d_nn_idx, d_nn_label,
-        d_nn_dist);
-    CK(cudaGetLastError());
-    CK(tm.mark(7));
-    if (stats) {
-        unsigned long long h[C_COUNT];
-        CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        fill_stats(stats, h, N, Q, L, Weff, cnt != nullptr);
-    }
-    return NNDTW_OK;
+    const Set32 set{d_train, d_train_labels, N, d_test, Q, L, W, V, d_env, flags,
+                    d_nn_idx, d_nn_label, d_nn_dist, d_workspace};
+    return run32(&set, 1, stats != nullptr, timing, stats, tm, s);
 }
 
 int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int64_t N,
@@ -917,12 +1316,18 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     CK(launch_dtw64(j, sms, s));
     CK(tm.mark(3));
     {
-        UbOf<double> ubd{};
-        const int np = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
+        const dim3 gc = grid_compact(Q, N);
+        CompactJob<double> cj{};
+        cj.lb = ws.lb; cj.Q = Q; cj.N = N; cj.bsf = ws.bsf64; cj.seed = ws.seed;
+        cj.ubof = UbOf<double>{};
+        cj.no_prune = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
+        cj.gx = (int)gc.x;
+        cj.bcount = ws.buckets; cj.bcursor = ws.buckets + kBuckets;
+        cj.qcount = ws.counters + C_QUEUE; cj.queue = ws.queue;
         for (int pass = 0; pass < 2; pass++) {
-            compact_kernel<double><<<grid_compact(Q, N), kSmallThreads, 0, s>>>(
-                ws.lb, Q, N, ws.bsf64, ws.seed, ubd, np, pass, ws.buckets, ws.buckets + kBuckets,
-                ws.queue, ws.counters + C_QUEUE);
+            cj.scatter = pass;
+            compact_kernel<double, Src1<CompactJob<double>>>
+                <<<gc.x * gc.y, kSmallThreads, 0, s>>>(Src1<CompactJob<double>>{cj});
             CK(cudaGetLastError());
         }
     }
@@ -957,6 +1362,64 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
         CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         fill_stats(stats, h, N, Q, L, Weff, cnt != nullptr);
+    }
+    return NNDTW_OK;
+}
+
+size_t nn_dtw_batch_workspace_size(const nndtw_dataset *h_sets, int n) {
+    if (!h_sets || n < 0) return 0;
+    size_t tot = 256;
+    for (int i = 0; i < n; i++) {
+        const nndtw_dataset &d = h_sets[i];
+        const size_t b = nn_dtw_workspace_size(d.N, d.Q, d.L, d.W, d.V, 0);
+        if (b == 0) return 0;
+        tot += (b + 255) & ~size_t(255);
+    }
+    return tot;
+}
+
+int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
+                          size_t workspace_bytes, unsigned flags, void *stream) {
+    if (n < 0 || (n > 0 && !h_sets)) return NNDTW_EINVAL;
+    if (n == 0) return NNDTW_OK;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return NNDTW_EINVAL;
+    std::vector<Set32> sets;
+    sets.reserve(n);
+    size_t off = 0;
+    for (int i = 0; i < n; i++) {
+        const nndtw_dataset &d = h_sets[i];
+        const size_t b = nn_dtw_workspace_size(d.N, d.Q, d.L, d.W, d.V, 0);
+        if (b == 0) return NNDTW_EINVAL;
+        const unsigned f = (flags | d.flags) & ~NNDTW_TIME_STAGES;
+        if ((f & NNDTW_LEAVE_ONE_OUT) && (d.Q != d.N || d.N < 2)) return NNDTW_EINVAL;
+        if (d.Q > 0 && (!d.d_train || !d.d_train_labels || !d.d_test || !d.d_nn_idx ||
+                        !d.d_nn_label || !d.d_nn_dist))
+            return NNDTW_EINVAL;
+        if (!dtw32_supported(d.W > d.L - 1 ? d.L - 1 : d.W)) return NNDTW_EUNSUPPORTED;
+        if (d.Q > 0)
+            sets.push_back(Set32{d.d_train, d.d_train_labels, d.N, d.d_test, d.Q, d.L, d.W, d.V,
+                                 d.d_env, f, d.d_nn_idx, d.d_nn_label, d.d_nn_dist,
+                                 static_cast<char *>(d_workspace) + off});
+        off += (b + 255) & ~size_t(255);
+    }
+    if (workspace_bytes < off) return NNDTW_ENOSPACE;
+    const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
+    if (timing && sets.size() > (size_t)kMaxSets) return NNDTW_EINVAL;
+    // the datasets with the most DTW work first: in every stage their CTAs
+    // start first, and the small datasets fill in behind them
+    std::stable_sort(sets.begin(), sets.end(), [](const Set32 &a, const Set32 &b) {
+        const double wa = (double)a.N * a.Q * band_cells(a.L, a.W);
+        const double wb = (double)b.N * b.Q * band_cells(b.L, b.W);
+        return wa > wb;
+    });
+    cudaStream_t s = (cudaStream_t)stream;
+    reset_launch_counts();
+    StageTimer tm;
+    CK(tm.start(timing, s));
+    for (size_t k = 0; k < sets.size(); k += kMaxSets) {
+        const int m = (int)std::min<size_t>(kMaxSets, sets.size() - k);
+        const int rc = run32(sets.data() + k, m, false, timing, nullptr, tm, s);
+        if (rc != NNDTW_OK) return rc;
     }
     return NNDTW_OK;
 }
@@ -1015,6 +1478,93 @@ int nn_dtw_search_host(const float *h_train, const int32_t *h_train_labels, int6
     CK(cudaMemcpyAsync(h_nn_idx, h.idx, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h_nn_label, h.lab, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h_nn_dist, h.dist, sizeof(double) * Q, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NNDTW_OK;
+}
+
+namespace {
+// Device buffer of nn_dtw_search_batched_host: every dataset's inputs and
+// outputs, then the batched search's workspace.
+struct HostBatchLayout {
+    std::vector<nndtw_dataset> dev;
+    size_t ws_off, ws_bytes, bytes;
+};
+bool host_batch_layout(const nndtw_host_dataset *h, int n, void *base, HostBatchLayout *lay) {
+    Carve c(base);
+    lay->dev.resize(n);
+    for (int i = 0; i < n; i++) {
+        const nndtw_host_dataset &x = h[i];
+        if (!search_sizes_ok(x.N, x.Q, x.L, x.W, x.V)) return false;
+        nndtw_dataset &d = lay->dev[i];
+        d = nndtw_dataset{};
+        d.d_train = c.take<float>((size_t)x.N * x.L);
+        d.d_train_labels = c.take<int32_t>(x.N);
+        d.N = x.N;
+        d.d_test = c.take<float>((size_t)x.Q * x.L);
+        d.Q = x.Q;
+        d.L = x.L; d.W = x.W; d.V = x.V;
+        d.d_env = nullptr;
+        d.d_nn_idx = c.take<int32_t>(x.Q);
+        d.d_nn_label = c.take<int32_t>(x.Q);
+        d.d_nn_dist = c.take<double>(x.Q);
+        d.flags = x.flags;
+    }
+    lay->ws_bytes = nn_dtw_batch_workspace_size(lay->dev.data(), n);
+    if (lay->ws_bytes == 0) return false;
+    lay->ws_off = (c.off + 255) & ~size_t(255);
+    lay->bytes = lay->ws_off + lay->ws_bytes + 256;
+    return true;
+}
+}  // namespace
+
+size_t nn_dtw_batch_host_buffer_size(const nndtw_host_dataset *h_sets, int n) {
+    if (!h_sets || n < 1) return 0;
+    HostBatchLayout lay;
+    return host_batch_layout(h_sets, n, nullptr, &lay) ? lay.bytes : 0;
+}
+
+int nn_dtw_search_batched_host(const nndtw_host_dataset *h_sets, int n, void *d_buffer,
+                               size_t buffer_bytes, unsigned flags, void *stream) {
+    if (n < 0 || (n > 0 && !h_sets)) return NNDTW_EINVAL;
+    if (n == 0) return NNDTW_OK;
+    if (!d_buffer || (reinterpret_cast<uintptr_t>(d_buffer) & 255u)) return NNDTW_EINVAL;
+    if (flags & NNDTW_TIME_STAGES) return NNDTW_EINVAL;
+    for (int i = 0; i < n; i++) {
+        const nndtw_host_dataset &x = h_sets[i];
+        if (x.Q > 0 && (!x.h_train || !x.h_train_labels || !x.h_test || !x.h_nn_idx ||
+                        !x.h_nn_label || !x.h_nn_dist))
+            return NNDTW_EINVAL;
+    }
+    HostBatchLayout lay;
+    if (!host_batch_layout(h_sets, n, d_buffer, &lay)) return NNDTW_EINVAL;
+    if (buffer_bytes < lay.bytes) return NNDTW_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < n; i++) {
+        const nndtw_host_dataset &x = h_sets[i];
+        const nndtw_dataset &d = lay.dev[i];
+        if (x.Q == 0) continue;
+        CK(cudaMemcpyAsync(const_cast<float *>(d.d_train), x.h_train, sizeof(float) * x.N * x.L,
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<int32_t *>(d.d_train_labels), x.h_train_labels,
+                           sizeof(int32_t) * x.N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<float *>(d.d_test), x.h_test, sizeof(float) * x.Q * x.L,
+                           cudaMemcpyHostToDevice, s));
+    }
+    const int rc = nn_dtw_search_batched(lay.dev.data(), n,
+                                         static_cast<char *>(d_buffer) + lay.ws_off, lay.ws_bytes,
+                                         flags, stream);
+    if (rc != NNDTW_OK) return rc;
+    for (int i = 0; i < n; i++) {
+        const nndtw_host_dataset &x = h_sets[i];
+        const nndtw_dataset &d = lay.dev[i];
+        if (x.Q == 0) continue;
+        CK(cudaMemcpyAsync(x.h_nn_idx, d.d_nn_idx, sizeof(int32_t) * x.Q, cudaMemcpyDeviceToHost,
+                           s));
+        CK(cudaMemcpyAsync(x.h_nn_label, d.d_nn_label, sizeof(int32_t) * x.Q,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(x.h_nn_dist, d.d_nn_dist, sizeof(double) * x.Q, cudaMemcpyDeviceToHost,
+                           s));
+    }
     CK(cudaStreamSynchronize(s));
     return NNDTW_OK;
 }

@@ -105,6 +105,14 @@ class DatasetDesc(ctypes.Structure):
                 ("d_nn_dist", _vp), ("flags", ctypes.c_uint)]
 
 
+class HostDatasetDesc(ctypes.Structure):
+    """Mirror of nndtw_host_dataset."""
+    _fields_ = [("h_train", _vp), ("h_train_labels", _vp), ("N", ctypes.c_int64),
+                ("h_test", _vp), ("Q", ctypes.c_int64), ("L", ctypes.c_int), ("W", ctypes.c_int),
+                ("V", ctypes.c_int), ("h_nn_idx", _vp), ("h_nn_label", _vp),
+                ("h_nn_dist", _vp), ("flags", ctypes.c_uint)]
+
+
 def _declare(lib):
     sig = {
         "nn_dtw_build_envelopes": [_vp, _i64, _int, _int, _vp, _vp],
@@ -141,12 +149,21 @@ def _declare(lib):
     lib.nn_dtw_strerror.restype = ctypes.c_char_p
     lib.nn_dtw_last_cuda_error.argtypes = []
     lib.nn_dtw_last_cuda_error.restype = ctypes.c_char_p
+    lib.nn_dtw_last_call_stage_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+    lib.nn_dtw_last_call_stage_launches.restype = _int
+    lib.nn_dtw_last_call_launches.argtypes = []
+    lib.nn_dtw_last_call_launches.restype = ctypes.c_longlong
     lib.nn_dtw_version.argtypes = []
     lib.nn_dtw_version.restype = _int
     lib.nn_dtw_batch_workspace_size.argtypes = [ctypes.POINTER(DatasetDesc), _int]
     lib.nn_dtw_batch_workspace_size.restype = _sz
     lib.nn_dtw_search_batched.argtypes = [ctypes.POINTER(DatasetDesc), _int, _vp, _sz, _uint, _vp]
     lib.nn_dtw_search_batched.restype = _int
+    lib.nn_dtw_batch_host_buffer_size.argtypes = [ctypes.POINTER(HostDatasetDesc), _int]
+    lib.nn_dtw_batch_host_buffer_size.restype = _sz
+    lib.nn_dtw_search_batched_host.argtypes = [ctypes.POINTER(HostDatasetDesc), _int, _vp, _sz,
+                                               _uint, _vp]
+    lib.nn_dtw_search_batched_host.restype = _int
     lib.nn_dtw_learn_window_workspace_size.argtypes = [_i64, _int, _vp, _int, _int]
     lib.nn_dtw_learn_window_workspace_size.restype = _sz
     lib.nn_dtw_learn_window.argtypes = [_vp, _vp, _i64, _int, _vp, _int, _int, _uint, _vp, _vp,
@@ -660,6 +677,51 @@ def nn_dtw_search_host(train, labels, test, W: int, V: int, flags: int = 0, buff
     return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
 
 
+class BatchedHostSearch:
+    """The batched search end to end on host (numpy) arrays through
+    nn_dtw_search_batched_host: every call copies each dataset's inputs to
+    the device, searches the whole batch and copies the results back.
+    ``sets``: list of dicts with numpy arrays train (float32 [N, L]), labels
+    (int32 [N]), test (float32 [Q, L]) and W, V (optional flags).  The
+    output arrays (one (idx, label, dist) triple per dataset, reused by every
+    call) and the device buffer are allocated once here; pass pinned arrays
+    (and ``outs``) for asynchronous copies."""
+
+    def __init__(self, sets, outs=None, device=None):
+        import torch
+        lib = load()
+        self.sets = sets
+        if outs is None:
+            outs = [(np.empty(d["test"].shape[0], np.int32), np.empty(d["test"].shape[0], np.int32),
+                     np.empty(d["test"].shape[0], np.float64)) for d in sets]
+        self.outs = outs
+        self.arr = (HostDatasetDesc * len(sets))()
+        for i, (d, o) in enumerate(zip(sets, outs)):
+            N, L = d["train"].shape
+            Q = d["test"].shape[0]
+            self.arr[i] = HostDatasetDesc(
+                _host(d["train"], np.float32, "train", (N, L)),
+                _host(d["labels"], np.int32, "labels", (N,)), N,
+                _host(d["test"], np.float32, "test", (Q, L)), Q, L, int(d["W"]), int(d["V"]),
+                _host(o[0], np.int32, "nn_idx", (Q,)), _host(o[1], np.int32, "nn_label", (Q,)),
+                _host(o[2], np.float64, "nn_dist", (Q,)), int(d.get("flags", 0)))
+        need = lib.nn_dtw_batch_host_buffer_size(self.arr, len(sets))
+        if need == 0:
+            raise NnDtwError(EINVAL, "nn_dtw_batch_host_buffer_size")
+        self.buffer = torch.empty((need,), dtype=torch.uint8,
+                                  device=device if device is not None else "cuda")
+
+    def run(self, flags: int = 0, stream=None):
+        lib = load()
+        with _on([self.buffer], stream):
+            _check(lib.nn_dtw_search_batched_host(self.arr, len(self.sets),
+                                                  _dev(self.buffer, self.buffer.dtype, "buffer"),
+                                                  self.buffer.numel(), int(flags),
+                                                  _stream(stream)),
+                   "nn_dtw_search_batched_host")
+        return self.outs
+
+
 def nn_dtw_stage_times() -> dict:
     """Stage times (ms) of this thread's last search run with TIME_STAGES."""
     lib = load()
@@ -678,6 +740,18 @@ def nn_dtw_probe_cell_rate(iters: int = 20000, stream=None) -> float:
     _check(lib.nn_dtw_probe_cell_rate(_dev(sink, torch.uint8, "sink"), n, int(iters),
                                       ctypes.byref(out), _stream(stream)), "nn_dtw_probe_cell_rate")
     return float(out.value)
+
+
+def nn_dtw_last_call_launches() -> int:
+    """Kernel launches issued by this thread's last FP32 search call."""
+    return int(load().nn_dtw_last_call_launches())
+
+
+def nn_dtw_last_call_stage_launches() -> dict:
+    """Kernel launches of this thread's last FP32 search call, per stage."""
+    buf = (ctypes.c_longlong * 8)()
+    _check(load().nn_dtw_last_call_stage_launches(buf), "nn_dtw_last_call_stage_launches")
+    return {name: int(buf[i]) for i, name in enumerate(STAGES[:7])}
 
 
 def nn_dtw_strerror(code: int) -> str:

@@ -2,16 +2,20 @@
 
 Training sets (and their envelopes, built once on the device) stay resident.
 Queries arrive one at a time (``submit``) for any of the sets.  A scheduler
-thread keeps up to ``n_slots`` batches in flight, each on its own CUDA stream:
-whenever a slot is free it takes the dataset whose oldest waiting query has
-waited longest, admits as many of that dataset's waiting queries as fit both
-``max_batch`` and the device-memory budget (the batch's search workspace,
-query and result buffers), copies them to the device and launches
-``nn_dtw_search`` on the slot's stream.  Batches on different slots overlap on
-the GPU; queries that arrive while others run are admitted as soon as a slot
-and memory free up.  Completed batches are detected by CUDA events, their
+thread keeps up to ``n_slots`` batches in flight, each on its own CUDA stream.
+Whenever a slot is free it forms a batch across datasets: it visits the sets
+in the order of their oldest waiting query and admits from each as many
+waiting queries as fit both ``max_batch`` (queries per batch, all sets
+together) and the device-memory budget (the batch's search workspace, query
+and result buffers); a set that does not fit ends the batch, so the oldest
+query is never passed over.  The batch's queries are copied to the device and
+searched by one ``nn_dtw_search_batched`` call on the slot's stream, every set
+of the batch in the same stage launches.  Batches on different slots overlap
+on the GPU; queries that arrive while others run are admitted as soon as a
+slot and memory free up.  Completed batches are detected by CUDA events, their
 results copied back and the futures resolved.  A query's result does not
-depend on which batch it joins (the search is exact per query).
+depend on which batch it joins (the search is exact per query).  A set whose
+one-query batch can never fit the budget is refused when the server starts.
 """
 from __future__ import annotations
 
@@ -48,12 +52,9 @@ class _Req:
 
 @dataclass(eq=False)
 class _Batch:
-    set_id: int
-    reqs: list
+    parts: list          # [(set_id, [requests], host outputs (idx, label, dist))]
     stream: object
     event: object
-    out: tuple
-    host_out: tuple
     nbytes: int
     t_launch: float
     keep: list = field(default_factory=list)
@@ -150,55 +151,73 @@ class Server:
             s.flags = nndtw.DTW_GROUP(g) if g else 0
 
     def _batch_bytes(self, s: _Set, Q: int) -> int:
-        return (nndtw.nn_dtw_workspace_size(s.N, Q, s.L, s.W, s.V) + Q * s.L * 4 + Q * 16 + 4096)
+        """Device bytes of Q queries of set s in a batch: their share of the
+        batched search's workspace, the query series and the outputs."""
+        return (nndtw.nn_dtw_workspace_size(s.N, Q, s.L, s.W, s.V) + 256 + Q * s.L * 4
+                + Q * 16 + 4096)
 
     def _pick(self):
-        """Dataset whose oldest waiting query is oldest, and how many fit."""
-        best, t_best = None, None
-        for sid, dq in self.pending.items():
-            if dq and (t_best is None or dq[0].t_arrival < t_best):
-                best, t_best = sid, dq[0].t_arrival
-        if best is None:
-            return None, 0
-        s = self.sets[best]
-        n = min(len(self.pending[best]), self.max_batch)
-        while n > 0 and self.in_use + self._batch_bytes(s, n) > self.budget:
-            n //= 2
-        return best, n
+        """The batch to launch: [(set_id, n)] in the order of the sets'
+        oldest waiting queries, within max_batch and the memory budget."""
+        order = sorted((dq[0].t_arrival, sid) for sid, dq in self.pending.items() if dq)
+        take, total, used = [], 0, 0
+        for _, sid in order:
+            room = self.max_batch - total
+            if room <= 0:
+                break
+            s = self.sets[sid]
+            n = min(len(self.pending[sid]), room)
+            while n > 0 and self.in_use + used + self._batch_bytes(s, n) > self.budget:
+                n //= 2
+            if n == 0:
+                break   # the next set in line waits for memory: nobody jumps it
+            take.append((sid, n))
+            total += n
+            used += self._batch_bytes(s, n)
+        return take, used
 
-    def _launch(self, slot: int, sid: int, n: int):
+    def _launch(self, slot: int, take, nbytes: int):
         torch = self.torch
-        s = self.sets[sid]
-        reqs = [self.pending[sid].popleft() for _ in range(n)]
-        nbytes = self._batch_bytes(s, n)
-        self.in_use += nbytes
         stream = self.streams[slot]
-        host_q = torch.from_numpy(np.stack([r.query for r in reqs])).pin_memory()
+        self.in_use += nbytes
+        parts, descs, keep = [], [], []
         with torch.cuda.stream(stream):
-            dq = host_q.to(self.dev, non_blocking=True)
-            ws = torch.empty(nndtw.nn_dtw_workspace_size(s.N, n, s.L, s.W, s.V),
-                             dtype=torch.uint8, device=self.dev)
-            out = (torch.empty(n, dtype=torch.int32, device=self.dev),
-                   torch.empty(n, dtype=torch.int32, device=self.dev),
-                   torch.empty(n, dtype=torch.float64, device=self.dev))
-            nndtw.nn_dtw_search(s.train, s.labels, dq, s.W, s.V, env=s.env, flags=s.flags,
-                                workspace=ws, out=out, stream=stream)
-            host_out = tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in out)
-            for h, o in zip(host_out, out):
-                h.copy_(o, non_blocking=True)
+            for sid, n in take:
+                s = self.sets[sid]
+                reqs = [self.pending[sid].popleft() for _ in range(n)]
+                host_q = torch.from_numpy(np.stack([r.query for r in reqs])).pin_memory()
+                dq = host_q.to(self.dev, non_blocking=True)
+                out = (torch.empty(n, dtype=torch.int32, device=self.dev),
+                       torch.empty(n, dtype=torch.int32, device=self.dev),
+                       torch.empty(n, dtype=torch.float64, device=self.dev))
+                descs.append(dict(train=s.train, labels=s.labels, test=dq, W=s.W, V=s.V,
+                                  env=s.env, flags=s.flags))
+                host_out = tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True)
+                                 for o in out)
+                parts.append((sid, reqs, host_out, out))
+                keep += [host_q, dq, *out]
+            ws = torch.empty(nndtw.nn_dtw_batch_workspace_size(descs), dtype=torch.uint8,
+                             device=self.dev)
+            nndtw.nn_dtw_search_batched(descs, workspace=ws, outs=[p[3] for p in parts],
+                                        stream=stream)
+            for _, _, host_out, out in parts:
+                for h, o in zip(host_out, out):
+                    h.copy_(o, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        self.inflight.append(_Batch(sid, reqs, stream, ev, out, host_out, nbytes,
-                                    time.perf_counter(), keep=[host_q, dq, ws]))
+        keep.append(ws)
+        self.inflight.append(_Batch([(sid, reqs, host_out) for sid, reqs, host_out, _ in parts],
+                                    stream, ev, nbytes, time.perf_counter(), keep=keep))
         self.batches += 1
 
     def _retire(self, b: _Batch, slot: int):
-        idx, lab, dist = (h.numpy() for h in b.host_out)
         now = time.perf_counter()
-        for k, r in enumerate(b.reqs):
-            r.future.set_result((int(idx[k]), int(lab[k]), float(dist[k])))
-            self.latencies.append(now - r.t_arrival)
-        self.completed += len(b.reqs)
+        for _, reqs, host_out in b.parts:
+            idx, lab, dist = (h.numpy() for h in host_out)
+            for k, r in enumerate(reqs):
+                r.future.set_result((int(idx[k]), int(lab[k]), float(dist[k])))
+                self.latencies.append(now - r.t_arrival)
+            self.completed += len(reqs)
         self.t_last = now
         self.in_use -= b.nbytes
         self.free_slots.append(slot)
@@ -210,9 +229,10 @@ class Server:
             with self.lock:
                 self.running = False
                 for b in self.inflight:
-                    for r in b.reqs:
-                        if not r.future.done():
-                            r.future.set_exception(e)
+                    for _, reqs, _ in b.parts:
+                        for r in reqs:
+                            if not r.future.done():
+                                r.future.set_exception(e)
                 self.inflight.clear()
                 for dq in self.pending.values():
                     while dq:
@@ -238,10 +258,10 @@ class Server:
                         progressed = True
                 # admit new batches into free slots
                 while self.free_slots:
-                    sid, n = self._pick()
-                    if sid is None or n == 0:
+                    take, nbytes = self._pick()
+                    if not take:
                         break
-                    self._launch(self.free_slots.pop(), sid, n)
+                    self._launch(self.free_slots.pop(), take, nbytes)
                     progressed = True
             if not progressed:
                 if self.inflight:

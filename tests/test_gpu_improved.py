@@ -78,7 +78,7 @@ def test_lb_improved_f64_parity(lib, orc, L, W, V):
     assert np.all(safe <= ref)
 
 
-def test_lb_improved_rejects_keogh_flag(lib):
+def test_lb_enhanced_improved_rejects_lb_new_flag(lib):
     import ctypes
     L, W, V = 16, 2, 2
     x = _t(_series(1, 4, L))
@@ -88,9 +88,9 @@ def test_lb_improved_rejects_keogh_flag(lib):
     raw = lib.load()
     rc = raw.lb_enhanced_improved(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(env.data_ptr()),
                                   4, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(env.data_ptr()),
-                                  ctypes.c_void_p(env2.data_ptr()), 4, L, W, V, lib.LB_KEOGH,
+                                  ctypes.c_void_p(env2.data_ptr()), 4, L, W, V, lib.LB_NEW,
                                   ctypes.c_void_p(out.data_ptr()), None)
-    assert rc == 1   # NNDTW_EINVAL
+    assert rc == 1   # NNDTW_EINVAL (NNDTW_LB_KEOGH selects LB_Improved itself)
 
 
 def _search(lib, train, labels, test, W, V, flags):
