@@ -30,7 +30,8 @@
  *  - Inputs must be finite with magnitude below 1e15 (FP32 entry points) or
  *    1e150 (FP64 entry points); the kernels use +-1e30 / +-1e200 sentinels
  *    outside the series.  NNDTW_CHECK_FINITE makes the search verify this.
- *  - Limits: 2 <= L <= NNDTW_MAX_L, 1 <= N and N*Q below 2^31 for the search.
+ *  - Limits: 2 <= L <= NNDTW_MAX_L, 1 <= N < 2^31 and 0 <= Q < 2^31 for the
+ *    search (any N x Q: queries run in chunks, see NNDTW_CHUNK_PAIRS).
  */
 #ifndef NNDTW_H
 #define NNDTW_H
@@ -49,6 +50,11 @@ extern "C" {
 #endif
 
 #define NNDTW_MAX_L 8192
+/* A search runs its queries in chunks of at most this many (query, training
+ * series) pairs, one after another in the same workspace, so that the
+ * workspace stays bounded (about 48 bytes per pair of a chunk) whatever Q x N
+ * is; results do not depend on the chunking. */
+#define NNDTW_CHUNK_PAIRS (1ll << 26)
 
 /* status codes */
 #define NNDTW_OK 0
@@ -257,8 +263,11 @@ NNDTW_API size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V
  * Q == 0 is a no-op.  d_workspace must hold nn_dtw_workspace_size() bytes
  * (NNDTW_ENOSPACE otherwise), 256-byte aligned.  stats may be NULL.
  * Errors: NNDTW_EINVAL for null pointers, N < 1, Q < 0, L < 2 or
- * > NNDTW_MAX_L, W < 0, V < 1, N*Q >= 2^31; NNDTW_ENONFINITE (with
- * NNDTW_CHECK_FINITE; the call then waits for the stream).
+ * > NNDTW_MAX_L, W < 0, V < 1, N or Q >= 2^31; NNDTW_ENONFINITE (with
+ * NNDTW_CHECK_FINITE; the call then waits for the stream).  Searches whose
+ * Q x N exceeds NNDTW_CHUNK_PAIRS run their queries in chunks; with
+ * NNDTW_TIME_STAGES the stage events then span the whole search but the
+ * boundaries between stages are those of the last chunk.
  */
 NNDTW_API int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N,
                   const float *d_test, int64_t Q, int L, int W, int V,

@@ -2,11 +2,12 @@
 // with a group of G = 8 or 16 lanes per pair (32 / G pairs per warp),
 // L <= 64 G.
 //
-// The same row layout as the one-pair-per-warp kernel: lane g of a group
-// owns C consecutive columns, split into two independent halves one row
-// apart, and the rows stream through the group.  With fewer lanes per pair
-// the wavefront fills in 2G steps instead of 64, which is what matters when
-// most pairs are abandoned after a few dozen rows.  The pairs of a warp
+// The row layout of the one-pair-per-warp kernel: lane g of a group owns C
+// consecutive columns, split into K independent parts (K = 2, one for C < 4),
+// each one row behind the one before, and the rows stream through the group.
+// With fewer lanes per pair the wavefront fills in K G steps instead of
+// 2 x 32, which is what matters when most pairs are abandoned after a few
+// dozen rows.  The pairs of a warp
 // advance independently, so everything that differs between them is kept
 // out of the step loop:
 //  - the G C columns are placed so that column L-1 is the last column of
@@ -35,43 +36,62 @@ __host__ __device__ constexpr int rowsg_min_blocks(int C) {
     return C <= 12 ? 6 : C <= 15 ? 5 : C <= 25 ? 4 : C <= 38 ? 3 : 2;
 }
 
-// One step of one lane from Din to Dout: the first half of its columns
-// advances to row i0 = s - K gl, the second half to row i0 - 1.
-template <int C, int K, int C0>
+// The K parts of a lane's C columns: part k holds columns [part_lo(k),
+// part_lo(k+1)), every part non-empty (K <= C).  Part k of lane gl works on
+// row s - K gl - k at step s: each part is a dependency chain along its row,
+// and the K chains of a lane are independent.  Two parts (K = 2) measured as
+// fast as four on the full-window datasets of the batched workload (7.0
+// Tcell/s with 16 lanes per pair at L = 1012 either way) and fill the
+// wavefront in half the steps, so the kernel uses two.
+template <int C> __host__ __device__ constexpr int rowsg_parts() {
+    return C >= 4 ? 2 : 1;
+}
+template <int C, int K> __host__ __device__ constexpr int part_lo(int k) { return k * C / K; }
+
+// One step of one lane from Din to Dout.  a[k] is part k's query value,
+// hprev[k] (k >= 1) the previous step's value of the column in front of part
+// k (part k-1's last column): the diagonal predecessor of part k's first cell.
+template <int C, int K>
 __device__ __forceinline__ void rowsg_step(const float (&Din)[C], float (&Dout)[C],
-                                           const float (&B)[C], float &a0, float &a1,
-                                           float &anext, float &diag_in, float &h0prev,
+                                           const float (&B)[C], float (&a)[K], float &anext,
+                                           float &diag_in, float (&hprev)[K],
                                            const float *ap, int s, int gl, int G, int L) {
     const unsigned FULL = 0xffffffffu;
     const float INF = inf_of<float>();
-    float a_in = __shfl_up_sync(FULL, K == 2 ? a1 : a0, 1, G);
+    // part 0 takes the query value lane gl-1's last part used at the last
+    // step; lane 0 takes a[s]
+    float a_in = __shfl_up_sync(FULL, a[K - 1], 1, G);
     if (gl == 0) a_in = anext;                 // query value a[s]
     anext = ap[min(s + 1, L - 1)];             // the next one (clamped)
-    if (K == 2) a1 = a0;
-    a0 = a_in;
-    float left0 = __shfl_up_sync(FULL, Din[C - 1], 1, G);
-    const int i0 = s - K * gl;
-    float diag0 = diag_in;
-    if (gl == 0) {
-        left0 = INF;
-        diag0 = (i0 == 0) ? 0.f : INF;
-    }
-    diag_in = left0;
-    const float left1 = Din[C0 - 1];
-    const float diag1 = h0prev;
-    if (K == 2) h0prev = left1;
 #pragma unroll
-    for (int c = 0; c < C0; c++) {
-        {
-            const float d = a0 - B[c];
-            Dout[c] = fmaf(d, d, min3f(Din[c], c == 0 ? left0 : Dout[c - 1],
-                                       c == 0 ? diag0 : Din[c - 1]));
-        }
-        if (K == 2 && C0 + c < C) {
-            const int e = C0 + c;
-            const float d = a1 - B[e];
-            Dout[e] = fmaf(d, d, min3f(Din[e], c == 0 ? left1 : Dout[e - 1],
-                                       c == 0 ? diag1 : Din[e - 1]));
+    for (int k = K - 1; k >= 1; k--) a[k] = a[k - 1];
+    a[0] = a_in;
+    float left[K], diag[K];
+    left[0] = __shfl_up_sync(FULL, Din[C - 1], 1, G);
+    const int i0 = s - K * gl;
+    diag[0] = diag_in;
+    if (gl == 0) {
+        left[0] = INF;
+        diag[0] = (i0 == 0) ? 0.f : INF;
+    }
+    diag_in = left[0];
+#pragma unroll
+    for (int k = 1; k < K; k++) {
+        left[k] = Din[part_lo<C, K>(k) - 1];
+        diag[k] = hprev[k];
+        hprev[k] = left[k];
+    }
+    constexpr int kMaxPart = (C + K - 1) / K;
+#pragma unroll
+    for (int c = 0; c < kMaxPart; c++) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int e = part_lo<C, K>(k) + c;
+            if (e < part_lo<C, K>(k + 1)) {
+                const float d = a[k] - B[e];
+                Dout[e] = fmaf(d, d, min3f(Din[e], c == 0 ? left[k] : Dout[e - 1],
+                                           c == 0 ? diag[k] : Din[e - 1]));
+            }
         }
     }
 }
@@ -82,8 +102,7 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
     int bid, nblk;
     const DtwJob32 &job = src.get(bid, nblk);
     const int G = job.lanes;
-    constexpr int K = C >= 4 ? 2 : 1;
-    constexpr int C0 = K == 2 ? (C + 1) / 2 : C;
+    constexpr int K = rowsg_parts<C>();
     const float INF = inf_of<float>();
     const float APAD = -Pad<float>::v;   // query before the start: delta = +inf
     const float BPAD = Pad<float>::v;    // columns in front of column 0
@@ -93,7 +112,7 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
     const int gl = lane & (G - 1);
     const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int off = G * C - L;                 // padding columns before column 0
-    const int steps_total = L + K * G - 1;     // the last half finishes row L-1 at step steps_total-1
+    const int steps_total = L + K * G - 1;     // the last part finishes row L-1 at step steps_total-1
     const int s_final = steps_total - 1;
     const long long n_work = job.pairs ? (job.count ? (long long)*job.count : job.n_pairs)
                                        : job.n_seed;
@@ -123,7 +142,10 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
     float ub = INF, res = INF;
     unsigned kb = ~0u;
     const float *ap = job.test;
-    float a0 = APAD, a1 = APAD, anext = 0.f, diag_in = INF, h0prev = INF;
+    float a[K], hprev[K];
+    float anext = 0.f, diag_in = INF;
+#pragma unroll
+    for (int k = 0; k < K; k++) { a[k] = APAD; hprev[k] = INF; }
 
     while (true) {
         // ---- start pairs (every 16 steps) ----------------------------------
@@ -152,9 +174,10 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
                         B[c] = j >= 0 ? bp[j] : (j == -1 ? APAD : BPAD);
                         D[c] = j == -1 ? 0.f : INF;
                     }
-                    a0 = APAD; a1 = APAD;
+#pragma unroll
+                    for (int k = 0; k < K; k++) { a[k] = APAD; hprev[k] = INF; }
                     anext = ap[0];
-                    diag_in = INF; h0prev = INF;
+                    diag_in = INF;
                     res = INF; ub = INF;
                     kb = check_bsf ? bsf_dist_bits(job.bsf, q) : ~0u;
                     ws = w;
@@ -169,9 +192,9 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
 #pragma unroll 1
         for (int it = 0; it < 8; it++) {
             const int s = w - ws;
-            rowsg_step<C, K, C0>(D, E, B, a0, a1, anext, diag_in, h0prev, ap, s, gl, G, L);
+            rowsg_step<C, K>(D, E, B, a, anext, diag_in, hprev, ap, s, gl, G, L);
             res = s == s_final ? E[C - 1] : res;
-            rowsg_step<C, K, C0>(E, D, B, a0, a1, anext, diag_in, h0prev, ap, s + 1, gl, G, L);
+            rowsg_step<C, K>(E, D, B, a, anext, diag_in, hprev, ap, s + 1, gl, G, L);
             res = s + 1 == s_final ? D[C - 1] : res;
             w += 2;
         }
@@ -201,7 +224,12 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
 
         // ---- early abandoning (selects per group) ---------------------------
         if (job.abandon) {
-            float mn = fminf(diag_in, h0prev);
+            // the cut: every part's last computed row (D), and the cell one
+            // row above it in the column in front of every part (hprev inside
+            // the lane, diag_in across lanes)
+            float mn = diag_in;
+#pragma unroll
+            for (int k = 1; k < K; k++) mn = fminf(mn, hprev[k]);
 #pragma unroll
             for (int c = 0; c < C; c++) mn = fminf(mn, D[c]);
             for (int o = 1; o < G; o <<= 1) mn = fminf(mn, __shfl_xor_sync(FULL, mn, o, G));
@@ -212,12 +240,12 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
             kb = live ? kbn : kb;
             const bool drop = live && lower32(mn, job.dtw_lo, job.abs32) > ub;
             if (drop && gl == 0 && job.counters) {
-                // half-block h of lane g has finished rows 0 .. sd-1 - (K g + h)
+                // part h of lane g has finished rows 0 .. sd-1 - (K g + h)
                 long long cells = 0;
                 for (int g = 0; g < G; g++) {
                     for (int h = 0; h < K; h++) {
-                        const int lo = max(g * C + (h ? C0 : 0) - off, 0);
-                        const int hi = min(g * C + (h ? C : C0) - off, L);
+                        const int lo = max(g * C + part_lo<C, K>(h) - off, 0);
+                        const int hi = min(g * C + part_lo<C, K>(h + 1) - off, L);
                         const int rows = min(sd - 1 - (K * g + h), L - 1) + 1;
                         if (rows > 0 && hi > lo) cells += (long long)(hi - lo) * rows;
                     }

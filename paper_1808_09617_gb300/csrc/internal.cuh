@@ -186,7 +186,7 @@ template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
                       T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
-                      bool loo, cudaStream_t s);
+                      bool loo, cudaStream_t s, int64_t q_base = 0);
 
 // The bound pass (and its squared norms) of one dataset as job structures,
 // for the batched search: launch_lb's arguments, its tile shape (small: 32 x
@@ -206,6 +206,7 @@ template <typename T> struct LbJob {
     const T *nq, *nt;
     T *ends_out;
     int loo, qfast, gx;
+    int64_t q_base;   // global index of query 0 (leave-one-out over query chunks)
 };
 template <typename T> struct SqnormJob {
     const T *a;
@@ -232,7 +233,7 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p);
+                    LbPlan<T> *p, int64_t q_base = 0);
 template <typename T> LbFns<T> lb_fns(bool small, bool ed);
 template <typename T> cudaError_t set_lb_smem(bool small, bool ed, size_t smem);
 

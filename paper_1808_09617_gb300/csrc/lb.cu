@@ -201,6 +201,7 @@ lb_kernel(const __grid_constant__ Src src) {
     const T *__restrict__ nt = job.nt;
     T *__restrict__ ends_out = job.ends_out;
     const int loo = job.loo, qfast = job.qfast;
+    const int64_t q_base = job.q_base;   // global index of query 0 (leave-one-out)
     // the CTA's tile: bx along the fast dimension (gx tiles), by along the other
     const int bx = bid % job.gx, by = bid / job.gx;
     using T2 = typename V2<T>::type;
@@ -367,7 +368,7 @@ lb_kernel(const __grid_constant__ Src src) {
             const T sv = safe_scale(raw, lb_lo, abs_slack);
             if (q < Q && t < N) {
                 // leave-one-out: a series is never its own candidate
-                const bool self = loo && q == t;
+                const bool self = loo && q + q_base == t;
                 if (lb_out) lb_out[q * N + t] = self ? POS : (safe ? sv : raw);
                 if (ED && !self) {
                     // squared distance from the norms and the dot product
@@ -405,7 +406,7 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p) {
+                    LbPlan<T> *p, int64_t q_base) {
     int nb = L / 2 < V ? L / 2 : V;
     if (nb < 1) nb = 1;
     const int Weff = W > L - 1 ? L - 1 : W;
@@ -420,7 +421,7 @@ cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int6
     j.nb = nb; j.keogh = keogh ? 1 : 0; j.safe = safe ? 1 : 0; j.lb_lo = lb_lo;
     j.abs_slack = abs_slack; j.lb_out = lb_out; j.seed_keys = seed_keys;
     j.nq = seed_keys ? norms : nullptr; j.nt = seed_keys ? norms + Q : nullptr;
-    j.ends_out = keogh ? nullptr : ends_out; j.loo = loo ? 1 : 0;
+    j.ends_out = keogh ? nullptr : ends_out; j.loo = loo ? 1 : 0; j.q_base = q_base;
     // query tiles vary fastest, so the CTAs resident at one time share a few
     // training tiles
     j.qfast = 1;
@@ -462,12 +463,12 @@ template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                       int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                       unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t q_base) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
     if (seed_keys && !norms) return cudaErrorInvalidValue;
     LbPlan<T> p{};
     cudaError_t e = plan_lb<T>(test, Q, train, env, N, L, W, V, keogh, safe, lb_lo, abs_slack,
-                               lb_out, seed_keys, norms, ends_out, loo, &p);
+                               lb_out, seed_keys, norms, ends_out, loo, &p, q_base);
     if (e != cudaSuccess) return e;
     const LbFns<T> f = lb_fns<T>(p.small, p.ed);
     if (p.sq_blocks > 0) {
@@ -486,15 +487,15 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                       int, int, int, bool, bool, float, float, float *,
                                       unsigned long long *, float *, float *, bool,
-                                      cudaStream_t);
+                                      cudaStream_t, int64_t);
 template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
                                        int64_t, int, int, int, bool, bool, double, double,
                                        double *, unsigned long long *, double *, double *,
-                                       bool, cudaStream_t);
+                                       bool, cudaStream_t, int64_t);
 template cudaError_t plan_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                     int, int, int, bool, bool, float, float, float *,
                                     unsigned long long *, float *, float *, bool,
-                                    LbPlan<float> *);
+                                    LbPlan<float> *, int64_t);
 template LbFns<float> lb_fns<float>(bool, bool);
 template cudaError_t set_lb_smem<float>(bool, bool, size_t);
 

@@ -451,8 +451,18 @@ Layout64 layout64(void *base, int64_t N, int64_t Q, int L) {
 bool search_sizes_ok(int64_t N, int64_t Q, int L, int W, int V) {
     if (N < 1 || Q < 0 || L < 2 || L > NNDTW_MAX_L || W < 0 || V < 1) return false;
     if (N > 0x7fffffffll || Q > 0x7fffffffll) return false;
-    if ((double)N * (double)Q >= 2147483648.0) return false;
     return true;
+}
+
+// Queries per chunk: a search runs its queries in chunks of at most
+// NNDTW_CHUNK_PAIRS (query, training series) pairs, one after another, so
+// that its workspace (about 48 bytes per pair of a chunk) never grows with
+// Q x N beyond that; each query's search is independent of the others, so the
+// results do not depend on the chunking.
+int64_t chunk_queries(int64_t N, int64_t Q) {
+    const int64_t per = (int64_t)NNDTW_CHUNK_PAIRS / N;
+    const int64_t qc = per < 1 ? 1 : per;
+    return Q < qc ? Q : qc;
 }
 
 unsigned grid_small(long long n) {
@@ -502,6 +512,19 @@ void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t
     }
 }
 
+void add_stats(nndtw_stats *t, const nndtw_stats &p) {
+    t->pairs += p.pairs;
+    t->lb_pruned += p.lb_pruned;
+    t->dtw_started += p.dtw_started;
+    t->dtw_abandoned += p.dtw_abandoned;
+    t->dtw_cells += p.dtw_cells;
+    t->rechecked += p.rechecked;
+    t->recheck_queries += p.recheck_queries;
+    t->seed_cells += p.seed_cells;
+    t->lb_pruned_reverse += p.lb_pruned_reverse;
+    t->lb_pruned_improved += p.lb_pruned_improved;
+}
+
 template <typename T>
 int check_finite(const T *x, int64_t n, T limit, unsigned long long *bad, cudaStream_t s) {
     if (n <= 0) return NNDTW_OK;
@@ -539,7 +562,12 @@ struct Set32 {
     unsigned flags;
     int32_t *nn_idx, *nn_label;
     double *nn_dist;
-    void *ws;           // nn_dtw_workspace_size() bytes, 256-byte aligned
+    void *ws;           // workspace laid out for q_cap queries, 256-byte aligned
+    int64_t q_base;     // index of the first query of this chunk (leave-one-out)
+    int64_t q_cap;      // queries the workspace layout holds (Q <= q_cap; the same
+                        // for every chunk of a search, so chunks find one layout)
+    bool train_ready;   // the training-side data (envelopes, second envelopes,
+                        // packed records) is already in the workspace
 };
 
 // One kernel (its two forms, block size, largest dynamic shared memory) and
@@ -714,7 +742,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
     for (int d = 0; d < n; d++) {
         const Set32 &x = sets[d];
         Prep32 &p = P[d];
-        p.ws = layout32(x.ws, x.N, x.Q, x.L);
+        p.ws = layout32(x.ws, x.N, x.q_cap, x.L);
         p.Weff = x.W > x.L - 1 ? x.L - 1 : x.W;
         p.m = make_margins(x.L);
         p.keogh = (x.flags & NNDTW_KEOGH_BOUND) != 0;
@@ -729,6 +757,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
         p.loo = (x.flags & NNDTW_LEAVE_ONE_OUT) != 0;
         p.exact = (x.flags & NNDTW_EXACT_DIST) != 0;
         p.env = x.env ? x.env : p.ws.env;
+        // (a later chunk of a search finds the training envelopes it built)
         p.cnt = (want_stats && !timing) ? p.ws.counters : nullptr;
     }
 
@@ -780,7 +809,8 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             g.add(f.fn1, f.fnN, kEnvelopeThreads, ep.smem, ep.job, ep.blocks);
         };
         for (int d = 0; d < n; d++) {
-            if (!sets[d].env) add(sets[d].train, nullptr, sets[d].N, d, P[d].ws.env);
+            if (!sets[d].env && !sets[d].train_ready)
+                add(sets[d].train, nullptr, sets[d].N, d, P[d].ws.env);
             if (P[d].second) add(sets[d].test, nullptr, sets[d].Q, d, P[d].ws.envq);
         }
         CK(g.launch(s));
@@ -788,7 +818,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
         Batches<PackJob> gp;
         const PackFns pf = pack_bgap_fns();
         for (int d = 0; d < n; d++) {
-            if (!P[d].imp) continue;
+            if (!P[d].imp || sets[d].train_ready) continue;
             const EnvPlan<float> ep = plan_envelopes<float>(nullptr, P[d].env, sets[d].N, sets[d].L,
                                                             P[d].Weff, P[d].ws.env2);
             const EnvFns<float> f = envelope_fns<float>(ep.one_pass);
@@ -813,7 +843,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             LbPlan<float> lp{};
             CK(plan_lb<float>(x.test, x.Q, x.train, p.env, x.N, x.L, p.Weff, x.V, p.keogh, true,
                               p.m.lb_lo, p.m.abs32, p.ws.lb, p.ws.seed, p.ws.norms,
-                              p.rev ? p.ws.ends : nullptr, p.loo, &lp));
+                              p.rev ? p.ws.ends : nullptr, p.loo, &lp, x.q_base));
             const LbFns<float> f = lb_fns<float>(lp.small, lp.ed);
             gs.add(f.sq1, f.sqN, 256, 0, lp.sq, lp.sq_blocks);
             gl.add(f.fn1, f.fnN, kLbThreads, lp.smem, lp.job, lp.blocks);
@@ -1223,7 +1253,8 @@ int dtw_windowed_f64(const double *d_test, const double *d_train, const int32_t 
 
 size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V, int fp64) {
     if (!search_sizes_ok(N, Q, L, W, V)) return 0;
-    return fp64 ? layout64(nullptr, N, Q, L).bytes : layout32(nullptr, N, Q, L).bytes;
+    const int64_t qc = chunk_queries(N, Q);
+    return fp64 ? layout64(nullptr, N, qc, L).bytes : layout32(nullptr, N, qc, L).bytes;
 }
 
 int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N,
@@ -1241,33 +1272,46 @@ int nn_dtw_search(const float *d_train, const int32_t *d_train_labels, int64_t N
         return NNDTW_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return NNDTW_EINVAL;
     if (!dtw32_supported(W > L - 1 ? L - 1 : W)) return NNDTW_EUNSUPPORTED;
-    if (workspace_bytes < layout32(nullptr, N, Q, L).bytes) return NNDTW_ENOSPACE;
+    const int64_t qc = chunk_queries(N, Q);
+    if (workspace_bytes < layout32(nullptr, N, qc, L).bytes) return NNDTW_ENOSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
     reset_launch_counts();
     StageTimer tm;
     CK(tm.start(timing, s));
-    const Set32 set{d_train, d_train_labels, N, d_test, Q, L, W, V, d_env, flags,
-                    d_nn_idx, d_nn_label, d_nn_dist, d_workspace};
-    return run32(&set, 1, stats != nullptr, timing, stats, tm, s);
+    nndtw_stats total{};
+    for (int64_t q0 = 0; q0 < Q; q0 += qc) {
+        const int64_t m = Q - q0 < qc ? Q - q0 : qc;
+        const Set32 set{d_train, d_train_labels, N, d_test + q0 * L, m, L, W, V, d_env, flags,
+                        d_nn_idx + q0, d_nn_label + q0, d_nn_dist + q0, d_workspace, q0, qc,
+                        q0 > 0};
+        nndtw_stats part{};
+        const int rc = run32(&set, 1, stats != nullptr, timing, stats ? &part : nullptr, tm, s);
+        if (rc != NNDTW_OK) return rc;
+        if (stats) add_stats(&total, part);
+    }
+    if (stats) *stats = total;
+    return NNDTW_OK;
 }
 
 int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int64_t N,
-                      const double *d_test, int64_t Q, int L, int W, int V, const double *d_env,
-                      unsigned flags, int32_t *d_nn_idx, int32_t *d_nn_label, double *d_nn_dist,
-                      void *d_workspace, size_t workspace_bytes, nndtw_stats *stats,
-                      void *stream) {
-    if (!search_sizes_ok(N, Q, L, W, V)) return NNDTW_EINVAL;
-    if ((flags & NNDTW_LEAVE_ONE_OUT) && (Q != N || N < 2)) return NNDTW_EINVAL;
-    if (Q == 0) {
+                      const double *d_test_all, int64_t Q_all, int L, int W, int V,
+                      const double *d_env, unsigned flags, int32_t *d_nn_idx_all,
+                      int32_t *d_nn_label_all, double *d_nn_dist_all, void *d_workspace,
+                      size_t workspace_bytes, nndtw_stats *stats, void *stream) {
+    if (!search_sizes_ok(N, Q_all, L, W, V)) return NNDTW_EINVAL;
+    if ((flags & NNDTW_LEAVE_ONE_OUT) && (Q_all != N || N < 2)) return NNDTW_EINVAL;
+    if (Q_all == 0) {
         if (stats) std::memset(stats, 0, sizeof(*stats));
         return NNDTW_OK;
     }
-    if (!d_train || !d_train_labels || !d_test || !d_nn_idx || !d_nn_label || !d_nn_dist ||
-        !d_workspace)
+    if (!d_train || !d_train_labels || !d_test_all || !d_nn_idx_all || !d_nn_label_all ||
+        !d_nn_dist_all || !d_workspace)
         return NNDTW_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return NNDTW_EINVAL;
-    const Layout64 ws = layout64(d_workspace, N, Q, L);
+    // queries in chunks of at most NNDTW_CHUNK_PAIRS pairs, one layout for all
+    const int64_t qc = chunk_queries(N, Q_all);
+    const Layout64 ws = layout64(d_workspace, N, qc, L);
     if (workspace_bytes < ws.bytes) return NNDTW_ENOSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     const int Weff = W > L - 1 ? L - 1 : W;
@@ -1277,94 +1321,104 @@ int nn_dtw_search_f64(const double *d_train, const int32_t *d_train_labels, int6
     const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
     StageTimer tm;
     CK(tm.start(timing, s));
-    CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
-    CK(cudaMemsetAsync(ws.buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, s));
-    CK(cudaMemsetAsync(ws.bsf64, 0x7f, sizeof(unsigned long long) * Q, s));
-    CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
-    CK(cudaMemsetAsync(ws.bestidx, 0x7f, sizeof(int32_t) * Q, s));
     if (flags & NNDTW_CHECK_FINITE) {
+        CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
         int rc = check_finite<double>(d_train, N * L, 1e150, ws.counters + C_BAD, s);
         if (rc) return rc;
-        rc = check_finite<double>(d_test, Q * L, 1e150, ws.counters + C_BAD, s);
+        rc = check_finite<double>(d_test_all, Q_all * L, 1e150, ws.counters + C_BAD, s);
         if (rc) return rc;
         unsigned long long bad = 0;
         CK(cudaMemcpyAsync(&bad, ws.counters + C_BAD, sizeof(bad), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (bad) return NNDTW_ENONFINITE;
     }
-    const double *env = d_env;
-    if (!env) {
-        CK(launch_envelopes<double>(d_train, N, L, Weff, ws.env, s));
-        env = ws.env;
-    }
     const bool keogh = (flags & NNDTW_KEOGH_BOUND) != 0;
     const bool rev = !keogh && !(flags & (NNDTW_NO_PRUNE | NNDTW_NO_REVERSE));
     const bool imp = (flags & NNDTW_IMPROVED) && !keogh && !(flags & NNDTW_NO_PRUNE);
-    if (rev || imp) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
-    if (imp) CK(launch_second_envelopes<double>(env, N, L, Weff, ws.env2, s));
-    CK(tm.mark(1));
-    CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, keogh, true, m.lb_lo64,
-                         m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
-                         (flags & NNDTW_LEAVE_ONE_OUT) != 0, s));
-    CK(tm.mark(2));
-    unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
-    DtwJob64 j{};
-    j.test = d_test; j.train = d_train; j.L = L; j.W = Weff;
-    j.bsf64 = ws.bsf64; j.cand = ws.cand; j.cand_count = ws.counters + C_CAND;
-    j.counters = cnt;
-    j.pairs = nullptr; j.seed_keys = ws.seed; j.n_pairs = Q; j.head = nullptr; j.abandon = 0;
-    CK(launch_dtw64(j, sms, s));
-    CK(tm.mark(3));
-    {
-        const dim3 gc = grid_compact(Q, N);
-        CompactJob<double> cj{};
-        cj.lb = ws.lb; cj.Q = Q; cj.N = N; cj.bsf = ws.bsf64; cj.seed = ws.seed;
-        cj.ubof = UbOf<double>{};
-        cj.no_prune = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
-        cj.gx = (int)gc.x;
-        cj.bcount = ws.buckets; cj.bcursor = ws.buckets + kBuckets;
-        cj.qcount = ws.counters + C_QUEUE; cj.queue = ws.queue;
-        for (int pass = 0; pass < 2; pass++) {
-            cj.scatter = pass;
-            compact_kernel<double, Src1<CompactJob<double>>>
-                <<<gc.x * gc.y, kSmallThreads, 0, s>>>(Src1<CompactJob<double>>{cj});
-            CK(cudaGetLastError());
+    const double *env = d_env ? d_env : ws.env;
+    nndtw_stats total{};
+    for (int64_t q0 = 0; q0 < Q_all; q0 += qc) {
+        const int64_t Q = Q_all - q0 < qc ? Q_all - q0 : qc;
+        const double *d_test = d_test_all + q0 * L;
+        int32_t *d_nn_idx = d_nn_idx_all + q0, *d_nn_label = d_nn_label_all + q0;
+        double *d_nn_dist = d_nn_dist_all + q0;
+        CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * C_COUNT, s));
+        CK(cudaMemsetAsync(ws.buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, s));
+        CK(cudaMemsetAsync(ws.bsf64, 0x7f, sizeof(unsigned long long) * Q, s));
+        CK(cudaMemsetAsync(ws.seed, 0xff, sizeof(unsigned long long) * Q, s));
+        CK(cudaMemsetAsync(ws.bestidx, 0x7f, sizeof(int32_t) * Q, s));
+        // the training side once, in the first chunk
+        if (q0 == 0 && !d_env) CK(launch_envelopes<double>(d_train, N, L, Weff, ws.env, s));
+        if (rev || imp) CK(launch_envelopes<double>(d_test, Q, L, Weff, ws.envq, s));
+        if (q0 == 0 && imp) CK(launch_second_envelopes<double>(env, N, L, Weff, ws.env2, s));
+        CK(tm.mark(1));
+        CK(launch_lb<double>(d_test, Q, d_train, env, N, L, Weff, V, keogh, true, m.lb_lo64,
+                             m.abs64, ws.lb, ws.seed, ws.norms, rev ? ws.ends : nullptr,
+                             (flags & NNDTW_LEAVE_ONE_OUT) != 0, s, q0));
+        CK(tm.mark(2));
+        unsigned long long *cnt = (stats && !timing) ? ws.counters : nullptr;
+        DtwJob64 j{};
+        j.test = d_test; j.train = d_train; j.L = L; j.W = Weff;
+        j.bsf64 = ws.bsf64; j.cand = ws.cand; j.cand_count = ws.counters + C_CAND;
+        j.counters = cnt;
+        j.pairs = nullptr; j.seed_keys = ws.seed; j.n_pairs = Q; j.head = nullptr; j.abandon = 0;
+        CK(launch_dtw64(j, sms, s));
+        CK(tm.mark(3));
+        {
+            const dim3 gc = grid_compact(Q, N);
+            CompactJob<double> cj{};
+            cj.lb = ws.lb; cj.Q = Q; cj.N = N; cj.bsf = ws.bsf64; cj.seed = ws.seed;
+            cj.ubof = UbOf<double>{};
+            cj.no_prune = (flags & NNDTW_NO_PRUNE) ? 1 : 0;
+            cj.gx = (int)gc.x;
+            cj.bcount = ws.buckets; cj.bcursor = ws.buckets + kBuckets;
+            cj.qcount = ws.counters + C_QUEUE; cj.queue = ws.queue;
+            for (int pass = 0; pass < 2; pass++) {
+                cj.scatter = pass;
+                compact_kernel<double, Src1<CompactJob<double>>>
+                    <<<gc.x * gc.y, kSmallThreads, 0, s>>>(Src1<CompactJob<double>>{cj});
+                CK(cudaGetLastError());
+            }
+        }
+        CK(tm.mark(4));
+        j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
+        j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
+        if (rev || imp) {
+            j.envq = reinterpret_cast<const double2 *>(ws.envq);
+            j.rev = rev;
+            j.ends_bands = ws.ends;
+            j.env2 = imp ? reinterpret_cast<const double2 *>(ws.env2) : nullptr;
+            j.lb = ws.lb;
+            j.N = N;
+            j.nb = bridge_start(L, V);
+            j.lb_lo = m.lb_lo64;
+            j.lb_abs = m.abs64;
+        }
+        CK(launch_dtw64(j, sms, s));
+        CK(tm.mark(5));
+        const long long cap = (long long)Q * N + Q;
+        ties64_kernel<<<grid_small(cap), kSmallThreads, 0, s>>>(ws.cand, ws.counters + C_CAND,
+                                                                ws.bsf64, ws.bestidx);
+        CK(cudaGetLastError());
+        CK(tm.mark(6));
+        finalize64_kernel<<<grid_small(Q), kSmallThreads, 0, s>>>(Q, ws.bsf64, ws.bestidx,
+                                                                  d_train_labels, d_nn_idx,
+                                                                  d_nn_label, d_nn_dist);
+        CK(cudaGetLastError());
+        CK(tm.mark(7));
+        if (stats) {
+            unsigned long long h[C_COUNT];
+            CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            nndtw_stats part{};
+            fill_stats(&part, h, N, Q, L, Weff, cnt != nullptr);
+            add_stats(&total, part);
         }
     }
-    CK(tm.mark(4));
-    j.pairs = ws.queue; j.seed_keys = nullptr; j.count = ws.counters + C_QUEUE;
-    j.head = ws.counters + C_HEAD; j.abandon = (flags & NNDTW_NO_ABANDON) ? 0 : 1;
-    if (rev || imp) {
-        j.envq = reinterpret_cast<const double2 *>(ws.envq);
-        j.rev = rev;
-        j.ends_bands = ws.ends;
-        j.env2 = imp ? reinterpret_cast<const double2 *>(ws.env2) : nullptr;
-        j.lb = ws.lb;
-        j.N = N;
-        j.nb = bridge_start(L, V);
-        j.lb_lo = m.lb_lo64;
-        j.lb_abs = m.abs64;
-    }
-    CK(launch_dtw64(j, sms, s));
-    CK(tm.mark(5));
-    const long long cap = (long long)Q * N + Q;
-    ties64_kernel<<<grid_small(cap), kSmallThreads, 0, s>>>(ws.cand, ws.counters + C_CAND,
-                                                            ws.bsf64, ws.bestidx);
-    CK(cudaGetLastError());
-    CK(tm.mark(6));
-    finalize64_kernel<<<grid_small(Q), kSmallThreads, 0, s>>>(Q, ws.bsf64, ws.bestidx,
-                                                              d_train_labels, d_nn_idx,
-                                                              d_nn_label, d_nn_dist);
-    CK(cudaGetLastError());
-    CK(tm.mark(7));
-    if (stats) {
-        unsigned long long h[C_COUNT];
-        CK(cudaMemcpyAsync(h, ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        fill_stats(stats, h, N, Q, L, Weff, cnt != nullptr);
-    }
+    if (stats) *stats = total;
     return NNDTW_OK;
 }
+
 
 size_t nn_dtw_batch_workspace_size(const nndtw_dataset *h_sets, int n) {
     if (!h_sets || n < 0) return 0;
@@ -1383,8 +1437,10 @@ int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
     if (n < 0 || (n > 0 && !h_sets)) return NNDTW_EINVAL;
     if (n == 0) return NNDTW_OK;
     if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return NNDTW_EINVAL;
-    std::vector<Set32> sets;
-    sets.reserve(n);
+    // round r holds chunk r of every dataset that has one (datasets whose
+    // Q x N exceeds NNDTW_CHUNK_PAIRS have several; a dataset's chunks share
+    // its workspace, so they run in successive rounds)
+    std::vector<std::vector<Set32>> rounds;
     size_t off = 0;
     for (int i = 0; i < n; i++) {
         const nndtw_dataset &d = h_sets[i];
@@ -1396,30 +1452,38 @@ int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
                         !d.d_nn_label || !d.d_nn_dist))
             return NNDTW_EINVAL;
         if (!dtw32_supported(d.W > d.L - 1 ? d.L - 1 : d.W)) return NNDTW_EUNSUPPORTED;
-        if (d.Q > 0)
-            sets.push_back(Set32{d.d_train, d.d_train_labels, d.N, d.d_test, d.Q, d.L, d.W, d.V,
-                                 d.d_env, f, d.d_nn_idx, d.d_nn_label, d.d_nn_dist,
-                                 static_cast<char *>(d_workspace) + off});
+        const int64_t qc = d.Q > 0 ? chunk_queries(d.N, d.Q) : 0;
+        for (int64_t q0 = 0, r = 0; q0 < d.Q; q0 += qc, r++) {
+            const int64_t m = d.Q - q0 < qc ? d.Q - q0 : qc;
+            if ((int64_t)rounds.size() <= r) rounds.resize(r + 1);
+            rounds[r].push_back(Set32{d.d_train, d.d_train_labels, d.N, d.d_test + q0 * d.L, m,
+                                      d.L, d.W, d.V, d.d_env, f, d.d_nn_idx + q0,
+                                      d.d_nn_label + q0, d.d_nn_dist + q0,
+                                      static_cast<char *>(d_workspace) + off, q0, qc, q0 > 0});
+        }
         off += (b + 255) & ~size_t(255);
     }
     if (workspace_bytes < off) return NNDTW_ENOSPACE;
     const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
-    if (timing && sets.size() > (size_t)kMaxSets) return NNDTW_EINVAL;
-    // the datasets with the most DTW work first: in every stage their CTAs
-    // start first, and the small datasets fill in behind them
-    std::stable_sort(sets.begin(), sets.end(), [](const Set32 &a, const Set32 &b) {
-        const double wa = (double)a.N * a.Q * band_cells(a.L, a.W);
-        const double wb = (double)b.N * b.Q * band_cells(b.L, b.W);
-        return wa > wb;
-    });
+    if (timing && (rounds.size() > 1 || (!rounds.empty() && rounds[0].size() > (size_t)kMaxSets)))
+        return NNDTW_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     reset_launch_counts();
     StageTimer tm;
     CK(tm.start(timing, s));
-    for (size_t k = 0; k < sets.size(); k += kMaxSets) {
-        const int m = (int)std::min<size_t>(kMaxSets, sets.size() - k);
-        const int rc = run32(sets.data() + k, m, false, timing, nullptr, tm, s);
-        if (rc != NNDTW_OK) return rc;
+    for (auto &sets : rounds) {
+        // the datasets with the most DTW work first: in every stage their CTAs
+        // start first, and the small datasets fill in behind them
+        std::stable_sort(sets.begin(), sets.end(), [](const Set32 &a, const Set32 &b) {
+            const double wa = (double)a.N * a.Q * band_cells(a.L, a.W);
+            const double wb = (double)b.N * b.Q * band_cells(b.L, b.W);
+            return wa > wb;
+        });
+        for (size_t k = 0; k < sets.size(); k += kMaxSets) {
+            const int m = (int)std::min<size_t>(kMaxSets, sets.size() - k);
+            const int rc = run32(sets.data() + k, m, false, timing, nullptr, tm, s);
+            if (rc != NNDTW_OK) return rc;
+        }
     }
     return NNDTW_OK;
 }

@@ -8,6 +8,7 @@ generator for its inputs.  Run from the repository root:
     python tests/golden/make_full_golden.py precision   # 3 windows x 2,000 queries
     python tests/golden/make_full_golden.py batched     # 64 datasets, 35,843 queries
     python tests/golden/make_full_golden.py serving     # 16 resident sets, 24 queries each
+    python tests/golden/make_full_golden.py large       # Q x N above 2^31, 24 sampled queries
 
 Each file is gzip-compressed text, one query per line:
 ``[dataset] query nn_index nn_label nn_dist(hex float)``.
@@ -33,6 +34,24 @@ def precision_path(ratio):
 
 
 BATCHED_PATH = os.path.join(HERE, "batched_nn.txt.gz")
+LARGE_PATH = os.path.join(HERE, "large_nn.txt.gz")
+# a search whose Q x N (50,000 x 43,000 = 2.15e9) is above 2^31, on short series
+LARGE_N, LARGE_Q, LARGE_L, LARGE_W, LARGE_V = 50_000, 43_000, 16, 2, 2
+LARGE_SAMPLE = 24
+
+
+def large_inputs():
+    """The large search's inputs: seeded z-normalised random walks, labels
+    uniform over 5 classes, and the sampled query indices."""
+    import numpy as np
+    train = synth.random_series(7101, LARGE_N, LARGE_L)
+    test = synth.random_series(7102, LARGE_Q, LARGE_L)
+    rng = np.random.default_rng(7103)
+    labels = rng.integers(0, 5, LARGE_N).astype(np.int32)
+    sample = np.sort(rng.choice(LARGE_Q, LARGE_SAMPLE, replace=False))
+    return train, labels, test, sample
+
+
 SERVING_PATH = os.path.join(HERE, "serving_nn.txt.gz")
 
 
@@ -104,6 +123,22 @@ def make_serving(threads=None):
     print(f"serving: {len(rows)} queries in {time.time() - t0:.0f} s", flush=True)
 
 
+def make_large(threads=None):
+    orc = oracle.get()
+    train, labels, test, sample = large_inputs()
+    t0 = time.time()
+    idx, lab, dist, _ = orc.nn_pruned(train, labels, test[sample], LARGE_W, LARGE_V,
+                                      threads=threads)
+    _write(LARGE_PATH,
+           [f"1-NN of {LARGE_SAMPLE} sampled queries of a search with Q x N above 2^31 "
+            f"(train {LARGE_N}, test {LARGE_Q}, L={LARGE_L}, W={LARGE_W}, V={LARGE_V}), FP64 "
+            "oracle (pruned search, ties to the lowest index)",
+            "written by tests/golden/make_full_golden.py",
+            "query nn_index nn_label nn_dist(hex float)"],
+           _rows([], idx, lab, dist, queries=sample))
+    print(f"large: {LARGE_SAMPLE} queries in {time.time() - t0:.0f} s", flush=True)
+
+
 def read(path):
     """Rows of a stored file as lists of ints, the distance as a float."""
     out = []
@@ -120,4 +155,5 @@ if __name__ == "__main__":
     what = sys.argv[1:] or ["precision", "batched", "serving"]
     th = int(os.environ.get("ORACLE_THREADS", "0")) or None
     for w in what:
-        {"precision": make_precision, "batched": make_batched, "serving": make_serving}[w](th)
+        {"precision": make_precision, "batched": make_batched, "serving": make_serving,
+         "large": make_large}[w](th)
