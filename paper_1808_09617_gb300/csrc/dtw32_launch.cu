@@ -63,6 +63,8 @@ int dtw32_wide_group(int W) {
 bool dtw32_supported(int W) { return W >= 0 && W < NNDTW_MAX_L; }
 
 cudaError_t plan_dtw32(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
+    // W = 0: the squared Euclidean distance, whatever layout is asked for
+    if (job.W == 0) return plan_dtw32_ed(job, sm_count, p);
     // full windows: the row kernels, unless a diagonal group width is asked for
     if (job.group == kRowsGroup + 1 && dtw32_rowsg_ok(job.L, job.W, 16))
         return plan_dtw32_rowsg(job, 16, sm_count, p);

@@ -281,6 +281,7 @@ struct Dtw32Plan {
 };
 cudaError_t plan_dtw32(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
 cudaError_t plan_dtw32_wide(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+cudaError_t plan_dtw32_ed(const DtwJob32 &job, int sm_count, Dtw32Plan *p);   // W = 0
 cudaError_t plan_dtw32_rows(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
 cudaError_t plan_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, Dtw32Plan *p);
 cudaError_t plan_dtw32_rowsc(const DtwJob32 &job, int sm_count, Dtw32Plan *p);

@@ -6,7 +6,8 @@
 // series tx + 16 c).  MR = MC = 4 (64 x 64 tiles) when the tile grid fills
 // the GPU, 2 x 2 (32 x 32) for small problems.  The Keogh bridge streams the series in chunks of 32 elements
 // staged transposed in shared memory (query values and (U, Lo) envelope
-// pairs), so every staged element feeds 4 pairs per thread and 64 per CTA.
+// pairs), so every staged element feeds 4 pairs per thread and 64 per CTA;
+// the next chunk is loaded into registers while the current one is used.
 // Elements outside the bridge range [n, L-n) are staged as A = 0 with the
 // envelope (+inf, -inf), which makes their term exactly 0; the inner loop is
 // therefore branch-free: d = A - clamp(A, Lo, U); acc += d * d.
@@ -70,19 +71,27 @@ __device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) 
     return v > 0.0 ? v : 0.0;
 }
 
-// Asynchronous copy of one element (4, 8 or 16 bytes) from global to shared
-// memory; when !valid nothing is read and the element is zero-filled.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n"
-                 :: "r"(sa), "l"(gmem), "n"(BYTES), "r"(valid ? BYTES : 0) : "memory");
+// Four consecutive tile rows of one column into shared memory with vector
+// stores: A16 when the destination is 16-byte aligned, else 8-byte stores.
+template <bool A16> __device__ __forceinline__ void sts4(float *d, const float (&v)[4]) {
+    if (A16) {
+        *reinterpret_cast<float4 *>(d) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<float2 *>(d)[0] = make_float2(v[0], v[1]);
+        reinterpret_cast<float2 *>(d)[1] = make_float2(v[2], v[3]);
+    }
 }
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+template <bool A16> __device__ __forceinline__ void sts4(double *d, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(d)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(d)[1] = make_double2(v[2], v[3]);
 }
-__device__ __forceinline__ void cp_async_wait_1() {
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+template <bool A16> __device__ __forceinline__ void sts4(float2 *d, const float2 (&v)[4]) {
+    reinterpret_cast<float4 *>(d)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    reinterpret_cast<float4 *>(d)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+template <bool A16> __device__ __forceinline__ void sts4(double2 *d, const double2 (&v)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) d[j] = v[j];
 }
 
 // The two ends and the V-1 left and right bands of Eq. 7 for one pair:
@@ -207,19 +216,19 @@ lb_kernel(const __grid_constant__ Src src) {
     using T2 = typename V2<T>::type;
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // Two stages of chunk tiles (the next chunk is copied in while the
+    // One stage of chunk tiles (the next chunk waits in registers while the
     // current one is used), then the band staging.  Offsets are taken from
     // the shared array itself (not through integer casts), so that every
     // access compiles to a shared-memory load.
     constexpr size_t kEsOff = lb_es_offset<T, kQT>();
     constexpr size_t kStage = lb_stage_bytes<T, kQT, kNT, ED>();
-    T *As0 = reinterpret_cast<T *>(smem_raw);                     // [kLC][kQT+kPadA]
-    T2 *Es0 = reinterpret_cast<T2 *>(smem_raw + kEsOff);          // [kLC][kNT+kPadN], 16-byte aligned
-    T *Bs0 = reinterpret_cast<T *>(Es0 + kLC * (kNT + kPadN));     // [kLC][kNT+kPadN] (ED only)
+    T *As = reinterpret_cast<T *>(smem_raw);                      // [kLC][kQT+kPadA]
+    T2 *Es = reinterpret_cast<T2 *>(smem_raw + kEsOff);           // [kLC][kNT+kPadN], 16-byte aligned
+    T *Bs = reinterpret_cast<T *>(Es + kLC * (kNT + kPadN));       // [kLC][kNT+kPadN] (ED only)
     // band staging, rows padded to an odd stride so that the 16 series a
     // warp reads at once fall in distinct banks
     const int bstride = 2 * nb + 1;
-    T *Ab = reinterpret_cast<T *>(smem_raw + 2 * kStage);          // [kQT][2nb+1]
+    T *Ab = reinterpret_cast<T *>(smem_raw + kStage);              // [kQT][2nb+1]
     T *Bb = Ab + kQT * (nb <= kNBMax ? bstride : 0);               // [kNT][2nb+1]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -243,48 +252,67 @@ lb_kernel(const __grid_constant__ Src src) {
     const T POS = inf_of<T>();
 
     const int cbeg = ED ? 0 : (mlo / kLC) * kLC, cend = ED ? L : mhi;
-    // copy the tiles of the chunk starting at c0 into stage st
-    auto stage = [&](int c0, int st) {
-        T *As = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(As0) + st * kStage);
-        T2 *Es = reinterpret_cast<T2 *>(reinterpret_cast<unsigned char *>(Es0) + st * kStage);
-        T *Bs = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(Bs0) + st * kStage);
-        for (int idx = tid; idx < kQT * kLC; idx += kThreads) {
-            const int row = idx / kLC, col = idx % kLC, i = c0 + col;
-            const int64_t q = q0 + row;
-            const bool ok = q < Q && i < L;
-            cp_async<sizeof(T)>(&As[col * (kQT + kPadA) + row], ok ? test + q * L + i : test, ok);
+    // Staging of a chunk of kLC elements: thread tid takes groups of four
+    // consecutive tile rows at one column (column = group % kLC, so a warp
+    // reads 32 consecutive elements of each of four rows: coalesced), loads
+    // them into registers one chunk ahead, and writes each group into the
+    // transposed tile with vector stores (consecutive columns of a warp land
+    // 16 bytes apart modulo 128: no bank conflicts).
+    constexpr int kGA = kQT * kLC / 4 / kThreads;   // query groups per thread
+    constexpr int kGN = kNT * kLC / 4 / kThreads;   // training groups per thread
+    static_assert(kGA * 4 * kThreads == kQT * kLC && kGN * 4 * kThreads == kNT * kLC,
+                  "tile groups divide among the threads");
+    const T2 *envp = reinterpret_cast<const T2 *>(env);
+    T ra[kGA][4], rb[kGN][4];
+    T2 re[kGN][4];
+    auto load = [&](int c0) {
+#pragma unroll
+        for (int k = 0; k < kGA; k++) {
+            const int g = tid + k * kThreads, col = g % kLC, row4 = (g / kLC) * 4;
+            const int i = c0 + col;
+            const T *p = test + (q0 + row4) * L + i;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                ra[k][j] = (i < L && q0 + row4 + j < Q) ? p[(int64_t)j * L] : T(0);
         }
-        if (ED) {
-            for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
-                const int row = idx / kLC, col = idx % kLC, i = c0 + col;
-                const int64_t t = t0 + row;
-                const bool ok = t < N && i < L;
-                cp_async<sizeof(T)>(&Bs[col * (kNT + kPadN) + row], ok ? train + t * L + i : train, ok);
-            }
-        }
-        for (int idx = tid; idx < kNT * kLC; idx += kThreads) {
-            const int row = idx / kLC, col = idx % kLC, i = c0 + col;
-            const int64_t t = t0 + row;
-            if (t < N && i >= mlo && i < mhi) {
-                cp_async<sizeof(T2)>(&Es[col * (kNT + kPadN) + row], env + 2 * (t * L + i), true);
-            } else {
-                T2 e;
-                e.x = POS; e.y = -POS;   // outside the bridge: the term is 0
-                Es[col * (kNT + kPadN) + row] = e;
+#pragma unroll
+        for (int k = 0; k < kGN; k++) {
+            const int g = tid + k * kThreads, col = g % kLC, row4 = (g / kLC) * 4;
+            const int i = c0 + col;
+            const bool in_bridge = i >= mlo && i < mhi;
+            const T2 *pe = envp + (t0 + row4) * L + i;
+            const T *pb = train + (t0 + row4) * L + i;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const bool rowok = t0 + row4 + j < N;
+                if (rowok && in_bridge) {
+                    re[k][j] = pe[(int64_t)j * L];
+                } else {
+                    re[k][j].x = POS; re[k][j].y = -POS;   // outside the bridge: term 0
+                }
+                if constexpr (ED) rb[k][j] = (rowok && i < L) ? pb[(int64_t)j * L] : T(0);
             }
         }
     };
-    if (cbeg < cend) stage(cbeg, 0);
-    cp_async_commit();
-    int st = 0;
-    for (int c0 = cbeg; c0 < cend; c0 += kLC, st ^= 1) {
-        if (c0 + kLC < cend) stage(c0 + kLC, st ^ 1);
-        cp_async_commit();
-        cp_async_wait_1();       // this chunk's copies have landed
+    auto store = [&]() {
+#pragma unroll
+        for (int k = 0; k < kGA; k++) {
+            const int g = tid + k * kThreads, col = g % kLC, row4 = (g / kLC) * 4;
+            sts4<true>(As + col * (kQT + kPadA) + row4, ra[k]);   // rows 16-byte aligned
+        }
+#pragma unroll
+        for (int k = 0; k < kGN; k++) {
+            const int g = tid + k * kThreads, col = g % kLC, row4 = (g / kLC) * 4;
+            sts4<true>(Es + col * (kNT + kPadN) + row4, re[k]);
+            // (training values: rows of kNT + kPadN, 8-byte aligned in FP32)
+            if constexpr (ED) sts4<false>(Bs + col * (kNT + kPadN) + row4, rb[k]);
+        }
+    };
+    if (cbeg < cend) load(cbeg);
+    for (int c0 = cbeg; c0 < cend; c0 += kLC) {
+        store();
         __syncthreads();
-        const T *As = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(As0) + st * kStage);
-        const T2 *Es = reinterpret_cast<const T2 *>(reinterpret_cast<unsigned char *>(Es0) + st * kStage);
-        const T *Bs = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(Bs0) + st * kStage);
+        if (c0 + kLC < cend) load(c0 + kLC);   // in flight while this chunk is used
 #pragma unroll 4
         for (int col = 0; col < kLC; col++) {
             T a[MR];
@@ -394,8 +422,7 @@ lb_kernel(const __grid_constant__ Src src) {
 template <typename T, int MR, int MC>
 size_t lb_smem(bool ed, bool keogh, int nb) {
     constexpr int kQT = 16 * MR, kNT = 16 * MC;
-    size_t smem = 2 * (ed ? lb_stage_bytes<T, kQT, kNT, true>()
-                          : lb_stage_bytes<T, kQT, kNT, false>());
+    size_t smem = ed ? lb_stage_bytes<T, kQT, kNT, true>() : lb_stage_bytes<T, kQT, kNT, false>();
     if (!keogh && nb <= kNBMax) smem += sizeof(T) * (size_t)(kQT + kNT) * (2 * nb + 1);
     return smem;
 }
