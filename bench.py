@@ -616,6 +616,9 @@ def main():
                     help="JSON file of per-dataset search flags: read if it exists (no tuning), "
                          "else written after tuning, so that a profiled run repeats the choices "
                          "of a plain one")
+    ap.add_argument("--lb-tile", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="tile shape of the bound pass for every dataset (1: 32 x 32, "
+                         "2: 64 x 64, 3: 128 x 64); 0: the library's or the tuner's choice")
     ap.add_argument("--dtw-group", type=int, default=0,
                     help="lanes per pair for every dataset (1..32, or 64 for the row layout); "
                          "implies --no-tune")
@@ -676,7 +679,8 @@ def main():
 
     def record(g, flags):
         return {"group": g, "reverse": bool(flags & nndtw.REVERSE),
-                "improved": bool(flags & nndtw.IMPROVED)}
+                "improved": bool(flags & nndtw.IMPROVED),
+                "lb_tile": (flags & nndtw.LB_TILE_MASK) >> 19}
     if args.dtw_group:
         for i, s in enumerate(sets):
             s["flags"] = nndtw.DTW_GROUP(args.dtw_group) | cascade
@@ -699,11 +703,14 @@ def main():
                 s["flags"] = autotune.tune_search_flags(s["train"], s["labels"], s["test"], d.W,
                                                         d.V, reps=2)
                 g = autotune.tune_search(s["train"], s["labels"], s["test"], d.W, d.V, reps=2)
-                if g or s["flags"] & (nndtw.REVERSE | nndtw.IMPROVED):
+                if g or s["flags"] & (nndtw.REVERSE | nndtw.IMPROVED | nndtw.LB_TILE_MASK):
                     tuned[i] = record(g, s["flags"])
         if args.tuned_flags and rank == 0:
             with open(args.tuned_flags, "w") as f:
                 json.dump({"flags": [s["flags"] for s in sets], "tuned": tuned}, f)
+    if args.lb_tile:
+        for s in sets:
+            s["flags"] = (s["flags"] & ~nndtw.LB_TILE_MASK) | nndtw.LB_TILE(args.lb_tile)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # counting pass (untimed): pruning and cells per dataset

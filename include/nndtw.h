@@ -104,6 +104,12 @@ extern "C" {
  * NNDTW_DTW_ROWS_LANES16 (L <= 1024) or NNDTW_DTW_ROWS_LANES8 (L <= 512) a
  * pair takes 16 or 8 lanes instead (a tuning choice; results never change;
  * ignored where L is too long). */
+/* search: tile shape of the bound pass (queries x training series per CTA),
+ * a tuning choice that never changes results: NNDTW_LB_TILE(1) 32 x 32,
+ * NNDTW_LB_TILE(2) 64 x 64, NNDTW_LB_TILE(3) 128 x 64; 0 (the default) lets
+ * the library choose (64 x 64 when such tiles give every SM two CTAs). */
+#define NNDTW_LB_TILE(k) ((unsigned)(k) << 19)
+#define NNDTW_LB_TILE_MASK (3u << 19)
 #define NNDTW_DTW_ROWS (7u << 8)
 #define NNDTW_DTW_ROWS_LANES16 (1u << 12)
 #define NNDTW_DTW_ROWS_LANES8 (2u << 12)
@@ -176,7 +182,8 @@ NNDTW_API int nn_dtw_build_second_envelopes_f64(const double *d_env, int64_t N, 
  *   + sum_{i=2..L-1} min over max(1,i-W) <= j <= min(L,i+W) of delta(A_i,B_j),
  * O(L (2W+1)) per pair (d_env is not read and may be NULL).
  * flags & NNDTW_LB_SAFE scales each value down by the FP32 (or FP64) rounding
- * margin so that it never exceeds the exact bound.
+ * margin so that it never exceeds the exact bound; NNDTW_LB_TILE(k) picks the
+ * bound pass's tile shape (a tuning choice).
  * d_test: [Q][L]; d_train: [N][L]; d_env: [N][L][2] from
  * nn_dtw_build_envelopes with the same W; d_lb_out: [Q][N], row-major.
  * Errors: NNDTW_EINVAL for null pointers, Q < 0, N < 0, L < 2 or > NNDTW_MAX_L,

@@ -25,6 +25,8 @@ _mem: dict = {}
 
 # the cascade's second stage: none, the reverse bound, the LB_Improved bridge
 CASCADE_CHOICES = (0, nndtw.REVERSE, nndtw.IMPROVED)
+# the bound pass's tile shapes tried against the library's own choice
+LB_TILE_CHOICES = (1, 2, 3)
 
 
 def _bucket(n: int) -> int:
@@ -124,10 +126,12 @@ def tune_search(train, labels, test, W: int, V: int, workspace=None, out=None, r
 
 def tune_search_flags(train, labels, test, W: int, V: int, reps: int = 3,
                       cache_path: str | None = None) -> int:
-    """Search flags for this data: the fastest lanes-per-pair choice, plus the
-    cascade's second stage that makes the search fastest: none, the reverse
-    bound (``nndtw.REVERSE``) or the bound with the LB_Improved bridge
-    (``nndtw.IMPROVED``).  Results never depend on any of them."""
+    """Search flags for this data: the fastest lanes-per-pair choice, the
+    cascade's second stage that makes the search fastest (none, the reverse
+    bound ``nndtw.REVERSE`` or the bound with the LB_Improved bridge
+    ``nndtw.IMPROVED``), then the fastest tile shape of the bound pass
+    (``nndtw.LB_TILE``: 32 x 32, 64 x 64 or 128 x 64 queries x training
+    series per CTA).  Results never depend on any of them."""
     import torch
     g = tune_search(train, labels, test, W, V, reps=reps, cache_path=cache_path)
     base = nndtw.DTW_GROUP(g) if g else 0
@@ -147,6 +151,14 @@ def tune_search_flags(train, labels, test, W: int, V: int, reps: int = 3,
         ms = _median_ms(train, labels, test, W, V, base | extra, workspace, out, reps)
         if best_ms is None or ms < best_ms:
             best, best_ms = extra, ms
+    # the bound pass's tile shape, with the chosen layout and cascade
+    tile, tile_ms = 0, best_ms
+    for t in LB_TILE_CHOICES:
+        ms = _median_ms(train, labels, test, W, V, base | best | nndtw.LB_TILE(t), workspace,
+                        out, reps)
+        if ms < tile_ms:
+            tile, tile_ms = t, ms
+    best |= nndtw.LB_TILE(tile) if tile else 0
     with _lock:
         _mem[k] = best
     return base | best

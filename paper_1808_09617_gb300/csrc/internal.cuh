@@ -186,12 +186,12 @@ template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N,
                       int L, int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack,
                       T *lb_out, unsigned long long *seed_keys, T *norms, T *ends_out,
-                      bool loo, cudaStream_t s, int64_t q_base = 0);
+                      bool loo, cudaStream_t s, int64_t q_base = 0, int tile = 0);
 
 // The bound pass (and its squared norms) of one dataset as job structures,
-// for the batched search: launch_lb's arguments, its tile shape (small: 32 x
-// 32 tiles, else 64 x 64; a kernel variant, as is ed, the fused Euclidean
-// seed) and launch shape.  The kernel runs kLbThreads threads per CTA, the
+// for the batched search: launch_lb's arguments, its tile shape (a kernel
+// variant, as is ed, the fused Euclidean seed; 0 lets the planner choose)
+// and launch shape.  The kernel runs kLbThreads threads per CTA, the
 // norms 256.
 constexpr int kLbThreads = 256;
 template <typename T> struct LbJob {
@@ -219,7 +219,8 @@ template <typename T> struct SqnormJob {
 template <typename T> struct LbPlan {
     LbJob<T> job;
     SqnormJob<T> sq;
-    bool small, ed;
+    int tile;    // 1: 32 x 32, 2: 64 x 64, 3: 128 x 64 (queries x training series)
+    bool ed;
     size_t smem;
     long long blocks, sq_blocks;
 };
@@ -233,9 +234,9 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p, int64_t q_base = 0);
-template <typename T> LbFns<T> lb_fns(bool small, bool ed);
-template <typename T> cudaError_t set_lb_smem(bool small, bool ed, size_t smem);
+                    LbPlan<T> *p, int64_t q_base = 0, int tile = 0);
+template <typename T> LbFns<T> lb_fns(int tile, bool ed);
+template <typename T> cudaError_t set_lb_smem(int tile, bool ed, size_t smem);
 
 // LB_New (Sec. 2.2.5) of every (query, training series) pair into out[Q][N]
 // (raw, or with safe: scaled down by the rounding margin).

@@ -2,9 +2,11 @@
 // test) or LB_Keogh (Sec. 2.2.3) for every (query, training series) pair.
 //
 // Tiling: a CTA of 256 threads owns 16 MR queries x 16 MC training series;
-// each thread owns an MR x MC register micro-tile of pairs (queries ty + 16 r,
-// series tx + 16 c).  MR = MC = 4 (64 x 64 tiles) when the tile grid fills
-// the GPU, 2 x 2 (32 x 32) for small problems.  The Keogh bridge streams the series in chunks of 32 elements
+// each thread owns an MR x MC register micro-tile of pairs (queries ty MR + r,
+// series in pairs of columns).  MR = MC = 4 (64 x 64 tiles) when the tile
+// grid fills the GPU, 2 x 2 (32 x 32) for small problems; 8 x 4 (128 x 64)
+// on request (a tuning choice: fewer shared loads per pair-element at half
+// the resident CTAs).  The Keogh bridge streams the series in chunks of 32 elements
 // staged transposed in shared memory (query values and (U, Lo) envelope
 // pairs), so every staged element feeds 4 pairs per thread and 64 per CTA;
 // the next chunk is loaded into registers while the current one is used.
@@ -159,7 +161,13 @@ __device__ __forceinline__ void lds2(double2 (&d)[2], const double2 *p) {
     d[0] = p[0]; d[1] = p[1];
 }
 template <typename T, int N> __device__ __forceinline__ void ldsn(T (&d)[N], const T *p) {
-    if constexpr (N == 4) lds4(d, p);
+    if constexpr (N == 8) {
+        T lo[4], hi[4];
+        lds4(lo, p);
+        lds4(hi, p + 4);
+#pragma unroll
+        for (int k = 0; k < 4; k++) { d[k] = lo[k]; d[4 + k] = hi[k]; }
+    } else if constexpr (N == 4) lds4(d, p);
     else if constexpr (N == 2) lds2(d, p);
     else {
 #pragma unroll
@@ -433,15 +441,19 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p, int64_t q_base) {
+                    LbPlan<T> *p, int64_t q_base, int tile) {
     int nb = L / 2 < V ? L / 2 : V;
     if (nb < 1) nb = 1;
     const int Weff = W > L - 1 ? L - 1 : W;
     // 64 x 64 tiles when they give at least two CTAs per SM, else 32 x 32
     const int sms = device_sm_count();
-    p->small = ((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms;
+    // tile shape: 64 x 64 when such tiles give at least two CTAs per SM, else
+    // 32 x 32, unless the caller asks for one (1: 32 x 32, 2: 64 x 64,
+    // 3: 128 x 64)
+    p->tile = tile ? tile : (((N + 63) / 64) * ((Q + 63) / 64) < 2ll * sms ? 1 : 2);
     p->ed = seed_keys != nullptr;
-    const int kQT = p->small ? 32 : 64, kNT = kQT;
+    const int kQT = p->tile == 1 ? 32 : p->tile == 2 ? 64 : 128;
+    const int kNT = p->tile == 1 ? 32 : 64;
     const long long qt = (Q + kQT - 1) / kQT, nt_tiles = (N + kNT - 1) / kNT;
     LbJob<T> &j = p->job;
     j.test = test; j.Q = Q; j.train = train; j.env = env; j.N = N; j.L = L; j.W = Weff;
@@ -454,31 +466,33 @@ cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int6
     j.qfast = 1;
     j.gx = (int)qt;
     p->blocks = qt * nt_tiles;
-    p->smem = p->small ? lb_smem<T, 2, 2>(p->ed, keogh, nb) : lb_smem<T, 4, 4>(p->ed, keogh, nb);
+    p->smem = p->tile == 1 ? lb_smem<T, 2, 2>(p->ed, keogh, nb)
+            : p->tile == 2 ? lb_smem<T, 4, 4>(p->ed, keogh, nb) : lb_smem<T, 8, 4>(p->ed, keogh, nb);
     p->sq = SqnormJob<T>{test, Q, train, N, L, norms, norms + Q};
     const int64_t rows = Q + N;
     p->sq_blocks = seed_keys ? ((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096) : 0;
     return cudaSuccess;
 }
 
+template <typename T, int MR, int MC> void lb_fns_of(bool ed, LbFns<T> *f) {
+    f->fn1 = ed ? lb_kernel<T, true, MR, MC, Src1<LbJob<T>>> : lb_kernel<T, false, MR, MC, Src1<LbJob<T>>>;
+    f->fnN = ed ? lb_kernel<T, true, MR, MC, SrcN<LbJob<T>>> : lb_kernel<T, false, MR, MC, SrcN<LbJob<T>>>;
+}
+
 template <typename T>
-LbFns<T> lb_fns(bool small, bool ed) {
+LbFns<T> lb_fns(int tile, bool ed) {
     LbFns<T> f;
-    if (small) {
-        f.fn1 = ed ? lb_kernel<T, true, 2, 2, Src1<LbJob<T>>> : lb_kernel<T, false, 2, 2, Src1<LbJob<T>>>;
-        f.fnN = ed ? lb_kernel<T, true, 2, 2, SrcN<LbJob<T>>> : lb_kernel<T, false, 2, 2, SrcN<LbJob<T>>>;
-    } else {
-        f.fn1 = ed ? lb_kernel<T, true, 4, 4, Src1<LbJob<T>>> : lb_kernel<T, false, 4, 4, Src1<LbJob<T>>>;
-        f.fnN = ed ? lb_kernel<T, true, 4, 4, SrcN<LbJob<T>>> : lb_kernel<T, false, 4, 4, SrcN<LbJob<T>>>;
-    }
+    if (tile == 1) lb_fns_of<T, 2, 2>(ed, &f);
+    else if (tile == 2) lb_fns_of<T, 4, 4>(ed, &f);
+    else lb_fns_of<T, 8, 4>(ed, &f);
     f.sq1 = sqnorm_kernel<T, Src1<SqnormJob<T>>>;
     f.sqN = sqnorm_kernel<T, SrcN<SqnormJob<T>>>;
     return f;
 }
 
 template <typename T>
-cudaError_t set_lb_smem(bool small, bool ed, size_t smem) {
-    const LbFns<T> f = lb_fns<T>(small, ed);
+cudaError_t set_lb_smem(int tile, bool ed, size_t smem) {
+    const LbFns<T> f = lb_fns<T>(tile, ed);
     cudaError_t e = cudaFuncSetAttribute(f.fn1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess)
@@ -490,14 +504,14 @@ template <typename T>
 cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                       int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                       unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                      cudaStream_t s, int64_t q_base) {
+                      cudaStream_t s, int64_t q_base, int tile) {
     if (Q <= 0 || N <= 0) return cudaSuccess;
     if (seed_keys && !norms) return cudaErrorInvalidValue;
     LbPlan<T> p{};
     cudaError_t e = plan_lb<T>(test, Q, train, env, N, L, W, V, keogh, safe, lb_lo, abs_slack,
-                               lb_out, seed_keys, norms, ends_out, loo, &p, q_base);
+                               lb_out, seed_keys, norms, ends_out, loo, &p, q_base, tile);
     if (e != cudaSuccess) return e;
-    const LbFns<T> f = lb_fns<T>(p.small, p.ed);
+    const LbFns<T> f = lb_fns<T>(p.tile, p.ed);
     if (p.sq_blocks > 0) {
         // squared norms of the queries (norms[0..Q)) and training series
         // (norms[Q..Q+N)) for the fused Euclidean distance
@@ -505,7 +519,7 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    e = set_lb_smem<T>(p.small, p.ed, p.smem);
+    e = set_lb_smem<T>(p.tile, p.ed, p.smem);
     if (e != cudaSuccess) return e;
     f.fn1<<<(unsigned)p.blocks, kThreads, p.smem, s>>>(Src1<LbJob<T>>{p.job});
     return cudaGetLastError();
@@ -514,16 +528,16 @@ cudaError_t launch_lb(const T *test, int64_t Q, const T *train, const T *env, in
 template cudaError_t launch_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                       int, int, int, bool, bool, float, float, float *,
                                       unsigned long long *, float *, float *, bool,
-                                      cudaStream_t, int64_t);
+                                      cudaStream_t, int64_t, int);
 template cudaError_t launch_lb<double>(const double *, int64_t, const double *, const double *,
                                        int64_t, int, int, int, bool, bool, double, double,
                                        double *, unsigned long long *, double *, double *,
-                                       bool, cudaStream_t, int64_t);
+                                       bool, cudaStream_t, int64_t, int);
 template cudaError_t plan_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                     int, int, int, bool, bool, float, float, float *,
                                     unsigned long long *, float *, float *, bool,
-                                    LbPlan<float> *, int64_t);
-template LbFns<float> lb_fns<float>(bool, bool);
-template cudaError_t set_lb_smem<float>(bool, bool, size_t);
+                                    LbPlan<float> *, int64_t, int);
+template LbFns<float> lb_fns<float>(int, bool);
+template cudaError_t set_lb_smem<float>(int, bool, size_t);
 
 }  // namespace nndtw

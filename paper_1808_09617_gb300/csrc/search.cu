@@ -843,8 +843,9 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             LbPlan<float> lp{};
             CK(plan_lb<float>(x.test, x.Q, x.train, p.env, x.N, x.L, p.Weff, x.V, p.keogh, true,
                               p.m.lb_lo, p.m.abs32, p.ws.lb, p.ws.seed, p.ws.norms,
-                              p.rev ? p.ws.ends : nullptr, p.loo, &lp, x.q_base));
-            const LbFns<float> f = lb_fns<float>(lp.small, lp.ed);
+                              p.rev ? p.ws.ends : nullptr, p.loo, &lp, x.q_base,
+                              (int)((x.flags & NNDTW_LB_TILE_MASK) >> 19)));
+            const LbFns<float> f = lb_fns<float>(lp.tile, lp.ed);
             gs.add(f.sq1, f.sqN, 256, 0, lp.sq, lp.sq_blocks);
             gl.add(f.fn1, f.fnN, kLbThreads, lp.smem, lp.job, lp.blocks);
         }
@@ -1148,7 +1149,8 @@ int lb_enhanced(const float *d_test, int64_t Q, const float *d_train, const floa
     }
     CK(launch_lb<float>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                         (flags & NNDTW_LB_SAFE) != 0, m.lb_lo, m.abs32, d_lb_out, nullptr,
-                        nullptr, nullptr, false, (cudaStream_t)stream));
+                        nullptr, nullptr, false, (cudaStream_t)stream, 0,
+                        (int)((flags & NNDTW_LB_TILE_MASK) >> 19)));
     return NNDTW_OK;
 }
 
@@ -1168,7 +1170,8 @@ int lb_enhanced_f64(const double *d_test, int64_t Q, const double *d_train, cons
     }
     CK(launch_lb<double>(d_test, Q, d_train, d_env, N, L, W, V, (flags & NNDTW_LB_KEOGH) != 0,
                          (flags & NNDTW_LB_SAFE) != 0, m.lb_lo64, m.abs64, d_lb_out, nullptr,
-                         nullptr, nullptr, false, (cudaStream_t)stream));
+                         nullptr, nullptr, false, (cudaStream_t)stream, 0,
+                        (int)((flags & NNDTW_LB_TILE_MASK) >> 19)));
     return NNDTW_OK;
 }
 

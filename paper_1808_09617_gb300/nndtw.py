@@ -41,9 +41,22 @@ KEOGH_BOUND = 1 << 17
 ROWS_GROUP = 64
 ROWS16_GROUP = 65
 ROWS8_GROUP = 66
+DTW_GROUP_MASK = 7 << 8
 DTW_ROWS = 7 << 8
 DTW_ROWS_LANES16 = 1 << 12
 DTW_ROWS_LANES8 = 2 << 12
+
+
+def LB_TILE(k: int) -> int:
+    """Flag selecting the bound pass's tile shape: 1 = 32 x 32, 2 = 64 x 64,
+    3 = 128 x 64 (queries x training series per CTA); 0 = the library's
+    choice.  A tuning choice: results never change."""
+    if k not in (0, 1, 2, 3):
+        raise ValueError("LB tile shape must be 0..3")
+    return k << 19
+
+
+LB_TILE_MASK = 3 << 19
 
 
 def DTW_GROUP(g: int) -> int:
@@ -275,8 +288,9 @@ def nn_dtw_build_envelopes(train, W: int, env=None, stream=None):
 
 
 def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: bool = False,
-                out=None, stream=None):
-    """LB_Enhanced^V (or LB_Keogh) for all pairs: tensor [Q, N]."""
+                out=None, stream=None, tile: int = 0):
+    """LB_Enhanced^V (or LB_Keogh) for all pairs: tensor [Q, N] (``tile``:
+    the bound pass's tile shape, see LB_TILE)."""
     import torch
     lib = load()
     f64 = _fp(test)
@@ -284,7 +298,7 @@ def lb_enhanced(test, train, env, W: int, V: int, keogh: bool = False, safe: boo
     N = train.shape[0]
     if out is None:
         out = torch.empty((Q, N), dtype=test.dtype, device=test.device)
-    flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0)
+    flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0) | LB_TILE(tile)
     fn = lib.lb_enhanced_f64 if f64 else lib.lb_enhanced
     with _on([test, train, env, out], stream):
         _check(fn(_dev(test, test.dtype, "test", 2), Q,

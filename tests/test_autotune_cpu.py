@@ -25,19 +25,22 @@ def test_key_buckets():
     assert autotune.key("GB300", 500, 500, 256, 300, 5) == autotune.key("GB300", 500, 500, 256, 255, 5)
 
 
-def test_tune_search_flags_picks_fastest_cascade(monkeypatch):
+def test_tune_search_flags_picks_fastest_cascade_and_tile(monkeypatch):
     """The cascade's second stage is the fastest of none / reverse bound /
-    LB_Improved bridge, chosen once per data key and then remembered (timings
-    faked: no GPU here)."""
+    LB_Improved bridge, then the bound pass's tile shape the fastest of the
+    three (or the library's own choice when none is faster), chosen once per
+    data key and then remembered (timings faked: no GPU here)."""
     import torch
 
     from paper_1808_09617_gb300 import nndtw
     calls = []
     fake_ms = {0: 5.0, nndtw.REVERSE: 4.0, nndtw.IMPROVED: 3.0}
+    tile_gain = {0: 0.0, 1: -1.0, 2: 0.0, 3: 0.5}
 
     def median_ms(train, labels, test, W, V, flags, workspace, out, reps):
         calls.append(flags)
-        return fake_ms[flags & (nndtw.REVERSE | nndtw.IMPROVED)]
+        tile = (flags & nndtw.LB_TILE_MASK) >> 19
+        return fake_ms[flags & (nndtw.REVERSE | nndtw.IMPROVED)] - tile_gain[tile]
 
     monkeypatch.setattr(autotune, "tune_search", lambda *a, **k: 8)
     monkeypatch.setattr(autotune, "_median_ms", median_ms)
@@ -48,13 +51,18 @@ def test_tune_search_flags_picks_fastest_cascade(monkeypatch):
     test = torch.zeros((40, 32))
     labels = torch.zeros(100, dtype=torch.int32)
     f = autotune.tune_search_flags(train, labels, test, 3, 2, reps=1)
-    assert f == nndtw.DTW_GROUP(8) | nndtw.IMPROVED
+    assert f == nndtw.DTW_GROUP(8) | nndtw.IMPROVED | nndtw.LB_TILE(3)
     cascade = nndtw.REVERSE | nndtw.IMPROVED
-    assert sorted(c & cascade for c in calls) == sorted(autotune.CASCADE_CHOICES)
-    assert all(c & ~cascade == nndtw.DTW_GROUP(8) for c in calls)
+    untiled = [c for c in calls if not c & nndtw.LB_TILE_MASK]
+    assert sorted(c & cascade for c in untiled) == sorted(autotune.CASCADE_CHOICES)
+    tiled = [c for c in calls if c & nndtw.LB_TILE_MASK]
+    assert sorted((c & nndtw.LB_TILE_MASK) >> 19 for c in tiled) == sorted(autotune.LB_TILE_CHOICES)
+    assert all(c & cascade == nndtw.IMPROVED for c in tiled)    # with the chosen cascade
+    assert all(c & nndtw.DTW_GROUP_MASK == nndtw.DTW_GROUP(8) for c in calls)
     n = len(calls)
     assert autotune.tune_search_flags(train, labels, test, 3, 2, reps=1) == f
     assert len(calls) == n                       # remembered
     fake_ms[nndtw.IMPROVED] = 9.0
+    tile_gain[3] = -2.0                          # no tile shape beats the library's choice
     f2 = autotune.tune_search_flags(train, labels, test[:3], 3, 2, reps=1)   # another Q bucket
     assert f2 == nndtw.DTW_GROUP(8) | nndtw.REVERSE

@@ -72,6 +72,26 @@ def test_lb_enhanced_parity(lib, orc, L, W, V):
     assert np.all(safe <= lb)
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("L,W,V", [(256, 26, 5), (77, 3, 2), (1000, 100, 8)])
+def test_lb_every_tile_shape(lib, orc, L, W, V, tile):
+    """Every tile shape of the bound pass (32 x 32, 64 x 64, 128 x 64) gives
+    the oracle's bounds, ragged tiles included; the search with each tile
+    shape gives the oracle's neighbours."""
+    test = _series(1500 + L, 141, L)
+    train = _series(1600 + W, 203, L)
+    env = lib.nn_dtw_build_envelopes(_t(train), W)
+    lb = lib.lb_enhanced(_t(test), _t(train), env, W, V, tile=tile).cpu().numpy()
+    ref = orc.lb_matrix(test, train, W, V, "enhanced")
+    np.testing.assert_allclose(lb, ref, rtol=RTOL32, atol=1e-6)
+    keo = lib.lb_enhanced(_t(test), _t(train), env, W, V, keogh=True, tile=tile).cpu().numpy()
+    np.testing.assert_allclose(keo, orc.lb_matrix(test, train, W, V, "keogh"), rtol=RTOL32,
+                               atol=1e-6)
+    labels = np.arange(train.shape[0], dtype=np.int32) % 5
+    brute = orc.nn_brute(train, labels, test[:40], W)
+    _check_search(lib, orc, train, labels, test[:40], W, V, flags=lib.LB_TILE(tile), brute=brute)
+
+
 @pytest.mark.parametrize("L,W,V", [(128, 13, 5), (33, 4, 16), (300, 299, 2)])
 def test_lb_enhanced_f64_parity(lib, orc, L, W, V):
     test = _series(3000 + L, 19, L, np.float64)
