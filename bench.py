@@ -561,6 +561,7 @@ def run_serving(args):
             srv.completed = 0
             srv.t_first = srv.t_last = None
             srv.batches = 0
+            srv.batch_sets = 0
             times = synth.arrival_times(rate, args.serve_seconds, seed_index=int(rate))
             which = rng.integers(0, len(sets), size=times.size)
             t0 = time.perf_counter() + 0.05

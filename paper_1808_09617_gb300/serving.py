@@ -98,6 +98,7 @@ class Server:
         self.latencies: list[float] = []
         self.completed = 0
         self.batches = 0
+        self.batch_sets = 0      # datasets over all batches (batches span datasets)
         self.t_first = None
         self.t_last = None
         if tune:
@@ -136,6 +137,7 @@ class Server:
         if lat.size == 0:
             return {"completed": 0}
         return {"completed": n, "batches": self.batches,
+                "mean_sets_per_batch": self.batch_sets / self.batches if self.batches else None,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3),
@@ -209,6 +211,7 @@ class Server:
         self.inflight.append(_Batch([(sid, reqs, host_out) for sid, reqs, host_out, _ in parts],
                                     stream, ev, nbytes, time.perf_counter(), keep=keep))
         self.batches += 1
+        self.batch_sets += len(take)
 
     def _retire(self, b: _Batch, slot: int):
         now = time.perf_counter()
