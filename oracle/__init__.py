@@ -21,6 +21,9 @@ Functions and the passage of the paper each one follows:
 ``lb_new``             Sec. 2.2.5 (LB_New)
 ``nn_brute``           1-NN by exhaustive DTW (Sec. 1, the task itself)
 ``nn_pruned``          the paper's lower-bound search protocol (Sec. 4)
+``*_var``              the same for series of unequal lengths (Sec. 2:
+                       the equal-length exposition generalises); ragged
+                       sets are (values, offsets) pairs
 =====================  ====================================================
 """
 from __future__ import annotations
@@ -95,6 +98,33 @@ def _declare(lib):
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32, _i32, _d,
                                      _i64, ctypes.c_int]
     lib.oracle_nn_pruned.restype = None
+    lib.oracle_envelope_var.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, _d]
+    lib.oracle_envelope_var.restype = None
+    lib.oracle_dtw_var.argtypes = [_d, ctypes.c_int, _d, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double]
+    lib.oracle_dtw_var.restype = ctypes.c_double
+    lib.oracle_lb_keogh_var.argtypes = [_d, ctypes.c_int, ctypes.c_int, _d, _d, ctypes.c_int]
+    lib.oracle_lb_keogh_var.restype = ctypes.c_double
+    lib.oracle_lb_enhanced_var.argtypes = [_d, ctypes.c_int, _d, ctypes.c_int, _d, _d,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    lib.oracle_lb_enhanced_var.restype = ctypes.c_double
+    lib.oracle_envelopes_var.argtypes = [_d, _i64, ctypes.c_int64, ctypes.c_int, _i64, _d, _d]
+    lib.oracle_envelopes_var.restype = None
+    lib.oracle_lb_matrix_var.argtypes = [_d, _i64, ctypes.c_int64, _d, _i64, _d, _d, _i64,
+                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _d, ctypes.c_int]
+    lib.oracle_lb_matrix_var.restype = None
+    lib.oracle_dtw_matrix_var.argtypes = [_d, _i64, ctypes.c_int64, _d, _i64, ctypes.c_int64,
+                                          ctypes.c_int, _d, ctypes.c_int]
+    lib.oracle_dtw_matrix_var.restype = None
+    lib.oracle_nn_brute_var.argtypes = [_d, _i64, _i32, ctypes.c_int64, _d, _i64,
+                                        ctypes.c_int64, ctypes.c_int, _i32, _i32, _d,
+                                        ctypes.c_int]
+    lib.oracle_nn_brute_var.restype = None
+    lib.oracle_nn_pruned_var.argtypes = [_d, _i64, _i32, _d, _d, _i64, ctypes.c_int64, _d,
+                                         _i64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         _i32, _i32, _d, _i64, ctypes.c_int]
+    lib.oracle_nn_pruned_var.restype = None
     return lib
 
 
@@ -254,6 +284,106 @@ class Oracle:
         self.lib.oracle_nn_pruned(_p(train), _p(labels, _i32), _p(U), _p(Lo), N, _p(test), Q,
                                   L, int(W), int(V), _p(idx, _i32), _p(lab, _i32), _p(dist),
                                   _p(st, _i64), threads or default_threads())
+        return idx, lab, dist, st
+
+    # -- unequal lengths (ragged sets: values and offsets) --------------------
+    def envelope_var(self, b, W, E=None):
+        """B's envelope for the rows 1..E of a series compared with it
+        (default E = len(b) + W, the longest series with a path)."""
+        b = _f64(b)
+        E = b.shape[0] + int(W) if E is None else int(E)
+        assert 1 <= E <= b.shape[0] + int(W)
+        U = np.empty(E); Lo = np.empty(E)
+        self.lib.oracle_envelope_var(_p(b), b.shape[0], int(W), E, _p(U), _p(Lo))
+        return U, Lo
+
+    def dtw_var(self, a, b, W, cutoff=np.inf):
+        a = _f64(a); b = _f64(b)
+        return self.lib.oracle_dtw_var(_p(a), a.shape[0], _p(b), b.shape[0], int(W),
+                                       float(cutoff))
+
+    def lb_keogh_var(self, a, b, W):
+        a = _f64(a); b = _f64(b)
+        U, Lo = self.envelope_var(b, W)
+        if a.shape[0] > U.shape[0]:
+            return np.inf
+        return self.lib.oracle_lb_keogh_var(_p(a), a.shape[0], b.shape[0], _p(U), _p(Lo),
+                                            int(W))
+
+    def lb_enhanced_var(self, a, b, W, V, D=np.inf):
+        a = _f64(a); b = _f64(b)
+        assert a.shape[0] >= 2 and b.shape[0] >= 2
+        U, Lo = self.envelope_var(b, W)
+        if a.shape[0] > U.shape[0]:
+            return np.inf
+        return self.lib.oracle_lb_enhanced_var(_p(a), a.shape[0], _p(b), b.shape[0], _p(U),
+                                               _p(Lo), int(W), int(V), float(D))
+
+    @staticmethod
+    def _ragged(vals, off):
+        vals = _f64(vals)
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        assert off.ndim == 1 and off[0] == 0 and off[-1] == vals.shape[0]
+        return vals, off
+
+    def envelopes_var(self, train, off, W):
+        """Envelopes of a ragged set: (U, Lo, eoff), series t's L_t + W rows
+        at eoff[t] = off[t] + t W."""
+        train, off = self._ragged(train, off)
+        N = off.shape[0] - 1
+        eoff = off + np.arange(N + 1, dtype=np.int64) * int(W)
+        U = np.empty(int(eoff[-1])); Lo = np.empty(int(eoff[-1]))
+        self.lib.oracle_envelopes_var(_p(train), _p(off, _i64), N, int(W), _p(eoff, _i64),
+                                      _p(U), _p(Lo))
+        return U, Lo, eoff
+
+    def lb_matrix_var(self, test, toff, train, off, W, V, kind="enhanced", env=None,
+                      threads=None):
+        test, toff = self._ragged(test, toff)
+        train, off = self._ragged(train, off)
+        Q, N = toff.shape[0] - 1, off.shape[0] - 1
+        U, Lo, eoff = env if env is not None else self.envelopes_var(train, off, W)
+        out = np.empty((Q, N))
+        k = {"enhanced": 0, "keogh": 1}[kind]
+        self.lib.oracle_lb_matrix_var(_p(test), _p(toff, _i64), Q, _p(train), _p(off, _i64),
+                                      _p(_f64(U)), _p(_f64(Lo)), _p(eoff, _i64), N, int(W),
+                                      int(V), k, _p(out), threads or default_threads())
+        return out
+
+    def dtw_matrix_var(self, test, toff, train, off, W, threads=None):
+        test, toff = self._ragged(test, toff)
+        train, off = self._ragged(train, off)
+        Q, N = toff.shape[0] - 1, off.shape[0] - 1
+        out = np.empty((Q, N))
+        self.lib.oracle_dtw_matrix_var(_p(test), _p(toff, _i64), Q, _p(train), _p(off, _i64),
+                                       N, int(W), _p(out), threads or default_threads())
+        return out
+
+    def nn_brute_var(self, train, off, labels, test, toff, W, threads=None):
+        train, off = self._ragged(train, off)
+        test, toff = self._ragged(test, toff)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        N, Q = off.shape[0] - 1, toff.shape[0] - 1
+        idx = np.empty(Q, np.int32); lab = np.empty(Q, np.int32); dist = np.empty(Q)
+        self.lib.oracle_nn_brute_var(_p(train), _p(off, _i64), _p(labels, _i32), N, _p(test),
+                                     _p(toff, _i64), Q, int(W), _p(idx, _i32), _p(lab, _i32),
+                                     _p(dist), threads or default_threads())
+        return idx, lab, dist
+
+    def nn_pruned_var(self, train, off, labels, test, toff, W, V, env=None, threads=None):
+        """Returns (idx, label, dist, stats), stats = (lb_pruned, abandoned, completed)."""
+        train, off = self._ragged(train, off)
+        test, toff = self._ragged(test, toff)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        N, Q = off.shape[0] - 1, toff.shape[0] - 1
+        U, Lo, eoff = env if env is not None else self.envelopes_var(train, off, W)
+        idx = np.empty(Q, np.int32); lab = np.empty(Q, np.int32); dist = np.empty(Q)
+        st = np.zeros(3, np.int64)
+        self.lib.oracle_nn_pruned_var(_p(train), _p(off, _i64), _p(labels, _i32),
+                                      _p(_f64(U)), _p(_f64(Lo)), _p(eoff, _i64), N, _p(test),
+                                      _p(toff, _i64), Q, int(W), int(V), _p(idx, _i32),
+                                      _p(lab, _i32), _p(dist), _p(st, _i64),
+                                      threads or default_threads())
         return idx, lab, dist, st
 
 

@@ -447,3 +447,291 @@ void oracle_nn_pruned(const double *train, const int32_t *labels, const double *
     }
     free(st);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Unequal lengths (Sec. 2: the equal-length exposition generalises).        */
+/*
+ * Reading: A has L_A points and B has L_B (both >= 2).  DTW is Eq. 1 on the
+ * L_A x L_B grid inside the window |i - j| <= W, ending at (L_A, L_B); when
+ * |L_A - L_B| > W no warping path fits the window and the distance is +inf.
+ * B's envelope is taken for the rows of A (i up to L_B + W); the bounds follow
+ * Eq. 7 with the end corner at (L_A, L_B) and n_bands = min(min(L_A, L_B)/2, V).
+ * With L_A = L_B every routine below computes what its equal-length
+ * counterpart above computes, in the same order.
+ */
+
+static int in_window(int i, int j, int W) { return i - j <= W && j - i <= W; }
+
+/* U_i, Lo_i = max, min of B_j over max(1, i-W) <= j <= min(LB, i+W), for
+ * i = 1..E (Eq. 3-4 for the rows of a series of up to E points); requires
+ * E <= LB + W, so that every window holds at least one point of B. */
+void oracle_envelope_var(const double *B, int LB, int W, int E, double *U, double *Lo) {
+    for (int i = 1; i <= E; i++) {
+        int jlo = imax(1, i - W), jhi = imin(LB, i + W);
+        double u = B[jlo - 1], l = B[jlo - 1];
+        for (int j = jlo; j <= jhi; j++) {
+            if (B[j - 1] > u) u = B[j - 1];
+            if (B[j - 1] < l) l = B[j - 1];
+        }
+        U[i - 1] = u;
+        Lo[i - 1] = l;
+    }
+}
+
+/* DTW_W(A, B) on the LA x LB grid (Eq. 1), row by row over the rows of A, with
+ * the same early abandoning as dtw_rows (every path crosses every row of A). */
+static double dtw_rows_var(const double *A, int LA, const double *B, int LB, int W,
+                           double cutoff, double *prev, double *cur) {
+    const double INF = INFINITY;
+    if (!in_window(LA, LB, W)) return INF;
+    prev[0] = 0.0;
+    for (int j = 1; j <= LB; j++) prev[j] = INF;
+    for (int i = 1; i <= LA; i++) {
+        int jlo = imax(1, i - W), jhi = imin(LB, i + W);
+        cur[jlo - 1] = INF;
+        double rowmin = INF;
+        for (int j = jlo; j <= jhi; j++) {
+            double m = dmin(dmin(prev[j - 1], cur[j - 1]), prev[j]);
+            double t = delta(A[i - 1], B[j - 1]);
+            cur[j] = t + m;
+            if (cur[j] < rowmin) rowmin = cur[j];
+        }
+        if (jhi + 1 <= LB) cur[jhi + 1] = INF;
+        if (rowmin > cutoff) return INF;
+        double *tmp = prev; prev = cur; cur = tmp;
+    }
+    return prev[LB];
+}
+
+double oracle_dtw_var(const double *A, int LA, const double *B, int LB, int W, double cutoff) {
+    double *buf = (double *)malloc(sizeof(double) * 2 * (size_t)(LB + 1));
+    double r = dtw_rows_var(A, LA, B, LB, W, cutoff, buf, buf + (LB + 1));
+    free(buf);
+    return r;
+}
+
+/* LB_Keogh over the LA rows of A against B's envelope (U, Lo) for those rows;
+ * +inf when |LA - LB| > W (no path). */
+double oracle_lb_keogh_var(const double *A, int LA, int LB, const double *U,
+                           const double *Lo, int W) {
+    if (!in_window(LA, LB, W)) return INFINITY;
+    return oracle_lb_keogh(A, U, Lo, LA);
+}
+
+/* LB_Enhanced^V_W(A, B) for LA != LB: Algorithm 1's steps with the right bands
+ * anchored at the end corner (LA, LB) and every band cell kept only inside
+ * the window; the bridge is LB_Keogh over rows n_bands+1 .. LA-n_bands.  D as
+ * in oracle_lb_enhanced; +inf when |LA - LB| > W. */
+double oracle_lb_enhanced_var(const double *A, int LA, const double *B, int LB,
+                              const double *U, const double *Lo, int W, int V, double D) {
+    if (!in_window(LA, LB, W)) return INFINITY;
+#define a(i) A[(i) - 1]
+#define b(j) B[(j) - 1]
+    double res = delta(a(1), b(1)) + delta(a(LA), b(LB));
+    int n_bands = imin(imin(LA, LB) / 2, V);
+    for (int i = 2; i <= n_bands; i++) {
+        double minL = delta(a(i), b(i));
+        double minR = delta(a(LA - i + 1), b(LB - i + 1));
+        for (int j = 1; j <= i - 1; j++) {
+            if (in_window(i, j, W)) {
+                minL = dmin(minL, delta(a(i), b(j)));
+                minL = dmin(minL, delta(a(j), b(i)));
+            }
+            if (in_window(LA - i + 1, LB - j + 1, W))
+                minR = dmin(minR, delta(a(LA - i + 1), b(LB - j + 1)));
+            if (in_window(LA - j + 1, LB - i + 1, W))
+                minR = dmin(minR, delta(a(LA - j + 1), b(LB - i + 1)));
+        }
+        res = res + minL + minR;
+    }
+    if (res >= D) return INFINITY;
+    for (int i = n_bands + 1; i <= LA - n_bands; i++) {
+        if (a(i) > U[i - 1]) res = res + delta(a(i), U[i - 1]);
+        else if (a(i) < Lo[i - 1]) res = res + delta(a(i), Lo[i - 1]);
+    }
+    return res;
+#undef a
+#undef b
+}
+
+/* Ragged sets: series k is x[off[k] .. off[k+1]); envelope of training
+ * series t at env + eoff[t], eoff[t] = off[t] + t * W (L_t + W rows). */
+typedef struct {
+    const double *test, *train, *U, *Lo;
+    const int64_t *toff, *off, *eoff;
+    const int32_t *labels;
+    int64_t Q, N;
+    int W, V, kind;
+    int64_t lo, hi;
+    double *out;
+    int32_t *nn_idx, *nn_label;
+    double *nn_dist;
+    int64_t *stats;
+} vjob_t;
+
+#define VLEN(o, k) ((int)((o)[(k) + 1] - (o)[k]))
+
+static void *lb_matrix_var_worker(void *p) {
+    vjob_t *j = (vjob_t *)p;
+    for (int64_t f = j->lo; f < j->hi; f++) {
+        int64_t q = f / j->N, t = f % j->N;
+        const double *A = j->test + j->toff[q], *B = j->train + j->off[t];
+        int LA = VLEN(j->toff, q), LB = VLEN(j->off, t);
+        const double *U = j->U + j->eoff[t], *Lo = j->Lo + j->eoff[t];
+        j->out[f] = j->kind == 1 ? oracle_lb_keogh_var(A, LA, LB, U, Lo, j->W)
+                                 : oracle_lb_enhanced_var(A, LA, B, LB, U, Lo, j->W, j->V,
+                                                          INFINITY);
+    }
+    return NULL;
+}
+
+static void *dtw_matrix_var_worker(void *p) {
+    vjob_t *j = (vjob_t *)p;
+    for (int64_t f = j->lo; f < j->hi; f++) {
+        int64_t q = f / j->N, t = f % j->N;
+        j->out[f] = oracle_dtw_var(j->test + j->toff[q], VLEN(j->toff, q),
+                                   j->train + j->off[t], VLEN(j->off, t), j->W, INFINITY);
+    }
+    return NULL;
+}
+
+/* 1-NN by exhaustive DTW, ties to the lowest index; -1 (index and label)
+ * when no training series is within the window. */
+static void *nn_brute_var_worker(void *p) {
+    vjob_t *j = (vjob_t *)p;
+    for (int64_t q = j->lo; q < j->hi; q++) {
+        const double *A = j->test + j->toff[q];
+        int LA = VLEN(j->toff, q);
+        double best = INFINITY;
+        int64_t bi = -1;
+        for (int64_t t = 0; t < j->N; t++) {
+            double d = oracle_dtw_var(A, LA, j->train + j->off[t], VLEN(j->off, t), j->W,
+                                      INFINITY);
+            if (d < best) { best = d; bi = t; }
+        }
+        j->nn_idx[q] = (int32_t)bi;
+        j->nn_label[q] = bi < 0 ? -1 : j->labels[bi];
+        j->nn_dist[q] = best;
+    }
+    return NULL;
+}
+
+/* The lower-bound search (Sec. 4) for unequal lengths: candidates in ascending
+ * LB_Enhanced order (the Euclidean order is undefined), each bounded by
+ * Algorithm 1 against the current D and, if not pruned, its DTW computed with
+ * early abandoning; the same strict tests and tie rule as nn_pruned_worker. */
+static void *nn_pruned_var_worker(void *p) {
+    vjob_t *j = (vjob_t *)p;
+    keyed_t *ord = (keyed_t *)malloc(sizeof(keyed_t) * (size_t)j->N);
+    int maxlb = 1;
+    for (int64_t t = 0; t < j->N; t++) maxlb = imax(maxlb, VLEN(j->off, t));
+    double *rows = (double *)malloc(sizeof(double) * 2 * (size_t)(maxlb + 1));
+    for (int64_t q = j->lo; q < j->hi; q++) {
+        const double *A = j->test + j->toff[q];
+        int LA = VLEN(j->toff, q);
+        for (int64_t t = 0; t < j->N; t++) {
+            ord[t].key = oracle_lb_enhanced_var(A, LA, j->train + j->off[t], VLEN(j->off, t),
+                                                j->U + j->eoff[t], j->Lo + j->eoff[t], j->W,
+                                                j->V, INFINITY);
+            ord[t].idx = t;
+        }
+        qsort(ord, (size_t)j->N, sizeof(keyed_t), keyed_cmp);
+        double D = INFINITY;
+        int64_t bi = -1;
+        for (int64_t r = 0; r < j->N; r++) {
+            int64_t t = ord[r].idx;
+            const double *B = j->train + j->off[t];
+            int LB = VLEN(j->off, t);
+            if (!in_window(LA, LB, j->W)) { j->stats[0]++; continue; }
+            double lb = oracle_lb_enhanced_var(A, LA, B, LB, j->U + j->eoff[t],
+                                               j->Lo + j->eoff[t], j->W, j->V,
+                                               nextafter(D, INFINITY));
+            if (lb > D) { j->stats[0]++; continue; }
+            double d = dtw_rows_var(A, LA, B, LB, j->W, D, rows, rows + (LB + 1));
+            if (isinf(d)) { j->stats[1]++; continue; }
+            j->stats[2]++;
+            if (d < D || (d == D && t < bi)) { D = d; bi = t; }
+        }
+        j->nn_idx[q] = (int32_t)bi;
+        j->nn_label[q] = bi < 0 ? -1 : j->labels[bi];
+        j->nn_dist[q] = D;
+    }
+    free(rows);
+    free(ord);
+    return NULL;
+}
+
+static void run_vthreads(void *(*fn)(void *), vjob_t *base, int64_t total, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((int64_t)nthreads > total) nthreads = (int)(total > 0 ? total : 1);
+    pthread_t th[256];
+    vjob_t jobs[256];
+    int64_t chunk = (total + nthreads - 1) / nthreads;
+    for (int k = 0; k < nthreads; k++) {
+        jobs[k] = *base;
+        jobs[k].lo = (int64_t)k * chunk;
+        jobs[k].hi = jobs[k].lo + chunk < total ? jobs[k].lo + chunk : total;
+        if (jobs[k].stats) jobs[k].stats = base->stats + 3 * k;
+        pthread_create(&th[k], NULL, fn, &jobs[k]);
+    }
+    for (int k = 0; k < nthreads; k++) pthread_join(th[k], NULL);
+}
+
+/* Envelopes of a ragged training set, L_t + W rows each at eoff[t]. */
+void oracle_envelopes_var(const double *train, const int64_t *off, int64_t N, int W,
+                          const int64_t *eoff, double *U, double *Lo) {
+    for (int64_t t = 0; t < N; t++)
+        oracle_envelope_var(train + off[t], VLEN(off, t), W, VLEN(off, t) + W,
+                            U + eoff[t], Lo + eoff[t]);
+}
+
+/* out[q*N + t] = LB(test_q, train_t): kind 0 = LB_Enhanced^V, 1 = LB_Keogh. */
+void oracle_lb_matrix_var(const double *test, const int64_t *toff, int64_t Q,
+                          const double *train, const int64_t *off, const double *U,
+                          const double *Lo, const int64_t *eoff, int64_t N, int W, int V,
+                          int kind, double *out, int nthreads) {
+    vjob_t b = {0};
+    b.test = test; b.toff = toff; b.Q = Q; b.train = train; b.off = off; b.U = U; b.Lo = Lo;
+    b.eoff = eoff; b.N = N; b.W = W; b.V = V; b.kind = kind; b.out = out;
+    run_vthreads(lb_matrix_var_worker, &b, Q * N, nthreads);
+}
+
+/* out[q*N + t] = DTW_W(test_q, train_t). */
+void oracle_dtw_matrix_var(const double *test, const int64_t *toff, int64_t Q,
+                           const double *train, const int64_t *off, int64_t N, int W,
+                           double *out, int nthreads) {
+    vjob_t b = {0};
+    b.test = test; b.toff = toff; b.Q = Q; b.train = train; b.off = off; b.N = N; b.W = W;
+    b.out = out;
+    run_vthreads(dtw_matrix_var_worker, &b, Q * N, nthreads);
+}
+
+void oracle_nn_brute_var(const double *train, const int64_t *off, const int32_t *labels,
+                         int64_t N, const double *test, const int64_t *toff, int64_t Q, int W,
+                         int32_t *nn_idx, int32_t *nn_label, double *nn_dist, int nthreads) {
+    vjob_t b = {0};
+    b.train = train; b.off = off; b.labels = labels; b.N = N; b.test = test; b.toff = toff;
+    b.Q = Q; b.W = W; b.nn_idx = nn_idx; b.nn_label = nn_label; b.nn_dist = nn_dist;
+    run_vthreads(nn_brute_var_worker, &b, Q, nthreads);
+}
+
+void oracle_nn_pruned_var(const double *train, const int64_t *off, const int32_t *labels,
+                          const double *U, const double *Lo, const int64_t *eoff, int64_t N,
+                          const double *test, const int64_t *toff, int64_t Q, int W, int V,
+                          int32_t *nn_idx, int32_t *nn_label, double *nn_dist,
+                          int64_t *stats3, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    int64_t *st = (int64_t *)calloc(3 * 256, sizeof(int64_t));
+    vjob_t b = {0};
+    b.train = train; b.off = off; b.labels = labels; b.U = U; b.Lo = Lo; b.eoff = eoff;
+    b.N = N; b.test = test; b.toff = toff; b.Q = Q; b.W = W; b.V = V;
+    b.nn_idx = nn_idx; b.nn_label = nn_label; b.nn_dist = nn_dist; b.stats = st;
+    run_vthreads(nn_pruned_var_worker, &b, Q, nthreads);
+    stats3[0] = stats3[1] = stats3[2] = 0;
+    for (int k = 0; k < 256; k++) {
+        stats3[0] += st[3 * k]; stats3[1] += st[3 * k + 1]; stats3[2] += st[3 * k + 2];
+    }
+    free(st);
+}

@@ -16,26 +16,15 @@ Indices here are 1-based as in the paper; arrays are 0-based.
 """
 from __future__ import annotations
 
+import functools
 import math
+
+import numpy as np
 
 
 def all_warping_paths(L: int, W: int):
-    """Yield every warping path (list of 1-based (i, j) links) inside the window."""
-    out = []
-
-    def rec(i, j, path):
-        if (i, j) == (L, L):
-            out.append(list(path))
-            return
-        for di, dj in ((1, 0), (0, 1), (1, 1)):
-            ni, nj = i + di, j + dj
-            if ni <= L and nj <= L and abs(ni - nj) <= W:
-                path.append((ni, nj))
-                rec(ni, nj, path)
-                path.pop()
-
-    rec(1, 1, [(1, 1)])
-    return out
+    """Every warping path (list of 1-based (i, j) links) inside the window."""
+    return all_warping_paths_var(L, L, W)
 
 
 def path_cost(a, b, path) -> float:
@@ -43,9 +32,36 @@ def path_cost(a, b, path) -> float:
     return math.fsum((float(a[i - 1]) - float(b[j - 1])) ** 2 for i, j in path)
 
 
+@functools.lru_cache(maxsize=None)
+def _incidence(LA: int, LB: int, W: int):
+    """Row k marks the cells of the k-th warping path of an LA x LB grid
+    (0/1 entries, cells in row-major order); None when no path fits."""
+    ps = all_warping_paths_var(LA, LB, W)
+    if not ps:
+        return None
+    M = np.zeros((len(ps), LA * LB))
+    for k, p in enumerate(ps):
+        for i, j in p:
+            M[k, (i - 1) * LB + (j - 1)] = 1.0
+    return M
+
+
+def _min_path_cost(a, b, W: int) -> float:
+    """Minimum over every warping path of the sum of its cells' deltas: all
+    path costs at once as the incidence matrix times the cell costs (each a
+    sum of at most LA + LB - 1 terms, exact for small integers)."""
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    M = _incidence(len(a), len(b), int(W))
+    if M is None:
+        return math.inf
+    cost = ((a[:, None] - b[None, :]) ** 2).ravel()
+    return float((M @ cost).min())
+
+
 def dtw_by_paths(a, b, W: int) -> float:
-    L = len(a)
-    return min(path_cost(a, b, p) for p in all_warping_paths(L, W))
+    assert len(a) == len(b)
+    return _min_path_cost(a, b, W)
 
 
 def left_band(i: int, L: int, W: int):
@@ -133,3 +149,87 @@ def full_right_band_bound(a, b, W: int) -> float:
     """Right-band analogue of Theorem 1."""
     L = len(a)
     return math.fsum(band_min(a, b, right_band(i, L, W)) for i in range(1, L + 1))
+
+
+# ------------------------------------------------------- unequal lengths ---
+# A has L_A points and B has L_B.  A warping path runs from (1, 1) to
+# (L_A, L_B) with the same three kinds of links, inside |i - j| <= W.
+
+def all_warping_paths_var(LA: int, LB: int, W: int):
+    out = []
+
+    def rec(i, j, path):
+        if (i, j) == (LA, LB):
+            out.append(list(path))
+            return
+        for di, dj in ((1, 0), (0, 1), (1, 1)):
+            ni, nj = i + di, j + dj
+            if ni <= LA and nj <= LB and abs(ni - nj) <= W:
+                path.append((ni, nj))
+                rec(ni, nj, path)
+                path.pop()
+
+    rec(1, 1, [(1, 1)])
+    return out
+
+
+def dtw_by_paths_var(a, b, W: int) -> float:
+    """Minimum path cost over every warping path of the L_A x L_B grid inside
+    the window; +inf when there is none."""
+    return _min_path_cost(a, b, W)
+
+
+def left_band_var(i: int, W: int):
+    """The start corner's L-shape of index i: (i, j) and (j, i), j <= i,
+    inside the window."""
+    return {c for j in range(1, i + 1) for c in ((i, j), (j, i)) if abs(c[0] - c[1]) <= W}
+
+
+def right_band_var(i: int, LA: int, LB: int, W: int):
+    """The end corner's L-shape of index i: (L_A-i+1, L_B-j+1) and
+    (L_A-j+1, L_B-i+1), j <= i, inside the window."""
+    cells = set()
+    for j in range(1, i + 1):
+        for c in ((LA - i + 1, LB - j + 1), (LA - j + 1, LB - i + 1)):
+            if abs(c[0] - c[1]) <= W:
+                cells.add(c)
+    return cells
+
+
+def keogh_term_var(a, b, i: int, W: int) -> float:
+    """Distance from A_i to the interval spanned by B over row i's window
+    max(1, i-W) .. min(L_B, i+W), window extremes by Python's max/min."""
+    window = [float(b[j - 1]) for j in range(max(1, i - W), min(len(b), i + W) + 1)]
+    lo, hi = min(window), max(window)
+    x = float(a[i - 1])
+    if x > hi:
+        return (x - hi) ** 2
+    if x < lo:
+        return (x - lo) ** 2
+    return 0.0
+
+
+def lb_enhanced_by_sets_var(a, b, W: int, V: int) -> float:
+    """LB_Enhanced^V for unequal lengths summed from explicit cell sets:
+    n_b start-corner bands, n_b end-corner bands, and the Keogh terms of
+    rows n_b+1 .. L_A-n_b; +inf when |L_A - L_B| > W."""
+    LA, LB = len(a), len(b)
+    if abs(LA - LB) > W:
+        return math.inf
+    nb = min(min(LA, LB) // 2, V)
+    terms = [band_min(a, b, left_band_var(i, W)) for i in range(1, nb + 1)]
+    terms += [band_min(a, b, right_band_var(i, LA, LB, W)) for i in range(1, nb + 1)]
+    terms += [keogh_term_var(a, b, i, W) for i in range(nb + 1, LA - nb + 1)]
+    return math.fsum(terms)
+
+
+def theorem2_intermediate_var(a, b, W: int, V: int) -> float:
+    """The bands as above with the minimum over each bridge row's whole
+    window instead of its Keogh term: between the bound and DTW."""
+    LA, LB = len(a), len(b)
+    nb = min(min(LA, LB) // 2, V)
+    terms = [band_min(a, b, left_band_var(i, W)) for i in range(1, nb + 1)]
+    terms += [band_min(a, b, right_band_var(i, LA, LB, W)) for i in range(1, nb + 1)]
+    terms += [band_min(a, b, {(i, j) for j in range(max(1, i - W), min(LB, i + W) + 1)})
+              for i in range(nb + 1, LA - nb + 1)]
+    return math.fsum(terms)

@@ -31,6 +31,12 @@ batched    64 datasets; L log-uniform in [24, 2048], train size log-uniform in
 serving    16 resident training sets; L cycles through {128, 512, 1500}; size
            log-uniform in [1000, 20000]; W = round(0.1 L), V=5, 8 classes as in
            ``tiny``; queries are drawn one at a time (split "serve").
+varlen     series of unequal lengths (ragged sets): train 8,000, test 2,000,
+           each series' length uniform in [L0 - dL, L0 + dL] (L0 = 512,
+           dL = 64), W = round(0.2 L0) = 102, V=5, float32; 8 classes, class c
+           a sinusoid of period (own length)/(2 + c) (the class pattern
+           stretched to the series' length), amplitude 1.5, random phase,
+           added to the series' own z-normalised walk.
 =========  ==================================================================
 """
 from __future__ import annotations
@@ -41,7 +47,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SEED_ROOT = 1808096170
-WORKLOADS = {"tiny": 0, "pairs": 1, "precision": 2, "batched": 3, "serving": 4}
+WORKLOADS = {"tiny": 0, "pairs": 1, "precision": 2, "batched": 3, "serving": 4, "varlen": 5}
 SPLITS = {"train": 0, "test": 1, "meta": 2, "serve": 3, "class": 4}
 
 
@@ -274,3 +280,59 @@ def random_series(seed: int, n: int, L: int, dtype=np.float32) -> np.ndarray:
     ss = np.random.SeedSequence([SEED_ROOT, 99, seed, 0])
     rng = np.random.Generator(np.random.PCG64(ss))
     return znormed_walks(rng, n, L).astype(dtype)
+
+
+@dataclass
+class RaggedDataset:
+    """A dataset whose series have unequal lengths: lists of 1-D arrays."""
+    name: str
+    train: list
+    train_labels: np.ndarray
+    test: list
+    test_labels: np.ndarray
+    W: int
+    V: int
+    n_classes: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return len(self.train)
+
+    @property
+    def Q(self) -> int:
+        return len(self.test)
+
+    @property
+    def max_len(self) -> int:
+        return max(max(len(x) for x in self.train), max(len(x) for x in self.test))
+
+    @staticmethod
+    def pack(series):
+        """(values, offsets): series k is values[offsets[k]:offsets[k+1]]."""
+        off = np.zeros(len(series) + 1, np.int64)
+        off[1:] = np.cumsum([len(x) for x in series])
+        return np.concatenate(series).astype(np.float32), off
+
+
+def make_varlen(n_train: int = 8000, n_test: int = 2000, L0: int = 512, dL: int = 64,
+                W_ratio: float = 0.2, V: int = 5, n_classes: int = 8,
+                dataset: int = 0) -> RaggedDataset:
+    parts = []
+    for split, n in (("train", n_train), ("test", n_test)):
+        rng = rng_for("varlen", dataset, split)
+        labels = rng.integers(0, n_classes, size=n).astype(np.int32)
+        lengths = rng.integers(L0 - dL, L0 + dL + 1, size=n)
+        phase = rng.uniform(0, 2 * np.pi, size=n)
+        xs = []
+        for k in range(n):
+            m = int(lengths[k])
+            x = znormed_walks(rng, 1, m)[0]
+            x += _sinusoid(m, m / (2.0 + labels[k]), phase[k:k + 1])[0]
+            xs.append(x.astype(np.float32))
+        parts.append((xs, labels))
+    (tr, trl), (te, tel) = parts
+    W = window_from_ratio(W_ratio, L0)
+    return RaggedDataset(f"varlen_{dataset}", tr, trl, te, tel, W=W, V=V, n_classes=n_classes,
+                         extra=dict(L0=L0, dL=dL))
+

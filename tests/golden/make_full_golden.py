@@ -9,6 +9,7 @@ generator for its inputs.  Run from the repository root:
     python tests/golden/make_full_golden.py batched     # 64 datasets, 35,843 queries
     python tests/golden/make_full_golden.py serving     # 16 resident sets, 24 queries each
     python tests/golden/make_full_golden.py large       # Q x N above 2^31, 24 sampled queries
+    python tests/golden/make_full_golden.py varlen      # unequal lengths, 2,000 queries
 
 Each file is gzip-compressed text, one query per line:
 ``[dataset] query nn_index nn_label nn_dist(hex float)``.
@@ -53,6 +54,7 @@ def large_inputs():
 
 
 SERVING_PATH = os.path.join(HERE, "serving_nn.txt.gz")
+VARLEN_PATH = os.path.join(HERE, "varlen_nn.txt.gz")
 
 
 def _write(path, header, rows):
@@ -139,6 +141,25 @@ def make_large(threads=None):
     print(f"large: {LARGE_SAMPLE} queries in {time.time() - t0:.0f} s", flush=True)
 
 
+def make_varlen(threads=None):
+    orc = oracle.get()
+    ds = synth.make_varlen()
+    tv, to = ds.pack(ds.train)
+    qv, qo = ds.pack(ds.test)
+    t0 = time.time()
+    idx, lab, dist, _ = orc.nn_pruned_var(tv, to, ds.train_labels, qv, qo, ds.W, ds.V,
+                                          threads=threads)
+    _write(VARLEN_PATH,
+           [f"1-NN of every query of the unequal-length workload ({ds.N} x {ds.Q}, lengths "
+            f"{ds.extra['L0'] - ds.extra['dL']}..{ds.extra['L0'] + ds.extra['dL']}, W={ds.W}, "
+            f"V={ds.V}), FP64 oracle (pruned search, ties to the lowest index; -1 without a "
+            "warping path)",
+            "written by tests/golden/make_full_golden.py",
+            "query nn_index nn_label nn_dist(hex float)"],
+           _rows([], idx, lab, dist))
+    print(f"varlen: {ds.Q} queries in {time.time() - t0:.0f} s", flush=True)
+
+
 def read(path):
     """Rows of a stored file as lists of ints, the distance as a float."""
     out = []
@@ -156,4 +177,4 @@ if __name__ == "__main__":
     th = int(os.environ.get("ORACLE_THREADS", "0")) or None
     for w in what:
         {"precision": make_precision, "batched": make_batched, "serving": make_serving,
-         "large": make_large}[w](th)
+         "large": make_large, "varlen": make_varlen}[w](th)

@@ -476,6 +476,205 @@ def pin_nn_loo_equals_removal(orc):
         assert c[k] == int((orc.nn_loo(tr, lab, W)[1] == lab).sum())
 
 
+# -------------------------------------------------------- unequal lengths ---
+
+def _lengths(rng, lo, hi):
+    return int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1))
+
+
+def pin_dtw_var_equals_min_over_all_paths(orc, max_L=6):
+    """DTW_W on an L_A x L_B grid is the minimum cost over every warping path
+    from (1, 1) to (L_A, L_B) inside the window, +inf when none fits."""
+    rng = _rng(31)
+    for LA in range(1, max_L + 1):
+        for LB in range(1, max_L + 1):
+            for W in range(0, max(LA, LB) + 1):
+                a, b = _series(rng, LA), _series(rng, LB)
+                exact = paths.dtw_by_paths_var(a, b, W)
+                got = orc.dtw_var(a, b, W)
+                if math.isinf(exact):
+                    assert math.isinf(got) and abs(LA - LB) > W, (LA, LB, W, got)
+                else:
+                    assert _rel_close(got, exact, 1e-12), (LA, LB, W, got, exact)
+
+
+def pin_dtw_var_symmetric_and_reduces(orc, trials=30):
+    """DTW_W(A, B) = DTW_W(B, A) bit for bit; with equal lengths it is the
+    equal-length DTW; it is +inf exactly when |L_A - L_B| > W; every W at or
+    above max(L_A, L_B) - 1 gives the same value; early abandoning only ever
+    answers +inf above the cutoff."""
+    rng = _rng(32)
+    for _ in range(trials):
+        LA, LB = _lengths(rng, 2, 40)
+        a, b = _series(rng, LA), _series(rng, LB)
+        for W in (0, abs(LA - LB), abs(LA - LB) + 3, max(LA, LB) - 1, 2 * max(LA, LB)):
+            d = orc.dtw_var(a, b, W)
+            assert orc.dtw_var(b, a, W) == d
+            assert math.isinf(d) == (abs(LA - LB) > W)
+            if not math.isinf(d):
+                assert orc.dtw_var(a, b, W, cutoff=d) == d
+                r = orc.dtw_var(a, b, W, cutoff=d * 0.5)
+                assert r == d or math.isinf(r)
+                # a cutoff below the first row's smallest cell abandons at once
+                assert math.isinf(orc.dtw_var(a, b, W, cutoff=-1.0))
+        assert orc.dtw_var(a, b, max(LA, LB) - 1) == orc.dtw_var(a, b, 10 * max(LA, LB))
+        c = _series(rng, LA)
+        for W in (0, 3, LA):
+            assert orc.dtw_var(a, c, W) == orc.dtw(a, c, W)
+
+
+def pin_envelope_var(orc, trials=30):
+    """B's envelope for the rows of a longer or shorter series: rows up to
+    L_B are scipy's sliding max / min, rows beyond L_B the max / min of B's
+    tail from i-W on."""
+    rng = _rng(33)
+    for _ in range(trials):
+        LB = int(rng.integers(1, 90))
+        W = int(rng.integers(0, LB + 3))
+        b = _series(rng, LB)
+        U, Lo = orc.envelope_var(b, W)
+        assert U.shape[0] == LB + W
+        size = 2 * W + 1
+        np.testing.assert_array_equal(U[:LB], maximum_filter1d(b, size=size, mode="nearest"))
+        np.testing.assert_array_equal(Lo[:LB], minimum_filter1d(b, size=size, mode="nearest"))
+        for i in range(LB + 1, LB + W + 1):
+            tail = b[max(1, i - W) - 1:]
+            assert U[i - 1] == tail.max() and Lo[i - 1] == tail.min(), (LB, W, i)
+        U0, Lo0 = orc.envelope(b, W)
+        np.testing.assert_array_equal(orc.envelope_var(b, W, E=LB)[0], U0)
+        np.testing.assert_array_equal(orc.envelope_var(b, W, E=LB)[1], Lo0)
+
+
+def pin_lb_enhanced_var_matches_band_sets(orc, max_L=10):
+    """LB_Enhanced^V for unequal lengths equals its sum from explicit cell
+    sets (start- and end-corner L-shapes inside the window, Keogh terms of
+    the bridge rows), and is +inf with no path."""
+    rng = _rng(34)
+    for LA in range(2, max_L + 1):
+        for LB in range(2, max_L + 1):
+            for W in range(0, max(LA, LB) + 1):
+                for V in (1, 2, 3, 5):
+                    a, b = _series(rng, LA), _series(rng, LB)
+                    got = orc.lb_enhanced_var(a, b, W, V)
+                    exact = paths.lb_enhanced_by_sets_var(a, b, W, V)
+                    if math.isinf(exact):
+                        assert math.isinf(got), (LA, LB, W, V, got)
+                    else:
+                        assert _rel_close(got, exact, 1e-12), (LA, LB, W, V, got, exact)
+
+
+def pin_lb_var_bounds_dtw(orc, trials=80):
+    """The unequal-length bounds stay below DTW: LB_Enhanced^V <= the proof's
+    intermediate sum (row minima over whole windows) <= DTW_W, checked by
+    path enumeration on small grids and by the oracle's DTW on longer ones;
+    LB_Keogh <= DTW_W; LB_Enhanced^1 >= LB_Keogh; Algorithm 1's abandon."""
+    rng = _rng(35)
+    for k in range(trials):
+        small = k % 2 == 0
+        LA, LB = _lengths(rng, 2, 7) if small else _lengths(rng, 8, 120)
+        W = int(rng.integers(abs(LA - LB), max(LA, LB) + 1))
+        V = int(rng.integers(1, min(LA, LB) // 2 + 2))
+        a, b = _series(rng, LA), _series(rng, LB)
+        d = paths.dtw_by_paths_var(a, b, W) if small else orc.dtw_var(a, b, W)
+        tol = 1 + 1e-12
+        lbe = orc.lb_enhanced_var(a, b, W, V)
+        mid = paths.theorem2_intermediate_var(a, b, W, V)
+        assert lbe <= mid * tol and mid <= d * tol, (LA, LB, W, V, lbe, mid, d)
+        lbk = orc.lb_keogh_var(a, b, W)
+        assert lbk <= d * tol
+        assert orc.lb_enhanced_var(a, b, W, 1) >= lbk * (1 - 1e-12)
+        assert math.isinf(orc.lb_enhanced_var(a, b, W, V, D=0.0))
+        assert orc.lb_enhanced_var(a, b, W, V, D=lbe * 2 + 1) == lbe
+    a, b = _series(rng, 10), _series(rng, 4)
+    assert math.isinf(orc.lb_enhanced_var(a, b, 5, 2)) and math.isinf(orc.lb_keogh_var(a, b, 5))
+
+
+def pin_lb_var_reduces_to_equal_length(orc, trials=30):
+    """With L_A = L_B the unequal-length bounds are the equal-length ones,
+    bit for bit."""
+    rng = _rng(36)
+    for _ in range(trials):
+        L = int(rng.integers(2, 60))
+        W = int(rng.integers(0, L + 2))
+        V = int(rng.integers(1, L // 2 + 2))
+        a, b = _series(rng, L), _series(rng, L)
+        U, Lo = orc.envelope(b, W)
+        assert orc.lb_enhanced_var(a, b, W, V) == orc.lb_enhanced(a, b, U, Lo, W, V)
+        assert orc.lb_keogh_var(a, b, W) == orc.lb_keogh(a, U, Lo)
+
+
+def _ragged_set(rng, n, lo, hi, dup_of=None):
+    lens = rng.integers(lo, hi + 1, n)
+    xs = [rng.standard_normal(int(m)).cumsum() for m in lens]
+    return xs
+
+
+def _pack(xs):
+    off = np.zeros(len(xs) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in xs])
+    return np.concatenate(xs), off
+
+
+def pin_nn_var(orc):
+    """1-NN over ragged sets: the brute force equals the argmin of the
+    path-enumeration DTW on tiny series (index -1 and label -1 when no
+    series fits the window), the lower-bound search equals the brute force
+    (ties to the lowest index, duplicates included), and the matrix drivers
+    equal the single-pair routines."""
+    rng = _rng(37)
+    tr = _ragged_set(rng, 8, 2, 6)
+    te = _ragged_set(rng, 5, 2, 6)
+    labels = rng.integers(0, 3, len(tr)).astype(np.int32)
+    trv, tro = _pack(tr)
+    tev, teo = _pack(te)
+    for W in (0, 1, 2, 5):
+        idx, lab, dist = orc.nn_brute_var(trv, tro, labels, tev, teo, W)
+        for q in range(len(te)):
+            ds = [paths.dtw_by_paths_var(te[q], tr[t], W) for t in range(len(tr))]
+            if all(math.isinf(x) for x in ds):
+                assert idx[q] == -1 and lab[q] == -1 and math.isinf(dist[q])
+            else:
+                best = int(np.argmin(ds))
+                assert idx[q] == best and lab[q] == labels[best]
+                assert _rel_close(dist[q], ds[best], 1e-12)
+    assert (orc.nn_brute_var(trv, tro, labels, tev, teo, 0)[0] == -1).any()
+    tr = _ragged_set(rng, 50, 20, 40)
+    tr += [x.copy() for x in tr[:10]]                  # duplicates at higher indices
+    te = _ragged_set(rng, 12, 18, 44)
+    labels = rng.integers(0, 4, len(tr)).astype(np.int32)
+    trv, tro = _pack(tr)
+    tev, teo = _pack(te)
+    for W in (0, 3, 12, 50):
+        bi, bl, bd = orc.nn_brute_var(trv, tro, labels, tev, teo, W)
+        for V in (1, 2, 5):
+            pi, pl, pd, _ = orc.nn_pruned_var(trv, tro, labels, tev, teo, W, V)
+            np.testing.assert_array_equal(bi, pi)
+            np.testing.assert_array_equal(bl, pl)
+            np.testing.assert_array_equal(bd, pd)
+        assert np.all(bi < 50)
+        dm = orc.dtw_matrix_var(tev, teo, trv, tro, W)
+        lm = orc.lb_matrix_var(tev, teo, trv, tro, W, 3)
+        km = orc.lb_matrix_var(tev, teo, trv, tro, W, 3, kind="keogh")
+        for q in (0, 5, 11):
+            for t in (0, 17, 59):
+                assert dm[q, t] == orc.dtw_var(te[q], tr[t], W)
+                assert lm[q, t] == orc.lb_enhanced_var(te[q], tr[t], W, 3)
+                assert km[q, t] == orc.lb_keogh_var(te[q], tr[t], W)
+    # integer-valued series: exact distance ties are common, and the search
+    # meets them in bound order, not index order
+    tr = [rng.integers(0, 3, int(m)).astype(float) for m in rng.integers(3, 7, 60)]
+    te = [rng.integers(0, 3, int(m)).astype(float) for m in rng.integers(3, 7, 30)]
+    labels = np.arange(len(tr), dtype=np.int32)
+    trv, tro = _pack(tr)
+    tev, teo = _pack(te)
+    for W in (1, 2, 4):
+        bi, _, bd = orc.nn_brute_var(trv, tro, labels, tev, teo, W)
+        for V in (1, 2):
+            pi, _, pd, _ = orc.nn_pruned_var(trv, tro, labels, tev, teo, W, V)
+            np.testing.assert_array_equal(bi, pi)
+            np.testing.assert_array_equal(bd, pd)
+
+
 ALL_PINS = [
     pin_dtw_w0_is_squared_euclidean,
     pin_dtw_equals_min_over_all_paths,
@@ -497,4 +696,11 @@ ALL_PINS = [
     pin_nn_w0_is_euclidean_nn,
     pin_nn_pruned_equals_brute,
     pin_nn_loo_equals_removal,
+    pin_dtw_var_equals_min_over_all_paths,
+    pin_dtw_var_symmetric_and_reduces,
+    pin_envelope_var,
+    pin_lb_enhanced_var_matches_band_sets,
+    pin_lb_var_bounds_dtw,
+    pin_lb_var_reduces_to_equal_length,
+    pin_nn_var,
 ]
