@@ -2,7 +2,7 @@
 """Benchmark of the exact NN-DTW search with LB_Enhanced^V pruning.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload batched|pairs|tiny|precision-R|serving]
+                    [--workload batched|pairs|tiny|precision-R|serving|window|vsweep|varlen]
 
 Default workload ("batched"): 64 seeded synthetic datasets of uneven shape
 (L log-uniform in [24, 2048], train size log-uniform in [16, 8000], test size
@@ -536,6 +536,126 @@ def run_window(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ unequal lengths
+
+def run_varlen(args):
+    """Series of unequal lengths (Sec. 2 generalised): one
+    ``nn_dtw_search_varlen`` per step over the ragged workload (train 8,000 x
+    test 2,000, lengths 448..576, W = 102, V = 5), stage events inside every
+    timed step; e2e through the host-buffer entry point."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw, synth
+    ds = synth.make_varlen()
+    dev = torch.device("cuda", 0)
+    nndtw.load()
+    tv, to = ds.pack(ds.train)
+    qv, qo = ds.pack(ds.test)
+    train = nndtw.Ragged(torch.from_numpy(tv).to(dev), torch.from_numpy(to).to(dev), ds.max_len)
+    test = nndtw.Ragged(torch.from_numpy(qv).to(dev), torch.from_numpy(qo).to(dev), ds.max_len)
+    labels = torch.from_numpy(ds.train_labels).to(dev)
+    N, Q, ml = ds.N, ds.Q, ds.max_len
+    ws = torch.empty(nndtw.nn_dtw_varlen_workspace_size(N, Q, ml, ds.W, ds.V), dtype=torch.uint8,
+                     device=dev)
+    outs = (torch.empty(Q, dtype=torch.int32, device=dev),
+            torch.empty(Q, dtype=torch.int32, device=dev),
+            torch.empty(Q, dtype=torch.float64, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    run = lambda flags=nndtw.TIME_STAGES, stats=False: nndtw.nn_dtw_search_varlen(
+        train, labels, test, ds.W, ds.V, flags=flags, workspace=ws, out=outs, stats=stats)
+    counted = run(flags=0, stats=True).stats          # work counters (slower: not timed)
+    for _ in range(args.warmup):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    launches = nndtw.nn_dtw_last_call_launches()
+    stage_launches = nndtw.nn_dtw_last_call_stage_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stages = []
+    sel = device_selector(torch, dev, 0)
+    with ClockSampler(sel) as clk:
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            run()
+            b.record(stream)
+            stages.append(nndtw.nn_dtw_stage_times())
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    clocks = clk.summary()
+    stage_ms = {k: sum(d[k] for d in stages) / len(stages) for k in STAGES}
+    idx = outs[0].cpu().numpy()
+    # e2e: the host-buffer C-ABI call, copies of the ragged sets in and the
+    # results out inside the timed region (pinned host arrays)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    hs = nndtw.VarlenHostSearch(pin(tv), pin(to), pin(ds.train_labels), pin(qv), pin(qo), ds.W,
+                                ds.V, ml, device=dev)
+    for _ in range(2):
+        hs()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hidx, _, _ = hs()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
+    h2d, d2h = hs.bytes_per_call()
+    # roofline of the DTW stage against the derived FP32 cell peak
+    peaks, peak_src = read_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0))
+    probe = nndtw.nn_dtw_probe_cell_rate(20000)
+    cells = counted["dtw_cells"]
+    dtw_ms = stage_ms["seed"] + stage_ms["dtw"]
+    achieved = cells / (dtw_ms * 1e-3) / 1e9
+    peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / INSTR_PER_CELL / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s",
+            "frac": achieved / peak, "kernel": "dtw (first candidates and survivors)",
+            "peak_basis": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                          f"{sm_max:.0f} MHz / {INSTR_PER_CELL} instructions per cell",
+            "probe_measured": probe / 1e9, "frac_of_probe": achieved / (probe / 1e9),
+            "launches_per_step": stage_launches["seed"] + stage_launches["dtw"],
+            "share_of_step": dtw_ms / stage_ms["total"] if stage_ms["total"] else None,
+            "traffic": None,
+            "stage_timing": "CUDA events between the search's stages in every timed step"}
+    line = {"metric": "unequal lengths: exact NN-DTW queries/s on 1 GB300 (FP32 with FP64 "
+                      "recheck)",
+            "value": Q / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"unequal lengths: train {N} x test {Q}, lengths "
+                                   f"{ds.extra['L0'] - ds.extra['dL']}..{ds.extra['L0'] + ds.extra['dL']}, "
+                                   f"W={ds.W}, V={ds.V}, float32",
+                       "l2": "flushed before every step (256 MiB write, outside the events)"},
+            "roofline": roof, "stage_ms": stage_ms,
+            "pruning": {k: counted[k] for k in ("pairs", "lb_pruned", "dtw_started",
+                                                "dtw_abandoned", "dtw_cells", "rechecked")},
+            "no_neighbour_queries": int((idx < 0).sum()),
+            "e2e": {"value": Q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+                    "results_equal_device_step": bool(np.array_equal(hidx, idx))},
+            "gpu_launches": launches * args.steps, "gpu_launches_per_step_by_stage": stage_launches,
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        orc = oracle.get()
+        env = orc.envelopes_var(tv, to, ds.W)
+        n = 256
+        t0 = time.perf_counter()
+        sv, so = ds.pack(ds.test[:n])
+        orc.nn_pruned_var(tv, to, ds.train_labels, sv, so, ds.W, ds.V, env=env)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": oracle.default_threads(),
+                                "kind": "oracle",
+                                "sample": f"first {n} queries against all {N} training series, "
+                                          f"lower-bound search in FP64 (envelopes precomputed), "
+                                          f"{dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 def run_serving(args):
@@ -647,6 +767,10 @@ def main():
     if args.workload == "vsweep":
         if rank == 0:
             run_vsweep(args)
+        return
+    if args.workload == "varlen":
+        if rank == 0:
+            run_varlen(args)
         return
     if args.workload == "batched":
         dsets, desc = batched_workload()

@@ -8,7 +8,8 @@
  * ---------------------------------------
  *  - Series are row-major, contiguous: a set of N series of length L is N*L
  *    elements, series t starting at element t*L.  All series of one call have
- *    the same length L (Sec. 2 assumes equal lengths).
+ *    the same length L (Sec. 2 assumes equal lengths), except in the *_varlen
+ *    entry points, which take ragged sets (series of unequal lengths).
  *  - delta(a, b) = (a - b)^2 and every distance and bound is in squared units:
  *    the square root of Eq. 2 is never taken (it does not change the nearest
  *    neighbour).
@@ -143,6 +144,9 @@ typedef struct nndtw_stats {
     int64_t lb_pruned_improved;/* survivors dropped by the bound with the
                                   LB_Improved bridge (NNDTW_IMPROVED) then;
                                   a pair both drop counts here only           */
+    int64_t lb_pruned_live; /* survivors dropped unstarted when their DTW was
+                               due: their bound exceeded the query's best by
+                               then (FP32 DTW kernels with live pruning)     */
 } nndtw_stats;
 
 /*
@@ -266,6 +270,10 @@ NNDTW_API size_t nn_dtw_workspace_size(int64_t N, int64_t Q, int L, int W, int V
  * margin of the best; d_nn_dist is FP64-exact for those queries (and for all
  * with NNDTW_EXACT_DIST), otherwise the FP32 value.  The FP64 entry point
  * computes everything in FP64 and its distances are exact.
+ * In the FP32 form the DTW kernels also drop, unstarted, a queued pair whose
+ * bound exceeds its query's best by the time the pair is due (the pruning
+ * test against a best the earlier pairs have tightened; not with
+ * NNDTW_NO_PRUNE).
  * d_env may be NULL (envelopes are then built into the workspace).
  * Q == 0 is a no-op.  d_workspace must hold nn_dtw_workspace_size() bytes
  * (NNDTW_ENOSPACE otherwise), 256-byte aligned.  stats may be NULL.
@@ -439,6 +447,116 @@ NNDTW_API int nn_dtw_search_batched_host(const nndtw_host_dataset *h_sets, int n
                                          size_t buffer_bytes, unsigned flags, void *stream);
 
 /*
+ * Series of UNEQUAL lengths within a dataset (Sec. 2: the paper assumes equal
+ * lengths for ease of exposition and states that the techniques generalise).
+ * A ragged set of n series is one value array d_x and an offset table d_off
+ * of n+1 int64 entries (device memory): series k is d_x[d_off[k] ..
+ * d_off[k+1]), of length L_k; d_off must be non-decreasing and address d_x.
+ * Every length must satisfy 2 <= L_k <= max_len <= NNDTW_MAX_L; max_len only
+ * bounds the lengths (and sizes the scratch), it need not be attained.  The
+ * reading of the method for A (length L_A) and B (length L_B):
+ *  - DTW_W(A, B) is Eq. 1 on the L_A x L_B grid inside |i - j| <= W, ending
+ *    at (L_A, L_B); when |L_A - L_B| > W no warping path fits the window and
+ *    the distance is +inf.  W >= max_len - 1 is treated as max_len - 1.
+ *  - B's envelope (Eq. 3-4) is taken for the rows i of A: U_i, Lo_i = max,
+ *    min of B_j over max(1, i-W) <= j <= min(L_B, i+W), i <= L_B + W.
+ *  - LB_Keogh sums over the rows of A.  LB_Enhanced^V uses
+ *    n = min(floor(min(L_A, L_B)/2), V) bands at each corner: at the start,
+ *    band i = the cells (i, j), (j, i), j <= i, inside the window; at the
+ *    end, band i = the cells (L_A-i+1, L_B-j+1), (L_A-j+1, L_B-i+1), j <= i,
+ *    inside the window; the LB_Keogh bridge covers rows n+1 .. L_A-n.  Both
+ *    are +inf when |L_A - L_B| > W.
+ *  - The search's first candidate for a query is the series with the
+ *    smallest bound (the Euclidean distance needs equal lengths).  A query
+ *    with no training series inside the window gets index -1, label -1 and
+ *    distance +inf.
+ * With all lengths equal every result equals that of the equal-length entry
+ * point.  A length outside [2, max_len] makes its series match nothing (the
+ * search reports it with NNDTW_CHECK_FINITE, see below).
+ */
+
+/* Envelopes of a ragged training set: d_env ([N][max_len][2], row stride
+ * max_len) gets (U_i, Lo_i) of series t for its rows i < min(L_t + W,
+ * max_len); other rows are not written.  Errors: NNDTW_EINVAL for null
+ * pointers, N < 0, max_len outside [2, NNDTW_MAX_L], W < 0. */
+NNDTW_API int nn_dtw_build_envelopes_varlen(const float *d_train, const int64_t *d_train_off,
+                                            int64_t N, int max_len, int W, float *d_env,
+                                            void *stream);
+
+/* LB_Enhanced^V (or, with NNDTW_LB_KEOGH, LB_Keogh) of every query of a
+ * ragged test set against every series of a ragged training set, unequal
+ * lengths allowed (reading above): d_lb_out [Q][N]; NNDTW_LB_SAFE scales
+ * each finite value down by the FP32 rounding margin.  d_env from
+ * nn_dtw_build_envelopes_varlen with the same W and max_len.  Errors:
+ * NNDTW_EINVAL for null pointers, Q < 0, N < 0, max_len outside
+ * [2, NNDTW_MAX_L], W < 0, V < 1, other flags. */
+NNDTW_API int lb_enhanced_varlen(const float *d_test, const int64_t *d_test_off, int64_t Q,
+                                 const float *d_train, const int64_t *d_train_off,
+                                 const float *d_env, int64_t N, int max_len, int W, int V,
+                                 unsigned flags, float *d_lb_out, void *stream);
+
+/* FP32 DTW_W of P explicit pairs (d_pairs [P][2] int32 (q, t)) of two ragged
+ * sets, unequal lengths allowed (+inf when |L_q - L_t| > W): d_out [P].
+ * Pair indices are not range-checked.  Errors: NNDTW_EINVAL for null
+ * pointers, P < 0, max_len outside [1, NNDTW_MAX_L], W < 0. */
+NNDTW_API int dtw_windowed_varlen(const float *d_test, const int64_t *d_test_off,
+                                  const float *d_train, const int64_t *d_train_off,
+                                  const int32_t *d_pairs, int64_t P, int max_len, int W,
+                                  float *d_out, void *stream);
+
+/* Bytes of device workspace nn_dtw_search_varlen needs.  0 on invalid sizes. */
+NNDTW_API size_t nn_dtw_varlen_workspace_size(int64_t N, int64_t Q, int max_len, int W, int V);
+
+/*
+ * nn_dtw_search for ragged training and test sets (unequal lengths, reading
+ * above): for every query q, d_nn_idx[q] = argmin_t DTW_W(test_q, train_t)
+ * with ties to the lowest t, d_nn_label[q] its label and d_nn_dist[q] that
+ * distance, as nn_dtw_search computes them (FP32 with rounding margins, an
+ * FP64 recheck of near ties, NNDTW_EXACT_DIST); -1, -1, +inf for a query with
+ * no training series inside the window.  The training envelopes are built
+ * into the workspace.  Flags: NNDTW_EXACT_DIST, NNDTW_NO_PRUNE,
+ * NNDTW_NO_ABANDON, NNDTW_KEOGH_BOUND, NNDTW_TIME_STAGES, NNDTW_DTW_GROUP;
+ * NNDTW_CHECK_FINITE also checks every value (NNDTW_ENONFINITE) and, after
+ * the search, every length (NNDTW_EINVAL if one lies outside [2, max_len]);
+ * it makes the call wait for the stream.  NNDTW_REVERSE, NNDTW_IMPROVED and
+ * NNDTW_LEAVE_ONE_OUT are rejected (NNDTW_EINVAL).  d_workspace:
+ * nn_dtw_varlen_workspace_size() bytes, 256-byte aligned.  Queries run in
+ * chunks of at most NNDTW_CHUNK_PAIRS pairs.  Q == 0 is a no-op.  Errors:
+ * NNDTW_EINVAL for null pointers, N < 1, Q < 0, max_len outside
+ * [2, NNDTW_MAX_L], W < 0, V < 1, N or Q >= 2^31; NNDTW_ENOSPACE;
+ * NNDTW_ECUDA.
+ */
+NNDTW_API int nn_dtw_search_varlen(const float *d_train, const int64_t *d_train_off,
+                                   const int32_t *d_train_labels, int64_t N, const float *d_test,
+                                   const int64_t *d_test_off, int64_t Q, int max_len, int W,
+                                   int V, unsigned flags, int32_t *d_nn_idx,
+                                   int32_t *d_nn_label, double *d_nn_dist, void *d_workspace,
+                                   size_t workspace_bytes, nndtw_stats *stats, void *stream);
+
+/* Bytes of device memory nn_dtw_search_varlen_host needs for these ragged
+ * sets (host offset tables of N+1 and Q+1 entries).  0 on invalid sizes or
+ * null tables. */
+NNDTW_API size_t nn_dtw_varlen_host_buffer_size(const int64_t *h_train_off, int64_t N,
+                                                const int64_t *h_test_off, int64_t Q,
+                                                int max_len, int W, int V);
+
+/*
+ * nn_dtw_search_varlen on HOST buffers: checks the offset tables on the host
+ * (offsets from 0, every length in [2, max_len]; NNDTW_EINVAL otherwise,
+ * before any copy), copies the values, offsets and labels to the caller's
+ * device buffer, runs the search, copies the results back and waits for the
+ * stream.  d_buffer: nn_dtw_varlen_host_buffer_size() bytes, 256-byte
+ * aligned.  Same results and errors as nn_dtw_search_varlen.
+ */
+NNDTW_API int nn_dtw_search_varlen_host(const float *h_train, const int64_t *h_train_off,
+                                        const int32_t *h_train_labels, int64_t N,
+                                        const float *h_test, const int64_t *h_test_off, int64_t Q,
+                                        int max_len, int W, int V, unsigned flags,
+                                        int32_t *h_nn_idx, int32_t *h_nn_label,
+                                        double *h_nn_dist, void *d_buffer, size_t buffer_bytes,
+                                        nndtw_stats *stats, void *stream);
+
+/*
  * Measurement aid, not part of the method.  A search called with
  * NNDTW_TIME_STAGES records CUDA events on its stream at every stage boundary
  * (events created once per thread and device; the call does not wait).  This
@@ -463,8 +581,9 @@ NNDTW_API int nn_dtw_probe_cell_rate(void *d_sink, size_t sink_bytes, int iters,
                                      double *h_cells_per_s, void *stream);
 
 /* Measurement aid, not part of the method: the number of kernel launches
- * that the calling thread's last FP32 search call (nn_dtw_search or
- * nn_dtw_search_batched, and the calls built on them) issued. */
+ * that the calling thread's last FP32 search call (nn_dtw_search,
+ * nn_dtw_search_batched or nn_dtw_search_varlen, and the calls built on
+ * them) issued. */
 NNDTW_API long long nn_dtw_last_call_launches(void);
 /* The same launches by stage: h_counts[k] (k < 7, NNDTW_STAGE_*) counts those
  * issued between stage boundaries k and k+1 (the start of the search counts

@@ -26,6 +26,13 @@
 // result after the sweep ends.  D(-1,-1) = 0 is seeded in the register of
 // diagonal W.
 //
+// Unequal lengths (VAR = true; Sec. 2 generalised): the pair's series come
+// from offset tables, query A of length L_A and training series B of length
+// L_B, and the sentinels above start at each series' own end.  The end cell
+// (L_A, L_B) lies on diagonal W + L_B - L_A; the cells after it on that
+// diagonal have both indices past the ends and inherit its value, and the
+// sweep ends once anti-diagonal L_A + L_B - 2 is behind it.
+//
 // Early abandoning: every path from (1,1) to (L,L) visits one of any two
 // consecutive anti-diagonals, and D never decreases along a path, so the
 // minimum of all current diagonal registers (which hold anti-diagonals t and
@@ -80,6 +87,19 @@ __device__ inline long long band_cells_upto(int L, int W, long long S) {
     return tot;
 }
 
+// Band cells (i, j) of an L_A x L_B grid with |i-j| <= W and i + j <= S
+// (work counters of the unequal-length form only), row by row.
+__device__ inline long long band_cells_var(int LA, int LB, int W, long long S) {
+    long long tot = 0;
+    for (int i = 0; i < LA; i++) {
+        const long long lo = i - W > 0 ? i - W : 0;
+        long long hi = i + W < LB - 1 ? i + W : LB - 1;
+        if (S - i < hi) hi = S - i;
+        if (hi >= lo) tot += hi - lo + 1;
+    }
+    return tot;
+}
+
 // Resident 128-thread blocks per SM requested from the register allocator for
 // each H (the diagonal registers, the two windows and the per-pair state need
 // about 4H + 2U + 50 registers); chosen from a compile sweep as the largest
@@ -88,7 +108,7 @@ __host__ __device__ constexpr int dtw32_min_blocks(int H) {
     return H <= 4 ? 8 : H <= 9 ? 6 : H <= 11 ? 5 : H <= 15 ? 4 : H <= 23 ? 3 : 2;
 }
 
-template <int H, int U, typename Src>
+template <int H, int U, typename Src, bool VAR = false>
 __global__ void __launch_bounds__(128, dtw32_min_blocks(H))
 dtw32_kernel(const __grid_constant__ Src src) {
     int bid, nblk;
@@ -143,6 +163,16 @@ dtw32_kernel(const __grid_constant__ Src src) {
         nxt += n_groups;
     }
     uint2 w1 = work_item(job, p1, n_work);
+    // Live pruning (job.lb): the next pair's safe bound and its query's best
+    // (float bits), requested with the claim and tested when the pair is
+    // due; a bound above the best's upper bound at that moment drops the
+    // pair unstarted (the compaction's test against a tighter best).
+    float lb1 = 0.f;
+    unsigned kb1 = ~0u;
+    if (job.lb && p1 < n_work) {
+        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+    }
 
     float R[C], Aw[H + U], Bw[H + U];
     // per-pair state
@@ -153,6 +183,10 @@ dtw32_kernel(const __grid_constant__ Src src) {
     float ub = INF;
     unsigned kb = ~0u;              // query best (float bits) read at one check, used at the next
     const float *ap = job.test, *bp = job.train;
+    // lengths, the super-steps of a full sweep and the end cell's register
+    // (the equal-length values unless VAR)
+    int LA = L, LB = L, ue = L, cE = cW;
+    bool hasE = hasW;
     // Stream values come in chunks of G, one per lane of the group: for warp
     // steps cG .. cG+G-1, lane k of the group holds the values of warp step
     // cG + k (the current chunk in ca/cb, the next one in na_/nb_).
@@ -165,12 +199,13 @@ dtw32_kernel(const __grid_constant__ Src src) {
         const bool need = done && !finished;
         if (__any_sync(FULL, need)) {
             if (need) {
-                if (p1 >= n_work) {
-                    finished = true;
-                    pid = -1;
-                } else {
+                // claim until a pair survives the live test or the list ends
+                bool take = false;
+                while (!take && p1 < n_work) {
                     pid = p1;
                     q = (int)w1.x; tt = (int)w1.y;
+                    const float lb_cur = lb1;
+                    const unsigned kb_cur = kb1;
                     if (job.head) {
                         p1 = __shfl_sync(gmask, nxt, 0, G);
                         if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
@@ -179,8 +214,33 @@ dtw32_kernel(const __grid_constant__ Src src) {
                         nxt += n_groups;
                     }
                     w1 = work_item(job, p1, n_work);
-                    ap = job.test + (long long)q * L;
-                    bp = job.train + (long long)tt * L;
+                    if (job.lb && p1 < n_work) {
+                        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+                        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+                    }
+                    take = kb_cur == ~0u ||
+                           !(lb_cur > upper32(__uint_as_float(kb_cur), job.dtw_hi, job.abs32));
+                    if (!take && job.counters && gl == 0)
+                        atomicAdd(job.counters + C_LIVEPRUNED, 1ull);
+                }
+                if (!take) {
+                    finished = true;
+                    pid = -1;
+                } else {
+                    if constexpr (VAR) {
+                        const long long a0 = job.test_off[q], b0 = job.train_off[tt];
+                        ap = job.test + a0;
+                        bp = job.train + b0;
+                        LA = (int)(job.test_off[q + 1] - a0);
+                        LB = (int)(job.train_off[tt + 1] - b0);
+                        ue = (LA + LB + (W & 1)) >> 1;
+                        const int kE = W + LB - LA;
+                        hasE = kE >= k0 && kE < k0 + Cg;
+                        cE = kE - k0;
+                    } else {
+                        ap = job.test + (long long)q * L;
+                        bp = job.train + (long long)tt * L;
+                    }
                     done = false;
                     ws = wblk;
                     ub = INF;
@@ -190,20 +250,20 @@ dtw32_kernel(const __grid_constant__ Src src) {
 #pragma unroll
                     for (int m = 0; m < H; m++) {
                         const int ia = I0 - m;
-                        Aw[m + U - 1] = (ia >= 0 && ia < L) ? ap[ia] : APAD;
+                        Aw[m + U - 1] = (ia >= 0 && ia < LA) ? ap[ia] : APAD;
                         const int jb = J0 + m;
-                        Bw[m] = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
+                        Bw[m] = jb < 0 ? BPAD : (jb < LB ? bp[jb] : EPAD);
                     }
 #pragma unroll
                     for (int c = 0; c < C; c++) R[c] = (hasW && c == cW) ? 0.f : INF;
                     {   // the stream chunks holding warp steps wblk and on
                         const int u0 = (wblk & ~(G - 1)) + gl - wblk;
                         const int ia = IA0 + u0, jb = JB0 + u0;
-                        ca = (ia >= 0 && ia < L) ? ap[ia] : APAD;
-                        cb = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
+                        ca = (ia >= 0 && ia < LA) ? ap[ia] : APAD;
+                        cb = jb < 0 ? BPAD : (jb < LB ? bp[jb] : EPAD);
                         const int ia2 = ia + G, jb2 = jb + G;
-                        na_ = (ia2 >= 0 && ia2 < L) ? ap[ia2] : APAD;
-                        nb_ = jb2 < 0 ? BPAD : (jb2 < L ? bp[jb2] : EPAD);
+                        na_ = (ia2 >= 0 && ia2 < LA) ? ap[ia2] : APAD;
+                        nb_ = jb2 < 0 ? BPAD : (jb2 < LB ? bp[jb2] : EPAD);
                     }
                     if (job.counters && gl == 0) atomicAdd(job.counters + C_STARTED, 1ull);
                 }
@@ -224,8 +284,8 @@ dtw32_kernel(const __grid_constant__ Src src) {
                 cb = nb_;
                 const int u2 = w + 1 + G + gl - ws;
                 const int ia = IA0 + u2, jb = JB0 + u2;
-                na_ = (ia >= 0 && ia < L) ? ap[ia] : APAD;
-                nb_ = jb < 0 ? BPAD : (jb < L ? bp[jb] : EPAD);
+                na_ = (ia >= 0 && ia < LA) ? ap[ia] : APAD;
+                nb_ = jb < 0 ? BPAD : (jb < LB ? bp[jb] : EPAD);
             }
             // step A: even slots
             {
@@ -295,12 +355,13 @@ dtw32_kernel(const __grid_constant__ Src src) {
         const int u = wblk - ws;     // super-steps of the current pair so far
 
         // ---- completion / abandon ------------------------------------------
-        const bool completed = !done && u >= L;
+        const bool completed = !done && u >= ue;
         if (completed) {
-            // the result: diagonal W holds D(L,L) (kept by the past-the-end cells)
+            // the result: diagonal W (W + L_B - L_A) holds D(L,L) (D(L_A,L_B)),
+            // kept by the past-the-end cells
             float r = INF;
 #pragma unroll
-            for (int c = 0; c < C; c++) r = (hasW && c == cW) ? R[c] : r;
+            for (int c = 0; c < C; c++) r = (hasE && c == cE) ? R[c] : r;
             for (int off = 1; off < G; off <<= 1) r = fminf(r, __shfl_xor_sync(gmask, r, off, G));
             if (gl == 0) {
                 if (job.out) job.out[pid] = r;
@@ -318,7 +379,8 @@ dtw32_kernel(const __grid_constant__ Src src) {
                 }
                 if (job.counters)
                     atomicAdd(job.counters + C_CELLS,
-                              (unsigned long long)band_cells_upto(L, W, 2ll * L));
+                              (unsigned long long)(VAR ? band_cells_var(LA, LB, W, 2ll * L)
+                                                       : band_cells_upto(L, W, 2ll * L)));
             }
             done = true;
         }
@@ -340,7 +402,8 @@ dtw32_kernel(const __grid_constant__ Src src) {
             if (drop && gl == 0 && job.counters) {
                 atomicAdd(job.counters + C_ABANDONED, 1ull);
                 atomicAdd(job.counters + C_CELLS,
-                          (unsigned long long)band_cells_upto(L, W, 2ll * u + t_first - 1));
+                          (unsigned long long)(VAR ? band_cells_var(LA, LB, W, 2ll * u + t_first - 1)
+                                                   : band_cells_upto(L, W, 2ll * u + t_first - 1)));
             }
             done = done || drop;
         }

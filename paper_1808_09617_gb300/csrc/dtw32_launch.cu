@@ -19,11 +19,52 @@ bool pick_fn(int H, Dtw32Fn1 *f1, Dtw32FnN *fn) {
     }
 }
 
+bool pick_var_fn(int H, Dtw32Fn1 *f1) {
+    switch (H) {
+#define C_(h) case h: *f1 = dtw32_var_fn<h>(); return true;
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13)
+        C_(14) C_(15) C_(16) C_(17) C_(18) C_(19) C_(20) C_(21) C_(22) C_(23) C_(24) C_(25)
+        C_(26) C_(27) C_(28) C_(29) C_(30) C_(31) C_(32)
+#undef C_
+        default: return false;
+    }
+}
+
 struct OccCache {
     std::mutex mu;
-    int blocks[33][64] = {};  // [H][device]
+    int blocks[2][33][64] = {};  // [form][H][device]
 };
 OccCache g_occ;
+
+// The persistent grid of the diagonal kernel f (form 0: equal lengths, 1:
+// unequal) with G lanes per pair: its resident CTAs on every SM, or fewer
+// for a short work list known on the host.
+cudaError_t diag_grid(const DtwJob32 &job, int form, int H, int G, Dtw32Fn1 f, int sm_count,
+                      long long *grid_out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_occ.mu);
+        if (dev < 64) bps = g_occ.blocks[form][H][dev];
+        if (bps == 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, 128, 0);
+            if (e != cudaSuccess) return e;
+            if (bps < 1) bps = 1;
+            if (dev < 64) g_occ.blocks[form][H][dev] = bps;
+        }
+    }
+    long long grid = (long long)sm_count * bps;
+    if (!job.pairs || !job.count) {
+        const long long n = job.pairs ? job.n_pairs : job.n_seed;
+        const long long groups_per_block = 128 / G;
+        const long long need = n > 0 ? (n + groups_per_block - 1) / groups_per_block : 0;
+        if (need < grid) grid = need;
+    }
+    *grid_out = grid;
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -77,27 +118,25 @@ cudaError_t plan_dtw32(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
     int G = 0, H = 0;
     if (!dtw32_shape(job.W, job.group, &G, &H)) return plan_dtw32_wide(job, sm_count, p);
     if (!pick_fn(H, &p->fn1, &p->fnN)) return cudaErrorNotSupported;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    long long grid = 0;
+    const cudaError_t e = diag_grid(job, 0, H, G, p->fn1, sm_count, &grid);
     if (e != cudaSuccess) return e;
-    int bps = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_occ.mu);
-        if (dev < 64) bps = g_occ.blocks[H][dev];
-        if (bps == 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->fn1, 128, 0);
-            if (e != cudaSuccess) return e;
-            if (bps < 1) bps = 1;
-            if (dev < 64) g_occ.blocks[H][dev] = bps;
-        }
-    }
-    long long grid = (long long)sm_count * bps;
-    if (!job.pairs || !job.count) {
-        const long long n = job.pairs ? job.n_pairs : job.n_seed;
-        const long long groups_per_block = 128 / G;
-        const long long need = n > 0 ? (n + groups_per_block - 1) / groups_per_block : 0;
-        if (need < grid) grid = need;
-    }
+    p->threads = 128;
+    p->smem = 0;
+    p->blocks = grid;
+    p->lanes = G;
+    return cudaSuccess;
+}
+
+cudaError_t plan_dtw32_var(const DtwJob32 &job, int sm_count, Dtw32Plan *p) {
+    if (!job.pairs || !job.test_off || !job.train_off) return cudaErrorInvalidValue;
+    int G = 0, H = 0;
+    if (!dtw32_shape(job.W, job.group, &G, &H)) return plan_dtw32_wide(job, sm_count, p);
+    if (!pick_var_fn(H, &p->fn1)) return cudaErrorNotSupported;
+    p->fnN = nullptr;
+    long long grid = 0;
+    const cudaError_t e = diag_grid(job, 1, H, G, p->fn1, sm_count, &grid);
+    if (e != cudaSuccess) return e;
     p->threads = 128;
     p->smem = 0;
     p->blocks = grid;

@@ -149,11 +149,20 @@ dtw32_rows_kernel(const __grid_constant__ Src src) {
         nxt += n_warps;
     }
     uint2 w1 = work_item(job, p1, n_work);
+    // live pruning (job.lb), as in the diagonal-layout kernel
+    float lb1 = 0.f;
+    unsigned kb1 = ~0u;
+    if (job.lb && p1 < n_work) {
+        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+    }
 
     while (true) {
         const long long p = p1;
         if (p >= n_work) break;
         const int q = (int)w1.x, t = (int)w1.y;
+        const float lb_cur = lb1;
+        const unsigned kb_cur = kb1;
         if (job.head) {
             p1 = __shfl_sync(FULL, nxt, 0);
             if (lane == 0) nxt = (long long)atomicAdd(job.head, 1ull);
@@ -162,6 +171,14 @@ dtw32_rows_kernel(const __grid_constant__ Src src) {
             nxt += n_warps;
         }
         w1 = work_item(job, p1, n_work);
+        if (job.lb && p1 < n_work) {
+            lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+            kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+        }
+        if (kb_cur != ~0u && lb_cur > upper32(__uint_as_float(kb_cur), job.dtw_hi, job.abs32)) {
+            if (lane == 0 && job.counters) atomicAdd(job.counters + C_LIVEPRUNED, 1ull);
+            continue;
+        }
 
         const float *ap = job.test + (long long)q * L;
         const float *bp = job.train + (long long)t * L;

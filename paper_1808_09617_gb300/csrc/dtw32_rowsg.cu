@@ -132,6 +132,13 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
         nxt += n_groups;
     }
     uint2 w1 = work_item(job, p1, n_work);
+    // live pruning (job.lb), as in the diagonal-layout kernel
+    float lb1 = 0.f;
+    unsigned kb1 = ~0u;
+    if (job.lb && p1 < n_work) {
+        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+    }
 
     float B[C], D[C], E[C];
 #pragma unroll
@@ -152,12 +159,13 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
         const bool need = done && !finished;
         if (__any_sync(FULL, need)) {
             if (need) {
-                if (p1 >= n_work) {
-                    finished = true;
-                    pid = -1;
-                } else {
+                // claim until a pair survives the live test or the list ends
+                bool take = false;
+                while (!take && p1 < n_work) {
                     pid = p1;
                     q = (int)w1.x; t = (int)w1.y;
+                    const float lb_cur = lb1;
+                    const unsigned kb_cur = kb1;
                     if (job.head) {
                         p1 = __shfl_sync(gmask, nxt, 0, G);
                         if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
@@ -166,6 +174,19 @@ dtw32_rowsg_kernel(const __grid_constant__ Src src) {
                         nxt += n_groups;
                     }
                     w1 = work_item(job, p1, n_work);
+                    if (job.lb && p1 < n_work) {
+                        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+                        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+                    }
+                    take = kb_cur == ~0u ||
+                           !(lb_cur > upper32(__uint_as_float(kb_cur), job.dtw_hi, job.abs32));
+                    if (!take && job.counters && gl == 0)
+                        atomicAdd(job.counters + C_LIVEPRUNED, 1ull);
+                }
+                if (!take) {
+                    finished = true;
+                    pid = -1;
+                } else {
                     ap = job.test + (long long)q * L;
                     const float *bp = job.train + (long long)t * L;
 #pragma unroll

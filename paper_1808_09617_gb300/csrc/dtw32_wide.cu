@@ -8,7 +8,8 @@
 // in the slot of diagonal W.  Same work list, margins, packed best-so-far
 // keys, candidate list and early abandoning as the register kernel (the
 // minimum over all slots is at most the minimum over anti-diagonals t-1 and
-// t, which every path crosses).
+// t, which every path crosses).  With offset tables (unequal lengths) the
+// pair's grid is L_A x L_B and its end cell lies on diagonal W + L_B - L_A.
 #include "dtw32.cuh"
 
 namespace nndtw {
@@ -51,8 +52,18 @@ dtw32_wide_kernel(const __grid_constant__ Src src) {
         } else {
             q = (int)p; t = (int)key_idx(job.seed_keys[p]);
         }
-        const float *a = job.test + (long long)q * L;
-        const float *b = job.train + (long long)t * L;
+        const float *a, *b;
+        int LA = L, LB = L;
+        if (job.test_off) {
+            const long long a0 = job.test_off[q], b0 = job.train_off[t];
+            a = job.test + a0;
+            b = job.train + b0;
+            LA = (int)(job.test_off[q + 1] - a0);
+            LB = (int)(job.train_off[t + 1] - b0);
+        } else {
+            a = job.test + (long long)q * L;
+            b = job.train + (long long)t * L;
+        }
         for (int k = lane; k < nslot; k += 32) Rs[k] = INF;
         __syncwarp();
         if (lane == 0) Rs[W + 1] = 0.f;
@@ -61,7 +72,7 @@ dtw32_wide_kernel(const __grid_constant__ Src src) {
 
         bool abandoned = false;
         long long cells = 0;
-        for (int s = 0; s <= 2 * L - 2; s++) {
+        for (int s = 0; s <= LA + LB - 2; s++) {
             if (job.abandon && job.bsf && (s & 15) == 15) {
                 float mn = INF;
                 for (int k = lane; k < nslot; k += 32) mn = fminf(mn, Rs[k]);
@@ -71,11 +82,12 @@ dtw32_wide_kernel(const __grid_constant__ Src src) {
                 const float ub = kb == ~0ull ? INF : upper32(key_dist(kb), job.dtw_hi, job.abs32);
                 if (lower32(mn, job.dtw_lo, job.abs32) > ub) { abandoned = true; break; }
             }
+            // cells (i, j) = ((s + W - k) / 2, s - i) inside [0, L_A) x [0, L_B)
             int klo = W - s;
-            if (klo < s + W - 2 * L + 2) klo = s + W - 2 * L + 2;
+            if (klo < s + W - 2 * LA + 2) klo = s + W - 2 * LA + 2;
             if (klo < 0) klo = 0;
             int khi = s + W;
-            if (khi > 2 * L - 2 - s + W) khi = 2 * L - 2 - s + W;
+            if (khi > 2 * LB - 2 - s + W) khi = 2 * LB - 2 - s + W;
             if (khi > 2 * W) khi = 2 * W;
             if (((s + W - klo) & 1) != 0) klo++;
             for (int k = klo + 2 * lane; k <= khi; k += 64) {
@@ -92,7 +104,9 @@ dtw32_wide_kernel(const __grid_constant__ Src src) {
                 if (abandoned) atomicAdd(job.counters + C_ABANDONED, 1ull);
             }
             if (!abandoned) {
-                const float res = Rs[W + 1];
+                // (|L_A - L_B| > W: no warping path inside the window)
+                const int kE = W + LB - LA;
+                const float res = (kE >= 0 && kE <= 2 * W) ? Rs[kE + 1] : INF;
                 if (job.out) job.out[p] = res;
                 if (job.bsf) {
                     const unsigned long long key = pack_key(res, (uint32_t)t);

@@ -29,6 +29,11 @@
 // series against the query's envelope, scaled down by the bound's rounding
 // margin) is compared with the same best, and the pair is dropped when it is
 // larger.
+//
+// With offset tables (unequal lengths, Sec. 2 generalised) series k of the
+// test / training set is [off[k], off[k+1]) of its array, the pair's grid is
+// L_A x L_B, and its end cell lies on diagonal W + L_B - L_A; L is then the
+// longest length (the staging size).
 #include <type_traits>
 
 #include "internal.cuh"
@@ -135,17 +140,28 @@ dtw64_kernel(const __grid_constant__ Src src) {
             if (drop) continue;
         }
         const IT *Ag, *Bg;
-        if (F32IN) {
-            Ag = reinterpret_cast<const IT *>(job.test32 + (long long)q * L);
-            Bg = reinterpret_cast<const IT *>(job.train32 + (long long)t * L);
+        const IT *tst = F32IN ? reinterpret_cast<const IT *>(job.test32)
+                              : reinterpret_cast<const IT *>(job.test);
+        const IT *trn = F32IN ? reinterpret_cast<const IT *>(job.train32)
+                              : reinterpret_cast<const IT *>(job.train);
+        int LA = L, LB = L;
+        if (job.test_off) {
+            const long long a0 = job.test_off[q], b0 = job.train_off[t];
+            Ag = tst + a0;
+            Bg = trn + b0;
+            LA = (int)(job.test_off[q + 1] - a0);
+            LB = (int)(job.train_off[t + 1] - b0);
         } else {
-            Ag = reinterpret_cast<const IT *>(job.test + (long long)q * L);
-            Bg = reinterpret_cast<const IT *>(job.train + (long long)t * L);
+            Ag = tst + (long long)q * L;
+            Bg = trn + (long long)t * L;
         }
+        // (a ragged length that does not fit the staging: no value)
+        if (LA < 1 || LB < 1 || LA > L || LB > L) continue;
         // staged copies (shared-memory loads in the sweep), or (FP64 inputs
         // only) the series in global memory
         if (STAGED) {
-            for (int i = tid; i < L; i += nthr) { As[i] = (ST)Ag[i]; Bs[i] = (ST)Bg[i]; }
+            for (int i = tid; i < LA; i += nthr) As[i] = (ST)Ag[i];
+            for (int i = tid; i < LB; i += nthr) Bs[i] = (ST)Bg[i];
         }
         const ST *Ap = STAGED ? As : reinterpret_cast<const ST *>(Ag);
         const ST *Bp = STAGED ? Bs : reinterpret_cast<const ST *>(Bg);
@@ -159,7 +175,7 @@ dtw64_kernel(const __grid_constant__ Src src) {
 
         bool abandoned = false;
         long long cells = 0;
-        for (int s = 0; s <= 2 * L - 2; s++) {
+        for (int s = 0; s <= LA + LB - 2; s++) {
             if (job.abandon && job.bsf64 && (s & 15) == 15) {
                 long long mn = INFB;
                 for (int k = tid; k < nslot; k += nthr) mn = lmin(mn, Rs[k]);
@@ -181,11 +197,12 @@ dtw64_kernel(const __grid_constant__ Src src) {
                 __syncthreads();
                 if (stop) { abandoned = true; break; }
             }
+            // cells (i, j) = ((s + W - k) / 2, s - i) inside [0, L_A) x [0, L_B)
             int klo = W - s;
-            if (klo < s + W - 2 * L + 2) klo = s + W - 2 * L + 2;
+            if (klo < s + W - 2 * LA + 2) klo = s + W - 2 * LA + 2;
             if (klo < 0) klo = 0;
             int khi = s + W;
-            if (khi > 2 * L - 2 - s + W) khi = 2 * L - 2 - s + W;
+            if (khi > 2 * LB - 2 - s + W) khi = 2 * LB - 2 - s + W;
             if (khi > 2 * W) khi = 2 * W;
             if (((s + W - klo) & 1) != 0) klo++;
             for (int k = klo + 2 * tid; k <= khi; k += 2 * nthr) {
@@ -204,7 +221,9 @@ dtw64_kernel(const __grid_constant__ Src src) {
                 if (abandoned) atomicAdd(job.counters + C_ABANDONED, 1ull);
             }
             if (!abandoned) {
-                const double D = __longlong_as_double(Rs[W + 1]);
+                const int kE = W + LB - LA;   // outside [0, 2W]: no warping path
+                const double D = (kE >= 0 && kE <= 2 * W) ? __longlong_as_double(Rs[kE + 1])
+                                                          : __longlong_as_double(INFB);
                 if (job.out) job.out[p] = D;
                 if (job.bsf64) {
                     const unsigned long long old = atomicMin(job.bsf64 + q, dbits(D));

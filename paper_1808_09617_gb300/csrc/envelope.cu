@@ -12,6 +12,13 @@
 // over tile maxima answers the middle range with two lookups.  min/max are
 // exact, so the result is bit-identical to a naive scan.
 //
+// Series of unequal lengths (offset table off: series s is
+// train[off[s] .. off[s+1]), of length L_s <= L): the envelope is taken for
+// the rows i < min(L_s + W, E) of a series compared with it (Sec. 2
+// generalised), written with a row stride of E; a window then ends at
+// min(L_s - 1, i + W), and a window that fits in one tile is a prefix of it
+// (starting at 0) or a suffix (ending at L_s - 1).
+//
 // The same kernel gives the second envelopes used by the LB_Improved bridge:
 // fed with a series' envelopes (U, Lo) instead of the series, it takes the
 // window maximum of Lo and the window minimum of U.
@@ -57,11 +64,17 @@ envelope_kernel(const __grid_constant__ Src src) {
     const T NEG = -inf_of<T>();
 
     for (int64_t s = bid; s < N; s += nblk) {
-        const T *x = env_in ? nullptr : train + s * (int64_t)L;
+        const int64_t x0 = job.off ? (int64_t)job.off[s] : s * (int64_t)L;
+        const int Ls = job.off ? (int)(job.off[s + 1] - x0) : L;   // this series' length
+        if (Ls < 1 || Ls > L) continue;   // (a ragged length out of range: no envelope)
+        const int E = job.off ? job.E : L;                         // output row stride
+        const int rows = Ls + W < E ? Ls + W : E;
+        const int nts = (Ls + T_tile - 1) / T_tile;
+        const T *x = env_in ? nullptr : train + x0;
         const T *ein = env_in ? env_in + s * 2 * (int64_t)L : nullptr;
-        T *out = env + s * 2 * (int64_t)L;
+        T *out = env + s * 2 * (int64_t)E;
         if (W == 0) {
-            for (int i = tid; i < L; i += kEnvThreads) {
+            for (int i = tid; i < Ls; i += kEnvThreads) {
                 out[2 * i] = ein ? ein[2 * i + 1] : x[i];
                 out[2 * i + 1] = ein ? ein[2 * i] : x[i];
             }
@@ -74,12 +87,12 @@ envelope_kernel(const __grid_constant__ Src src) {
                 return -(ein ? ein[2 * k] : x[k]);
             };
             // tile prefix / suffix scans
-            for (int base = 0; base < L; base += kEnvThreads) {
+            for (int base = 0; base < Ls; base += kEnvThreads) {
                 const int k = base + tid;
 #pragma unroll
                 for (int c = 0; c < NP; c++) {
                     const int ch = pass * NP + c;
-                    T pm = k < L ? value(ch, k) : NEG;
+                    T pm = k < Ls ? value(ch, k) : NEG;
                     T sm = pm;
                     for (int d = 1; d < T_tile; d <<= 1) {
                         const T a = __shfl_up_sync(0xffffffffu, pm, d);
@@ -87,7 +100,7 @@ envelope_kernel(const __grid_constant__ Src src) {
                         if (r >= d) pm = tmax(pm, a);
                         if (r + d < T_tile) sm = tmax(sm, b);
                     }
-                    if (k < L) {
+                    if (k < Ls) {
                         P[(size_t)c * L + k] = pm; S[(size_t)c * L + k] = sm;
                         if (r == 0) M[c * mstride + k / T_tile] = sm;
                     }
@@ -97,7 +110,7 @@ envelope_kernel(const __grid_constant__ Src src) {
             // sparse table over tile maxima (level j covers 2^j tiles)
             for (int j = 1; j <= levels; j++) {
                 const int half = 1 << (j - 1);
-                const int cnt = nt - (1 << j) + 1;
+                const int cnt = nts - (1 << j) + 1;
                 for (int idx = tid; idx < NP * cnt; idx += kEnvThreads) {
                     const int c = idx / cnt, t = idx % cnt;
                     const T *pm = M + c * mstride + (size_t)(j - 1) * nt;
@@ -105,15 +118,17 @@ envelope_kernel(const __grid_constant__ Src src) {
                 }
                 __syncthreads();
             }
-            for (int i = tid; i < L; i += kEnvThreads) {
+            for (int i = tid; i < rows; i += kEnvThreads) {
                 const int lo = i - W < 0 ? 0 : i - W;
-                const int hi = i + W > L - 1 ? L - 1 : i + W;
+                const int hi = i + W > Ls - 1 ? Ls - 1 : i + W;
                 const int a = lo / T_tile + 1, b = hi / T_tile - 1;
+                const bool one_tile = lo / T_tile == hi / T_tile;
 #pragma unroll
                 for (int c = 0; c < NP; c++) {
                     const int ch = pass * NP + c;
                     const T *Pc = P + (size_t)c * L, *Sc = S + (size_t)c * L, *Mc = M + c * mstride;
-                    T u = tmax(Sc[lo], Pc[hi]);
+                    // (one tile: the window is a suffix of the series or a prefix)
+                    T u = one_tile ? (hi == Ls - 1 ? Sc[lo] : Pc[hi]) : tmax(Sc[lo], Pc[hi]);
                     if (b >= a) {
                         if (levels == 0) {
                             for (int t = a; t <= b; t++) u = tmax(u, Mc[t]);
@@ -153,7 +168,7 @@ EnvPlan<T> plan_envelopes(const T *train, const T *env_in, int64_t N, int L, int
     p.smem = p.one_pass ? 2 * per_channel : per_channel;
     const int sms = device_sm_count();
     p.blocks = N < (int64_t)sms * 8 ? N : (int64_t)sms * 8;
-    p.job = EnvJob<T>{train, env_in, N, L, Weff, T_tile, levels, env};
+    p.job = EnvJob<T>{train, env_in, N, L, Weff, T_tile, levels, env, nullptr, 0};
     return p;
 }
 

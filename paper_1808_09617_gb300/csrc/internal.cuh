@@ -75,6 +75,9 @@ enum Counter : int {
     C_REVPRUNED,     // pairs dropped by the reverse bound LB_Enhanced(B, A)
     C_QUEUE2,        // survivors of the cascade's second stage (FP32 search)
     C_IMPPRUNED,     // pairs dropped by LB_Enhanced with the LB_Improved bridge
+    C_SEEDPAIRS,     // first-candidate pairs listed (unequal-length search)
+    C_BADLEN,        // series lengths out of range (unequal-length search)
+    C_LIVEPRUNED,    // queued pairs dropped unstarted by their bound against the live best
     C_COUNT
 };
 
@@ -160,6 +163,11 @@ template <typename T> struct EnvJob {
     int64_t N;
     int L, W, T_tile, levels;
     T *env;
+    // unequal lengths (nullptr: every series has L points): series s is
+    // train[off[s] .. off[s+1]), L is the longest length, and its envelope
+    // rows i < min(L_s + W, E) are written at env + 2 E s
+    const long long *off;
+    int E;
 };
 template <typename T> struct EnvPlan {
     EnvJob<T> job;
@@ -238,6 +246,34 @@ cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int6
 template <typename T> LbFns<T> lb_fns(int tile, bool ed);
 template <typename T> cudaError_t set_lb_smem(int tile, bool ed, size_t smem);
 
+// LB_Enhanced^V (or with keogh, LB_Keogh) of every pair of two ragged sets
+// (series k of a set is [off[k], off[k+1]) of its array), unequal lengths
+// allowed: +inf where |L_A - L_B| > W (no warping path) or a length lies
+// outside [2, max_len] (counted in *bad); env holds the training series'
+// envelope rows with stride E (the ragged envelope kernel).  lb_out[Q][N]
+// raw or (safe) scaled down by lb_lo and abs_slack; with seed_keys, each
+// query's smallest (bound, index) key among its finite bounds is merged in
+// with atomicMin (seed_keys must start at all ones).
+struct LbVarJob {
+    const float *test;
+    const long long *test_off;
+    int64_t Q;
+    const float *train;
+    const long long *train_off;
+    const float *env;
+    int E;
+    int64_t N;
+    int W, V, max_len, keogh, safe;
+    float lb_lo, abs_slack;
+    float *lb_out;
+    unsigned long long *seed_keys, *bad;
+};
+cudaError_t launch_lb_var(const LbVarJob &job, cudaStream_t s);
+// The pairs (q, key_idx(seed_keys[q])) of the queries with a key, appended
+// to pairs (count in *count, which must start at 0).
+cudaError_t launch_seed_pairs(const unsigned long long *seed_keys, int64_t Q, uint2 *pairs,
+                              unsigned long long *count, int sm_count, cudaStream_t s);
+
 // LB_New (Sec. 2.2.5) of every (query, training series) pair into out[Q][N]
 // (raw, or with safe: scaled down by the rounding margin).
 template <typename T>
@@ -264,6 +300,14 @@ struct DtwJob32 {
     int abandon;                        // 1: abandon against bsf
     int group;                          // lanes per pair (0: library's choice; kRowsGroup: rows)
     int lanes;                          // resolved lanes per pair (set by the launcher)
+    // unequal lengths (the *_var plans): series k of test / train is
+    // [off[k], off[k+1]) of its array; L is then the longest length
+    const long long *test_off, *train_off;
+    // live pruning (explicit pairs with bsf; nullptr: none): the pairs' safe
+    // bounds lb[q * lb_n + t], tested against the query's best when a pair
+    // is due
+    const float *lb;
+    long long lb_n;
 };
 // How one dataset's FP32 DTW pass is launched: the kernel in its one-dataset
 // and batch forms (every FP32 DTW kernel takes a DtwJob32 source), block
@@ -286,6 +330,10 @@ cudaError_t plan_dtw32_ed(const DtwJob32 &job, int sm_count, Dtw32Plan *p);   //
 cudaError_t plan_dtw32_rows(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
 cudaError_t plan_dtw32_rowsg(const DtwJob32 &job, int G, int sm_count, Dtw32Plan *p);
 cudaError_t plan_dtw32_rowsc(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
+// Unequal lengths (job.test_off / train_off set, explicit pairs): the
+// diagonal kernel's VAR form for W <= 1023, the shared-memory band kernel
+// beyond.
+cudaError_t plan_dtw32_var(const DtwJob32 &job, int sm_count, Dtw32Plan *p);
 // One dataset: plan and launch.
 cudaError_t launch_dtw32(const DtwJob32 &job, int sm_count, cudaStream_t s);
 bool dtw32_rowsg_ok(int L, int W, int G);
@@ -331,6 +379,8 @@ struct DtwJob64 {
     bool rev;
     const double2 *env2;
     const double *lb;
+    // unequal lengths: series offsets as in DtwJob32 (L the longest length)
+    const long long *test_off, *train_off;
 };
 cudaError_t launch_dtw64(const DtwJob64 &job, int sm_count, cudaStream_t s);
 using Dtw64Fn1 = void (*)(Src1<DtwJob64>);

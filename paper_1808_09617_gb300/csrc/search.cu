@@ -89,6 +89,7 @@ template <typename T> struct CompactJob {
     const unsigned long long *bsf, *seed;
     UbOf<T> ubof;
     int no_prune, gx;   // gx: CTAs along a row; the others stride over the rows
+    int finite_only;    // also drop pairs whose bound is +inf (no warping path)
     int scatter;        // 0: count the kept pairs per bucket; 1: write them
     unsigned long long *bcount, *bcursor, *qcount;
     uint2 *queue;
@@ -105,7 +106,7 @@ compact_kernel(const __grid_constant__ Src src) {
     const unsigned long long *__restrict__ bsf = job.bsf;
     const unsigned long long *__restrict__ seed = job.seed;
     const UbOf<T> ubof = job.ubof;
-    const int no_prune = job.no_prune;
+    const int no_prune = job.no_prune, finite_only = job.finite_only;
     unsigned long long *__restrict__ bcount = job.bcount;
     unsigned long long *__restrict__ bcursor = job.bcursor;
     uint2 *__restrict__ queue = job.queue;
@@ -148,7 +149,8 @@ compact_kernel(const __grid_constant__ Src src) {
                 if (t < N) {
                     const T v = row[t];
                     // (a leave-one-out pair (q, q) has the bound +inf: never kept)
-                    keep = (no_prune ? v < inf_of<T>() : v <= ub) && (uint32_t)t != st;
+                    keep = (no_prune ? v < inf_of<T>() : v <= ub) && (uint32_t)t != st &&
+                           (!finite_only || v < inf_of<T>());
                     if (keep) bk[e] = bucket_of(v, inv);
                 }
                 if (keep) {
@@ -253,6 +255,14 @@ __global__ void finalize32_kernel(const __grid_constant__ Src src) {
     for (int64_t q = (int64_t)bid * blockDim.x + threadIdx.x; q < j.Q;
          q += (int64_t)nblk * blockDim.x) {
         const unsigned long long kb = j.bsf[q];
+        if (kb == ~0ull) {
+            // no candidate: no training series has a warping path inside the
+            // window (unequal lengths only)
+            j.nn_idx[q] = -1;
+            j.nn_label[q] = -1;
+            j.nn_dist[q] = inf_of<double>();
+            continue;
+        }
         int32_t idx;
         double dist;
         if (j.exact || j.rcount[q] >= 2) {
@@ -509,6 +519,7 @@ void fill_stats(nndtw_stats *st, const unsigned long long *h, int64_t N, int64_t
         st->seed_cells = Q * band_cells(L, W);
         st->lb_pruned_reverse = (int64_t)h[C_REVPRUNED];
         st->lb_pruned_improved = (int64_t)h[C_IMPPRUNED];
+        st->lb_pruned_live = (int64_t)h[C_LIVEPRUNED];
     }
 }
 
@@ -523,6 +534,7 @@ void add_stats(nndtw_stats *t, const nndtw_stats &p) {
     t->seed_cells += p.seed_cells;
     t->lb_pruned_reverse += p.lb_pruned_reverse;
     t->lb_pruned_improved += p.lb_pruned_improved;
+    t->lb_pruned_live += p.lb_pruned_live;
 }
 
 template <typename T>
@@ -938,6 +950,10 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             j.pairs = p.second ? p.ws.rlist : p.ws.queue; j.seed_keys = nullptr;
             j.count = p.ws.counters + (p.second ? C_QUEUE2 : C_QUEUE);
             j.head = p.ws.counters + C_HEAD;
+            if (!p.no_prune) {   // live pruning against the tightening bests
+                j.lb = p.ws.lb;
+                j.lb_n = sets[d].N;
+            }
             j.abandon = (sets[d].flags & NNDTW_NO_ABANDON) ? 0 : 1;
             Dtw32Plan pl{};
             CK(plan_dtw32(j, sms, &pl));
@@ -998,6 +1014,207 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
         CK(cudaMemcpyAsync(h, P[0].ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         fill_stats(stats, h, sets[0].N, sets[0].Q, sets[0].L, P[0].Weff, P[0].cnt != nullptr);
+    }
+    return NNDTW_OK;
+}
+
+// ------------------------------------------------- unequal-length executor
+//
+// One chunk of queries of the unequal-length search (Sec. 2 generalised),
+// on the caller's stream: the stages of run32 over ragged sets.  The first
+// candidate of each query is the series with the smallest bound (the
+// Euclidean distance is undefined for unequal lengths); pairs without a
+// warping path inside the window (|L_A - L_B| > W) have the bound +inf and
+// are never kept; a query none of whose pairs has one gets index -1.
+struct SetVar {
+    const float *train;
+    const long long *train_off;
+    const int32_t *labels;
+    int64_t N;
+    const float *test;
+    const long long *test_off;   // the chunk's first query's entry (absolute offsets)
+    int64_t Q;
+    int max_len, W, V;
+    unsigned flags;
+    int32_t *nn_idx, *nn_label;
+    double *nn_dist;
+    void *ws;
+    int64_t q_cap;
+    bool train_ready;   // the training envelopes are already in the workspace
+};
+
+int run_var(const SetVar &x, bool want_stats, bool timing, nndtw_stats *stats, StageTimer &tm,
+            cudaStream_t s) {
+    const int sms = device_sm_count();
+    const Layout32 w = layout32(x.ws, x.N, x.q_cap, x.max_len);
+    const int Weff = x.W > x.max_len - 1 ? x.max_len - 1 : x.W;
+    const Margins m = make_margins(x.max_len);
+    const bool exact = (x.flags & NNDTW_EXACT_DIST) != 0;
+    unsigned long long *cnt = (want_stats && !timing) ? w.counters : nullptr;
+    auto launched = [&](int k) {
+        t_launches += k;
+        t_stage_launches[t_stage] += k;
+    };
+    t_stage = 0;
+    {
+        const InitJob32 j{w.counters, w.buckets, w.bsf, w.seed, w.best64, w.rcount, w.bestidx,
+                          x.Q};
+        init32_kernel<Src1<InitJob32>><<<std::min<unsigned>(grid_small(std::max<int64_t>(x.Q, 64)),
+                                                            64u),
+                                         kSmallThreads, 0, s>>>(Src1<InitJob32>{j});
+        CK(cudaGetLastError());
+        launched(1);
+    }
+    // S1: the training envelopes, rows up to L_t + W (not past max_len)
+    if (!x.train_ready) {
+        EnvPlan<float> ep = plan_envelopes<float>(x.train, nullptr, x.N, x.max_len, Weff, w.env);
+        ep.job.off = x.train_off;
+        ep.job.E = x.max_len;
+        CK(set_envelope_smem<float>(ep.one_pass, ep.smem));
+        envelope_fns<float>(ep.one_pass).fn1<<<(unsigned)ep.blocks, kEnvelopeThreads, ep.smem, s>>>(
+            Src1<EnvJob<float>>{ep.job});
+        CK(cudaGetLastError());
+        launched(1);
+    }
+    t_stage = 1;
+    CK(tm.mark(1));
+    // S2: the safe bounds of all pairs and each query's first candidate
+    {
+        LbVarJob j{};
+        j.test = x.test; j.test_off = x.test_off; j.Q = x.Q;
+        j.train = x.train; j.train_off = x.train_off; j.env = w.env; j.E = x.max_len; j.N = x.N;
+        j.W = Weff; j.V = x.V; j.max_len = x.max_len;
+        j.keogh = (x.flags & NNDTW_KEOGH_BOUND) ? 1 : 0; j.safe = 1;
+        j.lb_lo = m.lb_lo; j.abs_slack = m.abs32;
+        j.lb_out = w.lb; j.seed_keys = w.seed; j.bad = w.counters + C_BADLEN;
+        CK(launch_lb_var(j, s));
+        launched(1);
+    }
+    t_stage = 2;
+    CK(tm.mark(2));
+    // S4 on each query's first candidate (no abandoning); its pairs are
+    // listed in the queue's storage, which the compaction fills afterwards
+    DtwJob32 base{};
+    base.test = x.test; base.train = x.train; base.L = x.max_len; base.W = Weff;
+    base.test_off = x.test_off; base.train_off = x.train_off;
+    base.dtw_lo = m.dtw_lo; base.dtw_hi = m.dtw_hi; base.abs32 = m.abs32;
+    base.bsf = w.bsf; base.cand = w.cand; base.cand_count = w.counters + C_CAND;
+    base.counters = cnt;
+    base.group = group_from_flags(x.flags);
+    if (base.group >= kRowsGroup) base.group = 0;   // (no row layout for unequal lengths)
+    {
+        CK(launch_seed_pairs(w.seed, x.Q, w.queue, w.counters + C_SEEDPAIRS, sms, s));
+        DtwJob32 j = base;
+        j.pairs = w.queue; j.count = w.counters + C_SEEDPAIRS; j.head = w.counters + C_SEEDHEAD;
+        j.abandon = 0;
+        j.group = dtw32_wide_group(Weff);
+        Dtw32Plan pl{};
+        CK(plan_dtw32_var(j, sms, &pl));
+        j.lanes = pl.lanes;
+        if (pl.blocks > 0) {
+            pl.fn1<<<(unsigned)pl.blocks, pl.threads, pl.smem, s>>>(Src1<DtwJob32>{j});
+            CK(cudaGetLastError());
+        }
+        launched(2);
+    }
+    t_stage = 3;
+    CK(tm.mark(3));
+    // S3: compaction against the upper bounds (pairs with a finite bound only)
+    for (int pass = 0; pass < 2; pass++) {
+        const dim3 gc = grid_compact(x.Q, x.N);
+        CompactJob<float> j{};
+        j.lb = w.lb; j.Q = x.Q; j.N = x.N; j.bsf = w.bsf; j.seed = w.seed;
+        j.ubof = UbOf<float>{m.dtw_hi, m.abs32};
+        j.no_prune = (x.flags & NNDTW_NO_PRUNE) ? 1 : 0;
+        j.finite_only = 1;
+        j.gx = (int)gc.x;
+        j.scatter = pass;
+        j.bcount = w.buckets; j.bcursor = w.buckets + kBuckets;
+        j.qcount = w.counters + C_QUEUE; j.queue = w.queue;
+        compact_kernel<float, Src1<CompactJob<float>>><<<gc.x * gc.y, kSmallThreads, 0, s>>>(
+            Src1<CompactJob<float>>{j});
+        CK(cudaGetLastError());
+        launched(1);
+    }
+    t_stage = 4;
+    CK(tm.mark(4));
+    // S4 on the survivors, with early abandoning
+    {
+        DtwJob32 j = base;
+        j.pairs = w.queue; j.count = w.counters + C_QUEUE; j.head = w.counters + C_HEAD;
+        j.abandon = (x.flags & NNDTW_NO_ABANDON) ? 0 : 1;
+        if (!(x.flags & NNDTW_NO_PRUNE)) {   // live pruning against the tightening bests
+            j.lb = w.lb;
+            j.lb_n = x.N;
+        }
+        Dtw32Plan pl{};
+        CK(plan_dtw32_var(j, sms, &pl));
+        j.lanes = pl.lanes;
+        if (pl.blocks > 0) {
+            pl.fn1<<<(unsigned)pl.blocks, pl.threads, pl.smem, s>>>(Src1<DtwJob32>{j});
+            CK(cudaGetLastError());
+        }
+        launched(1);
+    }
+    t_stage = 5;
+    CK(tm.mark(5));
+    // S5: near-tie recheck in FP64 and the final argmin
+    FinishJob32 f{};
+    f.cand = w.cand; f.ccount = w.counters + C_CAND; f.bsf = w.bsf;
+    f.lo = m.dtw_lo; f.hi = m.dtw_hi; f.abs32 = m.abs32;
+    f.rcount = w.rcount; f.exact = exact ? 1 : 0; f.rlist = w.rlist;
+    f.counters = w.counters; f.d64 = w.d64; f.best64 = w.best64;
+    f.bestidx = w.bestidx; f.Q = x.Q; f.labels = x.labels;
+    f.nn_idx = x.nn_idx; f.nn_label = x.nn_label; f.nn_dist = x.nn_dist;
+    const unsigned fb = (unsigned)finish_blocks(x.Q, x.N);
+    filter32_kernel<Src1<FinishJob32>><<<fb, kSmallThreads, 0, s>>>(Src1<FinishJob32>{f});
+    CK(cudaGetLastError());
+    collect32_kernel<Src1<FinishJob32>><<<fb, kSmallThreads, 0, s>>>(Src1<FinishJob32>{f});
+    CK(cudaGetLastError());
+    {
+        DtwJob64 r{};
+        r.test32 = x.test; r.train32 = x.train; r.L = x.max_len; r.W = Weff;
+        r.test_off = x.test_off; r.train_off = x.train_off;
+        r.pairs = w.rlist; r.count = w.counters + C_RECHECK; r.head = nullptr;
+        r.bsf64 = w.best64; r.out = w.d64; r.abandon = 0;
+        Dtw64Plan pl{};
+        CK(plan_dtw64(r, sms, &pl));
+        const long long want = exact ? x.Q : std::max<long long>(4, (x.Q + 7) / 8);
+        const long long blocks = std::min(pl.blocks, want);
+        if (blocks > 0) {
+            pl.fn1<<<(unsigned)blocks, pl.threads, pl.smem, s>>>(Src1<DtwJob64>{r});
+            CK(cudaGetLastError());
+        }
+    }
+    ties32_kernel<Src1<FinishJob32>><<<fb, kSmallThreads, 0, s>>>(Src1<FinishJob32>{f});
+    CK(cudaGetLastError());
+    launched(4);
+    t_stage = 6;
+    CK(tm.mark(6));
+    finalize32_kernel<Src1<FinishJob32>><<<grid_small(x.Q), kSmallThreads, 0, s>>>(
+        Src1<FinishJob32>{f});
+    CK(cudaGetLastError());
+    launched(1);
+    t_stage = 7;
+    CK(tm.mark(7));
+    if (stats || (x.flags & NNDTW_CHECK_FINITE)) {
+        unsigned long long h[C_COUNT];
+        CK(cudaMemcpyAsync(h, w.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((x.flags & NNDTW_CHECK_FINITE) && h[C_BADLEN]) return NNDTW_EINVAL;
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            stats->pairs = x.Q * x.N;
+            stats->lb_pruned = x.Q * x.N - (int64_t)h[C_SEEDPAIRS] - (int64_t)h[C_QUEUE];
+            stats->rechecked = (int64_t)h[C_RECHECK];
+            stats->recheck_queries = (int64_t)h[C_RQUERIES];
+            if (cnt) {
+                stats->dtw_started = (int64_t)h[C_STARTED];
+                stats->dtw_abandoned = (int64_t)h[C_ABANDONED];
+                stats->dtw_cells = (int64_t)h[C_CELLS];
+                stats->lb_pruned_live = (int64_t)h[C_LIVEPRUNED];
+            }
+        }
     }
     return NNDTW_OK;
 }
@@ -1065,7 +1282,7 @@ using namespace nndtw;
 
 extern "C" {
 
-int nn_dtw_version(void) { return 104; }
+int nn_dtw_version(void) { return 106; }
 
 int nn_dtw_stage_times(float *h_ms) {
     if (!h_ms || t_last_dev < 0) return NNDTW_EINVAL;
@@ -1236,6 +1453,144 @@ int dtw_windowed_ex(const float *d_test, const float *d_train, const int32_t *d_
     j.dtw_lo = m.dtw_lo; j.dtw_hi = m.dtw_hi; j.abs32 = m.abs32;
     j.head = nullptr;  // static assignment: pair count known here
     CK(launch_dtw32(j, device_sm_count(), (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
+// ------------------------------------------------------- unequal lengths
+
+static bool varlen_sizes_ok(int64_t N, int64_t Q, int max_len, int W, int V) {
+    return search_sizes_ok(N, Q, max_len, W, V);
+}
+
+int nn_dtw_build_envelopes_varlen(const float *d_train, const int64_t *d_train_off, int64_t N,
+                                  int max_len, int W, float *d_env, void *stream) {
+    if (N < 0 || max_len < 2 || max_len > NNDTW_MAX_L || W < 0) return NNDTW_EINVAL;
+    if (N == 0) return NNDTW_OK;
+    if (!d_train || !d_train_off || !d_env) return NNDTW_EINVAL;
+    const int Weff = W > max_len - 1 ? max_len - 1 : W;
+    EnvPlan<float> ep = plan_envelopes<float>(d_train, nullptr, N, max_len, Weff, d_env);
+    ep.job.off = reinterpret_cast<const long long *>(d_train_off);
+    ep.job.E = max_len;
+    CK(set_envelope_smem<float>(ep.one_pass, ep.smem));
+    envelope_fns<float>(ep.one_pass).fn1<<<(unsigned)ep.blocks, kEnvelopeThreads, ep.smem,
+                                           (cudaStream_t)stream>>>(Src1<EnvJob<float>>{ep.job});
+    CK(cudaGetLastError());
+    return NNDTW_OK;
+}
+
+int lb_enhanced_varlen(const float *d_test, const int64_t *d_test_off, int64_t Q,
+                       const float *d_train, const int64_t *d_train_off, const float *d_env,
+                       int64_t N, int max_len, int W, int V, unsigned flags, float *d_lb_out,
+                       void *stream) {
+    if (Q < 0 || N < 0 || max_len < 2 || max_len > NNDTW_MAX_L || W < 0 || V < 1)
+        return NNDTW_EINVAL;
+    if (flags & ~(unsigned)(NNDTW_LB_KEOGH | NNDTW_LB_SAFE)) return NNDTW_EINVAL;
+    if (Q == 0 || N == 0) return NNDTW_OK;
+    if (!d_test || !d_test_off || !d_train || !d_train_off || !d_env || !d_lb_out)
+        return NNDTW_EINVAL;
+    if ((double)Q * (double)((N + 63) / 64) > 2147483647.0) return NNDTW_EUNSUPPORTED;
+    const Margins m = make_margins(max_len);
+    LbVarJob j{};
+    j.test = d_test; j.test_off = reinterpret_cast<const long long *>(d_test_off); j.Q = Q;
+    j.train = d_train; j.train_off = reinterpret_cast<const long long *>(d_train_off);
+    j.env = d_env; j.E = max_len; j.N = N;
+    j.W = W > max_len - 1 ? max_len - 1 : W; j.V = V; j.max_len = max_len;
+    j.keogh = (flags & NNDTW_LB_KEOGH) ? 1 : 0; j.safe = (flags & NNDTW_LB_SAFE) ? 1 : 0;
+    j.lb_lo = m.lb_lo; j.abs_slack = m.abs32; j.lb_out = d_lb_out;
+    CK(launch_lb_var(j, (cudaStream_t)stream));
+    return NNDTW_OK;
+}
+
+int dtw_windowed_varlen(const float *d_test, const int64_t *d_test_off, const float *d_train,
+                        const int64_t *d_train_off, const int32_t *d_pairs, int64_t P,
+                        int max_len, int W, float *d_out, void *stream) {
+    if (P < 0 || max_len < 1 || max_len > NNDTW_MAX_L || W < 0) return NNDTW_EINVAL;
+    if (P == 0) return NNDTW_OK;
+    if (!d_test || !d_test_off || !d_train || !d_train_off || !d_pairs || !d_out)
+        return NNDTW_EINVAL;
+    DtwJob32 j{};
+    j.test = d_test; j.train = d_train; j.L = max_len; j.W = W > max_len - 1 ? max_len - 1 : W;
+    j.test_off = reinterpret_cast<const long long *>(d_test_off);
+    j.train_off = reinterpret_cast<const long long *>(d_train_off);
+    j.pairs = reinterpret_cast<const uint2 *>(d_pairs);
+    j.n_pairs = P;
+    j.out = d_out;
+    const Margins m = make_margins(max_len);
+    j.dtw_lo = m.dtw_lo; j.dtw_hi = m.dtw_hi; j.abs32 = m.abs32;
+    Dtw32Plan pl{};
+    CK(plan_dtw32_var(j, device_sm_count(), &pl));
+    j.lanes = pl.lanes;
+    if (pl.blocks > 0) {
+        pl.fn1<<<(unsigned)pl.blocks, pl.threads, pl.smem, (cudaStream_t)stream>>>(
+            Src1<DtwJob32>{j});
+        CK(cudaGetLastError());
+    }
+    return NNDTW_OK;
+}
+
+size_t nn_dtw_varlen_workspace_size(int64_t N, int64_t Q, int max_len, int W, int V) {
+    if (!varlen_sizes_ok(N, Q, max_len, W, V)) return 0;
+    return layout32(nullptr, N, chunk_queries(N, Q), max_len).bytes;
+}
+
+int nn_dtw_search_varlen(const float *d_train, const int64_t *d_train_off,
+                         const int32_t *d_train_labels, int64_t N, const float *d_test,
+                         const int64_t *d_test_off, int64_t Q, int max_len, int W, int V,
+                         unsigned flags, int32_t *d_nn_idx, int32_t *d_nn_label,
+                         double *d_nn_dist, void *d_workspace, size_t workspace_bytes,
+                         nndtw_stats *stats, void *stream) {
+    if (!varlen_sizes_ok(N, Q, max_len, W, V)) return NNDTW_EINVAL;
+    if (flags & (NNDTW_LEAVE_ONE_OUT | NNDTW_REVERSE | NNDTW_IMPROVED)) return NNDTW_EINVAL;
+    if (Q == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return NNDTW_OK;
+    }
+    if (!d_train || !d_train_off || !d_train_labels || !d_test || !d_test_off || !d_nn_idx ||
+        !d_nn_label || !d_nn_dist || !d_workspace)
+        return NNDTW_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return NNDTW_EINVAL;
+    const int64_t qc = chunk_queries(N, Q);
+    const Layout32 ws = layout32(d_workspace, N, qc, max_len);
+    if (workspace_bytes < ws.bytes) return NNDTW_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long *toff = reinterpret_cast<const long long *>(d_test_off);
+    const long long *off = reinterpret_cast<const long long *>(d_train_off);
+    reset_launch_counts();
+    if (flags & NNDTW_CHECK_FINITE) {
+        // value counts from the offset tables' last entries (waits for the stream)
+        long long tot[2] = {0, 0};
+        CK(cudaMemcpyAsync(&tot[0], off + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&tot[1], toff + Q, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemsetAsync(ws.counters + C_BAD, 0, sizeof(unsigned long long), s));
+        CK(cudaStreamSynchronize(s));
+        if (tot[0] < 0 || tot[1] < 0) return NNDTW_EINVAL;
+        int rc = check_finite<float>(d_train, tot[0], 1e15f, ws.counters + C_BAD, s);
+        if (rc) return rc;
+        rc = check_finite<float>(d_test, tot[1], 1e15f, ws.counters + C_BAD, s);
+        if (rc) return rc;
+        unsigned long long bad = 0;
+        CK(cudaMemcpyAsync(&bad, ws.counters + C_BAD, sizeof(bad), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (bad) return NNDTW_ENONFINITE;
+    }
+    const bool timing = (flags & NNDTW_TIME_STAGES) != 0;
+    StageTimer tm;
+    CK(tm.start(timing, s));
+    nndtw_stats total{};
+    for (int64_t q0 = 0; q0 < Q; q0 += qc) {
+        const int64_t m = Q - q0 < qc ? Q - q0 : qc;
+        SetVar x{};
+        x.train = d_train; x.train_off = off; x.labels = d_train_labels; x.N = N;
+        x.test = d_test; x.test_off = toff + q0; x.Q = m;
+        x.max_len = max_len; x.W = W; x.V = V; x.flags = flags;
+        x.nn_idx = d_nn_idx + q0; x.nn_label = d_nn_label + q0; x.nn_dist = d_nn_dist + q0;
+        x.ws = d_workspace; x.q_cap = qc; x.train_ready = q0 > 0;
+        nndtw_stats part{};
+        const int rc = run_var(x, stats != nullptr, timing, stats ? &part : nullptr, tm, s);
+        if (rc != NNDTW_OK) return rc;
+        if (stats) add_stats(&total, part);
+    }
+    if (stats) *stats = total;
     return NNDTW_OK;
 }
 
@@ -1541,6 +1896,92 @@ int nn_dtw_search_host(const float *h_train, const int32_t *h_train_labels, int6
     CK(cudaMemcpyAsync(h.labels, h_train_labels, sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
     int rc = nn_dtw_search(h.train, h.labels, N, h.test, Q, L, W, V, nullptr, flags, h.idx, h.lab,
                            h.dist, h.ws, h.ws_bytes, stats, stream);
+    if (rc != NNDTW_OK) return rc;
+    CK(cudaMemcpyAsync(h_nn_idx, h.idx, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h_nn_label, h.lab, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h_nn_dist, h.dist, sizeof(double) * Q, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NNDTW_OK;
+}
+
+namespace {
+// Device buffer of nn_dtw_search_varlen_host: the ragged sets (values and
+// offsets), labels, outputs, then the search's workspace.
+struct VarHostLayout {
+    float *train, *test;
+    int64_t *train_off, *test_off;
+    int32_t *labels, *idx, *lab;
+    double *dist;
+    void *ws;
+    size_t ws_bytes, bytes;
+};
+VarHostLayout var_host_layout(void *base, int64_t N, int64_t n_train_values, int64_t Q,
+                              int64_t n_test_values, int max_len, int W, int V) {
+    Carve c(base);
+    VarHostLayout h;
+    h.train = c.take<float>((size_t)n_train_values);
+    h.test = c.take<float>((size_t)n_test_values);
+    h.train_off = c.take<int64_t>((size_t)N + 1);
+    h.test_off = c.take<int64_t>((size_t)Q + 1);
+    h.labels = c.take<int32_t>(N);
+    h.idx = c.take<int32_t>(Q);
+    h.lab = c.take<int32_t>(Q);
+    h.dist = c.take<double>(Q);
+    h.ws_bytes = nn_dtw_varlen_workspace_size(N, Q, max_len, W, V);
+    h.ws = c.take<unsigned char>(h.ws_bytes);
+    h.bytes = c.off + 256;
+    return h;
+}
+
+// Offsets start at 0, never decrease, and every length lies in [2, max_len].
+bool host_offsets_ok(const int64_t *off, int64_t n, int max_len) {
+    if (off[0] != 0) return false;
+    for (int64_t k = 0; k < n; k++) {
+        const int64_t len = off[k + 1] - off[k];
+        if (len < 2 || len > max_len) return false;
+    }
+    return true;
+}
+}  // namespace
+
+size_t nn_dtw_varlen_host_buffer_size(const int64_t *h_train_off, int64_t N,
+                                      const int64_t *h_test_off, int64_t Q, int max_len, int W,
+                                      int V) {
+    if (!varlen_sizes_ok(N, Q, max_len, W, V) || !h_train_off || !h_test_off) return 0;
+    return var_host_layout(nullptr, N, h_train_off[N], Q, h_test_off[Q], max_len, W, V).bytes;
+}
+
+int nn_dtw_search_varlen_host(const float *h_train, const int64_t *h_train_off,
+                              const int32_t *h_train_labels, int64_t N, const float *h_test,
+                              const int64_t *h_test_off, int64_t Q, int max_len, int W, int V,
+                              unsigned flags, int32_t *h_nn_idx, int32_t *h_nn_label,
+                              double *h_nn_dist, void *d_buffer, size_t buffer_bytes,
+                              nndtw_stats *stats, void *stream) {
+    if (!varlen_sizes_ok(N, Q, max_len, W, V)) return NNDTW_EINVAL;
+    if (Q == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return NNDTW_OK;
+    }
+    if (!h_train || !h_train_off || !h_train_labels || !h_test || !h_test_off || !h_nn_idx ||
+        !h_nn_label || !h_nn_dist || !d_buffer)
+        return NNDTW_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_buffer) & 255u) return NNDTW_EINVAL;
+    if (!host_offsets_ok(h_train_off, N, max_len) || !host_offsets_ok(h_test_off, Q, max_len))
+        return NNDTW_EINVAL;
+    const int64_t nt = h_train_off[N], nq = h_test_off[Q];
+    const VarHostLayout h = var_host_layout(d_buffer, N, nt, Q, nq, max_len, W, V);
+    if (buffer_bytes < h.bytes) return NNDTW_ENOSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h.train, h_train, sizeof(float) * nt, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h.train_off, h_train_off, sizeof(int64_t) * (N + 1),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h.test, h_test, sizeof(float) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h.test_off, h_test_off, sizeof(int64_t) * (Q + 1),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h.labels, h_train_labels, sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+    int rc = nn_dtw_search_varlen(h.train, h.train_off, h.labels, N, h.test, h.test_off, Q,
+                                  max_len, W, V, flags, h.idx, h.lab, h.dist, h.ws, h.ws_bytes,
+                                  stats, stream);
     if (rc != NNDTW_OK) return rc;
     CK(cudaMemcpyAsync(h_nn_idx, h.idx, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h_nn_label, h.lab, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));

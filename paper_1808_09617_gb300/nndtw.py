@@ -104,7 +104,8 @@ class Stats(ctypes.Structure):
                 ("dtw_started", ctypes.c_int64), ("dtw_abandoned", ctypes.c_int64),
                 ("dtw_cells", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("recheck_queries", ctypes.c_int64), ("seed_cells", ctypes.c_int64),
-                ("lb_pruned_reverse", ctypes.c_int64), ("lb_pruned_improved", ctypes.c_int64)]
+                ("lb_pruned_reverse", ctypes.c_int64), ("lb_pruned_improved", ctypes.c_int64),
+                ("lb_pruned_live", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -149,6 +150,14 @@ def _declare(lib):
                                _vp, _sz, _vp, _vp],
         "nn_dtw_search_noalloc": [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _uint, _vp,
                                   _vp, _vp, _vp, _vp],
+        "nn_dtw_build_envelopes_varlen": [_vp, _vp, _i64, _int, _int, _vp, _vp],
+        "lb_enhanced_varlen": [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _int, _int, _int, _uint, _vp,
+                               _vp],
+        "dtw_windowed_varlen": [_vp, _vp, _vp, _vp, _vp, _i64, _int, _int, _vp, _vp],
+        "nn_dtw_search_varlen": [_vp, _vp, _vp, _i64, _vp, _vp, _i64, _int, _int, _int, _uint,
+                                 _vp, _vp, _vp, _vp, _sz, _vp, _vp],
+        "nn_dtw_search_varlen_host": [_vp, _vp, _vp, _i64, _vp, _vp, _i64, _int, _int, _int,
+                                      _uint, _vp, _vp, _vp, _vp, _sz, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -158,6 +167,10 @@ def _declare(lib):
     lib.nn_dtw_workspace_size.restype = _sz
     lib.nn_dtw_host_buffer_size.argtypes = [_i64, _i64, _int, _int, _int]
     lib.nn_dtw_host_buffer_size.restype = _sz
+    lib.nn_dtw_varlen_workspace_size.argtypes = [_i64, _i64, _int, _int, _int]
+    lib.nn_dtw_varlen_workspace_size.restype = _sz
+    lib.nn_dtw_varlen_host_buffer_size.argtypes = [_vp, _i64, _vp, _i64, _int, _int, _int]
+    lib.nn_dtw_varlen_host_buffer_size.restype = _sz
     lib.nn_dtw_strerror.argtypes = [_int]
     lib.nn_dtw_strerror.restype = ctypes.c_char_p
     lib.nn_dtw_last_cuda_error.argtypes = []
@@ -734,6 +747,191 @@ class BatchedHostSearch:
                                                   _stream(stream)),
                    "nn_dtw_search_batched_host")
         return self.outs
+
+
+# ------------------------------------------------------------ unequal lengths
+
+@dataclass
+class Ragged:
+    """A set of series of unequal lengths on the device: series k is
+    ``values[offsets[k]:offsets[k+1]]`` (float32 values, int64 offsets with
+    n+1 entries); ``max_len`` is the longest length."""
+    values: object
+    offsets: object
+    max_len: int
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets.shape[0]) - 1
+
+
+def ragged(series, device="cuda") -> Ragged:
+    """Pack a list of 1-D series into a Ragged set on ``device``."""
+    import numpy as np
+    import torch
+    xs = [np.ascontiguousarray(np.asarray(x, dtype=np.float32).ravel()) for x in series]
+    off = np.zeros(len(xs) + 1, np.int64)
+    off[1:] = np.cumsum([x.shape[0] for x in xs])
+    vals = np.concatenate(xs) if xs else np.zeros(0, np.float32)
+    return Ragged(torch.from_numpy(vals).to(device), torch.from_numpy(off).to(device),
+                  int(max((x.shape[0] for x in xs), default=0)))
+
+
+def _ragged_ptrs(r: Ragged, name: str):
+    import torch
+    n = r.n
+    if n < 0:
+        raise ValueError(f"{name}.offsets must have at least one entry")
+    return (_dev(r.values, torch.float32, f"{name}.values", 1),
+            _dev(r.offsets, torch.int64, f"{name}.offsets", shape=(n + 1,)))
+
+
+def nn_dtw_build_envelopes_varlen(train: Ragged, W: int, env=None, max_len: int | None = None,
+                                  stream=None):
+    """Envelope rows of every series of a ragged set (rows i < min(L_t + W,
+    max_len) of each [max_len, 2] block): tensor [N, max_len, 2]."""
+    import torch
+    lib = load()
+    ml = int(max_len or train.max_len)
+    N = train.n
+    if env is None:
+        env = torch.empty((N, ml, 2), dtype=torch.float32, device=train.values.device)
+    v, o = _ragged_ptrs(train, "train")
+    with _on([train.values, train.offsets, env], stream):
+        _check(lib.nn_dtw_build_envelopes_varlen(
+            v, o, N, ml, int(W), _dev(env, torch.float32, "env", shape=(N, ml, 2)),
+            _stream(stream)), "nn_dtw_build_envelopes_varlen")
+    return env
+
+
+def lb_enhanced_varlen(test: Ragged, train: Ragged, env, W: int, V: int, keogh: bool = False,
+                       safe: bool = False, out=None, max_len: int | None = None, stream=None):
+    """LB_Enhanced^V (or LB_Keogh) of every pair of two ragged sets, unequal
+    lengths allowed (+inf without a warping path): tensor [Q, N]."""
+    import torch
+    lib = load()
+    ml = int(max_len or max(test.max_len, train.max_len))
+    Q, N = test.n, train.n
+    if out is None:
+        out = torch.empty((Q, N), dtype=torch.float32, device=test.values.device)
+    flags = (LB_KEOGH if keogh else 0) | (LB_SAFE if safe else 0)
+    tv, to = _ragged_ptrs(test, "test")
+    bv, bo = _ragged_ptrs(train, "train")
+    with _on([test.values, test.offsets, train.values, train.offsets, env, out], stream):
+        _check(lib.lb_enhanced_varlen(
+            tv, to, Q, bv, bo, _dev(env, torch.float32, "env", shape=(N, ml, 2)), N, ml, int(W),
+            int(V), flags, _dev(out, torch.float32, "out", shape=(Q, N)), _stream(stream)),
+            "lb_enhanced_varlen")
+    return out
+
+
+def dtw_windowed_varlen(test: Ragged, train: Ragged, pairs, W: int, out=None,
+                        max_len: int | None = None, stream=None):
+    """FP32 DTW_W of explicit (q, t) pairs of two ragged sets: tensor [P]."""
+    import torch
+    lib = load()
+    ml = int(max_len or max(test.max_len, train.max_len))
+    P = pairs.shape[0]
+    if out is None:
+        out = torch.empty((P,), dtype=torch.float32, device=test.values.device)
+    tv, to = _ragged_ptrs(test, "test")
+    bv, bo = _ragged_ptrs(train, "train")
+    with _on([test.values, train.values, pairs, out], stream):
+        _check(lib.dtw_windowed_varlen(
+            tv, to, bv, bo, _dev(pairs, torch.int32, "pairs", shape=(P, 2)), P, ml, int(W),
+            _dev(out, torch.float32, "out", shape=(P,)), _stream(stream)), "dtw_windowed_varlen")
+    return out
+
+
+def nn_dtw_varlen_workspace_size(N: int, Q: int, max_len: int, W: int, V: int) -> int:
+    return int(load().nn_dtw_varlen_workspace_size(N, Q, max_len, W, V))
+
+
+def nn_dtw_search_varlen(train: Ragged, labels, test: Ragged, W: int, V: int, flags: int = 0,
+                         workspace=None, out=None, stats: bool = False,
+                         max_len: int | None = None, stream=None) -> SearchResult:
+    """Exact 1-NN under DTW_W for series of unequal lengths (index -1,
+    label -1, distance +inf for a query with no training series inside the
+    window)."""
+    import torch
+    lib = load()
+    ml = int(max_len or max(test.max_len, train.max_len))
+    N, Q = train.n, test.n
+    need = lib.nn_dtw_varlen_workspace_size(N, Q, ml, int(W), int(V))
+    if need == 0:
+        raise NnDtwError(EINVAL, "nn_dtw_varlen_workspace_size")
+    dev = train.values.device
+    if workspace is None:
+        workspace = torch.empty((need,), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = (torch.empty((Q,), dtype=torch.int32, device=dev),
+               torch.empty((Q,), dtype=torch.int32, device=dev),
+               torch.empty((Q,), dtype=torch.float64, device=dev))
+    idx, lab, dist = out
+    st = Stats() if stats else None
+    tv, to = _ragged_ptrs(test, "test")
+    bv, bo = _ragged_ptrs(train, "train")
+    with _on([train.values, train.offsets, labels, test.values, test.offsets, idx, lab, dist,
+              workspace], stream):
+        _check(lib.nn_dtw_search_varlen(
+            bv, bo, _dev(labels, torch.int32, "labels", shape=(N,)), N, tv, to, Q, ml, int(W),
+            int(V), int(flags), _dev(idx, torch.int32, "nn_idx", shape=(Q,)),
+            _dev(lab, torch.int32, "nn_label", shape=(Q,)),
+            _dev(dist, torch.float64, "nn_dist", shape=(Q,)),
+            _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
+            ctypes.byref(st) if st is not None else None, _stream(stream)),
+            "nn_dtw_search_varlen")
+    return SearchResult(idx, lab, dist, st.as_dict() if st is not None else None)
+
+
+class VarlenHostSearch:
+    """nn_dtw_search_varlen_host with its device buffer allocated once: the
+    unequal-length search end to end on host arrays (values float32,
+    offsets int64 with n+1 entries, labels int32; pinned memory makes the
+    copies faster).  Results go to host arrays."""
+
+    def __init__(self, train_vals, train_off, labels, test_vals, test_off, W: int, V: int,
+                 max_len: int, flags: int = 0, device=None):
+        import torch
+        self.lib = load()
+        for a, dt, name in ((train_vals, np.float32, "train values"),
+                            (train_off, np.int64, "train offsets"), (labels, np.int32, "labels"),
+                            (test_vals, np.float32, "test values"),
+                            (test_off, np.int64, "test offsets")):
+            _host(a, dt, name)
+        self.tv, self.to, self.lab, self.qv, self.qo = (train_vals, train_off, labels, test_vals,
+                                                        test_off)
+        self.N, self.Q = self.to.shape[0] - 1, self.qo.shape[0] - 1
+        if self.lab.shape != (self.N,):
+            raise ValueError(f"labels must have shape ({self.N},)")
+        if self.to[-1] != self.tv.shape[0] or self.qo[-1] != self.qv.shape[0]:
+            raise ValueError("offsets must end at the number of values")
+        self.W, self.V, self.max_len, self.flags = int(W), int(V), int(max_len), int(flags)
+        need = self.lib.nn_dtw_varlen_host_buffer_size(
+            _vp(self.to.ctypes.data), self.N, _vp(self.qo.ctypes.data), self.Q, self.max_len,
+            self.W, self.V)
+        if need == 0:
+            raise NnDtwError(EINVAL, "nn_dtw_varlen_host_buffer_size")
+        self.buf = torch.empty((need,), dtype=torch.uint8, device=device or "cuda")
+        self.idx = np.empty(self.Q, np.int32)
+        self.nlab = np.empty(self.Q, np.int32)
+        self.dist = np.empty(self.Q, np.float64)
+
+    def bytes_per_call(self):
+        """(host-to-device, device-to-host) bytes copied by one call."""
+        h2d = self.tv.nbytes + self.to.nbytes + self.qv.nbytes + self.qo.nbytes + self.lab.nbytes
+        return h2d, self.idx.nbytes + self.nlab.nbytes + self.dist.nbytes
+
+    def __call__(self, stream=None):
+        with _on([self.buf], stream):
+            _check(self.lib.nn_dtw_search_varlen_host(
+                _vp(self.tv.ctypes.data), _vp(self.to.ctypes.data), _vp(self.lab.ctypes.data),
+                self.N, _vp(self.qv.ctypes.data), _vp(self.qo.ctypes.data), self.Q,
+                self.max_len, self.W, self.V, self.flags, _vp(self.idx.ctypes.data),
+                _vp(self.nlab.ctypes.data), _vp(self.dist.ctypes.data),
+                _vp(self.buf.data_ptr()), self.buf.numel(), None, _stream(stream)),
+                "nn_dtw_search_varlen_host")
+        return self.idx, self.nlab, self.dist
 
 
 def nn_dtw_stage_times() -> dict:

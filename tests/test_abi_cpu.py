@@ -128,3 +128,73 @@ def test_binding_requires_one_device():
         nndtw.one_device([torch.device("cpu")])
     with pytest.raises(ValueError):
         nndtw.one_device([])
+
+
+def test_varlen_arguments_rejected_before_cuda(clib):
+    """The unequal-length entry points check sizes, pointers, flags and the
+    workspace before any CUDA call."""
+    from paper_1808_09617_gb300 import nndtw
+    vp = ctypes.c_void_p
+    ws = nndtw.nn_dtw_varlen_workspace_size(50, 20, 128, 12, 5)
+    assert ws > 50 * 20 * 4
+    assert nndtw.nn_dtw_varlen_workspace_size(0, 20, 128, 12, 5) == 0
+    assert nndtw.nn_dtw_varlen_workspace_size(50, 20, 1, 12, 5) == 0
+    assert nndtw.nn_dtw_varlen_workspace_size(50, 20, nndtw.NNDTW_MAX_L + 1, 12, 5) == 0
+    assert nndtw.nn_dtw_varlen_workspace_size(50, 20, 128, -1, 5) == 0
+    args = lambda **kw: [kw.get("train", vp(8)), kw.get("toff", vp(8)), vp(8),
+                         kw.get("N", 50), vp(8), vp(8), kw.get("Q", 20),
+                         kw.get("max_len", 128), kw.get("W", 12), kw.get("V", 5),
+                         kw.get("flags", 0), vp(8), vp(8), vp(8), kw.get("ws", vp(256)),
+                         kw.get("ws_bytes", ws), None, None]
+    f = clib.nn_dtw_search_varlen
+    assert f(*args(N=0)) == nndtw.EINVAL
+    assert f(*args(train=None)) == nndtw.EINVAL
+    assert f(*args(toff=None)) == nndtw.EINVAL
+    assert f(*args(max_len=1)) == nndtw.EINVAL
+    assert f(*args(W=-2)) == nndtw.EINVAL
+    assert f(*args(V=0)) == nndtw.EINVAL
+    assert f(*args(ws=vp(257))) == nndtw.EINVAL
+    assert f(*args(ws_bytes=ws - 1)) == nndtw.ENOSPACE
+    for bad in (nndtw.LEAVE_ONE_OUT, nndtw.REVERSE, nndtw.IMPROVED):
+        assert f(*args(flags=bad)) == nndtw.EINVAL
+    assert f(*args(Q=0)) == nndtw.OK
+    assert clib.nn_dtw_build_envelopes_varlen(None, vp(8), 3, 16, 2, vp(8), None) == nndtw.EINVAL
+    assert clib.nn_dtw_build_envelopes_varlen(vp(8), vp(8), 0, 16, 2, vp(8), None) == nndtw.OK
+    assert clib.nn_dtw_build_envelopes_varlen(vp(8), vp(8), 3, 1, 2, vp(8), None) == nndtw.EINVAL
+    assert clib.lb_enhanced_varlen(vp(8), vp(8), 2, vp(8), vp(8), vp(8), 2, 16, 2, 0, 0, vp(8),
+                                   None) == nndtw.EINVAL
+    assert clib.lb_enhanced_varlen(vp(8), vp(8), 2, vp(8), vp(8), vp(8), 2, 16, 2, 1,
+                                   nndtw.LB_NEW, vp(8), None) == nndtw.EINVAL
+    assert clib.dtw_windowed_varlen(vp(8), vp(8), vp(8), vp(8), vp(8), -1, 16, 2, vp(8),
+                                    None) == nndtw.EINVAL
+    assert clib.dtw_windowed_varlen(vp(8), vp(8), vp(8), vp(8), vp(8), 0, 16, 2, vp(8),
+                                    None) == nndtw.OK
+
+
+def test_varlen_host_entry_checks_offsets_before_any_copy(clib):
+    """The host-buffer unequal-length search checks its offset tables on the
+    host: a length outside [2, max_len] or a table not starting at 0 is
+    rejected before any copy or CUDA call."""
+    import numpy as np
+    from paper_1808_09617_gb300 import nndtw
+    vp = ctypes.c_void_p
+    good = np.array([0, 5, 9, 15], np.int64)
+    qgood = np.array([0, 6, 12], np.int64)
+    assert clib.nn_dtw_varlen_host_buffer_size(vp(good.ctypes.data), 3, vp(qgood.ctypes.data),
+                                               2, 8, 2, 2) > 0
+    assert clib.nn_dtw_varlen_host_buffer_size(None, 3, vp(qgood.ctypes.data), 2, 8, 2, 2) == 0
+    vals = np.zeros(64, np.float32)
+    lab = np.zeros(3, np.int32)
+    out_i = np.zeros(2, np.int32)
+    out_d = np.zeros(2, np.float64)
+
+    def call(off, qoff, max_len=8):
+        return clib.nn_dtw_search_varlen_host(
+            vp(vals.ctypes.data), vp(off.ctypes.data), vp(lab.ctypes.data), 3,
+            vp(vals.ctypes.data), vp(qoff.ctypes.data), 2, max_len, 2, 2, 0,
+            vp(out_i.ctypes.data), vp(out_i.ctypes.data), vp(out_d.ctypes.data), vp(256),
+            1 << 30, None, None)
+    assert call(np.array([0, 5, 6, 15], np.int64), qgood) == nndtw.EINVAL   # length 1
+    assert call(good, np.array([0, 6, 15], np.int64)) == nndtw.EINVAL        # longer than 8
+    assert call(np.array([1, 5, 9, 15], np.int64), qgood) == nndtw.EINVAL   # not from 0
+    assert call(good, np.array([0, 7, 5], np.int64)) == nndtw.EINVAL         # decreasing

@@ -128,7 +128,10 @@ def test_search_improved_bound(lib, orc, fp64):
     assert s_on["lb_pruned_improved"] > 0 and s_off["lb_pruned_improved"] == 0
     assert s_on["lb_pruned_reverse"] == 0
     assert s_on["lb_pruned"] == s_off["lb_pruned"]
-    assert s_on["dtw_started"] + s_on["lb_pruned_improved"] == s_off["dtw_started"]
+    # every queued pair is dropped by the second stage, dropped unstarted by
+    # its bound against the live best, or started
+    assert (s_on["dtw_started"] + s_on["lb_pruned_live"] + s_on["lb_pruned_improved"]
+            == s_off["dtw_started"] + s_off["lb_pruned_live"])
 
 
 @pytest.mark.parametrize("fp64", [False, True])
@@ -145,7 +148,8 @@ def test_search_improved_with_reverse(lib, orc, fp64):
     s, s0 = both[3], off[3]
     dropped = s["lb_pruned_improved"] + s["lb_pruned_reverse"]
     assert s["lb_pruned_improved"] > 0
-    assert s["dtw_started"] + dropped == s0["dtw_started"]
+    assert (s["dtw_started"] + s["lb_pruned_live"] + dropped
+            == s0["dtw_started"] + s0["lb_pruned_live"])
 
 
 @pytest.mark.parametrize("L,W,V", [(160, 40, 4), (160, 159, 3), (96, 0, 2), (600, 60, 5),

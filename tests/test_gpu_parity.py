@@ -394,7 +394,8 @@ def test_search_reverse_bound(lib, orc, fp64):
     off = _check_search(lib, orc, train, labels, test, ds.W, 5, flags=lib.NO_REVERSE, brute=brute)
     assert on["lb_pruned_reverse"] > 0 and off["lb_pruned_reverse"] == 0
     assert on["lb_pruned"] == off["lb_pruned"]
-    assert on["dtw_started"] + on["lb_pruned_reverse"] == off["dtw_started"]
+    assert (on["dtw_started"] + on["lb_pruned_live"] + on["lb_pruned_reverse"]
+            == off["dtw_started"] + off["lb_pruned_live"])
 
 
 @pytest.mark.parametrize("g", [2, 8, 32, "rows", "rows16", "rows8"])
@@ -414,7 +415,8 @@ def test_search_reverse_bound_layouts(lib, orc, g):
     off = _check_search(lib, orc, train, labels, test, W, 4, flags=lib.DTW_GROUP(grp) | lib.NO_REVERSE,
                         brute=brute)
     assert on["lb_pruned_reverse"] > 0 and off["lb_pruned_reverse"] == 0
-    assert on["dtw_started"] + on["lb_pruned_reverse"] == off["dtw_started"]
+    assert (on["dtw_started"] + on["lb_pruned_live"] + on["lb_pruned_reverse"]
+            == off["dtw_started"] + off["lb_pruned_live"])
 
 
 def test_search_reverse_bound_defaults(lib, orc):
