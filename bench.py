@@ -561,8 +561,14 @@ def run_varlen(args):
             torch.empty(Q, dtype=torch.float64, device=dev))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuned = 0
+    if not args.no_tune:
+        from paper_1808_09617_gb300 import autotune
+        tuned = autotune.tune_search_varlen(train, labels, test, ds.W, ds.V, workspace=ws,
+                                            out=outs)
     run = lambda flags=nndtw.TIME_STAGES, stats=False: nndtw.nn_dtw_search_varlen(
-        train, labels, test, ds.W, ds.V, flags=flags, workspace=ws, out=outs, stats=stats)
+        train, labels, test, ds.W, ds.V, flags=flags | tuned, workspace=ws, out=outs,
+        stats=stats)
     counted = run(flags=0, stats=True).stats          # work counters (slower: not timed)
     for _ in range(args.warmup):
         flush.zero_()
@@ -629,10 +635,12 @@ def run_varlen(args):
             "config": {"workload": f"unequal lengths: train {N} x test {Q}, lengths "
                                    f"{ds.extra['L0'] - ds.extra['dL']}..{ds.extra['L0'] + ds.extra['dL']}, "
                                    f"W={ds.W}, V={ds.V}, float32",
-                       "l2": "flushed before every step (256 MiB write, outside the events)"},
+                       "l2": "flushed before every step (256 MiB write, outside the events)",
+                       "autotuned_dtw_group": (tuned >> 8) and 1 << (((tuned >> 8) & 7) - 1)},
             "roofline": roof, "stage_ms": stage_ms,
-            "pruning": {k: counted[k] for k in ("pairs", "lb_pruned", "dtw_started",
-                                                "dtw_abandoned", "dtw_cells", "rechecked")},
+            "pruning": {k: counted[k] for k in ("pairs", "lb_pruned", "lb_pruned_live",
+                                                "dtw_started", "dtw_abandoned", "dtw_cells",
+                                                "rechecked")},
             "no_neighbour_queries": int((idx < 0).sum()),
             "e2e": {"value": Q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
@@ -1025,6 +1033,7 @@ def main():
                         "lb_pruned_frac": sum(c["lb_pruned"] for c in counts) / pairs,
                         "lb_pruned_reverse": sum(c["lb_pruned_reverse"] for c in counts),
                         "lb_pruned_improved": sum(c["lb_pruned_improved"] for c in counts),
+                        "lb_pruned_live": sum(c["lb_pruned_live"] for c in counts),
                         "dtw_started": sum(c["dtw_started"] for c in counts),
                         "dtw_abandoned": sum(c["dtw_abandoned"] for c in counts),
                         "dtw_cells": main_cells + seed_cells,

@@ -162,3 +162,42 @@ def tune_search_flags(train, labels, test, W: int, V: int, reps: int = 3,
     with _lock:
         _mem[k] = best
     return base | best
+
+
+def tune_search_varlen(train, labels, test, W: int, V: int, workspace=None, out=None,
+                       reps: int = 3) -> int:
+    """Search flags for the unequal-length search (``nndtw.Ragged`` sets):
+    the fastest lanes-per-pair choice of its diagonal DTW kernel (0 when the
+    window has none to choose).  Results never depend on it."""
+    import torch
+    ml = max(train.max_len, test.max_len)
+    groups = admissible_groups(min(W, ml - 1))
+    if len(groups) < 2:
+        return 0
+    N, Q = train.n, test.n
+    dev = train.values.device
+    if workspace is None:
+        workspace = torch.empty(nndtw.nn_dtw_varlen_workspace_size(N, Q, ml, W, V),
+                                dtype=torch.uint8, device=dev)
+    if out is None:
+        out = (torch.empty(Q, dtype=torch.int32, device=dev),
+               torch.empty(Q, dtype=torch.int32, device=dev),
+               torch.empty(Q, dtype=torch.float64, device=dev))
+    run = lambda f: nndtw.nn_dtw_search_varlen(train, labels, test, W, V, flags=f,
+                                               workspace=workspace, out=out)
+    best, best_ms = 0, float("inf")
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for g in groups:
+        f = nndtw.DTW_GROUP(g)
+        run(f)
+        times = []
+        for _ in range(reps):
+            s.record()
+            run(f)
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+        ms = sorted(times)[len(times) // 2]
+        if ms < best_ms:
+            best, best_ms = f, ms
+    return best

@@ -15,21 +15,27 @@
 // B's envelope rows come from the ragged envelope kernel (rows up to
 // L_B + W, stride E).  With L_A = L_B this is Eq. 7 / Algorithm 1.
 //
-// One CTA of 256 threads takes one query (staged in shared memory) and
-// kVarChunk training series; each warp computes one pair at a time, its
-// lanes striding over the bridge rows (coalesced envelope loads, the query
-// read from shared memory) and, for the bands, one band per lane.  A pair's
-// value is summed per lane and then across the warp, at most 2 L + 16
-// roundings on any chain, the margin the caller's lb_lo covers.  The CTA's
-// smallest (bound, index) key of the query's feasible pairs is merged into
-// seed_keys[q] with one atomic per warp: the query's first candidate
-// (the Euclidean distance being undefined for unequal lengths).
+// One CTA of 256 threads takes QB queries (staged in shared memory) and
+// kVarChunk training series, a warp one training series at a time against
+// all QB queries: its lanes stride over the bridge rows, each envelope row
+// loaded once (coalesced) and applied to the QB queries, so a row is read
+// from L2 once per QB pairs.  The rows every pair shares, V .. L_A - V, run
+// without per-pair tests, up to the shortest query's end first and then
+// with a per-query row limit; the ends, the bands and (for series shorter
+// than 2V) the bridge rows between n and V are computed one (query, band)
+// per lane and added through shared memory.  A pair's value is summed per
+// lane and then across the warp, at most 2 L + 16 roundings on any chain,
+// the margin the caller's lb_lo covers.  Each query's smallest (bound,
+// index) key among its feasible pairs is merged into seed_keys[q]: the
+// query's first candidate (the Euclidean distance being undefined for
+// unequal lengths).
 #include "internal.cuh"
 
 namespace nndtw {
 namespace {
 
-constexpr int kVarThreads = 256, kVarChunk = 64;
+constexpr int kVarThreads = 256, kVarWarps = kVarThreads / 32, kVarChunk = 64;
+constexpr int kBandStage = 32;   // B values staged at each end for the band tasks
 
 __device__ __forceinline__ float sqd(float a, float b) {
     const float d = a - b;
@@ -40,82 +46,209 @@ __device__ __forceinline__ bool in_window(int i, int j, int W) {
     return i - j <= W && j - i <= W;
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// acc + the LB_Keogh term of a against envelope row e (one fused rounding)
+__device__ __forceinline__ float keogh_acc(float acc, float a, float2 e) {
+    const float d = max3f(a - e.x, e.y - a, 0.f);
+    return fmaf(d, d, acc);
+}
+
+// The part of pair (A, B)'s bound outside the shared bridge rows
+// [V, L_A - V): the ends, bands i = 2..n of both corners (1-based), and the
+// bridge rows [n, V) and [L_A - V, L_A - n) when n < V.  Band b of the task
+// (0-based, b < V) contributes band b+1; task b = 0 also the extra rows.
+// hd[x] = B[x] and tl[x] = B[L_B - 1 - x] for x < kBandStage (staged), else
+// read from B.
+__device__ float outer_part(const float *A, int LA, const float *B, const float *hd,
+                            const float *tl, int LB, const float2 *env, int W, int V, int n,
+                            int b) {
+    auto head = [&](int x) { return x < kBandStage ? hd[x] : B[x]; };
+    auto tail = [&](int x) { return x < kBandStage ? tl[x] : B[LB - 1 - x]; };
+    float v = 0.f;
+    if (b < n) {
+        const int i = b + 1;
+        if (i == 1) {
+            v = sqd(A[0], head(0)) + sqd(A[LA - 1], tail(0));
+        } else {
+            const float bi = head(i - 1), bti = tail(i - 1);
+            float mL = sqd(A[i - 1], bi);
+            float mR = sqd(A[LA - i], bti);
+            for (int j = 1; j < i; j++) {
+                if (in_window(i, j, W)) {
+                    mL = fminf(mL, sqd(A[i - 1], head(j - 1)));
+                    mL = fminf(mL, sqd(A[j - 1], bi));
+                }
+                if (in_window(LA - i + 1, LB - j + 1, W)) mR = fminf(mR, sqd(A[LA - i], tail(j - 1)));
+                if (in_window(LA - j + 1, LB - i + 1, W)) mR = fminf(mR, sqd(A[LA - j], bti));
+            }
+            v = mL + mR;
+        }
+    }
+    if (b == 0 && n < V) {
+        // bridge rows the shared loop leaves out (short series)
+        const int lo_end = V < LA - n ? V : LA - n;
+        for (int i = n; i < lo_end; i++) v = keogh_acc(v, A[i], env[i]);
+        for (int i = (LA - V > lo_end ? LA - V : lo_end); i < LA - n; i++)
+            v = keogh_acc(v, A[i], env[i]);
+    }
+    return v;
+}
+
+template <int QB>
 __global__ void __launch_bounds__(kVarThreads) lb_var_kernel(const LbVarJob job) {
-    extern __shared__ __align__(16) float As[];
+    extern __shared__ __align__(16) float As[];   // [QB][max_len]
+    __shared__ float bsum[kVarWarps][QB];
+    __shared__ float bends[kVarWarps][2][kBandStage];   // B's first and last values
+    __shared__ unsigned long long sbest[QB];
+    __shared__ int sLA[QB];
     const int chunks = (int)((job.N + kVarChunk - 1) / kVarChunk);
-    const int64_t q = (int64_t)(blockIdx.x / chunks);
+    const int64_t q0 = (int64_t)(blockIdx.x / chunks) * QB;
     const int64_t t_begin = (int64_t)(blockIdx.x % chunks) * kVarChunk;
     const int64_t t_end = t_begin + kVarChunk < job.N ? t_begin + kVarChunk : job.N;
-    const int W = job.W, V = job.V;
+    const int W = job.W, V = job.keogh ? 0 : job.V, ML = job.max_len;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float INF = inf_of<float>();
+    const unsigned FULL = 0xffffffffu;
 
-    const long long a0 = job.test_off[q];
-    const int LA = (int)(job.test_off[q + 1] - a0);
-    const bool qok = LA >= 2 && LA <= job.max_len;
-    if (qok)
-        for (int i = threadIdx.x; i < LA; i += kVarThreads) As[i] = job.test[a0 + i];
-    else if (threadIdx.x == 0 && t_begin == 0 && job.bad)
-        atomicAdd(job.bad, 1ull);
+    // the block's queries: lengths (0 = none or out of range) and values
+    if (threadIdx.x < QB) {
+        const int64_t q = q0 + threadIdx.x;
+        int la = 0;
+        if (q < job.Q) {
+            la = (int)(job.test_off[q + 1] - job.test_off[q]);
+            if (la < 2 || la > ML) {
+                if (t_begin == 0 && job.bad) atomicAdd(job.bad, 1ull);
+                la = 0;
+            }
+        }
+        sLA[threadIdx.x] = la;
+        sbest[threadIdx.x] = ~0ull;
+    }
+    __syncthreads();
+    int minlim = ML, maxlim = 0;
+#pragma unroll
+    for (int k = 0; k < QB; k++) {
+        const int la = sLA[k];
+        if (la) {
+            const long long a0 = job.test_off[q0 + k];
+            for (int i = threadIdx.x; i < la; i += kVarThreads) As[k * ML + i] = job.test[a0 + i];
+            const int lim = la - V;
+            minlim = lim < minlim ? lim : minlim;
+            maxlim = lim > maxlim ? lim : maxlim;
+        }
+    }
+    if (minlim > maxlim) minlim = maxlim;   // (no query in the block)
     __syncthreads();
 
-    unsigned long long best = ~0ull;
-    for (int64_t t = t_begin + warp; t < t_end; t += kVarThreads / 32) {
+    unsigned long long best[QB];
+#pragma unroll
+    for (int k = 0; k < QB; k++) best[k] = ~0ull;
+    for (int64_t t = t_begin + warp; t < t_end; t += kVarWarps) {
         const long long b0 = job.train_off[t];
         const int LB = (int)(job.train_off[t + 1] - b0);
-        const bool tok = LB >= 2 && LB <= job.max_len;
-        if (!tok && q == 0 && lane == 0 && job.bad) atomicAdd(job.bad, 1ull);
-        float lb = INF;
-        if (qok && tok && in_window(LA, LB, W)) {
-            const float *B = job.train + b0;
-            const float2 *env = reinterpret_cast<const float2 *>(job.env) + t * (int64_t)job.E;
-            const int n = job.keogh ? 0 : min(min(LA, LB) / 2, V);
-            float acc = 0.f;
-            // bridge: LB_Keogh terms of rows n+1 .. L_A-n (0-based [n, L_A-n))
-            for (int i = n + lane; i < LA - n; i += 32) {
-                const float a = As[i];
-                const float2 e = env[i];
-                const float d = fmaxf(fmaxf(a - e.x, e.y - a), 0.f);
-                acc = fmaf(d, d, acc);
-            }
-            // ends (lane 0) and bands i = 2..n (lane i-1), 1-based indices
-            if (lane < n) {
-                const int i = lane + 1;
-                if (i == 1) {
-                    acc += sqd(As[0], B[0]) + sqd(As[LA - 1], B[LB - 1]);
-                } else {
-                    float mL = sqd(As[i - 1], B[i - 1]);
-                    float mR = sqd(As[LA - i], B[LB - i]);
-                    for (int j = 1; j < i; j++) {
-                        if (in_window(i, j, W)) {
-                            mL = fminf(mL, sqd(As[i - 1], B[j - 1]));
-                            mL = fminf(mL, sqd(As[j - 1], B[i - 1]));
-                        }
-                        if (in_window(LA - i + 1, LB - j + 1, W))
-                            mR = fminf(mR, sqd(As[LA - i], B[LB - j]));
-                        if (in_window(LA - j + 1, LB - i + 1, W))
-                            mR = fminf(mR, sqd(As[LA - j], B[LB - i]));
-                    }
-                    acc += mL + mR;
+        const bool tok = LB >= 2 && LB <= ML;
+        if (!tok && q0 == 0 && lane == 0 && job.bad) atomicAdd(job.bad, 1ull);
+        const float2 *env = reinterpret_cast<const float2 *>(job.env) + t * (int64_t)job.E;
+        float acc[QB];
+#pragma unroll
+        for (int k = 0; k < QB; k++) acc[k] = 0.f;
+        if (tok) {
+            // shared bridge rows: every query up to the shortest one's end,
+            // four envelope rows per lane in flight ...
+            int i = V + lane;
+            for (; i + 96 < minlim; i += 128) {
+                const float2 e0 = env[i], e1 = env[i + 32], e2 = env[i + 64], e3 = env[i + 96];
+#pragma unroll
+                for (int k = 0; k < QB; k++) {
+                    const float *a = As + k * ML + i;
+                    acc[k] = keogh_acc(acc[k], a[0], e0);
+                    acc[k] = keogh_acc(acc[k], a[32], e1);
+                    acc[k] = keogh_acc(acc[k], a[64], e2);
+                    acc[k] = keogh_acc(acc[k], a[96], e3);
                 }
             }
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            lb = acc;
+            for (; i < minlim; i += 32) {
+                const float2 e = env[i];
+#pragma unroll
+                for (int k = 0; k < QB; k++) acc[k] = keogh_acc(acc[k], As[k * ML + i], e);
+            }
+            // ... then each query up to its own
+            for (i = (V > minlim ? V : minlim) + lane; i < maxlim; i += 32) {
+                const float2 e = env[i];
+#pragma unroll
+                for (int k = 0; k < QB; k++)
+                    if (i < sLA[k] - V) acc[k] = keogh_acc(acc[k], As[k * ML + i], e);
+            }
+            // ends, bands and short-series rows: one (query, band) per lane,
+            // B's first and last kBandStage values staged in shared memory
+            if (lane < QB) bsum[warp][lane] = 0.f;
+            {
+                const float *B = job.train + b0;
+                bends[warp][0][lane] = lane < LB ? B[lane] : 0.f;
+                bends[warp][1][lane] = LB - 1 - lane >= 0 ? B[LB - 1 - lane] : 0.f;
+            }
+            __syncwarp();
+            const int nt = V > 0 ? V : 1;
+            for (int task = lane; task < QB * nt; task += 32) {
+                const int k = task / nt, b = task % nt;
+                const int LA = sLA[k];
+                if (LA && in_window(LA, LB, W)) {
+                    const int n = job.keogh ? 0 : min(min(LA, LB) / 2, V);
+                    const float v = outer_part(As + k * ML, LA, job.train + b0, bends[warp][0],
+                                               bends[warp][1], LB, env, W, V, n, b);
+                    if (v != 0.f) atomicAdd(&bsum[warp][k], v);
+                }
+            }
+            __syncwarp();
         }
-        if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < QB; k++) {
+            float v = acc[k];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+            acc[k] = v;
+        }
+        if (lane < QB) {
+            const int k = lane;
+            const int LA = sLA[k];
+            float lb = INF;
+            if (tok && LA && in_window(LA, LB, W)) {
+                float s = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < QB; kk++) s = kk == k ? acc[kk] : s;
+                lb = s + bsum[warp][k];
+            }
             float v = lb;
             if (job.safe && lb < INF) {
                 v = __fsub_rd(__fmul_rd(lb, job.lb_lo), job.abs_slack);
                 v = v > 0.f ? v : 0.f;
             }
-            job.lb_out[q * job.N + t] = v;
-            if (lb < INF) {
-                const unsigned long long key = pack_key(v, (uint32_t)t);
-                best = key < best ? key : best;
+            if (q0 + k < job.Q) {
+                job.lb_out[(q0 + k) * job.N + t] = v;
+                if (lb < INF) {
+                    const unsigned long long key = pack_key(v, (uint32_t)t);
+#pragma unroll
+                    for (int kk = 0; kk < QB; kk++)
+                        if (kk == k) best[kk] = key < best[kk] ? key : best[kk];
+                }
             }
         }
+        __syncwarp();
     }
-    if (job.seed_keys && lane == 0 && best != ~0ull) atomicMin(job.seed_keys + q, best);
+    if (job.seed_keys) {
+        if (lane < QB) {
+#pragma unroll
+            for (int kk = 0; kk < QB; kk++)
+                if (kk == lane && best[kk] != ~0ull) atomicMin(&sbest[kk], best[kk]);
+        }
+        __syncthreads();
+        if (threadIdx.x < QB && sbest[threadIdx.x] != ~0ull)
+            atomicMin(job.seed_keys + q0 + threadIdx.x, sbest[threadIdx.x]);
+    }
 }
 
 // The first-candidate pairs (q, key index) of the queries that have one.
@@ -130,19 +263,29 @@ __global__ void seed_pairs_kernel(const unsigned long long *__restrict__ seed_ke
     }
 }
 
+template <int QB>
+cudaError_t launch_lb_var_qb(const LbVarJob &job, cudaStream_t s) {
+    const long long chunks = (job.N + kVarChunk - 1) / kVarChunk;
+    const long long blocks = chunks * ((job.Q + QB - 1) / QB);
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * (size_t)job.max_len * QB;
+    cudaError_t e = cudaFuncSetAttribute(lb_var_kernel<QB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    lb_var_kernel<QB><<<(unsigned)blocks, kVarThreads, smem, s>>>(job);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+// Queries per CTA: eight while their staging fits 64 KB of shared memory,
+// fewer for long series.
 cudaError_t launch_lb_var(const LbVarJob &job, cudaStream_t s) {
     if (job.Q <= 0 || job.N <= 0) return cudaSuccess;
-    const long long chunks = (job.N + kVarChunk - 1) / kVarChunk;
-    const long long blocks = chunks * job.Q;
-    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float) * (size_t)job.max_len;
-    cudaError_t e = cudaFuncSetAttribute(lb_var_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    lb_var_kernel<<<(unsigned)blocks, kVarThreads, smem, s>>>(job);
-    return cudaGetLastError();
+    const size_t per_query = sizeof(float) * (size_t)job.max_len;
+    if (8 * per_query <= 64u * 1024u) return launch_lb_var_qb<8>(job, s);
+    if (4 * per_query <= 64u * 1024u) return launch_lb_var_qb<4>(job, s);
+    return launch_lb_var_qb<2>(job, s);
 }
 
 cudaError_t launch_seed_pairs(const unsigned long long *seed_keys, int64_t Q, uint2 *pairs,
