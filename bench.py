@@ -561,8 +561,8 @@ def run_varlen(args):
             torch.empty(Q, dtype=torch.float64, device=dev))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    tuned = 0
-    if not args.no_tune:
+    tuned = nndtw.DTW_GROUP(args.dtw_group) if args.dtw_group else 0
+    if not args.no_tune and not args.dtw_group:
         from paper_1808_09617_gb300 import autotune
         tuned = autotune.tune_search_varlen(train, labels, test, ds.W, ds.V, workspace=ws,
                                             out=outs)

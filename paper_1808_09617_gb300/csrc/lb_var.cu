@@ -58,33 +58,49 @@ __device__ __forceinline__ float keogh_acc(float acc, float a, float2 e) {
     return fmaf(d, d, acc);
 }
 
+// Position of query k's value of row i in the interleaved staging: row i
+// holds the QB queries' values; with QB = 8 its two 16-byte halves swap
+// places every four rows, so that the 16-byte loads of a warp (one row per
+// lane, rows 32 bytes apart) spread over all banks.
+template <int QB> __device__ __forceinline__ int slot(int i, int k) {
+    if constexpr (QB == 8) return i * 8 + (k ^ (((i >> 2) & 1) << 2));
+    return i * QB + k;
+}
+
 // The part of pair (A, B)'s bound outside the shared bridge rows
 // [V, L_A - V): the ends, bands i = 2..n of both corners (1-based), and the
 // bridge rows [n, V) and [L_A - V, L_A - n) when n < V.  Band b of the task
 // (0-based, b < V) contributes band b+1; task b = 0 also the extra rows.
+// A's value x is As[slot<S>(x, k)] (the queries are interleaved in shared
+// memory);
 // hd[x] = B[x] and tl[x] = B[L_B - 1 - x] for x < kBandStage (staged), else
-// read from B.
-__device__ float outer_part(const float *A, int LA, const float *B, const float *hd,
+// read from B.  Without CHECK every band cell lies inside the window (W >=
+// V - 1 + |L_A - L_B|).
+template <int S, bool CHECK>
+__device__ float outer_part(const float *As, int k, int LA, const float *B, const float *hd,
                             const float *tl, int LB, const float2 *env, int W, int V, int n,
                             int b) {
     auto head = [&](int x) { return x < kBandStage ? hd[x] : B[x]; };
     auto tail = [&](int x) { return x < kBandStage ? tl[x] : B[LB - 1 - x]; };
+    auto in_win = [&](int i, int j) { return !CHECK || in_window(i, j, W); };
+    auto A = [&](int x) { return As[slot<S>(x, k)]; };
     float v = 0.f;
     if (b < n) {
         const int i = b + 1;
         if (i == 1) {
-            v = sqd(A[0], head(0)) + sqd(A[LA - 1], tail(0));
+            v = sqd(A(0), head(0)) + sqd(A(LA - 1), tail(0));
         } else {
             const float bi = head(i - 1), bti = tail(i - 1);
-            float mL = sqd(A[i - 1], bi);
-            float mR = sqd(A[LA - i], bti);
+            const float ai = A(i - 1), ati = A(LA - i);
+            float mL = sqd(ai, bi);
+            float mR = sqd(ati, bti);
             for (int j = 1; j < i; j++) {
-                if (in_window(i, j, W)) {
-                    mL = fminf(mL, sqd(A[i - 1], head(j - 1)));
-                    mL = fminf(mL, sqd(A[j - 1], bi));
+                if (in_win(i, j)) {
+                    mL = fminf(mL, sqd(ai, head(j - 1)));
+                    mL = fminf(mL, sqd(A(j - 1), bi));
                 }
-                if (in_window(LA - i + 1, LB - j + 1, W)) mR = fminf(mR, sqd(A[LA - i], tail(j - 1)));
-                if (in_window(LA - j + 1, LB - i + 1, W)) mR = fminf(mR, sqd(A[LA - j], bti));
+                if (in_win(LA - i + 1, LB - j + 1)) mR = fminf(mR, sqd(ati, tail(j - 1)));
+                if (in_win(LA - j + 1, LB - i + 1)) mR = fminf(mR, sqd(A(LA - j), bti));
             }
             v = mL + mR;
         }
@@ -92,16 +108,37 @@ __device__ float outer_part(const float *A, int LA, const float *B, const float 
     if (b == 0 && n < V) {
         // bridge rows the shared loop leaves out (short series)
         const int lo_end = V < LA - n ? V : LA - n;
-        for (int i = n; i < lo_end; i++) v = keogh_acc(v, A[i], env[i]);
+        for (int i = n; i < lo_end; i++) v = keogh_acc(v, A(i), env[i]);
         for (int i = (LA - V > lo_end ? LA - V : lo_end); i < LA - n; i++)
-            v = keogh_acc(v, A[i], env[i]);
+            v = keogh_acc(v, A(i), env[i]);
     }
     return v;
 }
 
+// The QB queries' values of row i (interleaved: As[slot<QB>(i, k)]).
 template <int QB>
-__global__ void __launch_bounds__(kVarThreads) lb_var_kernel(const LbVarJob job) {
-    extern __shared__ __align__(16) float As[];   // [QB][max_len]
+__device__ __forceinline__ void load_row(const float *As, int i, float (&a)[QB]) {
+    const float *p = As + i * QB;
+    if constexpr (QB == 8) {
+        const int sw = ((i >> 2) & 1) << 2;   // the halves' swap (slot)
+        const float4 u = reinterpret_cast<const float4 *>(p)[sw >> 2];
+        const float4 w = reinterpret_cast<const float4 *>(p)[1 - (sw >> 2)];
+        a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+        a[4] = w.x; a[5] = w.y; a[6] = w.z; a[7] = w.w;
+    } else if constexpr (QB == 4) {
+        const float4 u = reinterpret_cast<const float4 *>(p)[0];
+        a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+    } else {
+        const float2 u = reinterpret_cast<const float2 *>(p)[0];
+        a[0] = u.x; a[1] = u.y;
+    }
+}
+
+template <int QB>
+__global__ void __launch_bounds__(kVarThreads, 3) lb_var_kernel(const LbVarJob job) {
+    // the queries interleaved by row, As[slot<QB>(i, k)], so that one row of
+    // all QB queries is one or two vector loads
+    extern __shared__ __align__(16) float As[];
     __shared__ float bsum[kVarWarps][QB];
     __shared__ float bends[kVarWarps][2][kBandStage];   // B's first and last values
     __shared__ unsigned long long sbest[QB];
@@ -131,15 +168,17 @@ __global__ void __launch_bounds__(kVarThreads) lb_var_kernel(const LbVarJob job)
     }
     __syncthreads();
     int minlim = ML, maxlim = 0;
+    int lim[QB];   // each query's shared bridge rows end here (no query: -V)
 #pragma unroll
     for (int k = 0; k < QB; k++) {
         const int la = sLA[k];
+        lim[k] = la - V;
         if (la) {
             const long long a0 = job.test_off[q0 + k];
-            for (int i = threadIdx.x; i < la; i += kVarThreads) As[k * ML + i] = job.test[a0 + i];
-            const int lim = la - V;
-            minlim = lim < minlim ? lim : minlim;
-            maxlim = lim > maxlim ? lim : maxlim;
+            for (int i = threadIdx.x; i < la; i += kVarThreads)
+                As[slot<QB>(i, k)] = job.test[a0 + i];
+            minlim = lim[k] < minlim ? lim[k] : minlim;
+            maxlim = lim[k] > maxlim ? lim[k] : maxlim;
         }
     }
     if (minlim > maxlim) minlim = maxlim;   // (no query in the block)
@@ -162,27 +201,35 @@ __global__ void __launch_bounds__(kVarThreads) lb_var_kernel(const LbVarJob job)
             // four envelope rows per lane in flight ...
             int i = V + lane;
             for (; i + 96 < minlim; i += 128) {
-                const float2 e0 = env[i], e1 = env[i + 32], e2 = env[i + 64], e3 = env[i + 96];
+                float2 e[4];
 #pragma unroll
-                for (int k = 0; k < QB; k++) {
-                    const float *a = As + k * ML + i;
-                    acc[k] = keogh_acc(acc[k], a[0], e0);
-                    acc[k] = keogh_acc(acc[k], a[32], e1);
-                    acc[k] = keogh_acc(acc[k], a[64], e2);
-                    acc[k] = keogh_acc(acc[k], a[96], e3);
+                for (int r = 0; r < 4; r++) e[r] = env[i + 32 * r];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float a[QB];
+                    load_row<QB>(As, i + 32 * r, a);
+#pragma unroll
+                    for (int k = 0; k < QB; k++) acc[k] = keogh_acc(acc[k], a[k], e[r]);
                 }
             }
             for (; i < minlim; i += 32) {
                 const float2 e = env[i];
+                float a[QB];
+                load_row<QB>(As, i, a);
 #pragma unroll
-                for (int k = 0; k < QB; k++) acc[k] = keogh_acc(acc[k], As[k * ML + i], e);
+                for (int k = 0; k < QB; k++) acc[k] = keogh_acc(acc[k], a[k], e);
             }
-            // ... then each query up to its own
+            // ... then each query up to its own (rows past a query's end
+            // hold stale values: their terms are computed and discarded)
             for (i = (V > minlim ? V : minlim) + lane; i < maxlim; i += 32) {
                 const float2 e = env[i];
+                float a[QB];
+                load_row<QB>(As, i, a);
 #pragma unroll
-                for (int k = 0; k < QB; k++)
-                    if (i < sLA[k] - V) acc[k] = keogh_acc(acc[k], As[k * ML + i], e);
+                for (int k = 0; k < QB; k++) {
+                    const float t2 = keogh_acc(acc[k], a[k], e);
+                    acc[k] = i < lim[k] ? t2 : acc[k];
+                }
             }
             // ends, bands and short-series rows: one (query, band) per lane,
             // B's first and last kBandStage values staged in shared memory
@@ -199,8 +246,13 @@ __global__ void __launch_bounds__(kVarThreads) lb_var_kernel(const LbVarJob job)
                 const int LA = sLA[k];
                 if (LA && in_window(LA, LB, W)) {
                     const int n = job.keogh ? 0 : min(min(LA, LB) / 2, V);
-                    const float v = outer_part(As + k * ML, LA, job.train + b0, bends[warp][0],
-                                               bends[warp][1], LB, env, W, V, n, b);
+                    const int dl = LA > LB ? LA - LB : LB - LA;
+                    const float v =
+                        W >= V - 1 + dl
+                            ? outer_part<QB, false>(As, k, LA, job.train + b0, bends[warp][0],
+                                                    bends[warp][1], LB, env, W, V, n, b)
+                            : outer_part<QB, true>(As, k, LA, job.train + b0, bends[warp][0],
+                                                   bends[warp][1], LB, env, W, V, n, b);
                     if (v != 0.f) atomicAdd(&bsum[warp][k], v);
                 }
             }
