@@ -146,32 +146,80 @@ dtw32_kernel(const __grid_constant__ Src src) {
     // abandon checks every 16 super-steps, at the same block for the whole warp
     constexpr int kCheckBlocks = 16 / U > 1 ? 16 / U : 1;
 
-    // Claims run two pairs ahead per group so that no memory latency sits
-    // between two sweeps (the whole warp would wait for it): p1 is the
-    // group's next pair with its item w1 already requested.  `nxt` is the
-    // next static index, or (dynamic claims) the claim after p1, still in
-    // flight in the group's lane 0.
+    // Claiming, equal lengths: claims run two pairs ahead per group so that
+    // no memory latency sits between two sweeps (the whole warp would wait
+    // for it): p1 is the group's next pair with its item w1 already
+    // requested.  `nxt` is the next static index, or (dynamic claims) the
+    // claim after p1, still in flight in the group's lane 0.  Live pruning
+    // (job.lb): with p1 come its pair's safe bound and its query's best
+    // (float bits), tested when the pair is due; a bound above the best's
+    // upper bound at that moment drops the pair unstarted (the compaction's
+    // test against a tighter best).
     long long nxt = ((long long)bid * blockDim.x + threadIdx.x) / G;
-    long long p1;
-    if (job.head) {
-        unsigned long long v = 0;
-        if (gl == 0) v = atomicAdd(job.head, 1ull);
-        p1 = (long long)__shfl_sync(FULL, v, 0, G);
-        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
-    } else {
-        p1 = nxt;
-        nxt += n_groups;
-    }
-    uint2 w1 = work_item(job, p1, n_work);
-    // Live pruning (job.lb): the next pair's safe bound and its query's best
-    // (float bits), requested with the claim and tested when the pair is
-    // due; a bound above the best's upper bound at that moment drops the
-    // pair unstarted (the compaction's test against a tighter best).
+    long long p1 = 0;
+    uint2 w1 = make_uint2(0u, 0u);
     float lb1 = 0.f;
     unsigned kb1 = ~0u;
-    if (job.lb && p1 < n_work) {
-        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
-        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+    if constexpr (!VAR) {
+        if (job.head) {
+            unsigned long long v = 0;
+            if (gl == 0) v = atomicAdd(job.head, 1ull);
+            p1 = (long long)__shfl_sync(FULL, v, 0, G);
+            if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+        } else {
+            p1 = nxt;
+            nxt += n_groups;
+        }
+        w1 = work_item(job, p1, n_work);
+        if (job.lb && p1 < n_work) {
+            lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+            kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+        }
+    }
+    // Claiming, unequal lengths (VAR): batches of consecutive items, one item
+    // per lane of the group, two claims ahead: nw is this lane's item of the
+    // next batch (first item nb, nbs items), already requested with its
+    // pair's bound and its query's best, and bnxt the claim after it (nxs
+    // items), in flight in the group's lane 0.  When a batch is due, each
+    // lane applies the live test to its item and the group starts the
+    // batch's surviving pairs one after another (bits of bmask), so that a
+    // batch dropped whole waits once for the next batch's loads, not once
+    // per pair: the bound-nearest first candidate of the unequal-length
+    // search leaves most of its queue to be dropped live.  Dynamic claims
+    // take min(G, job.claim) items at a time, static assignment one.  (With
+    // equal lengths, where few queued pairs are dropped, batches of a
+    // query's consecutive pairs swept by one group were measured slower.)
+    const long long gidx = ((long long)bid * blockDim.x + threadIdx.x) / G;
+    const unsigned gbits = G == 32 ? FULL : ((1u << G) - 1u);
+    const int bs = job.head && job.claim > 1 ? (G < job.claim ? G : job.claim) : 1;
+    int nbs = 1, nxs = 1;
+    long long nb = 0, cbase = 0, bnxt = 0;
+    uint2 nw = make_uint2(0u, 0u), bw = make_uint2(0u, 0u);
+    float nlb = 0.f;
+    unsigned nkb = ~0u, bmask = 0u;
+    auto claim = [&](bool first) {
+        if (job.head) {
+            nb = (long long)__shfl_sync(gmask, bnxt, 0, G);
+            nbs = nxs;
+            if (gl == 0) bnxt = (long long)atomicAdd(job.head, (unsigned long long)bs);
+            nxs = bs;
+        } else {
+            nb = first ? gidx : nb + n_groups;
+            nbs = 1;
+        }
+        const bool mine = gl < nbs && nb + gl < n_work;
+        nw = mine ? work_item(job, nb + gl, n_work) : make_uint2(0u, 0u);
+        nlb = 0.f;
+        nkb = ~0u;
+        if (job.lb && mine) {
+            nlb = job.lb[(long long)nw.x * job.lb_n + nw.y];
+            nkb = bsf_dist_bits(job.bsf, (int)nw.x);
+        }
+    };
+    if constexpr (VAR) {
+        if (job.head && gl == 0) bnxt = (long long)atomicAdd(job.head, (unsigned long long)bs);
+        nxs = bs;
+        claim(true);
     }
 
     float R[C], Aw[H + U], Bw[H + U];
@@ -199,29 +247,57 @@ dtw32_kernel(const __grid_constant__ Src src) {
         const bool need = done && !finished;
         if (__any_sync(FULL, need)) {
             if (need) {
-                // claim until a pair survives the live test or the list ends
                 bool take = false;
-                while (!take && p1 < n_work) {
-                    pid = p1;
-                    q = (int)w1.x; tt = (int)w1.y;
-                    const float lb_cur = lb1;
-                    const unsigned kb_cur = kb1;
-                    if (job.head) {
-                        p1 = __shfl_sync(gmask, nxt, 0, G);
-                        if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
-                    } else {
-                        p1 = nxt;
-                        nxt += n_groups;
+                if constexpr (!VAR) {
+                    // claim until a pair survives the live test or the list ends
+                    while (!take && p1 < n_work) {
+                        pid = p1;
+                        q = (int)w1.x; tt = (int)w1.y;
+                        const float lb_cur = lb1;
+                        const unsigned kb_cur = kb1;
+                        if (job.head) {
+                            p1 = __shfl_sync(gmask, nxt, 0, G);
+                            if (gl == 0) nxt = (long long)atomicAdd(job.head, 1ull);
+                        } else {
+                            p1 = nxt;
+                            nxt += n_groups;
+                        }
+                        w1 = work_item(job, p1, n_work);
+                        if (job.lb && p1 < n_work) {
+                            lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
+                            kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+                        }
+                        take = kb_cur == ~0u ||
+                               !(lb_cur > upper32(__uint_as_float(kb_cur), job.dtw_hi, job.abs32));
+                        if (!take && job.counters && gl == 0)
+                            atomicAdd(job.counters + C_LIVEPRUNED, 1ull);
                     }
-                    w1 = work_item(job, p1, n_work);
-                    if (job.lb && p1 < n_work) {
-                        lb1 = job.lb[(long long)w1.x * job.lb_n + w1.y];
-                        kb1 = bsf_dist_bits(job.bsf, (int)w1.x);
+                } else {
+                    // the current batch's next surviving pair; batches are taken
+                    // in (and the next one claimed) until one has a survivor or
+                    // the list ends
+                    while (bmask == 0u && nb < n_work) {
+                        cbase = nb;
+                        bw = nw;
+                        const bool valid = gl < nbs && nb + gl < n_work;
+                        const bool keep = valid && (nkb == ~0u ||
+                            !(nlb > upper32(__uint_as_float(nkb), job.dtw_hi, job.abs32)));
+                        const int sh = lane & ~(G - 1);
+                        bmask = (__ballot_sync(gmask, keep) >> sh) & gbits;
+                        const unsigned vm = (__ballot_sync(gmask, valid) >> sh) & gbits;
+                        if (job.counters && gl == 0 && vm != bmask)
+                            atomicAdd(job.counters + C_LIVEPRUNED,
+                                      (unsigned long long)__popc(vm & ~bmask));
+                        claim(false);
                     }
-                    take = kb_cur == ~0u ||
-                           !(lb_cur > upper32(__uint_as_float(kb_cur), job.dtw_hi, job.abs32));
-                    if (!take && job.counters && gl == 0)
-                        atomicAdd(job.counters + C_LIVEPRUNED, 1ull);
+                    take = bmask != 0u;
+                    if (take) {
+                        const int k = __ffs(bmask) - 1;
+                        bmask &= bmask - 1u;
+                        pid = cbase + k;
+                        q = (int)__shfl_sync(gmask, bw.x, k, G);
+                        tt = (int)__shfl_sync(gmask, bw.y, k, G);
+                    }
                 }
                 if (!take) {
                     finished = true;

@@ -308,6 +308,9 @@ struct DtwJob32 {
     // is due
     const float *lb;
     long long lb_n;
+    // work items a group of the diagonal kernel claims at once with dynamic
+    // claims (at most its lanes; 0 or 1: one)
+    int claim;
 };
 // How one dataset's FP32 DTW pass is launched: the kernel in its one-dataset
 // and batch forms (every FP32 DTW kernel takes a DtwJob32 source), block

@@ -1146,6 +1146,9 @@ int run_var(const SetVar &x, bool want_stats, bool timing, nndtw_stats *stats, S
         if (!(x.flags & NNDTW_NO_PRUNE)) {   // live pruning against the tightening bests
             j.lb = w.lb;
             j.lb_n = x.N;
+            // the bound-nearest first candidate leaves most queued pairs to be
+            // dropped live: claims of 8 wait once per 8 of them
+            j.claim = 8;
         }
         Dtw32Plan pl{};
         CK(plan_dtw32_var(j, sms, &pl));
