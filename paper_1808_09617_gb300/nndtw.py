@@ -760,6 +760,24 @@ class Ragged:
     offsets: object
     max_len: int
 
+    def __post_init__(self):
+        # The kernels read series k at values[offsets[k] .. offsets[k+1]):
+        # offsets that leave the array would make them read past it, so the
+        # table is checked once here (one copy of the offsets to the host).
+        import torch
+        if not (isinstance(self.values, torch.Tensor) and isinstance(self.offsets, torch.Tensor)):
+            raise TypeError("Ragged values and offsets must be tensors")
+        if self.values.dim() != 1 or self.offsets.dim() != 1 or self.offsets.shape[0] < 1:
+            raise ValueError("Ragged values must be 1-D and offsets 1-D with n+1 entries")
+        off = self.offsets.detach().to("cpu", torch.int64)
+        lens = off[1:] - off[:-1]
+        if int(off[0]) != 0 or int(off[-1]) != int(self.values.shape[0]) or bool((lens < 0).any()):
+            raise ValueError("Ragged offsets must start at 0, never decrease and end at the "
+                             "number of values")
+        longest = int(lens.max()) if lens.numel() else 0
+        if self.max_len < longest:
+            raise ValueError(f"max_len {self.max_len} is below the longest series ({longest})")
+
     @property
     def n(self) -> int:
         return int(self.offsets.shape[0]) - 1

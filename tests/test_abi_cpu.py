@@ -198,3 +198,18 @@ def test_varlen_host_entry_checks_offsets_before_any_copy(clib):
     assert call(good, np.array([0, 6, 15], np.int64)) == nndtw.EINVAL        # longer than 8
     assert call(np.array([1, 5, 9, 15], np.int64), qgood) == nndtw.EINVAL   # not from 0
     assert call(good, np.array([0, 7, 5], np.int64)) == nndtw.EINVAL         # decreasing
+
+
+def test_ragged_set_checks_its_offsets():
+    """A ragged set's offset table is checked when the set is built: the
+    kernels would read past the values with a table that leaves them."""
+    import torch
+    from paper_1808_09617_gb300 import nndtw
+    v = torch.zeros(10)
+    ok = nndtw.Ragged(v, torch.tensor([0, 4, 10]), 6)
+    assert ok.n == 2
+    for off, ml in (([0, 4, 11], 7), ([1, 4, 10], 6), ([0, 6, 4, 10], 6), ([0, 4, 10], 5)):
+        with pytest.raises(ValueError):
+            nndtw.Ragged(v, torch.tensor(off), ml)
+    with pytest.raises(ValueError):
+        nndtw.Ragged(torch.zeros(2, 5), torch.tensor([0, 10]), 10)
