@@ -241,3 +241,26 @@ def test_search_varlen_full_workload_every_query(lib):
     # DTW kernel further against the live best)
     assert st["lb_pruned"] > 0.25 * st["pairs"]
     assert st["lb_pruned"] + st["lb_pruned_live"] > 0.5 * st["pairs"]
+
+
+def test_search_varlen_host_buffers(lib, orc):
+    """The host-buffer entry point (copies in, search, copies out) returns
+    the device search's results."""
+    tr = _series_set(111, 150, 40, 70)
+    te = _series_set(112, 40, 40, 70)
+    labels = _labels(113, len(tr))
+    tv, to = _pack(tr)
+    qv, qo = _pack(te)
+    hs = lib.VarlenHostSearch(tv, to, labels, qv, qo, 12, 4, max_len=70)
+    for _ in range(2):
+        idx, lab, dist = hs()
+        d_idx, d_lab, d_dist, _ = _search(lib, tr, labels, te, 12, 4, max_len=70)
+        np.testing.assert_array_equal(idx, d_idx)
+        np.testing.assert_array_equal(lab, d_lab)
+        np.testing.assert_array_equal(dist, d_dist)
+    bi, bl, _ = orc.nn_brute_var(tv, to, labels, qv, qo, 12)
+    np.testing.assert_array_equal(idx, bi)
+    np.testing.assert_array_equal(lab, bl)
+    h2d, d2h = hs.bytes_per_call()
+    assert h2d == tv.nbytes + to.nbytes + qv.nbytes + qo.nbytes + labels.nbytes
+    assert d2h == len(te) * 16
