@@ -678,7 +678,8 @@ def run_serving(args):
         ds = synth.make_serving_set(d, sp)
         sets[d] = (ds.train, ds.train_labels, sp["W"], sp["V"])
     pools = {d: synth.serving_queries(d, specs[d], 1024)[0] for d in sets}
-    srv = serving.Server(sets, n_slots=args.serve_slots, max_batch=args.serve_batch)
+    srv = serving.Server(sets, n_slots=args.serve_slots, max_batch=args.serve_batch,
+                         mix_ratio=args.serve_mix)
     rng = np.random.default_rng(7)
     results = []
     try:
@@ -716,7 +717,8 @@ def run_serving(args):
             "config": {"workload": "16 resident sets, L in {128, 512, 1500}, N log-uniform "
                                    "[1000, 20000], W=0.1 L, V=5; Poisson arrivals, set "
                                    "uniform per query", "slots": args.serve_slots,
-                       "max_batch": args.serve_batch, "seconds_per_rate": args.serve_seconds},
+                       "max_batch": args.serve_batch, "seconds_per_rate": args.serve_seconds,
+                       "mix_ratio": args.serve_mix if args.serve_mix != float("inf") else None},
             "rates": results}
     print(json.dumps(line), flush=True)
 
@@ -756,6 +758,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=512)
+    ap.add_argument("--serve-mix", type=float, default=float("inf"),
+                    help="sets share a serving batch only within this factor of cost per query")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
