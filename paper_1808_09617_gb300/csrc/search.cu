@@ -487,7 +487,14 @@ dim3 grid_compact(int64_t Q, int64_t N) {
     const long long per_block = (long long)kSmallThreads * kCompactE;
     long long gx = (N + per_block - 1) / per_block;
     if (gx > 64) gx = 64;
-    long long gy = Q < 65535 ? Q : 65535;
+    // rows per CTA (it strides over them): enough for about 8192 bounds, so
+    // that a CTA on short rows does more than its start-up and barriers
+    const long long per_row = (N + gx - 1) / gx;
+    long long rows = per_row > 0 ? 8192 / per_row : 1;
+    if (rows < 1) rows = 1;
+    if (rows > 32) rows = 32;
+    long long gy = (Q + rows - 1) / rows;
+    if (gy > 65535) gy = 65535;
     if (gy < 1) gy = 1;
     return dim3((unsigned)gx, (unsigned)gy);
 }
