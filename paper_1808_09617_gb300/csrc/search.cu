@@ -779,6 +779,22 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
         // (a later chunk of a search finds the training envelopes it built)
         p.cnt = (want_stats && !timing) ? p.ws.counters : nullptr;
     }
+    // Order of the datasets inside a stage's launches: the CTAs of a launch
+    // are dispatched roughly in job order, so the datasets with the longest
+    // CTAs (bound pass: the longest series; DTW: the most band cells per
+    // pair, whose persistent grids drain slowest) go first and the launch
+    // ends on short ones.
+    std::vector<int> ord_len(n), ord_band(n);
+    std::iota(ord_len.begin(), ord_len.end(), 0);
+    std::iota(ord_band.begin(), ord_band.end(), 0);
+    std::stable_sort(ord_len.begin(), ord_len.end(),
+                     [&](int a, int b) { return sets[a].L > sets[b].L; });
+    auto band_of = [&](int d) {
+        const long long w = 2ll * P[d].Weff + 1;
+        return (long long)sets[d].L * (w < sets[d].L ? w : sets[d].L);
+    };
+    std::stable_sort(ord_band.begin(), ord_band.end(),
+                     [&](int a, int b) { return band_of(a) > band_of(b); });
 
     // starting values of every dataset's counters, keys and tallies
     {
@@ -827,7 +843,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             const EnvFns<float> f = envelope_fns<float>(ep.one_pass);
             g.add(f.fn1, f.fnN, kEnvelopeThreads, ep.smem, ep.job, ep.blocks);
         };
-        for (int d = 0; d < n; d++) {
+        for (int d : ord_len) {
             if (!sets[d].env && !sets[d].train_ready)
                 add(sets[d].train, nullptr, sets[d].N, d, P[d].ws.env);
             if (P[d].second) add(sets[d].test, nullptr, sets[d].Q, d, P[d].ws.envq);
@@ -856,7 +872,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
     {
         Batches<SqnormJob<float>> gs;
         Batches<LbJob<float>> gl;
-        for (int d = 0; d < n; d++) {
+        for (int d : ord_len) {
             const Set32 &x = sets[d];
             const Prep32 &p = P[d];
             LbPlan<float> lp{};
@@ -877,7 +893,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
     std::vector<DtwJob32> main_jobs(n);
     {
         Batches<DtwJob32> g;
-        for (int d = 0; d < n; d++) {
+        for (int d : ord_band) {
             const Set32 &x = sets[d];
             const Prep32 &p = P[d];
             DtwJob32 j{};
@@ -951,7 +967,7 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
     // S4 on the survivors, with early abandoning
     {
         Batches<DtwJob32> g;
-        for (int d = 0; d < n; d++) {
+        for (int d : ord_band) {
             const Prep32 &p = P[d];
             DtwJob32 j = main_jobs[d];
             j.pairs = p.second ? p.ws.rlist : p.ws.queue; j.seed_keys = nullptr;
