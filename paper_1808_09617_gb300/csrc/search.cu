@@ -1856,8 +1856,8 @@ int nn_dtw_search_batched(const nndtw_dataset *h_sets, int n, void *d_workspace,
     StageTimer tm;
     CK(tm.start(timing, s));
     for (auto &sets : rounds) {
-        // the datasets with the most DTW work first: in every stage their CTAs
-        // start first, and the small datasets fill in behind them
+        // the datasets with the most DTW work first (the order of the groups
+        // of 64 and of the stages run32 does not reorder by a CTA's cost)
         std::stable_sort(sets.begin(), sets.end(), [](const Set32 &a, const Set32 &b) {
             const double wa = (double)a.N * a.Q * band_cells(a.L, a.W);
             const double wb = (double)b.N * b.Q * band_cells(b.L, b.W);
