@@ -678,7 +678,7 @@ template <typename Job> struct Batches {
 // its launches round-robin over them and joins back, so the stage events on
 // the caller's stream still bracket all of its launches (and a captured
 // graph holds the fork and the join).
-constexpr int kForkStreams = 4;
+constexpr int kForkStreams = 8;
 struct ForkSet {
     cudaStream_t st[kForkStreams] = {};
     cudaEvent_t fork = nullptr, join[kForkStreams] = {};
