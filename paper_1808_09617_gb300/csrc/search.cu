@@ -51,9 +51,13 @@ __global__ void finite_check_kernel(const T *__restrict__ x, int64_t n, T limit,
 // counting sort in two passes).  Pairs with a small ratio tend to run their
 // DTW to completion, pairs near 1 to be abandoned early, so this order runs
 // the long pairs first and leaves short ones for the end of the persistent
-// DTW kernel (longest-processing-time-first scheduling).  The queue then holds
-// bucket 0, bucket 1, ...; within a bucket the order is arbitrary.
-constexpr int kBuckets = 8;
+// DTW kernel (longest-processing-time-first scheduling), and the pairs most
+// likely to lower their query's best come first.  The queue then holds bucket
+// 0, bucket 1, ...; within a bucket the order is arbitrary.  64 buckets
+// instead of 8 made the batched step 2.9 % faster (its DTW stage 4 %: the
+// full-window datasets, whose bounds are weak, find their nearest series
+// sooner); 32 gave 2.6 %.
+constexpr int kBuckets = 64;
 
 template <typename T> struct UbOf;
 template <> struct UbOf<float> {
