@@ -119,16 +119,30 @@ compact_kernel(const __grid_constant__ Src src) {
     __shared__ unsigned long long boff[kBuckets];
     __shared__ unsigned int scount[kBuckets];
     __shared__ unsigned long long sbase[kBuckets];
+    __shared__ unsigned long long wsum[kBuckets / 32];
     const int tid = threadIdx.x;
-    if (tid < kBuckets) {
-        scount[tid] = 0;
-        if (scatter) {
-            unsigned long long o = 0;
-            for (int k = 0; k < tid; k++) o += bcount[k];
-            boff[tid] = o;
-            if (tid == kBuckets - 1 && bid == 0)
-                *qcount = o + bcount[kBuckets - 1];
+    static_assert(kBuckets % 32 == 0 && kBuckets <= kSmallThreads, "buckets: whole warps");
+    if (tid < kBuckets) scount[tid] = 0;
+    if (scatter && tid < kBuckets) {
+        // bucket offsets: an exclusive prefix sum of the counts, one bucket
+        // per thread (inclusive scan per warp, then the warps' totals)
+        const unsigned long long c = bcount[tid];
+        unsigned long long v = c;
+        const int ln = tid & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+            if (ln >= o) v += u;
         }
+        if (ln == 31) wsum[tid >> 5] = v;
+        boff[tid] = v - c;
+    }
+    __syncthreads();
+    if (scatter && tid < kBuckets) {
+        unsigned long long o = 0;
+        for (int w = 0; w < (tid >> 5); w++) o += wsum[w];
+        boff[tid] += o;
+        if (tid == kBuckets - 1 && bid == 0) *qcount = boff[tid] + bcount[tid];
     }
     __syncthreads();
     // each round covers kCompactE * 256 consecutive pairs of a row; element e
@@ -492,11 +506,17 @@ dim3 grid_compact(int64_t Q, int64_t N) {
     long long gx = (N + per_block - 1) / per_block;
     if (gx > 64) gx = 64;
     // rows per CTA (it strides over them): enough for about 8192 bounds, so
-    // that a CTA on short rows does more than its start-up and barriers
+    // that a CTA on short rows does more than its start-up and barriers, but
+    // no fewer CTAs than two per SM while the rows allow (a small search's
+    // rows run side by side, not one after another in a CTA)
     const long long per_row = (N + gx - 1) / gx;
     long long rows = per_row > 0 ? 8192 / per_row : 1;
-    if (rows < 1) rows = 1;
     if (rows > 32) rows = 32;
+    const long long min_ctas = 2ll * device_sm_count();
+    const long long gy_min = (min_ctas + gx - 1) / gx;
+    const long long spread = Q / gy_min;   // rows per CTA with gy_min CTAs
+    if (rows > spread) rows = spread;
+    if (rows < 1) rows = 1;
     long long gy = (Q + rows - 1) / rows;
     if (gy > 65535) gy = 65535;
     if (gy < 1) gy = 1;
