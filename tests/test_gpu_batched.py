@@ -101,6 +101,19 @@ def test_batched_other_flags_match_oracle(lib, batch, golden_batched):
                        golden_batched)
 
 
+def test_batched_order_and_groups_of_64(lib, batch, golden_batched):
+    """The datasets in another order and more than 64 of them (the 64 in
+    reverse, then the first 16 again: two groups of at most 64, and every
+    stage reorders its datasets by their cost): each dataset's results are
+    still the oracle's."""
+    dsets, sets = batch
+    order = list(range(63, -1, -1)) + list(range(16))
+    res = lib.nn_dtw_search_batched([sets[k] for k in order])
+    assert len(res) == len(order)
+    for k, r in zip(order, res):
+        _check_every_query([dsets[k]], [_np(r)], {0: golden_batched[k]})
+
+
 def test_batched_rejects_bad_descriptors(lib, batch):
     _, sets = batch
     bad = [dict(sets[0]), dict(sets[1])]
