@@ -597,7 +597,7 @@ def run_varlen(args):
     # results out inside the timed region (pinned host arrays)
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     hs = nndtw.VarlenHostSearch(pin(tv), pin(to), pin(ds.train_labels), pin(qv), pin(qo), ds.W,
-                                ds.V, ml, device=dev)
+                                ds.V, ml, flags=tuned, device=dev)
     for _ in range(2):
         hs()
     e2e_t = []
