@@ -215,6 +215,11 @@ template <typename T> struct LbJob {
     T *ends_out;
     int loo, qfast, gx;
     int64_t q_base;   // global index of query 0 (leave-one-out over query chunks)
+    // W = 0 in the search (FP32, no cascade): the bound is the squared
+    // Euclidean distance formed from the norms and dot products, less
+    // ed_gamma (sqrt|a|^2 + sqrt|b|^2)^2; no bridge or bands are computed
+    int edb;
+    T ed_gamma;
 };
 template <typename T> struct SqnormJob {
     const T *a;
@@ -242,7 +247,7 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p, int64_t q_base = 0, int tile = 0);
+                    LbPlan<T> *p, int64_t q_base = 0, int tile = 0, bool ed_bound = false);
 template <typename T> LbFns<T> lb_fns(int tile, bool ed);
 template <typename T> cudaError_t set_lb_smem(int tile, bool ed, size_t smem);
 

@@ -26,6 +26,8 @@
 // (one multiply-add per pair-element); it only picks that first candidate,
 // whose exact DTW then bounds the query, so its rounding never changes a
 // result.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace nndtw {
@@ -71,6 +73,14 @@ __device__ __forceinline__ float safe_scale(float x, float lo, float abs_s) {
 __device__ __forceinline__ double safe_scale(double x, double lo, double abs_s) {
     double v = __dmul_rd(x, lo) - abs_s;
     return v > 0.0 ? v : 0.0;
+}
+
+// A lower bound of the exact squared Euclidean distance from its value e
+// formed as |a|^2 + |b|^2 - 2 a.b: e less g (|a| + |b|)^2, rounded down (g
+// bounds the relative rounding of the norms and the dot product).
+__device__ __forceinline__ float ed_lower(float e, float na, float nb, float g) {
+    const float s = __fadd_ru(__fsqrt_ru(na), __fsqrt_ru(nb));
+    return __fsub_rd(e, __fmul_ru(g, __fmul_ru(s, s)));
 }
 
 // Four consecutive tile rows of one column into shared memory with vector
@@ -256,7 +266,11 @@ lb_kernel(const __grid_constant__ Src src) {
 #pragma unroll
         for (int c = 0; c < MC; c++) { acc[r][c] = T(0); ed[r][c] = T(0); }
 
-    const int mlo = keogh ? 0 : nb, mhi = keogh ? L : L - nb;
+    // W = 0 in the search: the bound comes from the dot products alone (no
+    // envelope is staged, no bridge or band term computed)
+    bool ed_only = false;
+    if constexpr (ED && std::is_same<T, float>::value) ed_only = job.edb != 0;
+    const int mlo = ed_only ? 0 : keogh ? 0 : nb, mhi = ed_only ? 0 : keogh ? L : L - nb;
     const T POS = inf_of<T>();
 
     const int cbeg = ED ? 0 : (mlo / kLC) * kLC, cend = ED ? L : mhi;
@@ -321,6 +335,25 @@ lb_kernel(const __grid_constant__ Src src) {
         store();
         __syncthreads();
         if (c0 + kLC < cend) load(c0 + kLC);   // in flight while this chunk is used
+        if (ed_only) {
+#pragma unroll 4
+            for (int col = 0; col < kLC; col++) {
+                T a[MR], b[MC];
+                ldsn<T, MR>(a, As + col * (kQT + kPadA) + ty * MR);
+#pragma unroll
+                for (int g = 0; g < MC / 2; g++) {
+                    T bg[2];
+                    lds2(bg, Bs + col * (kNT + kPadN) + g * 32 + 2 * tx);
+                    b[2 * g] = bg[0]; b[2 * g + 1] = bg[1];
+                }
+#pragma unroll
+                for (int r = 0; r < MR; r++)
+#pragma unroll
+                    for (int c = 0; c < MC; c++) ed[r][c] = fma(a[r], b[c], ed[r][c]);
+            }
+            __syncthreads();
+            continue;
+        }
 #pragma unroll 4
         for (int col = 0; col < kLC; col++) {
             T a[MR];
@@ -353,7 +386,7 @@ lb_kernel(const __grid_constant__ Src src) {
         __syncthreads();
     }
 
-    if (!keogh) {
+    if (!keogh && !ed_only) {
         // stage the first and last nb elements of the tile's series
         const bool staged = nb <= kNBMax;
         if (staged) {
@@ -400,8 +433,17 @@ lb_kernel(const __grid_constant__ Src src) {
 #pragma unroll
         for (int c = 0; c < MC; c++) {
             const int64_t t = t0 + col_of(c);
-            const T raw = acc[r][c];
-            const T sv = safe_scale(raw, lb_lo, abs_slack);
+            T raw = acc[r][c];
+            T sv = safe_scale(raw, lb_lo, abs_slack);
+            if constexpr (ED && std::is_same<T, float>::value) {
+                if (ed_only && q < Q && t < N) {
+                    const T na = nq[q], nb2 = nt[t];
+                    T e = na + nb2 - T(2) * ed[r][c];
+                    e = e > T(0) ? e : T(0);
+                    raw = e;
+                    sv = safe_scale(ed_lower(e, na, nb2, job.ed_gamma), lb_lo, abs_slack);
+                }
+            }
             if (q < Q && t < N) {
                 // leave-one-out: a series is never its own candidate
                 const bool self = loo && q + q_base == t;
@@ -441,7 +483,7 @@ template <typename T>
 cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int64_t N, int L,
                     int W, int V, bool keogh, bool safe, T lb_lo, T abs_slack, T *lb_out,
                     unsigned long long *seed_keys, T *norms, T *ends_out, bool loo,
-                    LbPlan<T> *p, int64_t q_base, int tile) {
+                    LbPlan<T> *p, int64_t q_base, int tile, bool ed_bound) {
     int nb = L / 2 < V ? L / 2 : V;
     if (nb < 1) nb = 1;
     const int Weff = W > L - 1 ? L - 1 : W;
@@ -461,6 +503,16 @@ cudaError_t plan_lb(const T *test, int64_t Q, const T *train, const T *env, int6
     j.abs_slack = abs_slack; j.lb_out = lb_out; j.seed_keys = seed_keys;
     j.nq = seed_keys ? norms : nullptr; j.nt = seed_keys ? norms + Q : nullptr;
     j.ends_out = keogh ? nullptr : ends_out; j.loo = loo ? 1 : 0; j.q_base = q_base;
+    // W = 0: DTW_0 is the squared Euclidean distance and so is the bound
+    // (every envelope is the series itself), so in the search the bound is
+    // taken from |a|^2 + |b|^2 - 2 a.b, which the fused first-candidate pass
+    // forms anyway.  Its rounding error is at most gamma_{L+4} (|a| + |b|)^2
+    // (the norms and the dot product are sums of L products, each within
+    // gamma_L of its exact value, |a.b| <= |a| |b|, and three more roundings
+    // combine them); the margin used is 1 - lb_lo = gamma_{2L+16}, larger.
+    j.edb = (ed_bound && std::is_same<T, float>::value && Weff == 0 && seed_keys && safe &&
+             !keogh && !j.ends_out) ? 1 : 0;
+    j.ed_gamma = T(1) - lb_lo;
     // query tiles vary fastest, so the CTAs resident at one time share a few
     // training tiles
     j.qfast = 1;
@@ -536,7 +588,7 @@ template cudaError_t launch_lb<double>(const double *, int64_t, const double *, 
 template cudaError_t plan_lb<float>(const float *, int64_t, const float *, const float *, int64_t,
                                     int, int, int, bool, bool, float, float, float *,
                                     unsigned long long *, float *, float *, bool,
-                                    LbPlan<float> *, int64_t, int);
+                                    LbPlan<float> *, int64_t, int, bool);
 template LbFns<float> lb_fns<float>(int, bool);
 template cudaError_t set_lb_smem<float>(int, bool, size_t);
 

@@ -903,7 +903,8 @@ int run32(const Set32 *sets, int n, bool want_stats, bool timing, nndtw_stats *s
             CK(plan_lb<float>(x.test, x.Q, x.train, p.env, x.N, x.L, p.Weff, x.V, p.keogh, true,
                               p.m.lb_lo, p.m.abs32, p.ws.lb, p.ws.seed, p.ws.norms,
                               p.rev ? p.ws.ends : nullptr, p.loo, &lp, x.q_base,
-                              (int)((x.flags & NNDTW_LB_TILE_MASK) >> 19)));
+                              (int)((x.flags & NNDTW_LB_TILE_MASK) >> 19),
+                              /*ed_bound=*/!p.rev && !p.imp));
             const LbFns<float> f = lb_fns<float>(lp.tile, lp.ed);
             gs.add(f.sq1, f.sqN, 256, 0, lp.sq, lp.sq_blocks);
             gl.add(f.fn1, f.fnN, kLbThreads, lp.smem, lp.job, lp.blocks);
