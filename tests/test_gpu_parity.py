@@ -262,6 +262,30 @@ def test_search_near_ties_recheck_fires(lib, orc):
     assert st["recheck_queries"] >= test.shape[0] - 2
 
 
+def test_search_w0_bound_near_ties(lib, orc):
+    """W = 0, where the search takes the bound from |a|^2 + |b|^2 - 2 a.b less
+    its rounding margin: planted near ties (elements one FP32 ulp apart),
+    also on series far from zero (offset 1000, where that form cancels most
+    of its digits), still give the oracle's index, label and distance."""
+    L, W, V = 300, 0, 5
+    rng = np.random.default_rng(78)
+    for offset in (0.0, 1000.0):
+        test = (_series(9201, 20, L) + offset).astype(np.float32)
+        train = [(_series(9202, 100, L) + offset).astype(np.float32)]
+        for q in range(test.shape[0]):
+            near = (test[q] + 0.05 * rng.standard_normal(L)).astype(np.float32)
+            nudged = near.copy()
+            pos = rng.choice(L, 6, replace=False)
+            nudged[pos] = np.nextafter(nudged[pos], np.float32(np.inf if q % 2 else -np.inf))
+            train.append(np.stack([nudged, near] if q % 3 == 0 else [near, nudged]))
+        train = np.concatenate(train, axis=0)
+        labels = (np.arange(train.shape[0]) % 5).astype(np.int32)
+        brute = orc.nn_brute(train, labels, test, W)
+        assert np.all(brute[0] >= 100)
+        _check_search(lib, orc, train, labels, test, W, V, brute=brute)
+        _check_search(lib, orc, train, labels, test, W, V, flags=lib.EXACT_DIST, brute=brute)
+
+
 @pytest.mark.parametrize("flag", ["NO_PRUNE", "NO_ABANDON", "EXACT_DIST", "CHECK_FINITE"])
 def test_search_flags(lib, orc, flag):
     ds = synth.make_pairs(5)
